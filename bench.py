@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the semiring MM library on GB300.
+
+Headline workload: (min,+) tropical MM, n = 4096, int32 entries uniform in
+[0, 1000] with 10% set to the +inf sentinel 2^30 (seed 1), run under the
+five workspace budgets 0, 1, 2, 4 and 8 extra n x n int32 buffers (split-K
+factors s = 1, 2, 3, 5, 9).  One step = the five calls; ops per call =
+2 n^3 (one (x) = add and one (+) = min per term).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GOp/s & % of dtype peak at stated error vs plain FP64 path; peak workspace bytes"
+N = 4096
+BUDGETS = (0, 1, 2, 4, 8)  # extra n x n int32 buffers
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mmsr", choices=["mmsr", "reference"])
+    p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id=None):
+        self.path = tempfile.mktemp(prefix="mmsr_clocks_", suffix=".csv")
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if gpu_id:
+            cmd.insert(1, "--id=" + gpu_id)
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                tok = [t.strip() for t in line.split(",")]
+                if len(tok) < 9:
+                    continue
+                try:
+                    sm.append(float(tok[1]))
+                    smax.append(float(tok[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, tok[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_uuid():
+    try:
+        import torch
+
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ measured peaks
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def ncu_traffic(kernel_file, key):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed after the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1911_05328_gb300", "csrc", kernel_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha") != h:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1911_05328_gb300 import inputs
+
+    A, B = inputs.tropical_i32(N, N, N, seed=1)
+    rows_per_step = 256
+    rng = np.random.default_rng(0)
+    times = []
+    for it in range(args.warmup + args.steps):
+        rows = np.sort(rng.choice(N, rows_per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle.mm_minplus(A, B, rows=rows)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    ops = 2.0 * rows_per_step * N * N
+    tot = sum(times)
+    value = ops * len(times) / tot / 1e9
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GOp/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
+        "data": "synthetic",
+        "config": {"workload": "minplus_n4096_int32_inf10pct_seed1", "n": N,
+                   "sample": "%d random rows of C per step" % rows_per_step},
+        "cpu_baseline": {"value": value, "unit": "GOp/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d rows x 4096 x 4096 per step" % rows_per_step},
+        "e2e": {"value": value, "unit": "GOp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- mmsr
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1911_05328_gb300 import inputs, mmsr
+
+    lib = mmsr.load()
+    SR = mmsr.MM_SR_MIN_PLUS_I32
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+
+    A_h, B_h = inputs.tropical_i32(N, N, N, seed=1)
+    dA = torch.from_numpy(A_h).cuda()
+    dB = torch.from_numpy(B_h).cuda()
+    outs = [torch.empty((N, N), dtype=torch.int32, device="cuda") for _ in BUDGETS]
+    max_budget = max(BUDGETS) * N * N * 4
+    ws = torch.empty((max_budget,), dtype=torch.uint8, device="cuda")
+    flush = torch.empty((L2_FLUSH_BYTES,), dtype=torch.uint8, device="cuda")
+    plans = [mmsr.mm_plan_query(SR, -1, N, N, N, b * N * N * 4) for b in BUDGETS]
+
+    def one_step():
+        for b, C in zip(BUDGETS, outs):
+            mmsr.mm_semiring(SR, N, N, N, dA, dB, C, ws, b * N * N * 4, sp)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    consistent = all(bool(torch.equal(outs[0], C)) for C in outs[1:])
+
+    # roofline denominators: measured probe of the fused add-min instruction
+    import ctypes
+
+    rate, pms = ctypes.c_double(), ctypes.c_double()
+    lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.mm_probe_peak(0, 2000, sp, ctypes.byref(rate), ctypes.byref(pms))
+    lib.mm_probe_peak(0, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
+    alu_peak_tops = rate.value / 1e12
+
+    # ---------------------------------------------------------- timed region
+    per_budget_ms = [0.0] * len(BUDGETS)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(BUDGETS) + 1)] for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_uuid())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    lib.mm_trace_enable(1)
+    for s in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (not timed)
+        e = ev[s]
+        e[0].record(stream)
+        for i, (b, C) in enumerate(zip(BUDGETS, outs)):
+            mmsr.mm_semiring(SR, N, N, N, dA, dB, C, ws, b * N * N * 4, sp)
+            e[i + 1].record(stream)
+    torch.cuda.synchronize()
+    lib.mm_trace_enable(0)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = []
+    for s in range(args.steps):
+        e = ev[s]
+        step_ms.append(e[0].elapsed_time(e[-1]))
+        for i in range(len(BUDGETS)):
+            per_budget_ms[i] += e[i].elapsed_time(e[i + 1])
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # per-kernel trace
+    kernels = {}
+    launches_total = 0
+    for kid in range(lib.mm_trace_kernel_count()):
+        cnt, tot = ctypes.c_int64(), ctypes.c_double()
+        lib.mm_trace_summary.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
+        if cnt.value:
+            lib.mm_trace_kernel_name.restype = ctypes.c_char_p
+            kernels[lib.mm_trace_kernel_name(kid).decode()] = {"launches": cnt.value, "ms": tot.value}
+            launches_total += cnt.value
+
+    ops_per_call = 2.0 * N * N * N
+    ops_per_step = ops_per_call * len(BUDGETS)
+    value = world * ops_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    leaf = kernels.get("minplus_leaf", {"launches": 1, "ms": float("nan")})
+    leaf_avg_ms = leaf["ms"] / leaf["launches"]
+    achieved_tops = ops_per_call / (leaf_avg_ms * 1e-3) / 1e12
+    traffic = ncu_traffic("minplus.cu", "minplus_leaf_n4096")
+    per_budget = []
+    for i, b in enumerate(BUDGETS):
+        ms = per_budget_ms[i] / args.steps
+        per_budget.append({"budget_buffers": b, "budget_bytes": b * N * N * 4, "split_k": plans[i].split_k,
+                           "workspace_used_bytes": int(plans[i].workspace_used), "ms": ms,
+                           "gops": ops_per_call / (ms * 1e-3) / 1e9})
+
+    # ----------------------------------------------------- end to end (host)
+    e2e = None
+    if True:
+        pA = torch.from_numpy(A_h).pin_memory()
+        pB = torch.from_numpy(B_h).pin_memory()
+        pC = [torch.empty((N, N), dtype=torch.int32).pin_memory() for _ in BUDGETS]
+        e2e_steps = max(2, min(args.steps, 5))
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for _ in range(e2e_steps):
+            dA.copy_(pA, non_blocking=True)
+            dB.copy_(pB, non_blocking=True)
+            for i, (b, C) in enumerate(zip(BUDGETS, outs)):
+                mmsr.mm_semiring(SR, N, N, N, dA, dB, C, ws, b * N * N * 4, sp)
+                pC[i].copy_(C, non_blocking=True)
+        evs[1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = evs[0].elapsed_time(evs[1])
+        if dist:
+            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * ops_per_step * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GOp/s",
+               "h2d_bytes_per_step": int(A_h.nbytes + B_h.nbytes),
+               "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in pC)), "steps": e2e_steps}
+        consistent = consistent and all(bool(torch.equal(pC[0], c)) for c in pC[1:])
+
+    # ----------------------------------------------------------- extras
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(mmsr, lib, torch, sp)
+
+    # ------------------------------------------------------ CPU baseline
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        rows = np.arange(0, N, 4, dtype=np.int64)  # 1024 rows, every 4th
+        t0 = time.perf_counter()
+        oracle.mm_minplus(A_h, B_h, rows=rows)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2.0 * len(rows) * N * N / dt / 1e9, "unit": "GOp/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "%d of 4096 rows (every 4th) of one n=4096 product, %.1f s"
+                                           % (len(rows), dt)}
+
+    peaks, peak_src = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "GOp/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": "minplus_n4096_int32_inf10pct_seed1_budgets_0_1_2_4_8", "n": N,
+                   "budgets_buffers": list(BUDGETS), "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "error": "bit-exact vs int64 oracle (tests); budgets agree: %s" % consistent,
+        "pct_of_dtype_peak": 100.0 * (value / world) / (alu_peak_tops * 1e3),
+        "peak_workspace_bytes": int(max(p.workspace_used for p in plans)),
+        "per_budget": per_budget,
+        "roofline": {"bound": "alu", "kernel": "minplus_leaf", "achieved": achieved_tops,
+                     "peak": alu_peak_tops, "unit": "TOp/s", "frac": achieved_tops / alu_peak_tops,
+                     "traffic": traffic,
+                     "peak_source": "measured: mm_probe_peak fused add-min u32 (2 ops/lane-instr), all SMs"},
+        "kernels": kernels,
+        "gpu_launches": launches_total,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "peaks_file": peak_src,
+        "extras": extras,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _time_call(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_extras(mmsr, lib, torch, sp):
+    """Secondary workloads (not the headline): reported for context."""
+    from paper_1911_05328_gb300 import inputs
+
+    out = {}
+    # FP64 classic n=256, uniform[-1,1], seed 0, budget 0 (plain FP64 path)
+    A, B = inputs.uniform_f64(256, 256, 256, seed=0)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((256, 256), dtype=torch.float64, device="cuda")
+    ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC, None, 0, sp), 50)
+    out["fp64_n256_budget0"] = {"ms": ms, "gops": 2 * 256 ** 3 / (ms * 1e-3) / 1e9}
+    # FP64 DFMA path at n=8192 (comparator of the FP32 split-precision path)
+    n = 8192
+    A, B = inputs.uniform_f64(n, n, n, seed=2)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, n, n, n, dA, dB, dC, None, 0, sp), 2)
+    out["fp64_dfma_n8192"] = {"ms": ms, "gops": 2 * n ** 3 / (ms * 1e-3) / 1e9}
+    import ctypes
+
+    rate, pms = ctypes.c_double(), ctypes.c_double()
+    lib.mm_probe_peak(2, 2000, sp, ctypes.byref(rate), ctypes.byref(pms))
+    out["fp64_fma_probe_tflops"] = rate.value / 1e12
+    lib.mm_probe_peak(1, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
+    out["addmin_u16x2_probe_tops"] = rate.value / 1e12
+    lib.mm_probe_peak(3, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
+    out["fp32_fma_probe_tflops"] = rate.value / 1e12
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * mmsr.h -- C ABI of the GB300 semiring / Strassen-Winograd matrix
+ * multiplication library (libmmsr.so).
+ *
+ * Problem (Section 2, "General MM C = A (x) B on a closed semiring
+ * SR = (S, (+), (x), 0, 1)", and the quadrant recursion of Eq. (mm-dac)):
+ *
+ *     C[i][j] = (+)_{t=0}^{k-1} A[i][t] (x) B[t][j]
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Layout: dense row-major, no leading dimensions.  A is m x k, B is k x n,
+ *    C is m x n.  A, B, C and the workspace must not overlap.
+ *  - Pointers A, B, C and `workspace` are DEVICE pointers (cudaMalloc'd or
+ *    torch-allocated memory on the current device).  The caller owns all of
+ *    them; the library never allocates device memory on these paths.
+ *  - C is OVERWRITTEN with A (x) B (it is not accumulated into).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call is asynchronous on that stream.
+ *  - `workspace_bytes` is a hard cap: the plan never touches more than that
+ *    many bytes of `workspace`, and never touches memory past it.  The
+ *    paper's space/time trade-off (CO2 in-place k-serial vs. CO3/SAR/STAR
+ *    k-parallel with temporaries, Sections 3-4) is realised as split-K:
+ *    k is divided into s slices, slice 0 is accumulated in C itself and
+ *    slices 1..s-1 in workspace buffers of m*n accumulators, followed by a
+ *    fixed-order (+)-reduction ("madd"/"atomic-madd", Figs. mm-n3, tar-mm).
+ *    s = 1 + floor(workspace_bytes / (m*n*sizeof(accumulator))), clamped so
+ *    that every slice holds at least one k-block.
+ *  - Errors detectable on the host return immediately, before any launch,
+ *    with one of the negative mm_status_t codes; nothing is written.
+ *  - Thread safety: calls are re-entrant as long as concurrent calls use
+ *    different C and workspace buffers.
+ */
+#ifndef MMSR_H_
+#define MMSR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Semirings.  Element types of A, B and C follow the name. */
+typedef enum {
+  /* (+, x) over FP64, plain FP64 CUDA-core (DFMA) path.  Accumulator FP64. */
+  MM_SR_PLUS_TIMES_F64 = 0,
+  /* (+, x) over FP32 in/out: each operand split into a bf16 (hi, lo) pair,
+   * products hi*hi + hi*lo + lo*hi on tcgen05 tensor cores, FP32 accumulate.
+   * Needs 4*(m*k + k*n) bytes of workspace for the split operands. */
+  MM_SR_PLUS_TIMES_F32 = 1,
+  /* (+, x) over FP64 in/out at FP64 accuracy from 16-bit tensor-core
+   * products of scaled integer slices, summed exactly / in FP64. */
+  MM_SR_PLUS_TIMES_F64ACC = 2,
+  /* (min, +) tropical semiring over int32 in [0, 2^30]; 2^30 is +infinity
+   * (the semiring's 0).  Sums saturate at 2^30 (never wrap).  Inputs outside
+   * [0, 2^30] are a precondition violation (not checked on the device). */
+  MM_SR_MIN_PLUS_I32 = 3,
+  /* Boolean (or, and) over uint8; nonzero = true, output is 0 or 1. */
+  MM_SR_OR_AND_U8 = 4
+} mm_semiring_t;
+
+typedef enum {
+  MM_OK = 0,
+  MM_ERR_ARG = -1,         /* null pointer, negative size, bad enum value     */
+  MM_ERR_UNSUPPORTED = -2, /* semiring/operation pair not defined (e.g.
+                              Strassen needs the inverse of (+), Section 5)  */
+  MM_ERR_WORKSPACE = -3,   /* workspace_bytes below the plan's minimum       */
+  MM_ERR_SHAPE = -4,       /* shape not allowed by the operation             */
+  MM_ERR_CUDA = -5,        /* a CUDA runtime call failed                     */
+  MM_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up             */
+  MM_ERR_ALIGN = -7        /* a pointer is not 16-byte aligned               */
+} mm_status_t;
+
+/* What a call would do for a given budget (filled by mm_plan_query). */
+typedef struct {
+  int32_t split_k;          /* s: number of k slices (1 = k-serial, CO2-like) */
+  int32_t levels;           /* Strassen levels (0 for mm_semiring)            */
+  int32_t tile_m, tile_n, tile_k; /* CTA tile of the leaf kernel              */
+  int32_t kernel;           /* internal leaf-kernel id (diagnostic)           */
+  int64_t workspace_used;   /* bytes of workspace the call touches            */
+  int64_t workspace_min;    /* smallest budget for which the call is valid    */
+} mm_plan_t;
+
+/*
+ * mm_semiring -- C := A (x) B on `semiring` with classic (8-way, Eq. mm-dac)
+ * blocking and budgeted split-K.
+ *   semiring         one of mm_semiring_t
+ *   m, n, k          sizes, m, n >= 1, k >= 0 (k = 0 writes the semiring 0)
+ *   A, B, C          device pointers, 16-byte aligned
+ *   workspace        device pointer (may be NULL iff workspace_bytes == 0)
+ *   workspace_bytes  budget, see the conventions above
+ *   stream           cudaStream_t
+ * Returns MM_OK or a negative mm_status_t.
+ */
+int mm_semiring(int semiring, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                void* C, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Strassen variants (Section 5 and the bilinear generalisation). */
+typedef enum {
+  MM_STRASSEN_PAPER = 0,   /* the paper's printed S/T/P/C formulas          */
+  MM_STRASSEN_WINOGRAD = 1 /* Strassen-Winograd: 7 products, 15 additions    */
+} mm_strassen_variant_t;
+
+/*
+ * mm_strassen -- C := A (x) B with `levels` levels of a Strassen-like
+ * recursion (Section 5, Lemma par-strassen, Theorem star-strassen-2) over
+ * classic leaves.  Requires a (+) with an inverse: only the (+, x) semirings
+ * are accepted (MM_ERR_UNSUPPORTED otherwise).  m, n and k must be
+ * divisible by 2^levels (MM_ERR_SHAPE otherwise); 0 <= levels <= 4.
+ * levels = 0 is mm_semiring.  The temporaries (operand sums S_r, T_r and
+ * products P_r of each level) are carved from `workspace`; the plan's
+ * workspace_min is O(n^2) and is reported by mm_plan_query.
+ */
+int mm_strassen(int levels, int variant, int semiring, int64_t m, int64_t n, int64_t k,
+                const void* A, const void* B, void* C, void* workspace, size_t workspace_bytes,
+                void* stream);
+
+/* One problem of a batch (host-side descriptor; pointers are device). */
+typedef struct {
+  int32_t semiring; /* MM_SR_PLUS_TIMES_F32 or MM_SR_MIN_PLUS_I32 */
+  int32_t levels;   /* reserved, must be 0 */
+  int64_t m, n, k;
+  const void* A;
+  const void* B;
+  void* C;
+} mm_problem_t;
+
+/*
+ * mm_batched -- C_p := A_p (x) B_p for `count` independent problems of
+ * mixed shapes and semirings in one persistent launch over a cost-sorted
+ * tile queue (the dynamic load balance of Section 6).  `problems` is a
+ * HOST array read during the call.  Workspace holds the tile queue and the
+ * split operands; mm_batched_query reports the minimum.
+ */
+int mm_batched(int count, const mm_problem_t* problems, void* workspace, size_t workspace_bytes,
+               void* stream);
+
+/* Workspace the batched call needs for these problems (0 on bad input). */
+size_t mm_batched_query(int count, const mm_problem_t* problems);
+
+/*
+ * mm_plan_query -- the plan mm_semiring (levels < 0) or mm_strassen
+ * (levels >= 0, variant ignored for the budget) would run for this budget.
+ * Host-only; launches nothing.  Returns MM_OK or the status the call
+ * itself would return.
+ */
+int mm_plan_query(int semiring, int levels, int64_t m, int64_t n, int64_t k,
+                  size_t workspace_bytes, mm_plan_t* plan);
+
+/*
+ * mm_last_device_status -- synchronises `stream` and returns, in *status,
+ * the device-side status word written by kernels that can fail on the
+ * device (bounded waits of the batched kernel); the word is then cleared.
+ * Returns MM_OK or MM_ERR_CUDA.
+ */
+int mm_last_device_status(void* stream, int* status);
+
+/*
+ * Tracing (diagnostics, no counterpart in the paper).  While enabled, the
+ * library brackets every kernel it launches with a pair of CUDA events on
+ * the launching stream.  mm_trace_enable(1) clears the record and turns
+ * tracing on, mm_trace_enable(0) turns it off (the record is kept).
+ * mm_trace_summary synchronises on the recorded events and returns, for one
+ * kernel id (0 <= id < mm_trace_kernel_count()), the number of launches and
+ * their summed device time in milliseconds.  Returns MM_OK, MM_ERR_ARG or
+ * MM_ERR_CUDA.
+ */
+int mm_trace_enable(int on);
+int mm_trace_kernel_count(void);
+const char* mm_trace_kernel_name(int kernel_id);
+int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
+
+/* Static string for a status code. */
+const char* mm_status_string(int status);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int mm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMSR_H_ */

@@ -1,0 +1,219 @@
+// api.cu -- the C ABI of libmmsr: argument validation, the budget planner
+// and dispatch to the leaf / reduction kernels.
+//
+// Planner (Sections 3-4 as split-K): the paper trades span against
+// temporary space -- CO2 keeps all k-work in place and serial (Fig. mm-n2),
+// CO3 runs the k-halves in parallel with a temporary D and a final madd
+// (Fig. mm-n3), and SAR/STAR bound the number of temporaries by what the
+// space budget allows (Theorems sar-mm, star-mm; "min{p, 4^d} copies per
+// depth").  Here the budget decides s, the number of k-slices: slice 0
+// accumulates in C (the lock winner of hlp, Fig. wrapper-sar-mm, which
+// works on its parent's storage) and each further slice owns one m x n
+// temporary; a fixed-order (+)-reduction (madd) folds them into C.
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mmsr {
+
+static int acc_bytes(int sr) {
+  switch (sr) {
+    case MM_SR_PLUS_TIMES_F64: return 8;
+    case MM_SR_PLUS_TIMES_F32: return 4;
+    case MM_SR_PLUS_TIMES_F64ACC: return 8;
+    case MM_SR_MIN_PLUS_I32: return 4;
+    case MM_SR_OR_AND_U8: return 4;
+    default: return 0;
+  }
+}
+
+int elem_bytes(int sr) {
+  switch (sr) {
+    case MM_SR_PLUS_TIMES_F64: return 8;
+    case MM_SR_PLUS_TIMES_F32: return 4;
+    case MM_SR_PLUS_TIMES_F64ACC: return 8;
+    case MM_SR_MIN_PLUS_I32: return 4;
+    case MM_SR_OR_AND_U8: return 1;
+    default: return 0;
+  }
+}
+
+// Split factor for a budget: as many k-slices as the budget can hold
+// partial buffers for, clamped so each slice has at least one k-block.
+static void split_for_budget(int64_t m, int64_t n, int64_t k, int tile_k, int accb,
+                             size_t budget, int* s_out, int* kbs_out, int64_t* used) {
+  const int64_t kb_total = (k + tile_k - 1) / tile_k;
+  const uint64_t slice = (uint64_t)m * (uint64_t)n * (uint64_t)accb;
+  uint64_t s = 1;
+  if (slice > 0) s = 1 + (uint64_t)budget / slice;
+  if (s > (uint64_t)kMaxSplit) s = kMaxSplit;
+  if (kb_total > 0 && s > (uint64_t)kb_total) s = (uint64_t)kb_total;
+  if (kb_total == 0) s = 1;
+  int64_t kbs = kb_total > 0 ? (kb_total + (int64_t)s - 1) / (int64_t)s : 0;
+  if (kbs > 0) s = (uint64_t)((kb_total + kbs - 1) / kbs);  // drop empty tail slices
+  *s_out = (int)s;
+  *kbs_out = (int)kbs;
+  *used = (int64_t)((s - 1) * slice);
+}
+
+int plan_semiring(int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
+  memset(p, 0, sizeof(*p));
+  int tile_k = 0;
+  switch (sr) {
+    case MM_SR_MIN_PLUS_I32:
+      tile_k = minplus_tile_k();
+      p->tile_m = 128; p->tile_n = 128; p->kernel = 1;
+      break;
+    case MM_SR_PLUS_TIMES_F64:
+      tile_k = dfma_tile_k();
+      p->tile_m = 64; p->tile_n = 64; p->kernel = 0;
+      break;
+    case MM_SR_PLUS_TIMES_F32:
+    case MM_SR_PLUS_TIMES_F64ACC:
+    case MM_SR_OR_AND_U8:
+      return plan_extended(sr, m, n, k, budget, p);
+    default:
+      return MM_ERR_ARG;
+  }
+  p->tile_k = tile_k;
+  int s = 1, kbs = 0;
+  int64_t used = 0;
+  split_for_budget(m, n, k, tile_k, acc_bytes(sr), budget, &s, &kbs, &used);
+  p->split_k = s;
+  p->workspace_used = used;
+  p->workspace_min = 0;
+  p->levels = 0;
+  return MM_OK;
+}
+
+int split_plan(int64_t m, int64_t n, int64_t k, int tile_k, int accb, size_t budget, int* s,
+               int* kbs, int64_t* used) {
+  split_for_budget(m, n, k, tile_k, accb, budget, s, kbs, used);
+  return MM_OK;
+}
+
+static int validate_common(int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                           const void* C, const void* ws, size_t ws_bytes) {
+  if (acc_bytes(sr) == 0) return MM_ERR_ARG;
+  if (m < 0 || n < 0 || k < 0) return MM_ERR_ARG;
+  if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return MM_ERR_SHAPE;
+  if (m == 0 || n == 0) return MM_OK;
+  if (!C || (k > 0 && (!A || !B))) return MM_ERR_ARG;
+  if (ws_bytes > 0 && !ws) return MM_ERR_ARG;
+  if (!aligned16(C) || (k > 0 && (!aligned16(A) || !aligned16(B)))) return MM_ERR_ALIGN;
+  if (ws && !aligned16(ws)) return MM_ERR_ALIGN;
+  return MM_OK;
+}
+
+static int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MM_OK;
+  fprintf(stderr, "libmmsr: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));
+  return MM_ERR_CUDA;
+}
+
+int run_semiring(int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
+                 void* ws, size_t ws_bytes, cudaStream_t st) {
+  mm_plan_t p;
+  int rc = plan_semiring(sr, m, n, k, ws_bytes, &p);
+  if (rc != MM_OK) return rc;
+  if ((size_t)p.workspace_min > ws_bytes) return MM_ERR_WORKSPACE;
+  const int s = p.split_k;
+  const int64_t kb_total = (k + p.tile_k - 1) / p.tile_k;
+  const int kbs = kb_total > 0 ? (int)((kb_total + s - 1) / s) : 0;
+  cudaError_t e = cudaSuccess;
+  switch (sr) {
+    case MM_SR_MIN_PLUS_I32: {
+      int32_t* W = s > 1 ? static_cast<int32_t*>(ws) : nullptr;
+      e = launch_minplus_leaf(m, n, k, static_cast<const int32_t*>(A),
+                              static_cast<const int32_t*>(B), static_cast<int32_t*>(C), W, s, kbs,
+                              st);
+      if (e == cudaSuccess && s > 1)
+        e = launch_min_reduce(m * n, static_cast<int32_t*>(C), W, s - 1, st);
+      break;
+    }
+    case MM_SR_PLUS_TIMES_F64: {
+      double* W = s > 1 ? static_cast<double*>(ws) : nullptr;
+      e = launch_dfma_leaf(m, n, k, static_cast<const double*>(A), static_cast<const double*>(B),
+                           static_cast<double*>(C), W, s, kbs, st);
+      if (e == cudaSuccess && s > 1)
+        e = launch_sum_reduce_f64(m * n, static_cast<double*>(C), W, s - 1, st);
+      break;
+    }
+    default:
+      return run_extended(sr, m, n, k, A, B, C, ws, ws_bytes, st, p);
+  }
+  return cuda_status(e);
+}
+
+}  // namespace mmsr
+
+using namespace mmsr;
+
+extern "C" {
+
+int mm_semiring(int semiring, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                void* C, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = validate_common(semiring, m, n, k, A, B, C, workspace, workspace_bytes);
+  if (rc != MM_OK || m == 0 || n == 0) return rc;
+  return run_semiring(semiring, m, n, k, A, B, C, workspace, workspace_bytes,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int mm_strassen(int levels, int variant, int semiring, int64_t m, int64_t n, int64_t k,
+                const void* A, const void* B, void* C, void* workspace, size_t workspace_bytes,
+                void* stream) {
+  int rc = validate_common(semiring, m, n, k, A, B, C, workspace, workspace_bytes);
+  if (rc != MM_OK) return rc;
+  if (levels < 0 || levels > kMaxLevels) return MM_ERR_ARG;
+  if (variant != MM_STRASSEN_PAPER && variant != MM_STRASSEN_WINOGRAD) return MM_ERR_ARG;
+  // Strassen-like recursions need the inverse of (+) (Section 5): only the
+  // (+, x) semirings qualify.
+  if (semiring == MM_SR_MIN_PLUS_I32 || semiring == MM_SR_OR_AND_U8) return MM_ERR_UNSUPPORTED;
+  const int64_t mask = ((int64_t)1 << levels) - 1;
+  if ((m & mask) || (n & mask) || (k & mask)) return MM_ERR_SHAPE;
+  if (m == 0 || n == 0) return MM_OK;
+  if (levels == 0)
+    return run_semiring(semiring, m, n, k, A, B, C, workspace, workspace_bytes,
+                        static_cast<cudaStream_t>(stream));
+  return run_strassen(levels, variant, semiring, m, n, k, A, B, C, workspace, workspace_bytes,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int mm_plan_query(int semiring, int levels, int64_t m, int64_t n, int64_t k,
+                  size_t workspace_bytes, mm_plan_t* plan) {
+  if (!plan) return MM_ERR_ARG;
+  if (acc_bytes(semiring) == 0 || m < 0 || n < 0 || k < 0) return MM_ERR_ARG;
+  if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return MM_ERR_SHAPE;
+  if (levels < 0) return plan_semiring(semiring, m, n, k, workspace_bytes, plan);
+  if (levels > kMaxLevels) return MM_ERR_ARG;
+  if (semiring == MM_SR_MIN_PLUS_I32 || semiring == MM_SR_OR_AND_U8) return MM_ERR_UNSUPPORTED;
+  const int64_t mask = ((int64_t)1 << levels) - 1;
+  if ((m & mask) || (n & mask) || (k & mask)) return MM_ERR_SHAPE;
+  if (levels == 0) return plan_semiring(semiring, m, n, k, workspace_bytes, plan);
+  return plan_strassen(levels, semiring, m, n, k, workspace_bytes, plan);
+}
+
+int mm_last_device_status(void* stream, int* status) {
+  if (!status) return MM_ERR_ARG;
+  return read_device_status(static_cast<cudaStream_t>(stream), status);
+}
+
+const char* mm_status_string(int status) {
+  switch (status) {
+    case MM_OK: return "MM_OK";
+    case MM_ERR_ARG: return "MM_ERR_ARG: invalid argument";
+    case MM_ERR_UNSUPPORTED: return "MM_ERR_UNSUPPORTED: operation not defined for this semiring";
+    case MM_ERR_WORKSPACE: return "MM_ERR_WORKSPACE: workspace budget below the plan's minimum";
+    case MM_ERR_SHAPE: return "MM_ERR_SHAPE: shape not allowed by the operation";
+    case MM_ERR_CUDA: return "MM_ERR_CUDA: a CUDA runtime call failed";
+    case MM_ERR_TIMEOUT: return "MM_ERR_TIMEOUT: a bounded device-side wait gave up";
+    case MM_ERR_ALIGN: return "MM_ERR_ALIGN: pointer not 16-byte aligned";
+    default: return "unknown mm_status_t";
+  }
+}
+
+int mm_version(void) { return 100; }
+
+}  // extern "C"

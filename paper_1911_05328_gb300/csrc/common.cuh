@@ -1,0 +1,81 @@
+// common.cuh -- internal helpers shared by the CUDA sources of libmmsr.
+// Nothing here is part of the C ABI (see include/mmsr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mmsr.h"
+
+namespace mmsr {
+
+constexpr int kInf = 1 << 30;  // +infinity of the (min,+) semiring on [0, 2^30]
+constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (queried at run time where it matters)
+
+#define MMSR_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t err_ = (expr);                                \
+    if (err_ != cudaSuccess) return err_;                     \
+  } while (0)
+
+// ---------------------------------------------------------------- cp.async
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__host__ __device__ inline bool aligned16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+// ------------------------------------------------------------------ tracing
+// Kernel ids of the optional event trace (names in trace.cu).
+enum TraceKernel {
+  kTrMinplusLeaf = 0, kTrMinReduce, kTrDfmaLeaf, kTrSumReduceF64, kTrSplitBf16, kTrTcBf16x3,
+  kTrSumReduceF32, kTrSplitF64Slices, kTrTcF64Acc, kTrStrassenCombine, kTrStrassenPost,
+  kTrBatched, kTrOrAndLeaf, kTrOrReduce, kTrMinplus16Leaf, kTrRangeScan, kTraceKernels
+};
+// RAII: records a start event now and an end event at scope exit, on `st`,
+// when tracing is enabled; otherwise does nothing.
+class TraceScope {
+ public:
+  TraceScope(int id, cudaStream_t st);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+
+ private:
+  int id_;
+  cudaStream_t st_;
+  void* a_;
+};
+
+// ------------------------------------------------------- internal launchers
+// Each returns the cudaError_t of its launch; all are asynchronous on `st`.
+
+// (min,+) leaf over k-slices: slice z of `s` writes C (z == 0) or
+// W + (z-1)*m*n; kb_per_slice k-blocks of the leaf's BK each.
+cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* A,
+                                const int32_t* B, int32_t* C, int32_t* W, int s,
+                                int kb_per_slice, cudaStream_t st);
+// C[i] = min(C[i], W_0[i], ..., W_{parts-1}[i]) for i < count.
+cudaError_t launch_min_reduce(int64_t count, int32_t* C, const int32_t* W, int parts,
+                              cudaStream_t st);
+int minplus_tile_k();
+
+// FP64 DFMA leaf, same slicing contract with FP64 partials.
+cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, const double* B,
+                             double* C, double* W, int s, int kb_per_slice, cudaStream_t st);
+// C[i] = C[i] + W_0[i] + ... + W_{parts-1}[i] (fixed order) for i < count.
+cudaError_t launch_sum_reduce_f64(int64_t count, double* C, const double* W, int parts,
+                                  cudaStream_t st);
+int dfma_tile_k();
+
+}  // namespace mmsr

@@ -1,0 +1,204 @@
+// dfma.cu -- plain FP64 (+,x) leaf on CUDA cores and the fixed-order FP64
+// sum of split-K partials.
+//
+// This is the paper's classic base-kernel (Section 3) in FP64 with the
+// k-serial CO2 order inside each k-slice (Fig. mm-n2); slices beyond the first
+// write m x n FP64 buffers and the reduction adds them into C in slice order
+// (the madd of CO3, Fig. mm-n3), so results are deterministic run to run.
+#include "common.cuh"
+
+namespace mmsr {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, STAGES = 3, THREADS = 256;
+constexpr int LDA = BK + 2;  // doubles; keeps 16-byte alignment of each row
+constexpr int SMEM_A = STAGES * BM * LDA;
+constexpr int SMEM_B = STAGES * BK * BN;
+constexpr size_t SMEM_BYTES = (SMEM_A + SMEM_B) * sizeof(double);
+
+__device__ __forceinline__ void load_stage(double* As, double* Bs, const double* __restrict__ A,
+                                           const double* __restrict__ B, int64_t m, int64_t n,
+                                           int64_t k, int64_t i0, int64_t j0, int64_t k0,
+                                           bool vec, int tid) {
+  const bool a_full = vec && (i0 + BM <= m) && (k0 + BK <= k);
+  const bool b_full = vec && (k0 + BK <= k) && (j0 + BN <= n);
+  // A: 64 rows x 16 doubles = 512 chunks of 2 doubles, 2 per thread.
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int idx = tid + q * THREADS;
+    const int row = idx >> 3, c2 = idx & 7;
+    double* dst = As + row * LDA + c2 * 2;
+    if (a_full) {
+      cp_async16(dst, A + (i0 + row) * k + k0 + c2 * 2);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t gi = i0 + row, gk = k0 + c2 * 2 + e;
+        dst[e] = (gi < m && gk < k) ? A[gi * k + gk] : 0.0;
+      }
+    }
+  }
+  // B: 16 rows x 64 doubles = 512 chunks, 2 per thread.
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int idx = tid + q * THREADS;
+    const int row = idx >> 5, c2 = idx & 31;
+    double* dst = Bs + row * BN + c2 * 2;
+    if (b_full) {
+      cp_async16(dst, B + (k0 + row) * n + j0 + c2 * 2);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t gk = k0 + row, gj = j0 + c2 * 2 + e;
+        dst[e] = (gk < k && gj < n) ? B[gk * n + gj] : 0.0;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(THREADS)
+    dfma_leaf_kernel(int64_t m, int64_t n, int64_t k, const double* __restrict__ A,
+                     const double* __restrict__ B, double* __restrict__ C,
+                     double* __restrict__ W, int kb_per_slice, bool vec) {
+  extern __shared__ __align__(16) double smem_d[];
+  double* As = smem_d;
+  double* Bs = smem_d + SMEM_A;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  const int z = blockIdx.z;
+  const int64_t kb_total = (k + BK - 1) / BK;
+  const int64_t kb_begin = (int64_t)z * kb_per_slice;
+  const int64_t kb_end = min(kb_total, kb_begin + kb_per_slice);
+  const int nkb = kb_end > kb_begin ? (int)(kb_end - kb_begin) : 0;
+
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < nkb)
+      load_stage(As + s * BM * LDA, Bs + s * BK * BN, A, B, m, n, k, i0, j0,
+                 (kb_begin + s) * BK, vec, tid);
+    cp_async_commit();
+  }
+  for (int kb = 0; kb < nkb; ++kb) {
+    cp_async_wait<STAGES - 2>();
+    __syncthreads();
+    {
+      const int nxt = kb + STAGES - 1;
+      if (nxt < nkb) {
+        const int sn = nxt % STAGES;
+        load_stage(As + sn * BM * LDA, Bs + sn * BK * BN, A, B, m, n, k, i0, j0,
+                   (kb_begin + nxt) * BK, vec, tid);
+      }
+      cp_async_commit();
+    }
+    const int sc = kb % STAGES;
+    const double* as = As + sc * BM * LDA;
+    const double* bs = Bs + sc * BK * BN;
+#pragma unroll
+    for (int kq = 0; kq < BK; kq += 2) {
+      double2 a2[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        a2[i] = *reinterpret_cast<const double2*>(as + (ty * 4 + i) * LDA + kq);
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const double2 b0 = *reinterpret_cast<const double2*>(bs + (kq + kk) * BN + tx * 2);
+        const double2 b1 = *reinterpret_cast<const double2*>(bs + (kq + kk) * BN + 32 + tx * 2);
+        const double b[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const double a = kk == 0 ? a2[i].x : a2[i].y;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a, b[j], acc[i][j]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+
+  double* out = (z == 0) ? C : W + (int64_t)(z - 1) * m * n;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gi = i0 + ty * 4 + i;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gj = j0 + h * 32 + tx * 2;
+      double* dst = out + gi * n + gj;
+      if (vec && gj + 2 <= n) {
+        *reinterpret_cast<double2*>(dst) = make_double2(acc[i][h * 2], acc[i][h * 2 + 1]);
+      } else {
+        if (gj < n) dst[0] = acc[i][h * 2];
+        if (gj + 1 < n) dst[1] = acc[i][h * 2 + 1];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) sum_reduce_f64_kernel(int64_t count, double* __restrict__ C,
+                                                             const double* __restrict__ W,
+                                                             int parts, bool vec) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    const int64_t nv = count >> 1;
+    for (int64_t v = t; v < nv; v += stride) {
+      double2 c = reinterpret_cast<const double2*>(C)[v];
+      for (int p = 0; p < parts; ++p) {
+        const double2 w = __ldcs(reinterpret_cast<const double2*>(W + (int64_t)p * count) + v);
+        c.x += w.x;
+        c.y += w.y;
+      }
+      reinterpret_cast<double2*>(C)[v] = c;
+    }
+  } else {
+    for (int64_t e = t; e < count; e += stride) {
+      double c = C[e];
+      for (int p = 0; p < parts; ++p) c += W[(int64_t)p * count + e];
+      C[e] = c;
+    }
+  }
+}
+
+}  // namespace
+
+int dfma_tile_k() { return BK; }
+
+cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, const double* B,
+                             double* C, double* W, int s, int kb_per_slice, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(dfma_leaf_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM_BYTES));
+    configured = true;
+  }
+  const bool vec = (k % 2 == 0) && (n % 2 == 0) && aligned16(A) && aligned16(B) && aligned16(C) &&
+                   (W == nullptr || aligned16(W));
+  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
+  TraceScope tr(kTrDfmaLeaf, st);
+  dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_reduce_f64(int64_t count, double* C, const double* W, int parts,
+                                  cudaStream_t st) {
+  if (parts <= 0 || count <= 0) return cudaSuccess;
+  const bool vec = aligned16(C) && aligned16(W) && (count % 2 == 0);
+  const int64_t work = vec ? count / 2 : count;
+  int64_t blocks = (work + 255) / 256;
+  const int64_t cap = (int64_t)kNumSMs * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  TraceScope tr(kTrSumReduceF64, st);
+  sum_reduce_f64_kernel<<<(unsigned)blocks, 256, 0, st>>>(count, C, W, parts, vec);
+  return cudaGetLastError();
+}
+
+}  // namespace mmsr

@@ -1,0 +1,37 @@
+// internal.h -- host-side interfaces between the ABI layer and the engines
+// (tensor-core modes, Strassen, batched).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mmsr.h"
+
+namespace mmsr {
+
+constexpr int kMaxSplit = 64;          // largest split-K factor the planner uses
+constexpr int64_t kMaxDim = 1 << 22;   // per-dimension cap (grid limits)
+constexpr int kMaxLevels = 4;          // Strassen levels accepted
+
+int elem_bytes(int sr);
+int plan_semiring(int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
+int run_semiring(int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
+                 void* ws, size_t ws_bytes, cudaStream_t st);
+int split_plan(int64_t m, int64_t n, int64_t k, int tile_k, int accb, size_t budget, int* s,
+               int* kbs, int64_t* used);
+
+// tensor-core and boolean semirings (plan + run)
+int plan_extended(int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
+int run_extended(int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
+                 void* ws, size_t ws_bytes, cudaStream_t st, const mm_plan_t& p);
+
+// Strassen engine
+int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget,
+                  mm_plan_t* p);
+int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,
+                 const void* B, void* C, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// device status word (bounded waits of the batched kernel)
+int read_device_status(cudaStream_t st, int* status);
+
+}  // namespace mmsr

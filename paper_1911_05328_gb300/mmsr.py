@@ -1,0 +1,170 @@
+"""Thin ctypes binding of libmmsr (include/mmsr.h) -- argument marshalling only.
+
+Every entry point keeps its C name.  Tensor arguments may be torch CUDA
+tensors (their ``data_ptr()`` is passed) or raw integer device addresses;
+``stream`` may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer or
+None (torch's current stream on the current device).  All compute happens in
+the library's CUDA kernels; there is no fallback: if libmmsr.so is missing
+the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmmsr.so")
+
+MM_SR_PLUS_TIMES_F64 = 0
+MM_SR_PLUS_TIMES_F32 = 1
+MM_SR_PLUS_TIMES_F64ACC = 2
+MM_SR_MIN_PLUS_I32 = 3
+MM_SR_OR_AND_U8 = 4
+
+MM_STRASSEN_PAPER = 0
+MM_STRASSEN_WINOGRAD = 1
+
+MM_OK = 0
+MM_ERR_ARG = -1
+MM_ERR_UNSUPPORTED = -2
+MM_ERR_WORKSPACE = -3
+MM_ERR_SHAPE = -4
+MM_ERR_CUDA = -5
+MM_ERR_TIMEOUT = -6
+MM_ERR_ALIGN = -7
+
+INF = 1 << 30
+
+
+class MMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s returned %d (%s)" % (what, status, status_string(status)))
+        self.status = status
+
+
+class mm_plan_t(ctypes.Structure):
+    _fields_ = [("split_k", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32), ("tile_k", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("workspace_used", ctypes.c_int64),
+                ("workspace_min", ctypes.c_int64)]
+
+
+class mm_problem_t(ctypes.Structure):
+    _fields_ = [("semiring", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Open libmmsr.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise OSError("libmmsr.so not found at %s: run __graft_entry__.build() "
+                              "(there is no CPU fallback)" % path)
+            lib = ctypes.CDLL(path)
+            i32, i64, vp, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+            lib.mm_semiring.argtypes = [i32, i64, i64, i64, vp, vp, vp, vp, sz, vp]
+            lib.mm_strassen.argtypes = [i32, i32, i32, i64, i64, i64, vp, vp, vp, vp, sz, vp]
+            lib.mm_batched.argtypes = [i32, ctypes.POINTER(mm_problem_t), vp, sz, vp]
+            lib.mm_batched_query.argtypes = [i32, ctypes.POINTER(mm_problem_t)]
+            lib.mm_batched_query.restype = sz
+            lib.mm_plan_query.argtypes = [i32, i32, i64, i64, i64, sz, ctypes.POINTER(mm_plan_t)]
+            lib.mm_last_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            lib.mm_status_string.argtypes = [i32]
+            lib.mm_status_string.restype = ctypes.c_char_p
+            lib.mm_version.argtypes = []
+            for f in ("mm_semiring", "mm_strassen", "mm_batched", "mm_plan_query",
+                      "mm_last_device_status", "mm_version"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _check(rc, what, check):
+    if check and rc != MM_OK:
+        raise MMError(rc, what)
+    return rc
+
+
+def status_string(status: int) -> str:
+    return load().mm_status_string(int(status)).decode()
+
+
+def mm_semiring(semiring, m, n, k, A, B, C, workspace=None, workspace_bytes=0, stream=None,
+                check=True) -> int:
+    rc = load().mm_semiring(int(semiring), int(m), int(n), int(k), _addr(A), _addr(B), _addr(C),
+                            _addr(workspace), int(workspace_bytes), _stream(stream))
+    return _check(rc, "mm_semiring", check)
+
+
+def mm_strassen(levels, variant, semiring, m, n, k, A, B, C, workspace=None, workspace_bytes=0,
+                stream=None, check=True) -> int:
+    rc = load().mm_strassen(int(levels), int(variant), int(semiring), int(m), int(n), int(k),
+                            _addr(A), _addr(B), _addr(C), _addr(workspace), int(workspace_bytes),
+                            _stream(stream))
+    return _check(rc, "mm_strassen", check)
+
+
+def _problems(problems):
+    arr = (mm_problem_t * len(problems))()
+    for i, p in enumerate(problems):
+        sr, m, n, k, A, B, C = p
+        arr[i] = mm_problem_t(int(sr), 0, int(m), int(n), int(k), _addr(A), _addr(B), _addr(C))
+    return arr
+
+
+def mm_batched(problems, workspace=None, workspace_bytes=0, stream=None, check=True) -> int:
+    """problems: sequence of (semiring, m, n, k, A, B, C)."""
+    arr = _problems(problems)
+    rc = load().mm_batched(len(problems), arr, _addr(workspace), int(workspace_bytes),
+                           _stream(stream))
+    return _check(rc, "mm_batched", check)
+
+
+def mm_batched_query(problems) -> int:
+    arr = _problems(problems)
+    return int(load().mm_batched_query(len(problems), arr))
+
+
+def mm_plan_query(semiring, levels, m, n, k, workspace_bytes=0, check=True) -> mm_plan_t:
+    plan = mm_plan_t()
+    rc = load().mm_plan_query(int(semiring), int(levels), int(m), int(n), int(k),
+                              int(workspace_bytes), ctypes.byref(plan))
+    _check(rc, "mm_plan_query", check)
+    plan.status = rc
+    return plan
+
+
+def mm_last_device_status(stream=None) -> int:
+    st = ctypes.c_int(0)
+    rc = load().mm_last_device_status(_stream(stream), ctypes.byref(st))
+    _check(rc, "mm_last_device_status", True)
+    return st.value
+
+
+def mm_version() -> int:
+    return int(load().mm_version())

@@ -11,3 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    """Compile libmmsr.so and the oracle once per session (no-op when fresh)."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    yield

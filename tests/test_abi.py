@@ -1,0 +1,101 @@
+"""Host-side tests of the C ABI: the library loads, exports every function
+include/mmsr.h declares, and rejects bad arguments before touching the GPU.
+No test here launches a kernel, so they run on a machine without a GPU."""
+import os
+import re
+
+import pytest
+
+from paper_1911_05328_gb300 import build as mmsr_build
+from paper_1911_05328_gb300 import mmsr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+FAKE = 1 << 20  # 16-byte aligned address that is never dereferenced by these tests
+
+
+@pytest.fixture(scope="module")
+def lib():
+    mmsr_build.build()
+    return mmsr.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert {"mm_semiring", "mm_strassen", "mm_batched", "mm_plan_query"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(0, -8, -1):
+        s = mmsr.status_string(code)
+        assert s.startswith("MM_")
+    assert mmsr.mm_version() >= 100
+
+
+def test_null_and_negative_arguments(lib):
+    S = mmsr.MM_SR_MIN_PLUS_I32
+    assert mmsr.mm_semiring(S, 4, 4, 4, None, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert mmsr.mm_semiring(S, 4, 4, 4, FAKE, FAKE, None, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert mmsr.mm_semiring(S, -1, 4, 4, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert mmsr.mm_semiring(99, 4, 4, 4, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    # a budget with no workspace pointer
+    assert mmsr.mm_semiring(S, 4, 4, 4, FAKE, FAKE, FAKE, None, 64, stream=0, check=False) == mmsr.MM_ERR_ARG
+    # empty output: nothing to do, no launch
+    assert mmsr.mm_semiring(S, 0, 4, 4, None, None, None, stream=0, check=False) == mmsr.MM_OK
+
+
+def test_misaligned_pointer(lib):
+    S = mmsr.MM_SR_PLUS_TIMES_F64
+    assert mmsr.mm_semiring(S, 4, 4, 4, FAKE + 8, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ALIGN
+
+
+def test_strassen_needs_additive_inverse(lib):
+    # Section 5: Strassen subtracts, so (min,+) and boolean are rejected.
+    for sr in (mmsr.MM_SR_MIN_PLUS_I32, mmsr.MM_SR_OR_AND_U8):
+        rc = mmsr.mm_strassen(1, mmsr.MM_STRASSEN_WINOGRAD, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False)
+        assert rc == mmsr.MM_ERR_UNSUPPORTED
+
+
+def test_strassen_shape_and_level_checks(lib):
+    sr = mmsr.MM_SR_PLUS_TIMES_F32
+    assert mmsr.mm_strassen(2, 1, sr, 10, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_SHAPE
+    assert mmsr.mm_strassen(5, 1, sr, 64, 64, 64, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert mmsr.mm_strassen(1, 7, sr, 64, 64, 64, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+
+
+@pytest.mark.parametrize("budget_buffers,expect_s", [(0, 1), (1, 2), (2, 3), (4, 5), (8, 9)])
+def test_budget_to_split_factor(lib, budget_buffers, expect_s):
+    # the (min,+) workload at n=4096: budgets of 0/1/2/4/8 extra n x n int32
+    # buffers give s = 1 + budget, and the plan uses exactly (s-1) buffers.
+    n = 4096
+    plan = mmsr.mm_plan_query(mmsr.MM_SR_MIN_PLUS_I32, -1, n, n, n, budget_buffers * n * n * 4)
+    assert plan.split_k == expect_s
+    assert plan.workspace_used == (expect_s - 1) * n * n * 4
+    assert plan.workspace_used <= budget_buffers * n * n * 4
+
+
+def test_split_never_exceeds_budget_or_kblocks(lib):
+    for (m, n, k) in [(1, 1, 1), (7, 9, 5), (100, 3, 1000), (512, 512, 64), (33, 65, 4097)]:
+        for budget in (0, 17, m * n * 4 - 1, m * n * 4, 3 * m * n * 4 + 5, 1 << 30):
+            for sr, accb in ((mmsr.MM_SR_MIN_PLUS_I32, 4), (mmsr.MM_SR_PLUS_TIMES_F64, 8)):
+                p = mmsr.mm_plan_query(sr, -1, m, n, k, budget)
+                assert p.workspace_used <= budget
+                assert p.workspace_used == (p.split_k - 1) * m * n * accb
+                assert 1 <= p.split_k <= max(1, -(-k // p.tile_k))
+                # monotone in the budget
+                q = mmsr.mm_plan_query(sr, -1, m, n, k, budget + m * n * accb)
+                assert q.split_k >= p.split_k

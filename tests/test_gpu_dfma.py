@@ -1,0 +1,62 @@
+"""Plain FP64 (+,x) path on the GPU vs the FP64 oracle (rel. Frobenius
+<= 1e-12), including split-K with the fixed-order FP64 reduction and the
+n=256 uniform[-1,1] workload (seed 0, budget 0) in full."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_05328_gb300 import inputs, mmsr
+
+from gpu_util import canary_intact, dev, empty, rel_fro, workspace
+
+pytestmark = pytest.mark.gpu
+SR = mmsr.MM_SR_PLUS_TIMES_F64
+TOL = 1e-12
+
+
+def run(A, B, budget=0):
+    import torch
+
+    m, k = A.shape
+    n = B.shape[1]
+    dC = empty((m, n), torch.float64)
+    ws = workspace(budget)
+    mmsr.mm_semiring(SR, m, n, k, dev(A), dev(B), dC, ws if budget else None, budget)
+    torch.cuda.synchronize()
+    assert canary_intact(ws, budget)
+    return dC.cpu().numpy()
+
+
+def test_n256_workload_full():
+    A, B = inputs.uniform_f64(256, 256, 256, seed=0)
+    assert rel_fro(run(A, B), oracle.mm_f64(A, B)) <= TOL
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 5, 3), (64, 64, 16), (65, 67, 33), (200, 130, 513), (512, 384, 1024)])
+def test_shapes(m, n, k):
+    A, B = inputs.uniform_f64(m, k, n, seed=m * 7 + n + k)
+    assert rel_fro(run(A, B), oracle.mm_f64(A, B)) <= TOL
+
+
+@pytest.mark.parametrize("parts", [2, 3, 7])
+def test_split_k(parts):
+    m, n, k = 192, 160, 2000
+    A, B = inputs.uniform_f64(m, k, n, seed=40 + parts)
+    budget = (parts - 1) * m * n * 8
+    assert mmsr.mm_plan_query(SR, -1, m, n, k, budget).split_k == parts
+    assert rel_fro(run(A, B, budget), oracle.mm_f64(A, B)) <= TOL
+
+
+def test_small_integers_exact():
+    A, B = inputs.small_int(130, 300, 70, seed=41)
+    np.testing.assert_array_equal(run(A, B, 2 * 130 * 70 * 8), oracle.mm_f64(A, B))
+
+
+def test_k_zero_writes_zero():
+    import torch
+
+    dC = empty((3, 4), torch.float64)
+    dC.fill_(7.0)
+    mmsr.mm_semiring(SR, 3, 4, 0, empty((3, 1), torch.float64), empty((1, 4), torch.float64), dC)
+    torch.cuda.synchronize()
+    assert np.all(dC.cpu().numpy() == 0.0)
