@@ -39,7 +39,7 @@ def test_leaf_matches_oracle(m, n, k):
 
 @pytest.mark.parametrize("parts", [1, 2, 3, 5, 9])
 def test_split_k_budgets_bit_identical(parts):
-    m, n, k = 300, 260, 1500
+    m, n, k = 300, 260, 1440  # 45 k-blocks of 32: divisible into 1, 2, 3, 5, 9 slices
     A, B = inputs.tropical_i32(m, k, n, seed=31)
     budget = (parts - 1) * m * n * 4
     plan = mmsr.mm_plan_query(SR, -1, m, n, k, budget)
