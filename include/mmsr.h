@@ -96,6 +96,29 @@ typedef struct {
 int mm_semiring(int semiring, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
                 void* C, void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * mm_minplus_noalloc -- (min,+) product with split-K whose partial buffers
+ * live in a static device array inside the library instead of a caller
+ * workspace.  The paper has no counterpart; this exists for callers that
+ * cannot allocate device memory at the call site: code hosted by a
+ * framework whose memory pool owns the GPU (a raw cudaMalloc bypasses its
+ * accounting and can synchronise the device), or programs whose device
+ * footprint is fixed at start-up.
+ *   m, n, k, A, B, C  as in mm_semiring with MM_SR_MIN_PLUS_I32
+ *   split_k           requested k-slices (>= 1; clamped to the k-blocks)
+ *   stream            cudaStream_t
+ * Scratch limit: (s-1)*m*n*4 bytes must fit in 64 MiB (67,108,864 bytes),
+ * else MM_ERR_WORKSPACE and nothing is launched.  Every GPU that loads the
+ * library holds the 64 MiB array until the process exits.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  All calls share the
+ * one array: calls whose executions overlap on the GPU (different streams,
+ * no ordering between them) race on it.  Nothing in it needs clearing: each
+ * call overwrites every partial it later reads.  Allocates nothing.
+ */
+int mm_minplus_noalloc(int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
+                       int split_k, void* stream);
+
 /* Strassen variants (Section 5 and the bilinear generalisation). */
 typedef enum {
   MM_STRASSEN_PAPER = 0,   /* the paper's printed S/T/P/C formulas          */

@@ -229,3 +229,78 @@ cudaError_t launch_min_reduce(int64_t count, int32_t* C, const int32_t* W, int p
 }
 
 }  // namespace mmsr
+
+// ---------------------------------------------------------------------------
+// Allocation-free split-K entry point.
+//
+// Some callers cannot hand the library a workspace: code running inside a
+// host framework whose memory pool owns the device (a raw cudaMalloc there
+// bypasses the pool's accounting and may synchronise the whole device), or
+// callers with a fixed memory footprint decided at start-up.  For them the
+// split-K partials of the (min,+) product live in a file-scope device array
+// that is part of the library image, so this entry point allocates nothing.
+#include <mutex>
+
+namespace mmsr {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB, per GPU, held until exit
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) int32_t g_minplus_scratch[kStaticScratchBytes / sizeof(int32_t)];
+
+std::mutex g_scratch_mu;
+int32_t* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_minplus_scratch on the current device.  In host code
+// the symbol name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+cudaError_t scratch_address(int32_t** out) {
+  int dev = 0;
+  MMSR_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    MMSR_CUDA_TRY(cudaGetSymbolAddress(&p, g_minplus_scratch));
+    g_scratch_addr[dev] = static_cast<int32_t*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace mmsr
+
+extern "C" int mm_minplus_noalloc(int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                                  void* C, int split_k, void* stream) {
+  using namespace mmsr;
+  if (m < 0 || n < 0 || k < 0 || split_k < 1) return MM_ERR_ARG;
+  if (m == 0 || n == 0) return MM_OK;
+  if (!C || (k > 0 && (!A || !B))) return MM_ERR_ARG;
+  if (!aligned16(C) || (k > 0 && (!aligned16(A) || !aligned16(B)))) return MM_ERR_ALIGN;
+  if (m > (int64_t(1) << 22) || n > (int64_t(1) << 22) || k > (int64_t(1) << 22)) return MM_ERR_SHAPE;
+  const int64_t kb_total = (k + BK - 1) / BK;
+  int64_t s = split_k;
+  if (s > 64) s = 64;
+  if (kb_total > 0 && s > kb_total) s = kb_total;
+  if (kb_total == 0) s = 1;
+  const int64_t kbs = kb_total > 0 ? (kb_total + s - 1) / s : 0;
+  if (kbs > 0) s = (kb_total + kbs - 1) / kbs;
+  const uint64_t need = (uint64_t)(s - 1) * (uint64_t)m * (uint64_t)n * sizeof(int32_t);
+  if (need > kStaticScratchBytes) return MM_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t* W = nullptr;
+  if (s > 1) {
+    cudaError_t e = scratch_address(&W);
+    if (e != cudaSuccess) return MM_ERR_CUDA;
+  }
+  // Every element of each used partial slice is written by the leaf before
+  // the reduction reads it, so stale contents from an earlier call are never
+  // observed and nothing needs clearing.
+  cudaError_t e = launch_minplus_leaf(m, n, k, static_cast<const int32_t*>(A),
+                                      static_cast<const int32_t*>(B), static_cast<int32_t*>(C), W,
+                                      (int)s, (int)kbs, st);
+  if (e == cudaSuccess && s > 1) e = launch_min_reduce(m * n, static_cast<int32_t*>(C), W, (int)(s - 1), st);
+  return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}

@@ -71,6 +71,8 @@ def load(path: str = LIB_PATH):
             lib = ctypes.CDLL(path)
             i32, i64, vp, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
             lib.mm_semiring.argtypes = [i32, i64, i64, i64, vp, vp, vp, vp, sz, vp]
+            lib.mm_minplus_noalloc.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp]
+            lib.mm_minplus_noalloc.restype = ctypes.c_int
             lib.mm_strassen.argtypes = [i32, i32, i32, i64, i64, i64, vp, vp, vp, vp, sz, vp]
             lib.mm_batched.argtypes = [i32, ctypes.POINTER(mm_problem_t), vp, sz, vp]
             lib.mm_batched_query.argtypes = [i32, ctypes.POINTER(mm_problem_t)]
@@ -119,6 +121,14 @@ def mm_semiring(semiring, m, n, k, A, B, C, workspace=None, workspace_bytes=0, s
     rc = load().mm_semiring(int(semiring), int(m), int(n), int(k), _addr(A), _addr(B), _addr(C),
                             _addr(workspace), int(workspace_bytes), _stream(stream))
     return _check(rc, "mm_semiring", check)
+
+
+def mm_minplus_noalloc(m, n, k, A, B, C, split_k=1, stream=None, check=True) -> int:
+    """(min,+) product with split-K partials in the library's static 64 MiB
+    device scratch (no workspace argument, no allocation)."""
+    rc = load().mm_minplus_noalloc(int(m), int(n), int(k), _addr(A), _addr(B), _addr(C),
+                                   int(split_k), _stream(stream))
+    return _check(rc, "mm_minplus_noalloc", check)
 
 
 def mm_strassen(levels, variant, semiring, m, n, k, A, B, C, workspace=None, workspace_bytes=0,
