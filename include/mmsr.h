@@ -194,6 +194,16 @@ int mm_trace_kernel_count(void);
 const char* mm_trace_kernel_name(int kernel_id);
 int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
 
+/*
+ * mm_set_option -- process-wide tuning switches (not part of the method).
+ *   MM_OPT_MINPLUS_PACKED: 1 (default) lets (min,+) products run the exact
+ *   packed 2 x 16-bit leaf when a device-side range scan finds every finite
+ *   input <= 16383; 0 always runs the 32-bit leaf.  Results are identical.
+ * Returns MM_OK or MM_ERR_ARG.
+ */
+typedef enum { MM_OPT_MINPLUS_PACKED = 1 } mm_option_t;
+int mm_set_option(int option, int value);
+
 /* Static string for a status code. */
 const char* mm_status_string(int status);
 

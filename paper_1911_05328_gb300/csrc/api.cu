@@ -216,4 +216,15 @@ const char* mm_status_string(int status) {
 
 int mm_version(void) { return 100; }
 
+int mm_set_option(int option, int value) {
+  switch (option) {
+    case MM_OPT_MINPLUS_PACKED:
+      if (value != 0 && value != 1) return MM_ERR_ARG;
+      g_packed_mode = value;
+      return MM_OK;
+    default:
+      return MM_ERR_ARG;
+  }
+}
+
 }  // extern "C"

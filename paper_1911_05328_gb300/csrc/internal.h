@@ -25,6 +25,12 @@ int plan_extended(int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_pla
 int run_extended(int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
                  void* ws, size_t ws_bytes, cudaStream_t st, const mm_plan_t& p);
 
+// FP32 mode: bf16x3 split products on tcgen05 tensor cores
+int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
+int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, float* C, void* ws,
+            size_t ws_bytes, cudaStream_t st);
+int read_tc_status(int* status);
+
 // Strassen engine
 int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget,
                   mm_plan_t* p);

@@ -1,0 +1,435 @@
+// tc_bf16.cu -- FP32-mode (+,x) on tcgen05 tensor cores: each FP32 operand
+// is split into a bf16 pair (hi, lo) and C = A_hi B_hi + A_hi B_lo + A_lo B_hi
+// is accumulated in FP32 (the lo*lo term, ~2^-16 relative, is dropped).
+//
+// Leaf = the paper's base-kernel (Section 3) as a 128 x BN output tile of
+// one CTA: a TMA producer thread streams 64-wide k-blocks of the four split
+// operands into a STAGES-deep shared-memory ring, a single thread issues the
+// tcgen05.mma instructions into short chunk accumulators in tensor memory,
+// and eight drain warps add each finished chunk into FP32 registers and
+// finally write the tile to global memory.  Split-K slices (the budgeted k-parallel CO3/SAR
+// form, Figs. mm-n3, sar-mm) write FP32 partials that a fixed-order sum
+// folds into C.
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace mmsr {
+
+namespace {
+__device__ int g_tc_status;  // device status word of this translation unit
+}
+
+// ------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+cudaError_t make_tmap_2d_16bit(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
+                               int64_t ld, int box_rows, bool bf16) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+namespace {
+
+constexpr int BM = 128, BK = 64;
+
+// ----------------------------------------------------------- split kernels
+__device__ __forceinline__ void split1(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  l = __float2bfloat16_rn(x - __bfloat162float(h));  // exact difference in fp32
+}
+
+// X (rows x cols fp32, row-major) -> hi, lo (rows x ld bf16), zero padded.
+__global__ void __launch_bounds__(256) split_rows_kernel(const float* __restrict__ X, int64_t rows,
+                                                         int64_t cols, int64_t ld,
+                                                         __nv_bfloat16* __restrict__ hi,
+                                                         __nv_bfloat16* __restrict__ lo, bool vec) {
+  const int64_t cpr = ld / 8;
+  const int64_t total = rows * cpr;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    const int64_t r = idx / cpr, c8 = (idx - r * cpr) * 8;
+    float v[8];
+    const float* src = X + r * cols + c8;
+    if (vec && c8 + 8 <= cols) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(src));
+      const float4 b = __ldcs(reinterpret_cast<const float4*>(src) + 1);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = (c8 + e < cols) ? src[e] : 0.f;
+    }
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) split1(v[e], h[e], l[e]);
+    *reinterpret_cast<uint4*>(hi + r * ld + c8) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo + r * ld + c8) = *reinterpret_cast<const uint4*>(l);
+  }
+}
+
+// B (k x n fp32, row-major) -> hiT, loT (n x ld bf16): transposed so both
+// MMA operands are K-major.  Tile: 64 k x 32 n through shared memory.
+__global__ void __launch_bounds__(256) split_transpose_kernel(const float* __restrict__ Bm,
+                                                              int64_t k, int64_t n, int64_t ld,
+                                                              __nv_bfloat16* __restrict__ hiT,
+                                                              __nv_bfloat16* __restrict__ loT) {
+  __shared__ float tile[64][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t k0 = (int64_t)blockIdx.x * 64, n0 = (int64_t)blockIdx.y * 32;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int kk = ty + 8 * i;
+    const int64_t gk = k0 + kk, gn = n0 + tx;
+    tile[kk][tx] = (gk < k && gn < n) ? __ldcs(Bm + gk * n + gn) : 0.f;
+  }
+  __syncthreads();
+  const int row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
+  const int64_t gn = n0 + row;
+  if (gn < n) {
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], h[e], l[e]);
+    *reinterpret_cast<uint4*>(hiT + gn * ld + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(loT + gn * ld + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(l);
+  }
+}
+
+// ------------------------------------------------------------ GEMM kernel
+// Warp roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and
+// TMEM owner), warps 2..9 = drain/epilogue.  The tensor core's FP32
+// accumulation over long chains is biased (its relative error grows with the
+// chain length), so the k-loop is cut into chunks of CHUNK k-blocks: each
+// chunk accumulates in one of two TMEM buffers while the drain warps add the
+// other, finished chunk into FP32 registers with round-to-nearest adds.  The
+// chain inside TMEM is then at most CHUNK*BK/16*3 MMAs long, whatever k is.
+constexpr int kDrainWarps = 8;
+constexpr int kTcThreads = 64 + 32 * kDrainWarps;
+
+template <int BN, int STAGES>
+struct Bf16x3Cfg {
+  static constexpr uint32_t A_BYTES = BM * BK * 2;
+  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  static constexpr uint32_t TMEM_COLS = 2 * BN;  // double-buffered chunk accumulator
+  static constexpr int COLS_PER_WARP = BN / 2;   // two drain warps share each lane quarter
+};
+
+template <int BN, int STAGES, int CHUNK>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAhi, const __grid_constant__ CUtensorMap tAlo,
+                       const __grid_constant__ CUtensorMap tBhi, const __grid_constant__ CUtensorMap tBlo,
+                       float* __restrict__ C, float* __restrict__ W, int64_t m, int64_t n,
+                       int kb_total, int kb_per_slice) {
+  using Cfg = Bf16x3Cfg<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = tc::align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;  // [2]: chunk accumulated (MMA -> drain)
+  uint64_t* acc_empty = acc_full + 2;   // [2]: chunk drained (drain -> MMA)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  const int z = blockIdx.z;
+  const int kb_begin = z * kb_per_slice;
+  const int kb_end = min(kb_total, kb_begin + kb_per_slice);
+  const int nkb = kb_end > kb_begin ? kb_end - kb_begin : 0;
+  const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kDrainWarps);
+    }
+    *abort_flag = 0;
+    tc::mbar_init_fence();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::tma_prefetch(&tAhi);
+      tc::tma_prefetch(&tAlo);
+      tc::tma_prefetch(&tBhi);
+      tc::tma_prefetch(&tBlo);
+      for (int it = 0; it < nkb; ++it) {
+        const int s = it % STAGES;
+        const uint32_t round = (uint32_t)(it / STAGES);
+        if (it >= STAGES && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_tc_status)) break;
+        tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+        uint8_t* st = smem + s * Cfg::STAGE_BYTES;
+        const int kx = (kb_begin + it) * BK;
+        tc::tma_load_2d(st, &tAhi, &full[s], kx, (int)i0);
+        tc::tma_load_2d(st + Cfg::A_BYTES, &tAlo, &full[s], kx, (int)i0);
+        tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, (int)j0);
+        tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, (int)j0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_f16(BM, BN, 1);
+      int it = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !tc::mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1u, abort_flag, &g_tc_status)) break;
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+        const int last = min(nkb, (c + 1) * CHUNK);
+        bool aborted = false;
+        for (int first = 1; it < last; ++it, first = 0) {
+          const int s = it % STAGES;
+          const uint32_t round = (uint32_t)(it / STAGES);
+          if (!tc::mbar_wait(&full[s], round & 1u, abort_flag, &g_tc_status)) { aborted = true; break; }
+          tc::fence_after_sync();
+          const uint32_t base = smem_u32(smem + s * Cfg::STAGE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ahi = tc::desc_sw128(base + kk * 32);
+            const uint64_t alo = tc::desc_sw128(base + Cfg::A_BYTES + kk * 32);
+            const uint64_t bhi = tc::desc_sw128(base + 2 * Cfg::A_BYTES + kk * 32);
+            const uint64_t blo = tc::desc_sw128(base + 2 * Cfg::A_BYTES + Cfg::B_BYTES + kk * 32);
+            tc::mma_f16(d, ahi, bhi, idesc, (first && kk == 0) ? 0u : 1u);
+            tc::mma_f16(d, ahi, blo, idesc, 1);
+            tc::mma_f16(d, alo, bhi, idesc, 1);
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(&acc_full[b]);
+        if (aborted) break;
+      }
+    }
+  } else {
+    // drain warps: lane quarter = warp % 4, column half = (warp - 2) / 4
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float sum[Cfg::COLS_PER_WARP];
+#pragma unroll
+    for (int e = 0; e < Cfg::COLS_PER_WARP; ++e) sum[e] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int b = c & 1;
+      ok = tc::mbar_wait(&acc_full[b], (c >> 1) & 1u, abort_flag, &g_tc_status);
+      tc::fence_after_sync();
+#pragma unroll
+      for (int cc = 0; cc < Cfg::COLS_PER_WARP; cc += 32) {
+        uint32_t r[32];
+        tc::tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)(b * BN + half * Cfg::COLS_PER_WARP + cc), r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 32; ++e) sum[cc + e] = __fadd_rn(sum[cc + e], __uint_as_float(r[e]));
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+    }
+    float* out = (z == 0) ? C : W + (int64_t)(z - 1) * m * n;
+    const int64_t row = i0 + q * 32 + lane;
+    if (row < m) {
+      const int64_t c0 = j0 + half * Cfg::COLS_PER_WARP;
+      float* dst = out + row * n + c0;
+      const int64_t cols_left = n - c0;
+      if (!ok) {
+#pragma unroll
+        for (int e = 0; e < Cfg::COLS_PER_WARP; ++e) sum[e] = 0.f;
+      }
+      if ((n % 4 == 0) && cols_left >= Cfg::COLS_PER_WARP) {
+#pragma unroll
+        for (int e = 0; e < Cfg::COLS_PER_WARP; e += 4)
+          *reinterpret_cast<float4*>(dst + e) = make_float4(sum[e], sum[e + 1], sum[e + 2], sum[e + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < Cfg::COLS_PER_WARP; ++e)
+          if (e < cols_left) dst[e] = sum[e];
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+__global__ void __launch_bounds__(256) sum_reduce_f32_kernel(int64_t count, float* __restrict__ C,
+                                                             const float* __restrict__ W, int parts,
+                                                             bool vec) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    for (int64_t v = t; v < count / 4; v += stride) {
+      float4 c = reinterpret_cast<const float4*>(C)[v];
+      for (int p = 0; p < parts; ++p) {
+        const float4 w = __ldcs(reinterpret_cast<const float4*>(W + (int64_t)p * count) + v);
+        c.x += w.x; c.y += w.y; c.z += w.z; c.w += w.w;
+      }
+      reinterpret_cast<float4*>(C)[v] = c;
+    }
+  } else {
+    for (int64_t e = t; e < count; e += stride) {
+      float c = C[e];
+      for (int p = 0; p < parts; ++p) c += W[(int64_t)p * count + e];
+      C[e] = c;
+    }
+  }
+}
+
+template <int BN, int STAGES, int CHUNK>
+cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
+                        const CUtensorMap& b_lo, float* C, float* W, int64_t m, int64_t n,
+                        int kb_total, int kbs, int s, cudaStream_t st) {
+  using Cfg = Bf16x3Cfg<BN, STAGES>;
+  static bool configured = false;
+  if (!configured) {
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    configured = true;
+  }
+  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
+  TraceScope tr(kTrTcBf16x3, st);
+  bf16x3_gemm_kernel<BN, STAGES, CHUNK><<<grid, kTcThreads, Cfg::SMEM, st>>>(
+      a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs);
+  return cudaGetLastError();
+}
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct F32Layout {
+  int64_t Kp, a_bytes, b_bytes, off_alo, off_bhi, off_blo, off_part, min_bytes;
+};
+
+F32Layout f32_layout(int64_t m, int64_t n, int64_t k) {
+  F32Layout L;
+  L.Kp = align_up(k > 0 ? k : 1, BK);
+  L.a_bytes = align_up(m * L.Kp * 2, 1024);
+  L.b_bytes = align_up(n * L.Kp * 2, 1024);
+  L.off_alo = L.a_bytes;
+  L.off_bhi = 2 * L.a_bytes;
+  L.off_blo = 2 * L.a_bytes + L.b_bytes;
+  L.off_part = 2 * L.a_bytes + 2 * L.b_bytes;
+  L.min_bytes = L.off_part;
+  return L;
+}
+
+constexpr int kTcBN = 256, kTcStages = 2, kTcChunk = 2;
+
+}  // namespace
+
+// Split an FP32 operand pair into the bf16 hi/lo layout the GEMM expects.
+cudaError_t launch_split_bf16(const float* A, const float* B, int64_t m, int64_t n, int64_t k,
+                              int64_t Kp, __nv_bfloat16* ahi, __nv_bfloat16* alo,
+                              __nv_bfloat16* bhi, __nv_bfloat16* blo, cudaStream_t st) {
+  TraceScope tr(kTrSplitBf16, st);
+  const bool vec = (k % 4 == 0) && aligned16(A);
+  int64_t blocks = (m * (Kp / 8) + 255) / 256;
+  if (blocks > (int64_t)kNumSMs * 16) blocks = (int64_t)kNumSMs * 16;
+  if (blocks < 1) blocks = 1;
+  split_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, Kp, ahi, alo, vec);
+  dim3 g((unsigned)(Kp / 64), (unsigned)((n + 31) / 32));
+  split_transpose_kernel<<<g, 256, 0, st>>>(B, k, n, Kp, bhi, blo);
+  return cudaGetLastError();
+}
+
+int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
+  memset(p, 0, sizeof(*p));
+  const F32Layout L = f32_layout(m, n, k);
+  p->tile_m = BM;
+  p->tile_n = kTcBN;
+  p->tile_k = BK;
+  p->kernel = 2;
+  p->workspace_min = L.min_bytes;
+  if (budget < (size_t)L.min_bytes) {
+    p->split_k = 1;
+    p->workspace_used = L.min_bytes;
+    return MM_OK;
+  }
+  int s = 1, kbs = 0;
+  int64_t used = 0;
+  split_plan(m, n, L.Kp, BK, 4, budget - (size_t)L.min_bytes, &s, &kbs, &used);
+  p->split_k = s;
+  p->workspace_used = L.min_bytes + used;
+  return MM_OK;
+}
+
+int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, float* C, void* ws,
+            size_t ws_bytes, cudaStream_t st) {
+  mm_plan_t p;
+  plan_f32(m, n, k, ws_bytes, &p);
+  if ((size_t)p.workspace_min > ws_bytes) return MM_ERR_WORKSPACE;
+  const F32Layout L = f32_layout(m, n, k);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  auto* ahi = reinterpret_cast<__nv_bfloat16*>(w);
+  auto* alo = reinterpret_cast<__nv_bfloat16*>(w + L.off_alo);
+  auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + L.off_bhi);
+  auto* blo = reinterpret_cast<__nv_bfloat16*>(w + L.off_blo);
+  float* part = p.split_k > 1 ? reinterpret_cast<float*>(w + L.off_part) : nullptr;
+  cudaError_t e = launch_split_bf16(A, B, m, n, k, L.Kp, ahi, alo, bhi, blo, st);
+  if (e != cudaSuccess) return MM_ERR_CUDA;
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  if (make_tmap_2d_16bit(&ta_hi, ahi, m, L.Kp, L.Kp, BM, true) != cudaSuccess ||
+      make_tmap_2d_16bit(&ta_lo, alo, m, L.Kp, L.Kp, BM, true) != cudaSuccess ||
+      make_tmap_2d_16bit(&tb_hi, bhi, n, L.Kp, L.Kp, kTcBN, true) != cudaSuccess ||
+      make_tmap_2d_16bit(&tb_lo, blo, n, L.Kp, L.Kp, kTcBN, true) != cudaSuccess)
+    return MM_ERR_CUDA;
+  const int kb_total = (int)(L.Kp / BK);
+  const int s = p.split_k;
+  const int kbs = (kb_total + s - 1) / s;
+  e = launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, C, part, m, n, kb_total, kbs, s, st);
+  if (e == cudaSuccess && s > 1) {
+    TraceScope tr(kTrSumReduceF32, st);
+    const bool vec = aligned16(C) && aligned16(part) && (m * n) % 4 == 0;
+    int64_t blocks = ((vec ? m * n / 4 : m * n) + 255) / 256;
+    if (blocks > (int64_t)kNumSMs * 8) blocks = (int64_t)kNumSMs * 8;
+    sum_reduce_f32_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(m * n, C, part, s - 1, vec);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}
+
+int read_tc_status(int* status) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
+  *status = v;
+  return MM_OK;
+}
+
+}  // namespace mmsr

@@ -25,6 +25,8 @@ MM_SR_OR_AND_U8 = 4
 MM_STRASSEN_PAPER = 0
 MM_STRASSEN_WINOGRAD = 1
 
+MM_OPT_MINPLUS_PACKED = 1
+
 MM_OK = 0
 MM_ERR_ARG = -1
 MM_ERR_UNSUPPORTED = -2
@@ -82,6 +84,8 @@ def load(path: str = LIB_PATH):
             lib.mm_status_string.argtypes = [i32]
             lib.mm_status_string.restype = ctypes.c_char_p
             lib.mm_version.argtypes = []
+            lib.mm_set_option.argtypes = [i32, i32]
+            lib.mm_set_option.restype = ctypes.c_int
             for f in ("mm_semiring", "mm_strassen", "mm_batched", "mm_plan_query",
                       "mm_last_device_status", "mm_version"):
                 getattr(lib, f).restype = ctypes.c_int
@@ -174,6 +178,11 @@ def mm_last_device_status(stream=None) -> int:
     rc = load().mm_last_device_status(_stream(stream), ctypes.byref(st))
     _check(rc, "mm_last_device_status", True)
     return st.value
+
+
+def mm_set_option(option, value, check=True) -> int:
+    rc = load().mm_set_option(int(option), int(value))
+    return _check(rc, "mm_set_option", check)
 
 
 def mm_version() -> int:

@@ -1,0 +1,59 @@
+"""Run one workload a few times on cuda:0, for profilers (ncu) and timing.
+
+    python -m paper_1911_05328_gb300.profile_case --case minplus4096 --reps 3
+
+Cases: minplus4096 (the (min,+) n=4096 product, budget 0 unless --budget),
+f32_<n> (FP32 mode, bf16x3 on tensor cores), f64_<n> (plain FP64 path).
+Inputs come from the seeded generators; nothing is checked here.
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="minplus4096")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--budget", type=int, default=0, help="extra m x n accumulator buffers")
+    a = ap.parse_args()
+    import torch
+
+    import __graft_entry__
+    from paper_1911_05328_gb300 import inputs, mmsr
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    if a.case.startswith("minplus"):
+        n = int(a.case[len("minplus"):] or 4096)
+        A, B = inputs.tropical_i32(n, n, n, seed=1)
+        sr, dt = mmsr.MM_SR_MIN_PLUS_I32, torch.int32
+        acc = 4
+    elif a.case.startswith("f32_"):
+        n = int(a.case[4:])
+        A, B = inputs.normal_f32(n, n, n, seed=2)
+        sr, dt = mmsr.MM_SR_PLUS_TIMES_F32, torch.float32
+        acc = 4
+    elif a.case.startswith("f64_"):
+        n = int(a.case[4:])
+        A, B = inputs.uniform_f64(n, n, n, seed=0)
+        sr, dt = mmsr.MM_SR_PLUS_TIMES_F64, torch.float64
+        acc = 8
+    else:
+        raise SystemExit("unknown case " + a.case)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((n, n), dtype=dt, device="cuda")
+    p0 = mmsr.mm_plan_query(sr, -1, n, n, n, 0)
+    budget = int(p0.workspace_min) + a.budget * n * n * acc
+    ws = torch.empty((max(budget, 16),), dtype=torch.uint8, device="cuda")
+    for _ in range(a.reps):
+        mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, budget)
+    torch.cuda.synchronize()
+    print("done", a.case, "reps", a.reps)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,94 @@
+"""FP32-mode (+,x): bf16x3 split products on tcgen05 tensor cores vs the FP64
+oracle.  Tolerance: relative Frobenius error <= 1e-5; integer-valued inputs
+whose products and sums are exact in bf16 / fp32 must match bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_05328_gb300 import inputs, mmsr
+
+from gpu_util import canary_intact, dev, empty, rel_fro, workspace
+
+pytestmark = pytest.mark.gpu
+SR = mmsr.MM_SR_PLUS_TIMES_F32
+TOL = 1e-5
+
+
+def run(A, B, extra_parts=0):
+    import torch
+
+    m, k = A.shape
+    n = B.shape[1]
+    p0 = mmsr.mm_plan_query(SR, -1, m, n, k, 0)
+    budget = int(p0.workspace_min) + extra_parts * m * n * 4
+    ws = workspace(budget)
+    dC = empty((m, n), torch.float32)
+    mmsr.mm_semiring(SR, m, n, k, dev(A.astype(np.float32)), dev(B.astype(np.float32)), dC, ws, budget)
+    torch.cuda.synchronize()
+    assert canary_intact(ws, budget)
+    assert mmsr.mm_last_device_status() == 0
+    return dC.cpu().numpy()
+
+
+def test_tiny_integer_tile_exact():
+    A, B = inputs.small_int(128, 64, 256, seed=50, dtype=np.float32)
+    np.testing.assert_array_equal(run(A, B), oracle.mm_f64(A, B).astype(np.float32))
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (128, 256, 64), (129, 257, 65), (300, 200, 1000), (256, 512, 2048)])
+def test_integer_inputs_exact(m, n, k):
+    A, B = inputs.small_int(m, k, n, seed=m + n + k, bound=4, dtype=np.float32)
+    np.testing.assert_array_equal(run(A, B), oracle.mm_f64(A, B).astype(np.float32))
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (200, 300, 777), (512, 512, 4096), (1000, 1100, 1200)])
+def test_normal_inputs_tolerance(m, n, k):
+    A, B = inputs.normal_f32(m, k, n, seed=m * 3 + k)
+    err = rel_fro(run(A, B), oracle.mm_f64(A, B))
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("parts", [1, 2, 5])
+def test_split_k(parts):
+    m, n, k = 256, 384, 2048
+    A, B = inputs.normal_f32(m, k, n, seed=60 + parts)
+    err = rel_fro(run(A, B, extra_parts=parts), oracle.mm_f64(A, B))
+    assert err <= TOL, err
+
+
+def test_workspace_below_minimum_rejected():
+    import torch
+
+    m = n = k = 256
+    p = mmsr.mm_plan_query(SR, -1, m, n, k, 0)
+    assert p.workspace_min == 4 * 256 * (m + n)
+    ws = empty((int(p.workspace_min),), torch.uint8)
+    dA = empty((m, k), torch.float32)
+    rc = mmsr.mm_semiring(SR, m, n, k, dA, dA, dA, ws, int(p.workspace_min) - 16, check=False)
+    assert rc == mmsr.MM_ERR_WORKSPACE
+
+
+def test_k_zero_writes_zero():
+    import torch
+
+    dC = empty((3, 5), torch.float32)
+    dC.fill_(9.0)
+    p = mmsr.mm_plan_query(SR, -1, 3, 5, 0, 0)
+    ws = empty((int(p.workspace_min),), torch.uint8)
+    mmsr.mm_semiring(SR, 3, 5, 0, empty((3, 1), torch.float32), empty((1, 5), torch.float32), dC, ws,
+                     int(p.workspace_min))
+    torch.cuda.synchronize()
+    assert np.all(dC.cpu().numpy() == 0.0)
+
+
+def test_full_size_n8192_sampled_rows():
+    import torch
+
+    n = 8192
+    A, B = inputs.normal_f32(n, n, n, seed=2)
+    C = run(A, B)
+    rows = oracle.sample_rows(n)
+    ref = oracle.mm_f64(A, B, rows=rows)
+    err = rel_fro(C[rows], ref)
+    assert err <= TOL, err
+    torch.cuda.empty_cache()

@@ -16,6 +16,13 @@ pytestmark = pytest.mark.gpu
 SR = mmsr.MM_SR_MIN_PLUS_I32
 
 
+@pytest.fixture(params=[1, 0], ids=["packed-auto", "int32-only"])
+def packed(request):
+    mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_PACKED, request.param)
+    yield request.param
+    mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_PACKED, 1)
+
+
 def run(A, B, budget=0):
     import torch
 
@@ -32,13 +39,13 @@ def run(A, B, budget=0):
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 5, 3), (64, 64, 64), (128, 128, 32), (129, 131, 67),
                                    (256, 256, 256), (130, 260, 1000), (1000, 1000, 1000), (333, 97, 4099)])
-def test_leaf_matches_oracle(m, n, k):
+def test_leaf_matches_oracle(m, n, k, packed):
     A, B = inputs.tropical_i32(m, k, n, seed=m + n + k)
     np.testing.assert_array_equal(run(A, B), oracle.mm_minplus(A, B))
 
 
 @pytest.mark.parametrize("parts", [1, 2, 3, 5, 9])
-def test_split_k_budgets_bit_identical(parts):
+def test_split_k_budgets_bit_identical(parts, packed):
     m, n, k = 300, 260, 1440  # 45 k-blocks of 32: divisible into 1, 2, 3, 5, 9 slices
     A, B = inputs.tropical_i32(m, k, n, seed=31)
     budget = (parts - 1) * m * n * 4
@@ -52,6 +59,27 @@ def test_budget_not_multiple_of_slice():
     A, B = inputs.tropical_i32(m, k, n, seed=32)
     budget = 2 * m * n * 4 + 1234  # 2 full buffers + change
     np.testing.assert_array_equal(run(A, B, budget), oracle.mm_minplus(A, B))
+
+
+@pytest.mark.parametrize("big", [16384, 20000, (1 << 30) - 1])
+def test_value_outside_packed_range_falls_back(big):
+    # one finite entry above 16383 must route the call to the 32-bit leaf
+    m, n, k = 200, 300, 500
+    A, B = inputs.tropical_i32(m, k, n, seed=35)
+    A[17, 123] = big
+    B[45, 7] = big
+    np.testing.assert_array_equal(run(A, B), oracle.mm_minplus(A, B))
+
+
+def test_packed_range_edge_values():
+    # largest packable entries: finite sums reach 32766, one below the
+    # 16-bit sentinel, and must not be confused with +inf
+    m, n, k = 130, 260, 70
+    A = np.full((m, k), 16383, np.int32)
+    B = np.full((k, n), 16383, np.int32)
+    A[::3, :] = inputs.INF
+    B[:, 5] = inputs.INF
+    np.testing.assert_array_equal(run(A, B), oracle.mm_minplus(A, B))
 
 
 def test_k_zero_is_semiring_zero():
