@@ -139,6 +139,16 @@ int mm_strassen(int levels, int variant, int semiring, int64_t m, int64_t n, int
                 const void* A, const void* B, void* C, void* workspace, size_t workspace_bytes,
                 void* stream);
 
+/*
+ * mm_strassen_tables -- the bilinear coefficients one level of `variant`
+ * uses (host copy of the device tables): alpha[7][4] (S_r = sum_q
+ * alpha[r][q] A_q), beta[7][4] (T_r = sum_q beta[r][q] B_q) and gamma[4][7]
+ * (C_q = sum_r gamma[q][r] P_r), quadrants ordered 00, 01, 10, 11, row-major
+ * int8 arrays of 28 entries each, written by the call.  Section 5 prints the
+ * MM_STRASSEN_PAPER table.  Returns MM_OK or MM_ERR_ARG.
+ */
+int mm_strassen_tables(int variant, int8_t* alpha, int8_t* beta, int8_t* gamma);
+
 /* One problem of a batch (host-side descriptor; pointers are device). */
 typedef struct {
   int32_t semiring; /* MM_SR_PLUS_TIMES_F32 or MM_SR_MIN_PLUS_I32 */

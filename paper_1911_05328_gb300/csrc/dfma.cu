@@ -59,14 +59,20 @@ __device__ __forceinline__ void load_stage(double* As, double* Bs, const double*
 __global__ void __launch_bounds__(THREADS)
     dfma_leaf_kernel(int64_t m, int64_t n, int64_t k, const double* __restrict__ A,
                      const double* __restrict__ B, double* __restrict__ C,
-                     double* __restrict__ W, int kb_per_slice, bool vec) {
+                     double* __restrict__ W, int kb_per_slice, bool vec, int slices,
+                     int64_t a_bs, int64_t b_bs, int64_t c_bs) {
   extern __shared__ __align__(16) double smem_d[];
+  // blockIdx.z = batch * slices + k-slice (batches: independent products)
+  const int batch = blockIdx.z / slices;
+  A += (int64_t)batch * a_bs;
+  B += (int64_t)batch * b_bs;
+  C += (int64_t)batch * c_bs;
   double* As = smem_d;
   double* Bs = smem_d + SMEM_A;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z % slices;
   const int64_t kb_total = (k + BK - 1) / BK;
   const int64_t kb_begin = (int64_t)z * kb_per_slice;
   const int64_t kb_end = min(kb_total, kb_begin + kb_per_slice);
@@ -183,7 +189,26 @@ cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, c
                    (W == nullptr || aligned16(W));
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
   TraceScope tr(kTrDfmaLeaf, st);
-  dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec);
+  dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec, s, 0, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int64_t m, int64_t n,
+                                int64_t k, int batches, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(dfma_leaf_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM_BYTES));
+    configured = true;
+  }
+  const bool vec = (k % 2 == 0) && (n % 2 == 0) && aligned16(A) && aligned16(B) && aligned16(C) &&
+                   ((m * k) % 2 == 0) && ((k * n) % 2 == 0) && ((m * n) % 2 == 0);
+  const int kb = (int)((k + BK - 1) / BK);
+  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)batches);
+  TraceScope tr(kTrDfmaLeaf, st);
+  dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, nullptr, kb > 0 ? kb : 1, vec, 1,
+                                                      m * k, k * n, m * n);
   return cudaGetLastError();
 }
 

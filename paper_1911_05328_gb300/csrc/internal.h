@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "../../include/mmsr.h"
 
 namespace mmsr {
@@ -30,6 +32,13 @@ int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
 int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, float* C, void* ws,
             size_t ws_bytes, cudaStream_t st);
 int read_tc_status(int* status);
+
+// batched leaves (independent products on stacked operands)
+cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
+                                  const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,
+                                  int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st);
+cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int64_t m, int64_t n,
+                                int64_t k, int batches, cudaStream_t st);
 
 // Strassen engine
 int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget,

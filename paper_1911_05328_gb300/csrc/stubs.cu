@@ -23,11 +23,6 @@ int run_extended(int sr, int64_t m, int64_t n, int64_t k, const void* A, const v
   }
 }
 
-int plan_strassen(int, int, int64_t, int64_t, int64_t, size_t, mm_plan_t*) { return MM_ERR_UNSUPPORTED; }
-int run_strassen(int, int, int, int64_t, int64_t, int64_t, const void*, const void*, void*, void*,
-                 size_t, cudaStream_t) {
-  return MM_ERR_UNSUPPORTED;
-}
 
 int read_device_status(cudaStream_t st, int* status) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return MM_ERR_CUDA;

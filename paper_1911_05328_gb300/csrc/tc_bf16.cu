@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAhi, const __grid_constant__ CUtensorMap tAlo,
                        const __grid_constant__ CUtensorMap tBhi, const __grid_constant__ CUtensorMap tBlo,
                        float* __restrict__ C, float* __restrict__ W, int64_t m, int64_t n,
-                       int kb_total, int kb_per_slice) {
+                       int kb_total, int kb_per_slice, int slices, int64_t a_batch_rows,
+                       int64_t b_batch_rows, int64_t c_batch_stride) {
   using Cfg = Bf16x3Cfg<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
@@ -162,7 +163,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
-  const int z = blockIdx.z;
+  // blockIdx.z = batch * slices + k-slice; a batch is one independent product
+  // whose operands sit at row offset batch * {a,b}_batch_rows of the stacks
+  const int z = blockIdx.z % slices;
+  const int batch = blockIdx.z / slices;
+  const int ya = (int)(batch * a_batch_rows + i0), yb = (int)(batch * b_batch_rows + j0);
   const int kb_begin = z * kb_per_slice;
   const int kb_end = min(kb_total, kb_begin + kb_per_slice);
   const int nkb = kb_end > kb_begin ? kb_end - kb_begin : 0;
@@ -199,10 +204,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
         uint8_t* st = smem + s * Cfg::STAGE_BYTES;
         const int kx = (kb_begin + it) * BK;
-        tc::tma_load_2d(st, &tAhi, &full[s], kx, (int)i0);
-        tc::tma_load_2d(st + Cfg::A_BYTES, &tAlo, &full[s], kx, (int)i0);
-        tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, (int)j0);
-        tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, (int)j0);
+        tc::tma_load_2d(st, &tAhi, &full[s], kx, ya);
+        tc::tma_load_2d(st + Cfg::A_BYTES, &tAlo, &full[s], kx, ya);
+        tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, yb);
+        tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, yb);
       }
     }
   } else if (warp == 1) {
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
     }
-    float* out = (z == 0) ? C : W + (int64_t)(z - 1) * m * n;
+    float* out = (z == 0) ? C + (int64_t)batch * c_batch_stride : W + (int64_t)(z - 1) * m * n;
     const int64_t row = i0 + q * 32 + lane;
     if (row < m) {
       const int64_t c0 = j0 + half * Cfg::COLS_PER_WARP;
@@ -314,7 +319,9 @@ __global__ void __launch_bounds__(256) sum_reduce_f32_kernel(int64_t count, floa
 template <int BN, int STAGES, int CHUNK>
 cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
                         const CUtensorMap& b_lo, float* C, float* W, int64_t m, int64_t n,
-                        int kb_total, int kbs, int s, cudaStream_t st) {
+                        int kb_total, int kbs, int s, cudaStream_t st, int batches = 1,
+                        int64_t a_batch_rows = 0, int64_t b_batch_rows = 0,
+                        int64_t c_batch_stride = 0) {
   using Cfg = Bf16x3Cfg<BN, STAGES>;
   static bool configured = false;
   if (!configured) {
@@ -322,10 +329,10 @@ cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const 
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     configured = true;
   }
-  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
+  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)(s * batches));
   TraceScope tr(kTrTcBf16x3, st);
   bf16x3_gemm_kernel<BN, STAGES, CHUNK><<<grid, kTcThreads, Cfg::SMEM, st>>>(
-      a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs);
+      a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride);
   return cudaGetLastError();
 }
 
@@ -365,6 +372,22 @@ cudaError_t launch_split_bf16(const float* A, const float* B, int64_t m, int64_t
   dim3 g((unsigned)(Kp / 64), (unsigned)((n + 31) / 32));
   split_transpose_kernel<<<g, 256, 0, st>>>(B, k, n, Kp, bhi, blo);
   return cudaGetLastError();
+}
+
+// `batches` independent bf16x3 products on stacked split operands:
+// A stack (batches*m) x Kp, B stack (batches*n) x Kp (both K-major, hi/lo),
+// output P + b*m*n (row-major m x n each).
+cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
+                                  const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,
+                                  int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st) {
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_hi, ahi, batches * m, Kp, Kp, BM, true));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_lo, alo, batches * m, Kp, Kp, BM, true));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_hi, bhi, batches * n, Kp, Kp, kTcBN, true));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, batches * n, Kp, Kp, kTcBN, true));
+  const int kb_total = (int)(Kp / BK);
+  return launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, P, nullptr, m, n,
+                                                 kb_total, kb_total, 1, st, batches, m, n, m * n);
 }
 
 int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {

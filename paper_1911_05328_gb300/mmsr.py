@@ -187,3 +187,19 @@ def mm_set_option(option, value, check=True) -> int:
 
 def mm_version() -> int:
     return int(load().mm_version())
+
+
+def mm_strassen_tables(variant):
+    """(alpha[7][4], beta[7][4], gamma[4][7]) int8 tables of one level."""
+    import numpy as np
+
+    a = (ctypes.c_int8 * 28)()
+    b = (ctypes.c_int8 * 28)()
+    g = (ctypes.c_int8 * 28)()
+    lib = load()
+    lib.mm_strassen_tables.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mm_strassen_tables.restype = ctypes.c_int
+    _check(lib.mm_strassen_tables(int(variant), ctypes.addressof(a), ctypes.addressof(b),
+                                  ctypes.addressof(g)), "mm_strassen_tables", True)
+    return (np.array(a[:], dtype=np.int64).reshape(7, 4), np.array(b[:], dtype=np.int64).reshape(7, 4),
+            np.array(g[:], dtype=np.int64).reshape(4, 7))

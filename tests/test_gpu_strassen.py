@@ -1,0 +1,123 @@
+"""Strassen / Strassen-Winograd levels on the GPU vs the oracle.
+
+* Integer-valued inputs whose every intermediate is exact (bf16 split, FP32
+  sums below 2^24) must reproduce the classic oracle product bit for bit,
+  for L = 1..4 and both variants (the paper's pin: exact agreement of
+  Strassen with the classic result on small-integer inputs).
+* Plain FP64 mode must stay within 1e-12 relative Frobenius error.
+* FP32 mode (bf16x3 leaves) has an error that grows with the number of
+  levels (the operand sums are larger than the entries and the post-additions
+  cancel); it is reported per level and checked against 1.5e-5 * 2.8^(L-1)
+  (measured growth: about 2x per level for the paper's formulas and 2.7x for
+  Winograd's, whose operand sums have up to four terms).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_05328_gb300 import inputs, mmsr
+
+from gpu_util import canary_intact, dev, empty, rel_fro, workspace
+
+pytestmark = pytest.mark.gpu
+VARIANTS = [mmsr.MM_STRASSEN_PAPER, mmsr.MM_STRASSEN_WINOGRAD]
+
+
+def run(L, variant, sr, A, B):
+    import torch
+
+    m, k = A.shape
+    n = B.shape[1]
+    p = mmsr.mm_plan_query(sr, L, m, n, k, 0)
+    budget = int(p.workspace_min)
+    ws = workspace(budget)
+    dt = torch.float32 if sr == mmsr.MM_SR_PLUS_TIMES_F32 else torch.float64
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    dC = empty((m, n), dt)
+    mmsr.mm_strassen(L, variant, sr, m, n, k, dev(A.astype(npdt)), dev(B.astype(npdt)), dC, ws, budget)
+    torch.cuda.synchronize()
+    assert canary_intact(ws, budget)
+    return dC.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L,m,k,n,bound", [(1, 256, 256, 256, 2), (2, 512, 256, 384, 2),
+                                           (3, 512, 512, 256, 2), (4, 1024, 1024, 768, 1)])
+def test_fp32_integer_inputs_exact(variant, L, m, k, n, bound):
+    A, B = inputs.small_int(m, k, n, seed=70 + L, bound=bound, dtype=np.float32)
+    C = run(L, variant, mmsr.MM_SR_PLUS_TIMES_F32, A, B)
+    np.testing.assert_array_equal(C, oracle.mm_f64(A, B).astype(np.float32))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_fp64_integer_inputs_exact(variant, L):
+    m, k, n = 256, 512, 320
+    A, B = inputs.small_int(m, k, n, seed=80 + L, bound=5)
+    np.testing.assert_array_equal(run(L, variant, mmsr.MM_SR_PLUS_TIMES_F64, A, B), oracle.mm_f64(A, B))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_fp64_uniform_tolerance(variant, L):
+    m, k, n = 512, 768, 256
+    A, B = inputs.uniform_f64(m, k, n, seed=3)
+    err = rel_fro(run(L, variant, mmsr.MM_SR_PLUS_TIMES_F64, A, B), oracle.mm_f64(A, B))
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_fp32_uniform_error_per_level(variant, L):
+    m, k, n = 1024, 2048, 768
+    A, B = inputs.uniform_f64(m, k, n, seed=3)
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    err = rel_fro(run(L, variant, mmsr.MM_SR_PLUS_TIMES_F32, A32, B32), oracle.mm_f64(A32, B32))
+    print("fp32 strassen variant %d L %d rel_fro %.3e" % (variant, L, err))
+    assert err <= 1.5e-5 * 2.8 ** (L - 1), err
+
+
+def test_rectangular_shape_all_levels():
+    # the 12288 x 16384 x 8192 shape scaled down by 16, FP64 mode
+    m, k, n = 768, 1024, 512
+    A, B = inputs.uniform_f64(m, k, n, seed=3)
+    ref = oracle.mm_f64(A, B)
+    for L in (1, 2, 3, 4):
+        assert rel_fro(run(L, mmsr.MM_STRASSEN_WINOGRAD, mmsr.MM_SR_PLUS_TIMES_F64, A, B), ref) <= 1e-12
+
+
+def test_workspace_below_minimum_rejected():
+    import torch
+
+    p = mmsr.mm_plan_query(mmsr.MM_SR_PLUS_TIMES_F32, 2, 256, 256, 256, 0)
+    ws = empty((int(p.workspace_min),), torch.uint8)
+    d = empty((256, 256), torch.float32)
+    rc = mmsr.mm_strassen(2, 1, mmsr.MM_SR_PLUS_TIMES_F32, 256, 256, 256, d, d, d, ws,
+                          int(p.workspace_min) - 1024, check=False)
+    assert rc == mmsr.MM_ERR_WORKSPACE
+
+
+def test_full_size_n16384_fp32_sampled_rows():
+    # the Strassen-Winograd workload: n = 16384, uniform[-1,1] (seed 3) cast
+    # to float32; error per level on the sampled rows (incl. quadrant edges)
+    import torch
+
+    n = 16384
+    A, B = inputs.uniform_f64(n, n, n, seed=3)
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    del A, B
+    rows = oracle.sample_rows(n)
+    ref = oracle.mm_f64(A32, B32, rows=rows)
+    dA, dB = dev(A32), dev(B32)
+    dC = empty((n, n), torch.float32)
+    for L in (1, 2, 3, 4):
+        p = mmsr.mm_plan_query(mmsr.MM_SR_PLUS_TIMES_F32, L, n, n, n, 0)
+        ws = empty((int(p.workspace_min),), torch.uint8)
+        mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, mmsr.MM_SR_PLUS_TIMES_F32, n, n, n, dA, dB, dC, ws,
+                         int(p.workspace_min))
+        torch.cuda.synchronize()
+        err = rel_fro(dC.cpu().numpy()[rows], ref)
+        print("n16384 fp32 winograd L %d rel_fro %.3e workspace %.2f n^2*4B" % (L, err, p.workspace_min / (n * n * 4)))
+        assert err <= 1.5e-5 * 2.8 ** (L - 1), err
+        del ws
+        torch.cuda.empty_cache()
