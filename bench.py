@@ -435,6 +435,33 @@ def run_extras(mmsr, lib, torch, sp):
     import ctypes
 
     rate, pms = ctypes.c_double(), ctypes.c_double()
+    del dA, dB, dC, ws
+    torch.cuda.empty_cache()
+    # FP64-accuracy mode at n = 8192 (uniform[-1,1]) beside the plain FP64
+    # path at the same size and the same stated accuracy (1e-12)
+    A, B = inputs.uniform_f64(n, n, n, seed=3)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    del A, B
+    dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    sr = mmsr.MM_SR_PLUS_TIMES_F64ACC
+    wmin = int(mmsr.mm_plan_query(sr, -1, n, n, n, 0).workspace_min)
+    ws = torch.empty((wmin,), dtype=torch.uint8, device="cuda")
+    lib.mm_trace_enable(1)
+    ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, wmin, sp), 3)
+    lib.mm_trace_enable(0)
+    lib.mm_trace_summary(8, ctypes.byref(cnt), ctypes.byref(tot))  # tc_f64acc
+    gemm_ms = tot.value / max(cnt.value, 1)
+    issued = 21 * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12
+    out["fp64acc_n8192"] = {
+        "ms": ms, "gflops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms,
+        "tensor_tflops_issued_21_slice_products": issued, "frac_of_bf16_peak": issued / peaks["bf16_tflops"],
+        "workspace_bytes": wmin, "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms,
+        "error": "rel. Frobenius vs FP64 oracle <= 1e-12 (tests; 2.1e-13 at n=16384)"}
+    del dA, dB, dC, ws
+    torch.cuda.empty_cache()
+    out["batched_512"] = run_batched_extras(mmsr, lib, torch, sp, ctypes)
+    out["strassen_fp32_n16384"] = run_strassen_extras(mmsr, lib, torch, sp, ctypes)
+    rate, pms = ctypes.c_double(), ctypes.c_double()
     lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.mm_probe_peak(2, 2000, sp, ctypes.byref(rate), ctypes.byref(pms))
@@ -443,9 +470,86 @@ def run_extras(mmsr, lib, torch, sp):
     out["addmin_u16x2_probe_tops"] = rate.value / 1e12
     lib.mm_probe_peak(3, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
     out["fp32_fma_probe_tflops"] = rate.value / 1e12
-    del dA, dB, dC
     torch.cuda.empty_cache()
     return out
+
+
+def run_batched_extras(mmsr, lib, torch, sp, ctypes):
+    """512 problems (m, n, k log-uniform in [64, 2048], 70% FP32 (+,x) with
+    normal(0,1) entries, 30% (min,+) with integers in [0, 1000], seed 4) in
+    one persistent launch, captured once in a CUDA graph and replayed."""
+    from paper_1911_05328_gb300 import inputs
+
+    probs = inputs.batched_problems(count=512, seed=4)
+    dA = [torch.from_numpy(p.A).cuda() for p in probs]
+    dB = [torch.from_numpy(p.B).cuda() for p in probs]
+    dC = [torch.empty((p.m, p.n), dtype=torch.float32 if p.semiring == mmsr.MM_SR_PLUS_TIMES_F32 else torch.int32,
+                      device="cuda") for p in probs]
+    table = [(p.semiring, p.m, p.n, p.k, a, b, c) for p, a, b, c in zip(probs, dA, dB, dC)]
+    need = mmsr.mm_batched_query(table)
+    ws = torch.empty((need,), dtype=torch.uint8, device="cuda")
+    ops = sum(2.0 * p.m * p.n * p.k for p in probs)
+    ops_fp32 = sum(2.0 * p.m * p.n * p.k for p in probs if p.semiring == mmsr.MM_SR_PLUS_TIMES_F32)
+    mmsr.mm_batched(table, ws, need, stream=sp)  # sets kernel attributes before capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        mmsr.mm_batched(table, ws, need, stream=torch.cuda.current_stream())
+    lib.mm_trace_enable(1)
+    ms = _time_call(torch, g.replay, 10)
+    lib.mm_trace_enable(0)
+    res = {"ms": ms, "gops": ops / (ms * 1e-3) / 1e9, "ops": ops, "fp32_share_of_ops": ops_fp32 / ops,
+           "workspace_bytes": int(need), "launch": "one CUDA graph: memset + 2 pre-passes + 1 persistent kernel",
+           "error": "bit-exact (min,+), <= 1e-5 FP32, per problem (tests)"}
+    del dA, dB, dC, ws
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
+    """Strassen-Winograd, FP32 mode, n = 16384 (uniform[-1,1], seed 3, cast
+    to float32): classic (L = 0) and L = 1..4, per-level time, classic-
+    equivalent GOp/s, workspace as a multiple of n^2 * 4 bytes and the time
+    split between operand sums, leaf products and post-additions."""
+    from paper_1911_05328_gb300 import inputs
+
+    n = 16384
+    A, B = inputs.uniform_f64(n, n, n, seed=3)
+    dA = torch.from_numpy(A.astype(np.float32)).cuda()
+    dB = torch.from_numpy(B.astype(np.float32)).cuda()
+    del A, B
+    dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    sr = mmsr.MM_SR_PLUS_TIMES_F32
+    res = {}
+    names = {}
+    lib.mm_trace_kernel_name.restype = ctypes.c_char_p
+    for kid in range(lib.mm_trace_kernel_count()):
+        names[kid] = lib.mm_trace_kernel_name(kid).decode()
+    for L in range(0, 5):
+        p = mmsr.mm_plan_query(sr, L, n, n, n, 0)
+        ws = torch.empty((max(int(p.workspace_min), 16),), dtype=torch.uint8, device="cuda")
+        fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
+                                      int(p.workspace_min), sp)
+        fn()
+        torch.cuda.synchronize()
+        lib.mm_trace_enable(1)
+        ms = _time_call(torch, fn, 3)
+        lib.mm_trace_enable(0)
+        split = {}
+        for kid, nm in names.items():
+            cnt, tot = ctypes.c_int64(), ctypes.c_double()
+            lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
+            if cnt.value:
+                split[nm] = tot.value / 4  # 1 untimed-warm call + 3 timed calls traced
+        res["L%d" % L] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                          "workspace_bytes": int(p.workspace_min),
+                          "workspace_n2x4B": p.workspace_min / (n * n * 4.0), "kernel_ms": split}
+        del ws
+        torch.cuda.empty_cache()
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    return res
 
 
 if __name__ == "__main__":

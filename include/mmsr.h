@@ -49,14 +49,20 @@ typedef enum {
    * products hi*hi + hi*lo + lo*hi on tcgen05 tensor cores, FP32 accumulate.
    * Needs 4*(m*k + k*n) bytes of workspace for the split operands. */
   MM_SR_PLUS_TIMES_F32 = 1,
-  /* (+, x) over FP64 in/out at FP64 accuracy from 16-bit tensor-core
-   * products of scaled integer slices, summed exactly / in FP64. */
+  /* (+, x) over FP64 in/out at FP64 accuracy: every row of A / column of B
+   * is scaled by a power of two and cut into seven 7-bit integer digit
+   * slices (bf16); the 28 slice products of digit order <= 6 run on tcgen05
+   * tensor cores with exact chunked integer accumulation, combined once in
+   * FP64.  Needs 14*(m+n)*Kp + 4*(m+n) + 8*n bytes of workspace
+   * (Kp = k rounded up to 32); mm_plan_query reports it. */
   MM_SR_PLUS_TIMES_F64ACC = 2,
   /* (min, +) tropical semiring over int32 in [0, 2^30]; 2^30 is +infinity
    * (the semiring's 0).  Sums saturate at 2^30 (never wrap).  Inputs outside
    * [0, 2^30] are a precondition violation (not checked on the device). */
   MM_SR_MIN_PLUS_I32 = 3,
-  /* Boolean (or, and) over uint8; nonzero = true, output is 0 or 1. */
+  /* Boolean (or, and) over uint8; nonzero = true, output is 0 or 1.
+   * Operands are bit-packed along k in the workspace (4*(m+n)*ceil(k/32)
+   * bytes); split-K partials are one byte per output. */
   MM_SR_OR_AND_U8 = 4
 } mm_semiring_t;
 

@@ -107,6 +107,11 @@ static int validate_common(int sr, int64_t m, int64_t n, int64_t k, const void* 
   return MM_OK;
 }
 
+int report_cuda(cudaError_t e, const char* where) {
+  fprintf(stderr, "libmmsr: %s failed: CUDA error %d (%s)\n", where, (int)e, cudaGetErrorString(e));
+  return MM_ERR_CUDA;
+}
+
 static int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return MM_OK;
   fprintf(stderr, "libmmsr: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));

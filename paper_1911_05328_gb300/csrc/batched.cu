@@ -1,0 +1,439 @@
+// batched.cu -- many independent products of mixed shapes and semirings in
+// one persistent launch (the dynamic load balancing a processor-oblivious
+// schedule relies on, Section 6: idle workers take the next available task).
+//
+// Host side: problems are sorted by cost (2 m n k, longest first) and cut
+// into output tiles; the sorted problem table travels by value as a kernel
+// parameter.  FP32 problems are split into bf16 hi/lo operands by one
+// pre-pass into stacked buffers with a common row pitch (so four tensor maps
+// describe every FP32 problem of the batch); a second pre-pass decides, per
+// (min,+) problem, whether the exact packed 2 x 16-bit leaf applies.
+//
+// Device side: one CTA per SM pops tile indices from an atomic counter.  A
+// FP32 tile runs the tcgen05 pipeline (TMA producer warp, MMA warp, eight
+// drain warps, chunked TMEM accumulation); a (min,+) tile runs the CUDA-core
+// mainloop on the eight drain warps.  The shared-memory ring and the TMEM
+// accumulators persist across tiles with running phase counters, so no
+// barrier is ever re-initialised while an asynchronous arrive may be pending.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string.h>
+#include <vector>
+
+#include "internal.h"
+#include "minplus_tile.cuh"
+#include "tcgen05.cuh"
+
+namespace mmsr {
+namespace {
+
+__device__ int g_batched_status;
+
+constexpr int kMaxBatch = 512;
+constexpr int TBM = 128, TBN = 128, TBK = 64, TSTAGES = 3, TCHUNK = 2;
+constexpr int kDrainW = 8, kBThreads = 64 + 32 * kDrainW;
+constexpr uint32_t TA_BYTES = TBM * TBK * 2, TB_BYTES = TBN * TBK * 2;
+constexpr uint32_t TSTAGE = 2 * TA_BYTES + 2 * TB_BYTES;
+constexpr size_t BSMEM = 1024 + (size_t)TSTAGES * TSTAGE + 256;
+constexpr uint32_t BTMEM_COLS = 2 * TBN;
+constexpr int MPN = 256;  // (min,+) tile: 128 x 256
+
+struct BatchTable {
+  int count;
+  int total_tiles;
+  int kind[kMaxBatch];  // 0: FP32 (+,x) on tensor cores, 1: (min,+)
+  int m[kMaxBatch], n[kMaxBatch], k[kMaxBatch];
+  int tile_start[kMaxBatch + 1];
+  int row0a[kMaxBatch];  // FP32: first row of this A in the stacked split buffers
+  int row0b[kMaxBatch];  // FP32: first row of this B^T in the stacked split buffers
+  const void* A[kMaxBatch];
+  const void* B[kMaxBatch];
+  void* C[kMaxBatch];
+};
+static_assert(sizeof(BatchTable) + 4 * sizeof(CUtensorMap) + 64 < 32764, "kernel parameter space");
+
+// ----------------------------------------------------------- pre-passes
+__device__ __forceinline__ void split1(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// FP32 problems: A -> stacked hi/lo rows (pitch KP), B -> stacked hi/lo of
+// B^T (pitch KP); columns k..roundup(k, 64) are zero.  blockIdx.y = problem.
+__global__ void __launch_bounds__(256) batched_split_kernel(const __grid_constant__ BatchTable T,
+                                                            int64_t KP, __nv_bfloat16* __restrict__ ahi,
+                                                            __nv_bfloat16* __restrict__ alo,
+                                                            __nv_bfloat16* __restrict__ bhi,
+                                                            __nv_bfloat16* __restrict__ blo) {
+  const int p = blockIdx.y;
+  if (T.kind[p] != 0) return;
+  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+  const int64_t kp = (k + TBK - 1) / TBK * TBK;
+  const float* A = static_cast<const float*>(T.A[p]);
+  const float* B = static_cast<const float*>(T.B[p]);
+  // A rows: one thread per 8 output columns
+  const int64_t cpr = kp / 8;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < m * cpr; e += (int64_t)gridDim.x * 256) {
+    const int64_t r = e / cpr, c8 = (e - r * cpr) * 8;
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) split1(c8 + t < k ? A[r * k + c8 + t] : 0.f, h[t], l[t]);
+    const int64_t off = (T.row0a[p] + r) * KP + c8;
+    *reinterpret_cast<uint4*>(ahi + off) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(alo + off) = *reinterpret_cast<const uint4*>(l);
+  }
+  // B^T: 64 (k) x 32 (n) tiles through shared memory
+  __shared__ float tile[64][33];
+  const int64_t tk = kp / 64, tn = (n + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t tt = blockIdx.x; tt < tk * tn; tt += gridDim.x) {
+    const int64_t k0 = (tt / tn) * 64, n0 = (tt % tn) * 32;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int kk = ty + 8 * i;
+      const int64_t gk = k0 + kk, gn = n0 + tx;
+      tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.f;
+    }
+    __syncthreads();
+    const int row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
+    const int64_t gn = n0 + row;
+    if (gn < n) {
+      __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], h[e], l[e]);
+      const int64_t off = (T.row0b[p] + gn) * KP + k0 + chunk * 8;
+      *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(l);
+    }
+  }
+}
+
+// (min,+) problems: flag any entry outside the packed range (violation[p]
+// starts at 0, set by a memset before the launch).
+__global__ void __launch_bounds__(256) batched_range_kernel(const __grid_constant__ BatchTable T,
+                                                            int* __restrict__ violation) {
+  const int p = blockIdx.y;
+  if (T.kind[p] != 1) return;
+  int bad = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int32_t* X = static_cast<const int32_t*>(pass ? T.B[p] : T.A[p]);
+    const int64_t cnt = pass ? (int64_t)T.k[p] * T.n[p] : (int64_t)T.m[p] * T.k[p];
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * 256)
+      bad |= mp::out_of_pack_range(X[e]);
+  }
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) atomicOr(&violation[p], 1);
+}
+
+// 32-bit fallback for a (min,+) tile whose inputs fall outside the packed
+// range; the light variant keeps its register demand within the persistent
+// kernel's budget.
+__device__ __forceinline__ void minplus32_tile_pair(const int32_t* A, const int32_t* B, int32_t* C,
+                                                 int64_t m, int64_t n, int64_t k, int64_t i0,
+                                                 int64_t j0, bool vec, int tid, int32_t* smem) {
+  const int nkb = (int)((k + mp::BK - 1) / mp::BK);
+  for (int h = 0; h < 2; ++h) {
+    if (j0 + h * 128 >= n) break;
+    mp::minplus32_tile<mp::SyncNamed256, true>(A, B, C, (int32_t*)nullptr, 0, m, n, k, i0, j0 + h * 128,
+                                               (int64_t)0, nkb, vec, tid, smem, mp::SyncNamed256());
+    mp::SyncNamed256()();
+  }
+}
+
+// ------------------------------------------------------ persistent kernel
+__global__ void __launch_bounds__(kBThreads, 1)
+    batched_kernel(const __grid_constant__ BatchTable T, const __grid_constant__ CUtensorMap tAhi,
+                   const __grid_constant__ CUtensorMap tAlo, const __grid_constant__ CUtensorMap tBhi,
+                   const __grid_constant__ CUtensorMap tBlo, int* __restrict__ counter,
+                   const int* __restrict__ violation) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = tc::align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TSTAGES * TSTAGE);
+  uint64_t* empty = full + TSTAGES;
+  uint64_t* acc_full = empty + TSTAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int* s_tile = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TSTAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kDrainW);
+    }
+    *abort_flag = 0;
+    tc::mbar_init_fence();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, BTMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  // running positions of the TMA ring and of the TMEM chunk buffers; each
+  // role advances its own copy over the same sequence of tensor-core tiles
+  uint32_t ring = 0, chunk = 0;
+
+  for (;;) {
+    if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = *s_tile;
+    if (t >= T.total_tiles) break;
+    int lo = 0, hi = T.count - 1;  // last p with tile_start[p] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (T.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int p = lo;
+    const int local = t - T.tile_start[p];
+    const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+
+    if (T.kind[p] == 0) {
+      // ------------------------------------------------ FP32 tensor-core tile
+      const int tiles_n = (int)((n + TBN - 1) / TBN);
+      const int64_t i0 = (int64_t)(local / tiles_n) * TBM, j0 = (int64_t)(local % tiles_n) * TBN;
+      const int nkb = (int)((k + TBK - 1) / TBK);
+      const int nchunks = (nkb + TCHUNK - 1) / TCHUNK;
+      if (warp == 0) {
+        if (lane == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const int ya = T.row0a[p] + (int)i0, yb = T.row0b[p] + (int)j0;
+          for (int it = 0; it < nkb; ++it, ++ring) {
+            const int s = ring % TSTAGES;
+            const uint32_t round = ring / TSTAGES;
+            if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_batched_status)) break;
+            tc::mbar_expect_tx(&full[s], TSTAGE);
+            uint8_t* st = smem + s * TSTAGE;
+            tc::tma_load_2d(st, &tAhi, &full[s], it * TBK, ya);
+            tc::tma_load_2d(st + TA_BYTES, &tAlo, &full[s], it * TBK, ya);
+            tc::tma_load_2d(st + 2 * TA_BYTES, &tBhi, &full[s], it * TBK, yb);
+            tc::tma_load_2d(st + 2 * TA_BYTES + TB_BYTES, &tBlo, &full[s], it * TBK, yb);
+          }
+        }
+      } else if (warp == 1) {
+        if (lane == 0) {
+          constexpr uint32_t idesc = tc::idesc_f16(TBM, TBN, 1);
+          int it = 0;
+          for (int c = 0; c < nchunks; ++c, ++chunk) {
+            const int b = chunk & 1;
+            if (chunk >= 2 && !tc::mbar_wait(&acc_empty[b], ((chunk >> 1) - 1) & 1u, abort_flag, &g_batched_status)) break;
+            tc::fence_after_sync();
+            const uint32_t d = tmem + (uint32_t)(b * TBN);
+            const int last = min(nkb, (c + 1) * TCHUNK);
+            for (int first = 1; it < last; ++it, ++ring, first = 0) {
+              const int s = ring % TSTAGES;
+              if (!tc::mbar_wait(&full[s], (ring / TSTAGES) & 1u, abort_flag, &g_batched_status)) break;
+              tc::fence_after_sync();
+              const uint32_t base = smem_u32(smem + s * TSTAGE);
+#pragma unroll
+              for (int kk = 0; kk < TBK / 16; ++kk) {
+                const uint64_t ahi = tc::desc_sw128(base + kk * 32);
+                const uint64_t alo = tc::desc_sw128(base + TA_BYTES + kk * 32);
+                const uint64_t bhi = tc::desc_sw128(base + 2 * TA_BYTES + kk * 32);
+                const uint64_t blo = tc::desc_sw128(base + 2 * TA_BYTES + TB_BYTES + kk * 32);
+                tc::mma_f16(d, ahi, bhi, idesc, (first && kk == 0) ? 0u : 1u);
+                tc::mma_f16(d, ahi, blo, idesc, 1);
+                tc::mma_f16(d, alo, bhi, idesc, 1);
+              }
+              tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(&acc_full[b]);
+          }
+        }
+      } else {
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        float sum[TBN / 2];
+#pragma unroll
+        for (int e = 0; e < TBN / 2; ++e) sum[e] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c, ++chunk) {
+          const int b = chunk & 1;
+          if (ok) ok = tc::mbar_wait(&acc_full[b], (chunk >> 1) & 1u, abort_flag, &g_batched_status);
+          tc::fence_after_sync();
+#pragma unroll
+          for (int cc = 0; cc < TBN / 2; cc += 16) {
+            uint32_t r[16];
+            tc::tmem_ld_32x32b_x16(tmem + lane_base + (uint32_t)(b * TBN + half * (TBN / 2) + cc), r);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sum[cc + e] = __fadd_rn(sum[cc + e], __uint_as_float(r[e]));
+          }
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+        }
+        float* C = static_cast<float*>(T.C[p]);
+        const int64_t row = i0 + q * 32 + lane;
+        if (row < m) {
+          const int64_t c0 = j0 + half * (TBN / 2);
+#pragma unroll
+          for (int e = 0; e < TBN / 2; ++e)
+            if (c0 + e < n) C[row * n + c0 + e] = ok ? sum[e] : 0.f;
+        }
+      }
+    } else if (warp >= 2) {
+      // ------------------------------------------------ (min,+) CUDA-core tile
+      const int tiles_n = (int)((n + MPN - 1) / MPN);
+      const int64_t i0 = (int64_t)(local / tiles_n) * 128, j0 = (int64_t)(local % tiles_n) * MPN;
+      const int32_t* A = static_cast<const int32_t*>(T.A[p]);
+      const int32_t* B = static_cast<const int32_t*>(T.B[p]);
+      int32_t* C = static_cast<int32_t*>(T.C[p]);
+      const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
+      const int tid = threadIdx.x - 64;
+      if (__ldcg(&violation[p]) == 0) {
+        mp::minplus16_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, i0, j0, (int64_t)0, k, vec, tid,
+                           reinterpret_cast<uint32_t*>(smem), mp::SyncNamed256());
+      } else {
+        minplus32_tile_pair(A, B, C, m, n, k, i0, j0, vec, tid, reinterpret_cast<int32_t*>(smem));
+      }
+    }
+    __syncthreads();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, BTMEM_COLS);
+}
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct BatchPlan {
+  BatchTable T;
+  int64_t KP = 0, rows_a = 0, rows_b = 0;
+  int64_t off_viol = 256, off_ahi = 0, off_alo = 0, off_bhi = 0, off_blo = 0, total = 0;
+};
+
+int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
+  if (count < 0 || count > kMaxBatch || (count > 0 && !probs)) return MM_ERR_ARG;
+  BatchTable& T = P->T;
+  memset(&T, 0, sizeof(T));
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  for (int i = 0; i < count; ++i) {
+    const mm_problem_t& q = probs[i];
+    if (q.semiring != MM_SR_PLUS_TIMES_F32 && q.semiring != MM_SR_MIN_PLUS_I32) return MM_ERR_UNSUPPORTED;
+    if (q.levels != 0) return MM_ERR_UNSUPPORTED;
+    if (q.m < 0 || q.n < 0 || q.k < 0 || q.m > (1 << 20) || q.n > (1 << 20) || q.k > (1 << 20))
+      return MM_ERR_SHAPE;
+    if (q.m > 0 && q.n > 0 && (!q.C || (q.k > 0 && (!q.A || !q.B)))) return MM_ERR_ARG;
+    if (!aligned16(q.C) || !aligned16(q.A) || !aligned16(q.B)) return MM_ERR_ALIGN;
+  }
+  // longest first (cost 2 m n k), ties by index for determinism
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const double ca = (double)probs[a].m * probs[a].n * (double)std::max<int64_t>(probs[a].k, 1);
+    const double cb = (double)probs[b].m * probs[b].n * (double)std::max<int64_t>(probs[b].k, 1);
+    return ca > cb;
+  });
+  int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    const mm_problem_t& q = probs[order[i]];
+    T.kind[i] = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : 1;
+    T.m[i] = (int)q.m;
+    T.n[i] = (int)q.n;
+    T.k[i] = (int)q.k;
+    T.A[i] = q.A;
+    T.B[i] = q.B;
+    T.C[i] = q.C;
+    T.tile_start[i] = (int)tiles;
+    const int64_t bn = T.kind[i] == 0 ? TBN : MPN;
+    if (q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + bn - 1) / bn);
+    if (T.kind[i] == 0) {
+      T.row0a[i] = (int)ra;
+      T.row0b[i] = (int)rb;
+      ra += q.m;
+      rb += q.n;
+      kp_max = std::max<int64_t>(kp_max, align_up(q.k > 0 ? q.k : 1, TBK));
+    }
+  }
+  if (tiles > (int64_t)1 << 30 || ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30) return MM_ERR_SHAPE;
+  T.tile_start[count] = (int)tiles;
+  T.count = count;
+  T.total_tiles = (int)tiles;
+  P->KP = kp_max;
+  P->rows_a = ra;
+  P->rows_b = rb;
+  P->off_ahi = align_up(256 + 4 * kMaxBatch, 1024);
+  P->off_alo = P->off_ahi + align_up(ra * kp_max * 2, 1024);
+  P->off_bhi = P->off_alo + align_up(ra * kp_max * 2, 1024);
+  P->off_blo = P->off_bhi + align_up(rb * kp_max * 2, 1024);
+  P->total = P->off_blo + align_up(rb * kp_max * 2, 1024);
+  return MM_OK;
+}
+
+}  // namespace
+
+int read_batched_status(int* status) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_batched_status, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_batched_status, &zero, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
+  *status = v;
+  return MM_OK;
+}
+
+}  // namespace mmsr
+
+using namespace mmsr;
+
+extern "C" size_t mm_batched_query(int count, const mm_problem_t* problems) {
+  BatchPlan local;  // planning is host-only and cheap
+  if (make_plan(count, problems, &local) != MM_OK) return 0;
+  return (size_t)local.total;
+}
+
+extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  BatchPlan P;
+  int rc = make_plan(count, problems, &P);
+  if (rc != MM_OK) return rc;
+  if (count == 0 || P.T.total_tiles == 0) return MM_OK;
+  if (!workspace) return MM_ERR_ARG;
+  if (!aligned16(workspace)) return MM_ERR_ALIGN;
+  if ((size_t)P.total > workspace_bytes) return MM_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* w = static_cast<uint8_t*>(workspace);
+  int* counter = reinterpret_cast<int*>(w);
+  int* violation = reinterpret_cast<int*>(w + P.off_viol);
+  auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + P.off_ahi);
+  auto* alo = reinterpret_cast<__nv_bfloat16*>(w + P.off_alo);
+  auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + P.off_bhi);
+  auto* blo = reinterpret_cast<__nv_bfloat16*>(w + P.off_blo);
+  MMSR_TRY_STATUS(cudaMemsetAsync(w, 0, P.off_viol + 4 * kMaxBatch, st));
+  {
+    TraceScope tr(kTrSplitBf16, st);
+    batched_split_kernel<<<dim3(16, (unsigned)count), 256, 0, st>>>(P.T, P.KP, ahi, alo, bhi, blo);
+    batched_range_kernel<<<dim3(8, (unsigned)count), 256, 0, st>>>(P.T, violation);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  const int64_t ra = std::max<int64_t>(P.rows_a, 1), rb = std::max<int64_t>(P.rows_b, 1);
+  const int64_t kp = std::max<int64_t>(P.KP, TBK);
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&ta_hi, ahi, ra, kp, kp, TBM, true));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&ta_lo, alo, ra, kp, kp, TBM, true));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_hi, bhi, rb, kp, kp, TBN, true));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_lo, blo, rb, kp, kp, TBN, true));
+  static bool configured = false;
+  if (!configured) {
+    MMSR_TRY_STATUS(
+        cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BSMEM));
+    configured = true;
+  }
+  int dev = 0, sms = kNumSMs;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(sms, P.T.total_tiles);
+  {
+    TraceScope tr(kTrBatched, st);
+    batched_kernel<<<grid, kBThreads, BSMEM, st>>>(P.T, ta_hi, ta_lo, tb_hi, tb_lo, counter, violation);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  return MM_OK;
+}

@@ -18,6 +18,15 @@ constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (queried at run time wh
     if (err_ != cudaSuccess) return err_;                     \
   } while (0)
 
+// Report a failed CUDA call on stderr (where it failed and why) and map it to
+// MM_ERR_CUDA.
+int report_cuda(cudaError_t e, const char* where);
+#define MMSR_TRY_STATUS(expr)                                            \
+  do {                                                                   \
+    cudaError_t err_ = (expr);                                           \
+    if (err_ != cudaSuccess) return ::mmsr::report_cuda(err_, #expr);    \
+  } while (0)
+
 // ---------------------------------------------------------------- cp.async
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -40,7 +49,7 @@ __host__ __device__ inline bool aligned16(const void* p) {
 enum TraceKernel {
   kTrMinplusLeaf = 0, kTrMinReduce, kTrDfmaLeaf, kTrSumReduceF64, kTrSplitBf16, kTrTcBf16x3,
   kTrSumReduceF32, kTrSplitF64Slices, kTrTcF64Acc, kTrStrassenCombine, kTrStrassenPost,
-  kTrBatched, kTrOrAndLeaf, kTrOrReduce, kTrMinplus16Leaf, kTrRangeScan, kTraceKernels
+  kTrBatched, kTrOrAndLeaf, kTrOrReduce, kTrMinplus16Leaf, kTrRangeScan, kTrOrPack, kTraceKernels
 };
 // RAII: records a start event now and an end event at scope exit, on `st`,
 // when tracing is enabled; otherwise does nothing.

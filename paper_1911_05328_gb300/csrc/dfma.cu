@@ -147,6 +147,45 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
+// Small-tile variant for products whose 64 x 64 grid would leave most SMs
+// idle (n = 256 gives 16 CTAs): a 16 x 16 tile per CTA, one output per
+// thread, k staged through shared memory in blocks of 32.
+constexpr int SBM = 16, SBK = 32;
+
+__global__ void __launch_bounds__(256)
+    dfma_small_kernel(int64_t m, int64_t n, int64_t k, const double* __restrict__ A,
+                      const double* __restrict__ B, double* __restrict__ C, double* __restrict__ W,
+                      int kb_per_slice) {
+  __shared__ double As[SBM][SBK + 1];
+  __shared__ double Bs[SBK][SBM + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * SBM, j0 = (int64_t)blockIdx.x * SBM;
+  const int z = blockIdx.z;
+  // slices are counted in the 16-wide k-blocks of the 64 x 64 leaf
+  const int64_t kbeg = (int64_t)z * kb_per_slice * BK;
+  const int64_t kend = min(k, kbeg + (int64_t)kb_per_slice * BK);
+  double acc = 0.0;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += SBK) {
+    // 512 elements of each operand block, two per thread
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int ar = e >> 5, ac = e & 31;   // A block 16 x 32
+      const int br = e >> 4, bc = e & 15;   // B block 32 x 16
+      const int64_t ga = i0 + ar, gk = k0 + ac;
+      As[ar][ac] = (ga < m && gk < kend) ? A[ga * k + gk] : 0.0;
+      const int64_t gkb = k0 + br, gb = j0 + bc;
+      Bs[br][bc] = (gkb < kend && gb < n) ? B[gkb * n + gb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < SBK; ++t) acc = fma(As[ty][t], Bs[t][tx], acc);
+    __syncthreads();
+  }
+  const int64_t gi = i0 + ty, gj = j0 + tx;
+  if (gi < m && gj < n) ((z == 0) ? C : W + (int64_t)(z - 1) * m * n)[gi * n + gj] = acc;
+}
+
 __global__ void __launch_bounds__(256) sum_reduce_f64_kernel(int64_t count, double* __restrict__ C,
                                                              const double* __restrict__ W,
                                                              int parts, bool vec) {
@@ -189,6 +228,12 @@ cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, c
                    (W == nullptr || aligned16(W));
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
   TraceScope tr(kTrDfmaLeaf, st);
+  if ((int64_t)grid.x * grid.y * s < 2 * kNumSMs) {
+    // too few 64 x 64 tiles to occupy the GPU: 16 x 16 tiles instead
+    dim3 sg((unsigned)((n + SBM - 1) / SBM), (unsigned)((m + SBM - 1) / SBM), (unsigned)s);
+    dfma_small_kernel<<<sg, 256, 0, st>>>(m, n, k, A, B, C, W, kb_per_slice);
+    return cudaGetLastError();
+  }
   dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec, s, 0, 0, 0);
   return cudaGetLastError();
 }

@@ -33,6 +33,23 @@ int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, flo
             size_t ws_bytes, cudaStream_t st);
 int read_tc_status(int* status);
 
+// boolean (or, and) semiring on bit-packed operands
+int plan_orand(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
+int run_orand(int64_t m, int64_t n, int64_t k, const uint8_t* A, const uint8_t* B, uint8_t* C,
+              void* ws, size_t ws_bytes, cudaStream_t st);
+
+// FP64-accuracy mode: six 7-bit digit slices per operand on tcgen05
+int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
+int run_f64acc(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
+               void* ws, size_t ws_bytes, cudaStream_t st);
+int read_f64acc_status(int* status);
+// `batches` stacked FP64-accuracy products (Strassen leaves): A is batches x
+// m x k, B batches x k x n, C batches x m x n, all contiguous.
+size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches);
+int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, int64_t n, int64_t k,
+                       int batches, void* ws, cudaStream_t st);
+int read_batched_status(int* status);
+
 // batched leaves (independent products on stacked operands)
 cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
                                   const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,

@@ -1,0 +1,199 @@
+// orand.cu -- boolean (or, and) semiring: C[i][j] = OR_t (A[i][t] AND B[t][j]).
+//
+// Operands are bit-packed along k into the workspace (A as m x KW words,
+// B transposed as n x KW words, KW = ceil(k / 32), bit t % 32 of word t / 32
+// set iff the entry is nonzero), so one 32-bit AND/OR covers 32 terms of the
+// (+)-sum.  The leaf is the paper's base-kernel (Section 3) on this semiring:
+// a 128 x 128 CTA tile, 256 threads with 8 x 8 register accumulators, words
+// staged through shared memory, k-serial within a slice (Fig. mm-n2).  Split-K
+// slices write byte partials that an OR folds into C (the madd of Fig. mm-n3).
+#include <string.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mmsr {
+namespace {
+
+constexpr int OBM = 128, OBN = 128, OBW = 32;  // tile rows, cols, words per stage (1024 k)
+constexpr int OLD = OBW + 1;                   // padded smem row (words)
+
+__global__ void __launch_bounds__(256) pack_rows_kernel(const uint8_t* __restrict__ A, int64_t m,
+                                                        int64_t k, int64_t KW,
+                                                        uint32_t* __restrict__ P) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * KW;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / KW, w = e - i * KW;
+    uint32_t word = 0;
+    const int64_t t0 = w * 32;
+    for (int b = 0; b < 32; ++b) {
+      const int64_t t = t0 + b;
+      if (t < k && A[i * k + t]) word |= 1u << b;
+    }
+    P[e] = word;
+  }
+}
+
+// B (k x n) -> bits of B^T (n x KW); threads over columns read 32 rows each.
+__global__ void __launch_bounds__(256) pack_cols_kernel(const uint8_t* __restrict__ B, int64_t k,
+                                                        int64_t n, int64_t KW,
+                                                        uint32_t* __restrict__ P) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t w = blockIdx.y;
+  if (j >= n) return;
+  uint32_t word = 0;
+  const int64_t t0 = w * 32;
+  for (int b = 0; b < 32; ++b) {
+    const int64_t t = t0 + b;
+    if (t < k && B[t * n + j]) word |= 1u << b;
+  }
+  P[j * KW + w] = word;
+}
+
+__global__ void __launch_bounds__(256)
+    orand_leaf_kernel(int64_t m, int64_t n, int64_t KW, const uint32_t* __restrict__ PA,
+                      const uint32_t* __restrict__ PB, uint8_t* __restrict__ C,
+                      uint8_t* __restrict__ W, int words_per_slice) {
+  __shared__ uint32_t As[OBM][OLD];
+  __shared__ uint32_t Bs[OBN][OLD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * OBM, j0 = (int64_t)blockIdx.x * OBN;
+  const int z = blockIdx.z;
+  const int64_t wb = (int64_t)z * words_per_slice;
+  const int64_t we = min(KW, wb + words_per_slice);
+  uint32_t acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0u;
+  for (int64_t w0 = wb; w0 < we; w0 += OBW) {
+    // 128 rows x 32 words of each operand, 16 per thread
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q;
+      const int r = e >> 5, c = e & 31;
+      const int64_t gw = w0 + c;
+      const int64_t ga = i0 + r, gb = j0 + r;
+      As[r][c] = (ga < m && gw < we) ? PA[ga * KW + gw] : 0u;
+      Bs[r][c] = (gb < n && gw < we) ? PB[gb * KW + gw] : 0u;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < OBW; ++c) {
+      uint32_t a[8], b[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        a[i] = As[(i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4)][c];
+        b[i] = Bs[(i < 4) ? (tx * 4 + i) : (64 + tx * 4 + i - 4)][c];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] |= a[i] & b[j];
+    }
+    __syncthreads();
+  }
+  uint8_t* out = (z == 0) ? C : W + (int64_t)(z - 1) * m * n;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t gi = i0 + ((i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4));
+    if (gi >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t gj = j0 + ((j < 4) ? (tx * 4 + j) : (64 + tx * 4 + j - 4));
+      if (gj < n) out[gi * n + gj] = acc[i][j] ? 1 : 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) or_reduce_kernel(int64_t count, uint8_t* __restrict__ C,
+                                                        const uint8_t* __restrict__ W, int parts) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t c = C[e];
+    for (int p = 0; p < parts; ++p) c |= W[(int64_t)p * count + e];
+    C[e] = c;
+  }
+}
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+unsigned grid_for(int64_t work) {
+  int64_t b = (work + 255) / 256;
+  if (b > (int64_t)kNumSMs * 16) b = (int64_t)kNumSMs * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+struct OrLayout {
+  int64_t KW, off_b, off_part, min_bytes;
+};
+
+OrLayout or_layout(int64_t m, int64_t n, int64_t k) {
+  OrLayout L;
+  L.KW = (k + 31) / 32;
+  L.off_b = align_up(m * L.KW * 4, 1024);
+  L.off_part = L.off_b + align_up(n * L.KW * 4, 1024);
+  L.min_bytes = L.off_part;
+  return L;
+}
+
+}  // namespace
+
+int plan_orand(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
+  memset(p, 0, sizeof(*p));
+  const OrLayout L = or_layout(m, n, k);
+  p->tile_m = OBM;
+  p->tile_n = OBN;
+  p->tile_k = OBW * 32;
+  p->kernel = 4;
+  p->workspace_min = L.min_bytes;
+  if (budget < (size_t)L.min_bytes) {
+    p->split_k = 1;
+    p->workspace_used = L.min_bytes;
+    return MM_OK;
+  }
+  int s = 1, kbs = 0;
+  int64_t used = 0;
+  // k-blocks of OBW words (1024 terms); partials are one byte per output
+  split_plan(m, n, L.KW * 32, OBW * 32, 1, budget - (size_t)L.min_bytes, &s, &kbs, &used);
+  p->split_k = s;
+  p->workspace_used = L.min_bytes + used;
+  return MM_OK;
+}
+
+int run_orand(int64_t m, int64_t n, int64_t k, const uint8_t* A, const uint8_t* B, uint8_t* C,
+              void* ws, size_t ws_bytes, cudaStream_t st) {
+  mm_plan_t p;
+  plan_orand(m, n, k, ws_bytes, &p);
+  if ((size_t)p.workspace_min > ws_bytes) return MM_ERR_WORKSPACE;
+  const OrLayout L = or_layout(m, n, k);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  uint32_t* PA = reinterpret_cast<uint32_t*>(w);
+  uint32_t* PB = reinterpret_cast<uint32_t*>(w + L.off_b);
+  uint8_t* part = p.split_k > 1 ? w + L.off_part : nullptr;
+  const int s = p.split_k;
+  const int64_t kb_total = (L.KW + OBW - 1) / OBW;
+  const int words_per_slice = (int)(((kb_total + s - 1) / s) * OBW);
+  {
+    TraceScope tr(kTrOrPack, st);
+    if (L.KW > 0) {
+      pack_rows_kernel<<<grid_for(m * L.KW), 256, 0, st>>>(A, m, k, L.KW, PA);
+      pack_cols_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)L.KW), 256, 0, st>>>(B, k, n, L.KW, PB);
+    }
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  {
+    TraceScope tr(kTrOrAndLeaf, st);
+    dim3 grid((unsigned)((n + OBN - 1) / OBN), (unsigned)((m + OBM - 1) / OBM), (unsigned)s);
+    orand_leaf_kernel<<<grid, 256, 0, st>>>(m, n, L.KW, PA, PB, C, part, words_per_slice > 0 ? words_per_slice : OBW);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  if (s > 1) {
+    TraceScope tr(kTrOrReduce, st);
+    or_reduce_kernel<<<grid_for(m * n), 256, 0, st>>>(m * n, C, part, s - 1);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  return MM_OK;
+}
+
+}  // namespace mmsr

@@ -215,7 +215,7 @@ int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct StrassenLayout {
   int64_t pp_bytes;   // each of the two ping-pong stack buffers
-  int64_t off_pp1, off_ahi, off_alo, off_bhi, off_blo, off_p, total;
+  int64_t off_pp1, off_ahi, off_alo, off_bhi, off_blo, off_p, off_leafws, total;
   int64_t mL, nL, kL, KpL, leaves;
 };
 
@@ -262,6 +262,9 @@ StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
   }
   s.off_p = off;
   off += align_up(s.leaves * s.mL * s.nL * esz, 1024);
+  s.off_leafws = off;  // FP64-accuracy leaves: digit slices and exponents
+  if (sr == MM_SR_PLUS_TIMES_F64ACC)
+    off += align_up((int64_t)f64acc_batched_bytes(s.mL, s.nL, s.kL, (int)s.leaves), 1024);
   s.total = off;
   return s;
 }
@@ -344,14 +347,15 @@ void strassen_tables(int variant, int8_t* alpha, int8_t* beta, int8_t* gamma) {
 
 int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
   memset(p, 0, sizeof(*p));
-  if (sr != MM_SR_PLUS_TIMES_F32 && sr != MM_SR_PLUS_TIMES_F64) return MM_ERR_UNSUPPORTED;
+  if (sr != MM_SR_PLUS_TIMES_F32 && sr != MM_SR_PLUS_TIMES_F64 && sr != MM_SR_PLUS_TIMES_F64ACC)
+    return MM_ERR_UNSUPPORTED;
   const StrassenLayout S = strassen_layout(levels, sr, m, n, k);
   p->levels = levels;
   p->split_k = 1;
-  p->tile_m = 128;
+  p->tile_m = sr == MM_SR_PLUS_TIMES_F64 ? 64 : 128;
   p->tile_n = sr == MM_SR_PLUS_TIMES_F32 ? 256 : 64;
-  p->tile_k = sr == MM_SR_PLUS_TIMES_F32 ? 64 : 16;
-  p->kernel = sr == MM_SR_PLUS_TIMES_F32 ? 2 : 0;
+  p->tile_k = sr == MM_SR_PLUS_TIMES_F32 ? 64 : (sr == MM_SR_PLUS_TIMES_F64 ? 16 : 32);
+  p->kernel = sr == MM_SR_PLUS_TIMES_F32 ? 2 : (sr == MM_SR_PLUS_TIMES_F64 ? 0 : 3);
   p->workspace_min = S.total;
   p->workspace_used = S.total;
   (void)budget;
@@ -360,7 +364,8 @@ int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t bu
 
 int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,
                  const void* B, void* C, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (sr != MM_SR_PLUS_TIMES_F32 && sr != MM_SR_PLUS_TIMES_F64) return MM_ERR_UNSUPPORTED;
+  if (sr != MM_SR_PLUS_TIMES_F32 && sr != MM_SR_PLUS_TIMES_F64 && sr != MM_SR_PLUS_TIMES_F64ACC)
+    return MM_ERR_UNSUPPORTED;
   const StrassenLayout S = strassen_layout(levels, sr, m, n, k);
   if ((size_t)S.total > ws_bytes) return MM_ERR_WORKSPACE;
   uint8_t* w = static_cast<uint8_t*>(ws);
@@ -392,7 +397,14 @@ int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t 
       if (e == cudaSuccess)
         e = expand_f64(levels, variant, 1, static_cast<const double*>(B), k, n, w, S, lb, st);
     }
-    if (e == cudaSuccess) e = launch_dfma_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, st);
+    if (e == cudaSuccess) {
+      if (sr == MM_SR_PLUS_TIMES_F64ACC) {
+        const int rc = run_f64acc_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, w + S.off_leafws, st);
+        if (rc != MM_OK) return rc;
+      } else {
+        e = launch_dfma_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, st);
+      }
+    }
     if (e == cudaSuccess) {
       TraceScope tr(kTrStrassenPost, st);
       e = fold<double>(levels, variant, P, m, n, w, S, static_cast<double*>(C), false, st);

@@ -9,6 +9,8 @@ namespace mmsr {
 int plan_extended(int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
   switch (sr) {
     case MM_SR_PLUS_TIMES_F32: return plan_f32(m, n, k, budget, p);
+    case MM_SR_PLUS_TIMES_F64ACC: return plan_f64acc(m, n, k, budget, p);
+    case MM_SR_OR_AND_U8: return plan_orand(m, n, k, budget, p);
     default: memset(p, 0, sizeof(*p)); return MM_ERR_UNSUPPORTED;
   }
 }
@@ -19,6 +21,12 @@ int run_extended(int sr, int64_t m, int64_t n, int64_t k, const void* A, const v
     case MM_SR_PLUS_TIMES_F32:
       return run_f32(m, n, k, static_cast<const float*>(A), static_cast<const float*>(B),
                      static_cast<float*>(C), ws, ws_bytes, st);
+    case MM_SR_OR_AND_U8:
+      return run_orand(m, n, k, static_cast<const uint8_t*>(A), static_cast<const uint8_t*>(B),
+                       static_cast<uint8_t*>(C), ws, ws_bytes, st);
+    case MM_SR_PLUS_TIMES_F64ACC:
+      return run_f64acc(m, n, k, static_cast<const double*>(A), static_cast<const double*>(B),
+                        static_cast<double*>(C), ws, ws_bytes, st);
     default: return MM_ERR_UNSUPPORTED;
   }
 }
@@ -26,15 +34,13 @@ int run_extended(int sr, int64_t m, int64_t n, int64_t k, const void* A, const v
 
 int read_device_status(cudaStream_t st, int* status) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return MM_ERR_CUDA;
-  int v = MM_OK;
-  if (read_tc_status(&v) != MM_OK) return MM_ERR_CUDA;
-  *status = v;
+  int v[3] = {MM_OK, MM_OK, MM_OK};
+  if (read_tc_status(&v[0]) != MM_OK) return MM_ERR_CUDA;
+  if (read_f64acc_status(&v[1]) != MM_OK) return MM_ERR_CUDA;
+  if (read_batched_status(&v[2]) != MM_OK) return MM_ERR_CUDA;
+  *status = v[0] != MM_OK ? v[0] : (v[1] != MM_OK ? v[1] : v[2]);
   return MM_OK;
 }
 
 }  // namespace mmsr
 
-extern "C" {
-int mm_batched(int, const mm_problem_t*, void*, size_t, void*) { return MM_ERR_UNSUPPORTED; }
-size_t mm_batched_query(int, const mm_problem_t*) { return 0; }
-}

@@ -44,16 +44,17 @@ static EncodeTiledFn get_encode() {
 }
 
 cudaError_t make_tmap_2d_16bit(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
-                               int64_t ld, int box_rows, bool bf16) {
+                               int64_t ld, int box_rows, bool bf16, int box_cols) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1u, 1u};
   CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __res
 // other, finished chunk into FP32 registers with round-to-nearest adds.  The
 // chain inside TMEM is then at most CHUNK*BK/16*3 MMAs long, whatever k is.
 constexpr int kDrainWarps = 8;
+constexpr int kGroupM = 16;  // tile rows per rasterisation band
 constexpr int kTcThreads = 64 + 32 * kDrainWarps;
 
 template <int BN, int STAGES>
@@ -162,7 +164,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  // Grouped rasterisation: consecutive CTAs walk a band of kGroupM tile rows
+  // column by column, so a wave shares its A and B panels through L2 instead
+  // of streaming all of B once per band of rows.
+  int64_t i0, j0;
+  {
+    const int tiles_n = gridDim.x, tiles_m = gridDim.y;
+    const int pid = blockIdx.y * tiles_n + blockIdx.x;
+    const int band = pid / (kGroupM * tiles_n);
+    const int first_m = band * kGroupM;
+    const int rows = min(kGroupM, tiles_m - first_m);
+    const int in_band = pid - band * kGroupM * tiles_n;
+    i0 = (int64_t)(first_m + in_band % rows) * BM;
+    j0 = (int64_t)(in_band / rows) * BN;
+  }
   // blockIdx.z = batch * slices + k-slice; a batch is one independent product
   // whose operands sit at row offset batch * {a,b}_batch_rows of the stacks
   const int z = blockIdx.z % slices;

@@ -1,0 +1,431 @@
+// tc_f64acc.cu -- FP64-accuracy (+,x) from 16-bit tensor-core products.
+//
+// Each row of A (column of B) is scaled by a power of two 2^-E so that its
+// entries lie in (-1, 1), and every scaled entry is cut into seven signed
+// digits of 7 bits:  a' = sum_{s=0..6} d_s 2^-7(s+1) + r,  |d_0| <= 128,
+// |d_s| <= 64 (s >= 1), |r| <= 2^-50.  Digits are small integers, exact in
+// bf16, and digit products are exact in the FP32 tensor-core accumulator.
+// The product groups by digit order g = s + u:
+//
+//   a'b' ~ sum_{g=0..6} 2^-7(g+2) G_g,   G_g = sum_{s+u=g} sum_t d_s(i,t) d'_u(t,j)
+//
+// (28 slice products; the dropped orders g >= 7 and the residuals are below
+// 2^-49 of the scaled magnitudes, which leaves room for the error growth of
+// Strassen levels above these leaves).  Each G_g is an integer: it
+// accumulates in its own TMEM accumulator over chunks of 64 k, where every
+// partial sum is an integer of magnitude < 2^21.2 (so the FP32 accumulation
+// is exact whatever its rounding), and drain warps move each chunk into two
+// int64 registers per output (hi = G0 2^14 + G1 2^7 + G2, lo = G3 2^21 +
+// G4 2^14 + G5 2^7 + G6).  The epilogue forms 2^(E_i+F_j) (hi 2^-28 +
+// lo 2^-56) in FP64.  FP64 arithmetic is used only for that final sum and
+// for split-K partials.
+//
+// Tile 128 x 64, k-blocks of 32 (64-byte swizzled rows), 2-stage TMA ring of
+// the 14 slice tiles, 7 x 64 TMEM columns, warp roles as in the FP32 mode.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace mmsr {
+namespace {
+
+__device__ int g_f64acc_status;
+
+constexpr int kSlices = 7, kDigitBits = 7, kGroups = 7;
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2, CHUNK = 2;  // CHUNK k-blocks per drain
+constexpr int kDrain = 8, kThreads = 64 + 32 * kDrain;
+constexpr uint32_t A_TILE = BM * BK * 2, B_TILE = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = kSlices * (A_TILE + B_TILE);
+constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+constexpr uint32_t TMEM_COLS = 512;  // 7 groups x 64 columns used
+
+// ----------------------------------------------------------- split kernels
+// Exponent E with max|x| < 2^E (0 for an all-zero line).
+__device__ __forceinline__ int line_exponent(double maxabs) {
+  if (!(maxabs > 0.0)) return 0;
+  int e;
+  frexp(maxabs, &e);  // maxabs = f 2^e, f in [0.5, 1)
+  return e;
+}
+
+// Row maxima of A (one warp per row), stored as the exponent E of the row.
+__global__ void __launch_bounds__(256) row_exponent_kernel(const double* __restrict__ A, int64_t m,
+                                                           int64_t k, int* __restrict__ E) {
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  double mx = 0.0;
+  for (int64_t t = lane; t < k; t += 32) mx = fmax(mx, fabs(A[row * k + t]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) E[row] = line_exponent(mx);
+}
+
+// Column maxima of B (k x n, batch blockIdx.z of a contiguous stack): each
+// thread scans 256 rows of one column and folds its maximum into Fmax with
+// an atomic max on the bit pattern (for non-negative doubles the unsigned
+// bit order is the numeric order; Fmax starts at +0.0).
+__global__ void __launch_bounds__(256) col_max_kernel(const double* __restrict__ B, int64_t k,
+                                                      int64_t n, unsigned long long* __restrict__ Fmax) {
+  B += (int64_t)blockIdx.z * k * n;
+  Fmax += (int64_t)blockIdx.z * n;
+  const int64_t col = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (col >= n) return;
+  const int64_t r0 = (int64_t)blockIdx.y * 256, r1 = min(k, r0 + 256);
+  double mx = 0.0;
+  for (int64_t t = r0; t < r1; ++t) mx = fmax(mx, fabs(B[t * n + col]));
+  if (mx > 0.0) atomicMax(&Fmax[col], (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void __launch_bounds__(256) col_exponent_kernel(const unsigned long long* __restrict__ Fmax,
+                                                           int64_t count, int* __restrict__ F) {
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (j < count) F[j] = line_exponent(__longlong_as_double((long long)Fmax[j]));
+}
+
+// Seven digits of x * 2^-E: one rounding of x * 2^(49-E) to an integer M
+// (|M| < 2^49, residual below 2^-50 of 2^E), then balanced base-128 digits
+// by integer arithmetic (FP64 throughput is the scarce resource here):
+// M = sum_s d_s 128^(6-s) with d_1..d_6 in [-64, 63] and |d_0| <= 128.
+__device__ __forceinline__ void digits7(double x, int E, __nv_bfloat16 (&d)[kSlices]) {
+  long long M = __double2ll_rn(ldexp(x, kDigitBits * kSlices - E));
+#pragma unroll
+  for (int s = kSlices - 1; s >= 1; --s) {
+    const int ds = (int)(((M + 64) & 127) - 64);
+    d[s] = __int2bfloat16_rn(ds);  // |ds| <= 64: exact
+    M = (M - ds) >> kDigitBits;    // exact: M - ds is a multiple of 128
+  }
+  d[0] = __int2bfloat16_rn((int)M);  // |M| <= 128 here: exact
+}
+
+// A (m x k) -> seven digit slices, slice s at S + s*m*Kp (row pitch Kp, zero pad).
+__global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restrict__ A, int64_t m,
+                                                          int64_t k, int64_t Kp,
+                                                          const int* __restrict__ E,
+                                                          __nv_bfloat16* __restrict__ S) {
+  const int64_t total = m * Kp;
+  const int64_t slice = m * Kp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / Kp, t = e - i * Kp;
+    __nv_bfloat16 d[kSlices];
+    digits7(t < k ? A[i * k + t] : 0.0, E[i], d);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) S[s * slice + e] = d[s];
+  }
+}
+
+// B (k x n, batch blockIdx.z of a contiguous stack of `batches`) -> seven
+// digit slices of B^T: slice s holds batches*n rows of pitch Kp, batch b at
+// rows [b*n, (b+1)*n).  Via a 32 x 32 shared tile.
+__global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restrict__ B, int64_t k,
+                                                          int64_t n, int64_t Kp,
+                                                          const int* __restrict__ F,
+                                                          __nv_bfloat16* __restrict__ S, int batches) {
+  __shared__ double tile[32][33];
+  const int64_t b = blockIdx.z;
+  B += b * k * n;
+  F += b * n;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t k0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int kk = ty + 8 * it;
+    const int64_t gk = k0 + kk, gn = n0 + tx;
+    tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.0;
+  }
+  __syncthreads();
+  const int64_t slice = (int64_t)batches * n * Kp;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int nn = ty + 8 * it;
+    const int64_t gn = n0 + nn, gk = k0 + tx;
+    if (gn >= n || gk >= Kp) continue;
+    __nv_bfloat16 d[kSlices];
+    digits7(tile[tx][nn], F[gn], d);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) S[s * slice + (b * n + gn) * Kp + gk] = d[s];
+  }
+}
+
+// ------------------------------------------------------------ GEMM kernel
+__device__ __forceinline__ int exact_int(uint32_t fbits) {
+  // fbits holds an integer-valued float of magnitude < 2^22; adding 1.5*2^23
+  // leaves the integer in the low mantissa bits exactly.
+  const float t = __uint_as_float(fbits) + 12582912.0f;
+  return (int)(__float_as_uint(t) - 0x4B400000u);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    f64acc_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+                       const int* __restrict__ E, const int* __restrict__ F, double* __restrict__ C,
+                       double* __restrict__ W, int64_t m, int64_t n, int64_t a_slice_rows,
+                       int64_t b_slice_rows, int kb_total, int kb_per_slice, int kslices) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = tc::align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  // blockIdx.z = batch * kslices + k-slice; batch b uses rows [b*m, (b+1)*m)
+  // of every A slice (and of E), rows [b*n, (b+1)*n) of every B^T slice
+  const int z = blockIdx.z % kslices;
+  const int batch = blockIdx.z / kslices;
+  const int64_t ra = (int64_t)batch * m, rb = (int64_t)batch * n;
+  const int kb_begin = z * kb_per_slice;
+  const int kb_end = min(kb_total, kb_begin + kb_per_slice);
+  const int nkb = kb_end > kb_begin ? kb_end - kb_begin : 0;
+  const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, kDrain);
+    *abort_flag = 0;
+    tc::mbar_init_fence();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::tma_prefetch(&tA);
+      tc::tma_prefetch(&tB);
+      for (int it = 0; it < nkb; ++it) {
+        const int s = it % STAGES;
+        const uint32_t round = (uint32_t)(it / STAGES);
+        if (it >= STAGES && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_f64acc_status)) break;
+        tc::mbar_expect_tx(&full[s], STAGE_BYTES);
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int kx = (kb_begin + it) * BK;
+#pragma unroll
+        for (int sl = 0; sl < kSlices; ++sl) {
+          tc::tma_load_2d(st + sl * A_TILE, &tA, &full[s], kx, (int)(sl * a_slice_rows + ra + i0));
+          tc::tma_load_2d(st + kSlices * A_TILE + sl * B_TILE, &tB, &full[s], kx,
+                          (int)(sl * b_slice_rows + rb + j0));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_f16(BM, BN, 1);
+      int it = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        if (c >= 1 && !tc::mbar_wait(acc_empty, (c - 1) & 1u, abort_flag, &g_f64acc_status)) break;
+        tc::fence_after_sync();
+        const int last = min(nkb, (c + 1) * CHUNK);
+        bool aborted = false;
+        for (int first = 1; it < last; ++it, first = 0) {
+          const int s = it % STAGES;
+          const uint32_t round = (uint32_t)(it / STAGES);
+          if (!tc::mbar_wait(&full[s], round & 1u, abort_flag, &g_f64acc_status)) { aborted = true; break; }
+          tc::fence_after_sync();
+          const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) {
+#pragma unroll
+              for (int sa = 0; sa <= g; ++sa) {
+                const int sb = g - sa;
+                const uint64_t ad = tc::desc_sw64(base + sa * A_TILE + kk * 32);
+                const uint64_t bd = tc::desc_sw64(base + kSlices * A_TILE + sb * B_TILE + kk * 32);
+                tc::mma_f16(tmem + (uint32_t)(g * BN), ad, bd, idesc,
+                            (first && kk == 0 && sa == 0) ? 0u : 1u);
+              }
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(acc_full);
+        if (aborted) break;
+      }
+    }
+  } else {
+    // drain warps: lane quarter q, column half h (32 of the 64 columns)
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    long long hi[32], lo[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) hi[e] = lo[e] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      ok = tc::mbar_wait(acc_full, c & 1u, abort_flag, &g_f64acc_status);
+      tc::fence_after_sync();
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) {
+        const long long wgt = g < 3 ? (1ll << (7 * (2 - g))) : (1ll << (7 * (6 - g)));
+#pragma unroll
+        for (int half16 = 0; half16 < 2; ++half16) {
+          uint32_t r[16];
+          tc::tmem_ld_32x32b_x16(tmem + lane_base + (uint32_t)(g * BN + h * 32 + half16 * 16), r);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const long long v = (long long)exact_int(r[e]) * wgt;
+            if (g < 3)
+              hi[half16 * 16 + e] += v;
+            else
+              lo[half16 * 16 + e] += v;
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty);
+    }
+    double* out = (z == 0) ? C + ra * n : W + (int64_t)(z - 1) * m * n;
+    const int64_t row = i0 + q * 32 + lane;
+    if (row < m) {
+      const int Ei = E[ra + row];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const int64_t col = j0 + h * 32 + e;
+        if (col >= n) break;
+        double v = ok ? ((double)hi[e] * 0x1p-28 + (double)lo[e] * 0x1p-56) : 0.0;
+        out[row * n + col] = ldexp(v, Ei + F[rb + col]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct F64AccLayout {
+  int64_t Kp, a_bytes, b_bytes, off_b, off_e, off_f, off_fmax, off_part, min_bytes;
+};
+
+F64AccLayout layout(int64_t m, int64_t n, int64_t k, int64_t batches = 1) {
+  F64AccLayout L;
+  L.Kp = align_up(k > 0 ? k : 1, BK);
+  L.a_bytes = align_up((int64_t)kSlices * batches * m * L.Kp * 2, 1024);
+  L.b_bytes = align_up((int64_t)kSlices * batches * n * L.Kp * 2, 1024);
+  L.off_b = L.a_bytes;
+  L.off_e = L.a_bytes + L.b_bytes;
+  L.off_f = L.off_e + align_up(batches * m * 4, 256);
+  L.off_fmax = L.off_f + align_up(batches * n * 4, 256);
+  L.off_part = L.off_fmax + align_up(batches * n * 8, 1024);
+  L.min_bytes = L.off_part;
+  return L;
+}
+
+unsigned grid_for(int64_t work, int per_sm = 16) {
+  int64_t b = (work + 255) / 256;
+  if (b > (int64_t)kNumSMs * per_sm) b = (int64_t)kNumSMs * per_sm;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
+  memset(p, 0, sizeof(*p));
+  const F64AccLayout L = layout(m, n, k);
+  p->tile_m = BM;
+  p->tile_n = BN;
+  p->tile_k = BK;
+  p->kernel = 3;
+  p->workspace_min = L.min_bytes;
+  if (budget < (size_t)L.min_bytes) {
+    p->split_k = 1;
+    p->workspace_used = L.min_bytes;
+    return MM_OK;
+  }
+  int s = 1, kbs = 0;
+  int64_t used = 0;
+  split_plan(m, n, L.Kp, BK, 8, budget - (size_t)L.min_bytes, &s, &kbs, &used);
+  p->split_k = s;
+  p->workspace_used = L.min_bytes + used;
+  return MM_OK;
+}
+
+// Digits, exponents and the tensor-core product for `batches` independent
+// products stacked contiguously (A: batches x m x k, B: batches x k x n,
+// C: batches x m x n), with `s` k-slices (s > 1 only when batches == 1).
+int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
+                uint8_t* w, const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
+  auto* SA = reinterpret_cast<__nv_bfloat16*>(w);
+  auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
+  int* E = reinterpret_cast<int*>(w + L.off_e);
+  int* F = reinterpret_cast<int*>(w + L.off_f);
+  const int64_t rows_a = (int64_t)batches * m;
+  {
+    TraceScope tr(kTrSplitF64Slices, st);
+    row_exponent_kernel<<<(unsigned)((rows_a + 7) / 8), 256, 0, st>>>(A, rows_a, k, E);
+    auto* Fmax = reinterpret_cast<unsigned long long*>(w + L.off_fmax);
+    MMSR_TRY_STATUS(cudaMemsetAsync(Fmax, 0, (size_t)batches * n * 8, st));
+    col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256, 0,
+                     st>>>(B, k, n, Fmax);
+    col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
+    digits_rows_kernel<<<grid_for(rows_a * L.Kp), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA);
+    dim3 g((unsigned)(L.Kp / 32), (unsigned)((n + 31) / 32), (unsigned)batches);
+    digits_cols_kernel<<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  CUtensorMap tA, tB;
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tA, SA, kSlices * rows_a, L.Kp, L.Kp, BM, true, BK));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tB, SB, kSlices * (int64_t)batches * n, L.Kp, L.Kp, BN, true, BK));
+  static bool configured = false;
+  if (!configured) {
+    MMSR_TRY_STATUS(cudaFuncSetAttribute(f64acc_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
+    configured = true;
+  }
+  const int kb_total = (int)(L.Kp / BK);
+  const int kbs = (kb_total + s - 1) / s;
+  {
+    TraceScope tr(kTrTcF64Acc, st);
+    dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)(s * batches));
+    f64acc_gemm_kernel<<<grid, kThreads, SMEM, st>>>(tA, tB, E, F, C, part, m, n, rows_a,
+                                                    (int64_t)batches * n, kb_total, kbs, s);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  if (s > 1) MMSR_TRY_STATUS(launch_sum_reduce_f64(m * n, C, part, s - 1, st));
+  return MM_OK;
+}
+
+int run_f64acc(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
+               void* ws, size_t ws_bytes, cudaStream_t st) {
+  mm_plan_t p;
+  plan_f64acc(m, n, k, ws_bytes, &p);
+  if ((size_t)p.workspace_min > ws_bytes) return MM_ERR_WORKSPACE;
+  const F64AccLayout L = layout(m, n, k);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  double* part = p.split_k > 1 ? reinterpret_cast<double*>(w + L.off_part) : nullptr;
+  return f64acc_core(m, n, k, A, B, C, w, L, 1, p.split_k, part, st);
+}
+
+size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches) {
+  return (size_t)layout(m, n, k, batches).min_bytes;
+}
+
+int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, int64_t n, int64_t k,
+                       int batches, void* ws, cudaStream_t st) {
+  const F64AccLayout L = layout(m, n, k, batches);
+  return f64acc_core(m, n, k, A, B, C, static_cast<uint8_t*>(ws), L, batches, 1, nullptr, st);
+}
+
+int read_f64acc_status(int* status) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_f64acc_status, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_f64acc_status, &zero, sizeof(int)) != cudaSuccess) return MM_ERR_CUDA;
+  *status = v;
+  return MM_OK;
+}
+
+}  // namespace mmsr

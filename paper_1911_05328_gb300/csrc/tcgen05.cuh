@@ -106,6 +106,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
          ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// Same, 64-byte swizzle: rows of 64 B, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
+         ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
 // Instruction descriptor, kind::f16: D fp32, A/B of `ab_fmt` (0 = f16,
 // 1 = bf16), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, uint32_t ab_fmt) {
@@ -142,6 +147,16 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
+// Same shape, 16 columns.
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -157,6 +172,6 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 // Host: encode a 2-D bf16/f16 K-major tensor map (rows x cols, row pitch
 // `ld` elements) with a (64 x box_rows) box and 128-byte swizzle.
 cudaError_t make_tmap_2d_16bit(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
-                               int64_t ld, int box_rows, bool bf16);
+                               int64_t ld, int box_rows, bool bf16, int box_cols = 64);
 
 }  // namespace mmsr

@@ -1,0 +1,109 @@
+"""mm_batched: mixed FP32 (+,x) and (min,+) problems of uneven shapes in one
+persistent launch, each checked against the oracle (bit-exact for (min,+)
+and for integer-valued FP32 inputs, rel. Frobenius <= 1e-5 otherwise)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_05328_gb300 import inputs, mmsr
+
+from gpu_util import dev, empty, rel_fro
+
+pytestmark = pytest.mark.gpu
+F32, MP = mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_MIN_PLUS_I32
+
+
+def _launch(probs, capture=False):
+    """probs: list of inputs.Problem; returns the list of output arrays."""
+    import torch
+
+    dA = [dev(p.A) for p in probs]
+    dB = [dev(p.B) for p in probs]
+    dC = [empty((p.m, p.n), torch.float32 if p.semiring == F32 else torch.int32) for p in probs]
+    table = [(p.semiring, p.m, p.n, p.k, a, b, c) for p, a, b, c in zip(probs, dA, dB, dC)]
+    need = mmsr.mm_batched_query(table)
+    assert need > 0
+    ws = empty((need,), torch.uint8)
+    if capture:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            mmsr.mm_batched(table, ws, need, stream=s)  # warm-up (sets kernel attributes)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        for c in dC:
+            c.zero_()
+        with torch.cuda.graph(g):
+            mmsr.mm_batched(table, ws, need, stream=torch.cuda.current_stream())
+        for c in dC:
+            c.fill_(-1)
+        g.replay()
+    else:
+        mmsr.mm_batched(table, ws, need)
+    torch.cuda.synchronize()
+    assert mmsr.mm_last_device_status() == 0
+    return [c.cpu().numpy() for c in dC]
+
+
+def _check(probs, outs, exact_fp32=False):
+    for p, C in zip(probs, outs):
+        if p.semiring == MP:
+            np.testing.assert_array_equal(C, oracle.mm_minplus(p.A, p.B), err_msg=str((p.m, p.n, p.k)))
+        elif exact_fp32:
+            np.testing.assert_array_equal(C, oracle.mm_f64(p.A, p.B).astype(np.float32))
+        else:
+            ref = oracle.mm_f64(p.A, p.B)
+            assert rel_fro(C, ref) <= 1e-5, (p.m, p.n, p.k, rel_fro(C, ref))
+
+
+def _mixed(count, seed, lo=1, hi=300, integer=False):
+    rng = np.random.default_rng(seed)
+    dims = rng.integers(lo, hi + 1, size=(count, 3))
+    probs = inputs.batched_problems(count=count, seed=seed, dims=dims)
+    if integer:
+        for p in probs:
+            if p.semiring == F32:
+                p.A = rng.integers(-4, 5, size=p.A.shape).astype(np.float32)
+                p.B = rng.integers(-4, 5, size=p.B.shape).astype(np.float32)
+    return probs
+
+
+def test_small_mixed_batch_integer_exact():
+    probs = _mixed(24, seed=200, integer=True)
+    _check(probs, _launch(probs), exact_fp32=True)
+
+
+def test_small_mixed_batch_normal():
+    probs = _mixed(40, seed=201, lo=1, hi=700)
+    _check(probs, _launch(probs))
+
+
+def test_minplus_out_of_packed_range_in_batch():
+    probs = _mixed(10, seed=202, lo=50, hi=400)
+    for p in probs:
+        if p.semiring == MP:
+            p.A[0, 0] = 30000
+            p.A[p.m // 2, p.k - 1] = inputs.INF
+    _check(probs, _launch(probs))
+
+
+def test_graph_capture_replay():
+    probs = _mixed(16, seed=203, lo=30, hi=500)
+    _check(probs, _launch(probs, capture=True))
+
+
+def test_rejects_unsupported_semiring():
+    import torch
+
+    d = empty((8, 8), torch.float64)
+    rc = mmsr.mm_batched([(mmsr.MM_SR_PLUS_TIMES_F64, 8, 8, 8, d, d, d)], d, 64, check=False)
+    assert rc == mmsr.MM_ERR_UNSUPPORTED
+
+
+def test_workload_512_problems():
+    # 512 problems, m, n, k log-uniform in [64, 2048], 70% FP32 normal(0,1),
+    # 30% (min,+) integers in [0, 1000], seed 4
+    probs = inputs.batched_problems(count=512, seed=4)
+    assert sum(p.semiring == F32 for p in probs) == 358
+    _check(probs, _launch(probs))

@@ -1,0 +1,104 @@
+"""FP64-accuracy mode (+,x): six 7-bit digit slices per operand, 21 exact
+slice products on tcgen05, vs the FP64 oracle at 1e-12 relative Frobenius
+error.  Integer inputs pin the exactness of the chunked TMEM accumulation:
+their digits are exact integers and so is the whole product."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_05328_gb300 import inputs, mmsr
+
+from gpu_util import canary_intact, dev, empty, rel_fro, workspace
+
+pytestmark = pytest.mark.gpu
+SR = mmsr.MM_SR_PLUS_TIMES_F64ACC
+TOL = 1e-12
+
+
+def run(A, B, extra_parts=0):
+    import torch
+
+    m, k = A.shape
+    n = B.shape[1]
+    p0 = mmsr.mm_plan_query(SR, -1, m, n, k, 0)
+    budget = int(p0.workspace_min) + extra_parts * m * n * 8
+    ws = workspace(budget)
+    dC = empty((m, n), torch.float64)
+    mmsr.mm_semiring(SR, m, n, k, dev(A), dev(B), dC, ws, budget)
+    torch.cuda.synchronize()
+    assert canary_intact(ws, budget)
+    assert mmsr.mm_last_device_status() == 0
+    return dC.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 64, 32), (128, 64, 64), (200, 130, 300), (512, 384, 2048)])
+def test_integer_inputs_exact(m, n, k):
+    A, B = inputs.small_int(m, k, n, seed=90 + k, bound=100)
+    np.testing.assert_array_equal(run(A, B), oracle.mm_f64(A, B))
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 5, 3), (128, 64, 32), (129, 65, 33), (300, 200, 1000), (1024, 768, 4096)])
+def test_uniform_tolerance(m, n, k):
+    A, B = inputs.uniform_f64(m, k, n, seed=m + n + k)
+    err = rel_fro(run(A, B), oracle.mm_f64(A, B))
+    assert err <= TOL, err
+
+
+def test_row_and_column_scaling():
+    # rows of A and columns of B spanning 2^-300 .. 2^300: the per-line
+    # power-of-two scales must carry the exponent range exactly
+    rng = np.random.default_rng(91)
+    m, n, k = 256, 192, 512
+    A, B = inputs.uniform_f64(m, k, n, seed=92)
+    A *= np.exp2(rng.integers(-300, 300, size=(m, 1)).astype(np.float64))
+    B *= np.exp2(rng.integers(-300, 300, size=(1, n)).astype(np.float64))
+    C = run(A, B)
+    ref = oracle.mm_f64(A, B)
+    # compare row/column-normalised products (the scales make a plain
+    # Frobenius norm meaningless across 600 binades)
+    rs = np.abs(ref).max(axis=1, keepdims=True)
+    cs = np.abs(ref / rs).max(axis=0, keepdims=True)
+    assert rel_fro(C / rs / cs, ref / rs / cs) <= TOL
+
+
+@pytest.mark.parametrize("parts", [2, 5])
+def test_split_k(parts):
+    m, n, k = 256, 192, 4096
+    A, B = inputs.uniform_f64(m, k, n, seed=93)
+    assert rel_fro(run(A, B, extra_parts=parts), oracle.mm_f64(A, B)) <= TOL
+
+
+def test_zero_rows_and_columns():
+    A, B = inputs.uniform_f64(130, 70, 90, seed=94)
+    A[5] = 0.0
+    B[:, 7] = 0.0
+    C = run(A, B)
+    assert np.all(C[5] == 0.0) and np.all(C[:, 7] == 0.0)
+    assert rel_fro(C, oracle.mm_f64(A, B)) <= TOL
+
+
+def test_full_size_n16384_sampled_rows():
+    import torch
+
+    n = 16384
+    A, B = inputs.uniform_f64(n, n, n, seed=3)
+    rows = oracle.sample_rows(n)
+    ref = oracle.mm_f64(A, B, rows=rows)
+    C = run(A, B)
+    err = rel_fro(C[rows], ref)
+    print("f64acc n16384 rel_fro %.3e" % err)
+    assert err <= TOL, err
+    torch.cuda.empty_cache()
+
+
+def test_k_zero_writes_zero():
+    import torch
+
+    p = mmsr.mm_plan_query(SR, -1, 4, 6, 0, 0)
+    ws = empty((int(p.workspace_min),), torch.uint8)
+    dC = empty((4, 6), torch.float64)
+    dC.fill_(5.0)
+    mmsr.mm_semiring(SR, 4, 6, 0, empty((4, 1), torch.float64), empty((1, 6), torch.float64), dC, ws,
+                     int(p.workspace_min))
+    torch.cuda.synchronize()
+    assert np.all(dC.cpu().numpy() == 0.0)

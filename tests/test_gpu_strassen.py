@@ -121,3 +121,46 @@ def test_full_size_n16384_fp32_sampled_rows():
         assert err <= 1.5e-5 * 2.8 ** (L - 1), err
         del ws
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_f64acc_integer_inputs_exact(variant, L):
+    m, k, n = 256, 512, 320
+    A, B = inputs.small_int(m, k, n, seed=110 + L, bound=50)
+    C = run(L, variant, mmsr.MM_SR_PLUS_TIMES_F64ACC, A, B)
+    np.testing.assert_array_equal(C, oracle.mm_f64(A, B))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_f64acc_uniform_tolerance_every_level(variant, L):
+    # FP64-accuracy mode must meet 1e-12 at every level
+    m, k, n = 512, 1024, 384
+    A, B = inputs.uniform_f64(m, k, n, seed=3)
+    err = rel_fro(run(L, variant, mmsr.MM_SR_PLUS_TIMES_F64ACC, A, B), oracle.mm_f64(A, B))
+    print("f64acc strassen variant %d L %d rel_fro %.3e" % (variant, L, err))
+    assert err <= 1e-12, err
+
+
+def test_full_size_n16384_f64acc_sampled_rows():
+    import torch
+
+    n = 16384
+    A, B = inputs.uniform_f64(n, n, n, seed=3)
+    rows = oracle.sample_rows(n)
+    ref = oracle.mm_f64(A, B, rows=rows)
+    dA, dB = dev(A), dev(B)
+    del A, B
+    dC = empty((n, n), torch.float64)
+    for L in (1, 2, 3, 4):
+        p = mmsr.mm_plan_query(mmsr.MM_SR_PLUS_TIMES_F64ACC, L, n, n, n, 0)
+        ws = empty((int(p.workspace_min),), torch.uint8)
+        mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, mmsr.MM_SR_PLUS_TIMES_F64ACC, n, n, n, dA, dB, dC, ws,
+                         int(p.workspace_min))
+        torch.cuda.synchronize()
+        err = rel_fro(dC.cpu().numpy()[rows], ref)
+        print("n16384 f64acc winograd L %d rel_fro %.3e workspace %.2f n^2*8B" % (L, err, p.workspace_min / (n * n * 8)))
+        assert err <= 1e-12, err
+        del ws
+        torch.cuda.empty_cache()
