@@ -1,0 +1,160 @@
+"""Per-shape autotuner for the budget / split-K / Strassen-depth choices.
+
+The C ABI takes a workspace *budget*; the paper's point (Sections 3-4) is that
+more temporary space buys a shorter critical path, but on a GPU a larger
+split factor is not always faster (extra partial traffic, smaller tiles per
+CTA).  The tuner times the candidate plans a budget allows and remembers the
+fastest per shape bucket:
+
+* ``mm_semiring``: split factors s = 1 .. s_max, requested by handing the
+  library a smaller budget (``budget_for_split``);
+* ``mm_strassen``: Strassen depths L = 0 .. 4 whose workspace fits the budget
+  and whose shape divides by 2^L.
+
+Choices are cached in JSON (``MMSR_TUNE_CACHE``, default
+``~/.cache/mmsr_tune.json``) keyed by semiring, power-of-two shape bucket and
+budget bucket.  Timing uses CUDA events by default; any callable
+``timer(fn) -> ms`` can be injected (the CPU tests do).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+from . import mmsr
+
+_ACC_BYTES = {mmsr.MM_SR_PLUS_TIMES_F64: 8, mmsr.MM_SR_PLUS_TIMES_F32: 4, mmsr.MM_SR_PLUS_TIMES_F64ACC: 8,
+              mmsr.MM_SR_MIN_PLUS_I32: 4, mmsr.MM_SR_OR_AND_U8: 1}
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("MMSR_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "mmsr_tune.json"))
+
+
+def _bucket(x: int) -> int:
+    return 0 if x <= 0 else 1 << int(math.ceil(math.log2(x)))
+
+
+def key(op: str, semiring: int, m: int, n: int, k: int, budget: int) -> str:
+    return "%s/%d/%dx%dx%d/%d" % (op, semiring, _bucket(m), _bucket(n), _bucket(k), _bucket(budget))
+
+
+def load_cache(path=None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path=None) -> None:
+    path = path or cache_path()
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
+    tmp = path + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def budget_for_split(semiring: int, m: int, n: int, k: int, s: int) -> int:
+    """Smallest budget whose plan uses split factor s (for s the planner can reach)."""
+    base = int(mmsr.mm_plan_query(semiring, -1, m, n, k, 0).workspace_min)
+    return base + (s - 1) * m * n * _ACC_BYTES[semiring]
+
+
+def split_candidates(semiring: int, m: int, n: int, k: int, budget: int):
+    """Distinct split factors the budget allows, as (s, budget_to_pass)."""
+    smax = mmsr.mm_plan_query(semiring, -1, m, n, k, budget).split_k
+    seen, out = set(), []
+    for s in sorted({1, 2, 3, 4, 5, 8, 9, 16, smax}):
+        if s > smax:
+            continue
+        b = budget_for_split(semiring, m, n, k, s)
+        got = mmsr.mm_plan_query(semiring, -1, m, n, k, b).split_k
+        if got not in seen and b <= budget:
+            seen.add(got)
+            out.append((got, b))
+    return out
+
+
+def strassen_candidates(semiring: int, m: int, n: int, k: int, budget: int):
+    """Strassen depths whose workspace fits the budget, as (L, workspace)."""
+    out = []
+    for L in range(0, 5):
+        mask = (1 << L) - 1
+        if (m & mask) or (n & mask) or (k & mask):
+            break
+        p = mmsr.mm_plan_query(semiring, L if L else -1, m, n, k, budget, check=False)
+        if p.status != mmsr.MM_OK:
+            continue
+        if int(p.workspace_min) <= budget:
+            out.append((L, int(p.workspace_min)))
+    return out
+
+
+def cuda_timer(fn, reps=3):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_semiring(semiring, m, n, k, A, B, C, workspace, budget, timer=cuda_timer, cache=None, persist=True):
+    """Time every split factor the budget allows; returns {"split_k", "budget", "ms"}."""
+    kk = key("semiring", semiring, m, n, k, budget)
+    with _lock:
+        c = load_cache() if cache is None else cache
+        if kk in c:
+            return c[kk]
+    best = None
+    for s, b in split_candidates(semiring, m, n, k, budget):
+        ms = timer(lambda: mmsr.mm_semiring(semiring, m, n, k, A, B, C, workspace, b))
+        if best is None or ms < best["ms"]:
+            best = {"split_k": s, "budget": b, "ms": ms}
+    with _lock:
+        c[kk] = best
+        if persist and cache is None:
+            save_cache(c)
+    return best
+
+
+def tune_strassen(semiring, m, n, k, A, B, C, workspace, budget, variant=mmsr.MM_STRASSEN_WINOGRAD,
+                  timer=cuda_timer, cache=None, persist=True):
+    """Time every Strassen depth the budget allows; returns {"levels", "workspace", "ms"}."""
+    kk = key("strassen%d" % variant, semiring, m, n, k, budget)
+    with _lock:
+        c = load_cache() if cache is None else cache
+        if kk in c:
+            return c[kk]
+    best = None
+    for L, w in strassen_candidates(semiring, m, n, k, budget):
+        ms = timer(lambda: mmsr.mm_strassen(L, variant, semiring, m, n, k, A, B, C, workspace, w))
+        if best is None or ms < best["ms"]:
+            best = {"levels": L, "workspace": w, "ms": ms}
+    with _lock:
+        c[kk] = best
+        if persist and cache is None:
+            save_cache(c)
+    return best
+
+
+def mm_semiring_tuned(semiring, m, n, k, A, B, C, workspace, budget, stream=None):
+    """mm_semiring with the cached best split factor for this shape and budget
+    (falls back to the planner's own choice when the shape was never tuned)."""
+    c = load_cache()
+    rec = c.get(key("semiring", semiring, m, n, k, budget))
+    b = rec["budget"] if rec and rec["budget"] <= budget else budget
+    return mmsr.mm_semiring(semiring, m, n, k, A, B, C, workspace, b, stream)

@@ -46,6 +46,8 @@ struct BatchTable {
   int kind[kMaxBatch];  // 0: FP32 (+,x) on tensor cores, 1: (min,+)
   int m[kMaxBatch], n[kMaxBatch], k[kMaxBatch];
   int tile_start[kMaxBatch + 1];
+  int mp_tile_start[kMaxBatch + 1];  // 128 x 128 tiles of (min,+) problems, for the fallback
+  int mp_total;
   int row0a[kMaxBatch];  // FP32: first row of this A in the stacked split buffers
   int row0b[kMaxBatch];  // FP32: first row of this B^T in the stacked split buffers
   const void* A[kMaxBatch];
@@ -112,35 +114,55 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const __grid_constan
 }
 
 // (min,+) problems: flag any entry outside the packed range (violation[p]
-// starts at 0, set by a memset before the launch).
+// starts at 0, set by a memset before the launch).  blockIdx.y = problem.
 __global__ void __launch_bounds__(256) batched_range_kernel(const __grid_constant__ BatchTable T,
                                                             int* __restrict__ violation) {
   const int p = blockIdx.y;
   if (T.kind[p] != 1) return;
   int bad = 0;
+  const int64_t stride = (int64_t)gridDim.x * 256;
+  const int64_t t0 = (int64_t)blockIdx.x * 256 + threadIdx.x;
   for (int pass = 0; pass < 2; ++pass) {
     const int32_t* X = static_cast<const int32_t*>(pass ? T.B[p] : T.A[p]);
     const int64_t cnt = pass ? (int64_t)T.k[p] * T.n[p] : (int64_t)T.m[p] * T.k[p];
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * 256)
-      bad |= mp::out_of_pack_range(X[e]);
+    const int64_t nv = aligned16(X) ? cnt / 4 : 0;
+#pragma unroll 4
+    for (int64_t v = t0; v < nv; v += stride) {
+      const int4 q = __ldcs(reinterpret_cast<const int4*>(X) + v);
+      bad |= mp::out_of_pack_range(q.x) | mp::out_of_pack_range(q.y) | mp::out_of_pack_range(q.z) |
+             mp::out_of_pack_range(q.w);
+    }
+    for (int64_t e = nv * 4 + t0; e < cnt; e += stride) bad |= mp::out_of_pack_range(X[e]);
   }
   bad = __syncthreads_or(bad);
   if (bad && threadIdx.x == 0) atomicOr(&violation[p], 1);
 }
 
-// 32-bit fallback for a (min,+) tile whose inputs fall outside the packed
-// range; the light variant keeps its register demand within the persistent
-// kernel's budget.
-__device__ __forceinline__ void minplus32_tile_pair(const int32_t* A, const int32_t* B, int32_t* C,
-                                                 int64_t m, int64_t n, int64_t k, int64_t i0,
-                                                 int64_t j0, bool vec, int tid, int32_t* smem) {
-  const int nkb = (int)((k + mp::BK - 1) / mp::BK);
-  for (int h = 0; h < 2; ++h) {
-    if (j0 + h * 128 >= n) break;
-    mp::minplus32_tile<mp::SyncNamed256, true>(A, B, C, (int32_t*)nullptr, 0, m, n, k, i0, j0 + h * 128,
-                                               (int64_t)0, nkb, vec, tid, smem, mp::SyncNamed256());
-    mp::SyncNamed256()();
+// 32-bit fallback for (min,+) problems whose inputs fall outside the packed
+// range: one 128 x 128 tile per CTA over a compact list of those problems'
+// tiles; CTAs of in-range problems exit at once.  Kept out of the persistent
+// kernel so its register demand does not press on the kernel's main paths.
+__global__ void __launch_bounds__(256, 2)
+    batched_minplus32_kernel(const __grid_constant__ BatchTable T, const int* __restrict__ violation) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = T.count - 1;  // last p with mp_tile_start[p] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (T.mp_tile_start[mid] <= t) lo = mid; else hi = mid - 1;
   }
+  const int p = lo;
+  if (T.kind[p] != 1 || __ldcg(&violation[p]) == 0) return;
+  extern __shared__ __align__(16) int32_t fsmem[];
+  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+  const int local = t - T.mp_tile_start[p];
+  const int tiles_n = (int)((n + mp::BN - 1) / mp::BN);
+  const int32_t* A = static_cast<const int32_t*>(T.A[p]);
+  const int32_t* B = static_cast<const int32_t*>(T.B[p]);
+  int32_t* C = static_cast<int32_t*>(T.C[p]);
+  const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
+  mp::minplus32_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, (int64_t)(local / tiles_n) * mp::BM,
+                     (int64_t)(local % tiles_n) * mp::BN, (int64_t)0, (int)((k + mp::BK - 1) / mp::BK), vec,
+                     (int)threadIdx.x, fsmem, mp::SyncCta());
 }
 
 // ------------------------------------------------------ persistent kernel
@@ -289,12 +311,10 @@ __global__ void __launch_bounds__(kBThreads, 1)
       int32_t* C = static_cast<int32_t*>(T.C[p]);
       const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
       const int tid = threadIdx.x - 64;
-      if (__ldcg(&violation[p]) == 0) {
+      // out-of-range problems are left to the 32-bit fallback launch
+      if (__ldcg(&violation[p]) == 0)
         mp::minplus16_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, i0, j0, (int64_t)0, k, vec, tid,
                            reinterpret_cast<uint32_t*>(smem), mp::SyncNamed256());
-      } else {
-        minplus32_tile_pair(A, B, C, m, n, k, i0, j0, vec, tid, reinterpret_cast<int32_t*>(smem));
-      }
     }
     __syncthreads();
   }
@@ -332,7 +352,7 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     const double cb = (double)probs[b].m * probs[b].n * (double)std::max<int64_t>(probs[b].k, 1);
     return ca > cb;
   });
-  int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0;
+  int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0;
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[order[i]];
     T.kind[i] = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : 1;
@@ -343,6 +363,9 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     T.B[i] = q.B;
     T.C[i] = q.C;
     T.tile_start[i] = (int)tiles;
+    T.mp_tile_start[i] = (int)mp_tiles;
+    if (q.semiring == MM_SR_MIN_PLUS_I32 && q.m > 0 && q.n > 0)
+      mp_tiles += ((q.m + mp::BM - 1) / mp::BM) * ((q.n + mp::BN - 1) / mp::BN);
     const int64_t bn = T.kind[i] == 0 ? TBN : MPN;
     if (q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + bn - 1) / bn);
     if (T.kind[i] == 0) {
@@ -353,8 +376,12 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
       kp_max = std::max<int64_t>(kp_max, align_up(q.k > 0 ? q.k : 1, TBK));
     }
   }
-  if (tiles > (int64_t)1 << 30 || ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30) return MM_ERR_SHAPE;
+  if (tiles > (int64_t)1 << 30 || mp_tiles > (int64_t)1 << 30 || ra > (int64_t)1 << 30 ||
+      rb > (int64_t)1 << 30)
+    return MM_ERR_SHAPE;
   T.tile_start[count] = (int)tiles;
+  T.mp_tile_start[count] = (int)mp_tiles;
+  T.mp_total = (int)mp_tiles;
   T.count = count;
   T.total_tiles = (int)tiles;
   P->KP = kp_max;
@@ -409,8 +436,8 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   MMSR_TRY_STATUS(cudaMemsetAsync(w, 0, P.off_viol + 4 * kMaxBatch, st));
   {
     TraceScope tr(kTrSplitBf16, st);
-    batched_split_kernel<<<dim3(16, (unsigned)count), 256, 0, st>>>(P.T, P.KP, ahi, alo, bhi, blo);
-    batched_range_kernel<<<dim3(8, (unsigned)count), 256, 0, st>>>(P.T, violation);
+    batched_split_kernel<<<dim3(32, (unsigned)count), 256, 0, st>>>(P.T, P.KP, ahi, alo, bhi, blo);
+    batched_range_kernel<<<dim3(32, (unsigned)count), 256, 0, st>>>(P.T, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
@@ -433,6 +460,18 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   {
     TraceScope tr(kTrBatched, st);
     batched_kernel<<<grid, kBThreads, BSMEM, st>>>(P.T, ta_hi, ta_lo, tb_hi, tb_lo, counter, violation);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  if (P.T.mp_total > 0) {
+    TraceScope tr(kTrMinplusLeaf, st);
+    static bool fb_configured = false;
+    if (!fb_configured) {
+      MMSR_TRY_STATUS(cudaFuncSetAttribute(batched_minplus32_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)mp::SMEM_BYTES));
+      fb_configured = true;
+    }
+    batched_minplus32_kernel<<<(unsigned)P.T.mp_total, 256, mp::SMEM_BYTES, st>>>(P.T, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   return MM_OK;

@@ -244,9 +244,7 @@ __device__ __forceinline__ void minplus16_tile(const int32_t* __restrict__ A, co
 
 // One 128 x 128 output tile of the 32-bit leaf over k-blocks
 // [kb_begin, kb_begin + nkb), executed by 256 threads that synchronise with `bar`.
-// kLight reads one k-column of A at a time (fewer live registers, more
-// shared-memory loads), for callers with a tighter register budget.
-template <class Bar, bool kLight = false>
+template <class Bar>
 __device__ __forceinline__ void minplus32_tile(const int32_t* __restrict__ A, const int32_t* __restrict__ B,
                                                int32_t* __restrict__ C, int32_t* __restrict__ W, int z,
                                                int64_t m, int64_t n, int64_t k,
@@ -286,40 +284,23 @@ __device__ __forceinline__ void minplus32_tile(const int32_t* __restrict__ A, co
     const int32_t* as = As + sc * BM * LDA;
     const int32_t* bs = Bs + sc * BK * BN;
 #pragma unroll
-    if (kLight) {
-#pragma unroll 4
-      for (int kk = 0; kk < BK; ++kk) {
-        const uint4 b0 = *reinterpret_cast<const uint4*>(bs + kk * BN + tx * 4);
-        const uint4 b1 = *reinterpret_cast<const uint4*>(bs + kk * BN + 64 + tx * 4);
+    for (int kq = 0; kq < BK; kq += 4) {
+      uint4 a4[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = (i < 4) ? (ty * 4 + i) : (64 + ty * 4 + (i - 4));
+        a4[i] = *reinterpret_cast<const uint4*>(as + row * LDA + kq);
+      }
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint4 b0 = *reinterpret_cast<const uint4*>(bs + (kq + kk) * BN + tx * 4);
+        const uint4 b1 = *reinterpret_cast<const uint4*>(bs + (kq + kk) * BN + 64 + tx * 4);
         const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int row = (i < 4) ? (ty * 4 + i) : (64 + ty * 4 + (i - 4));
-          const uint32_t a = (uint32_t)as[row * LDA + kk];
+          const uint32_t a = kk == 0 ? a4[i].x : kk == 1 ? a4[i].y : kk == 2 ? a4[i].z : a4[i].w;
 #pragma unroll
           for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_u32(a, b[j], acc[i][j]);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int kq = 0; kq < BK; kq += 4) {
-        uint4 a4[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int row = (i < 4) ? (ty * 4 + i) : (64 + ty * 4 + (i - 4));
-          a4[i] = *reinterpret_cast<const uint4*>(as + row * LDA + kq);
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint4 b0 = *reinterpret_cast<const uint4*>(bs + (kq + kk) * BN + tx * 4);
-          const uint4 b1 = *reinterpret_cast<const uint4*>(bs + (kq + kk) * BN + 64 + tx * 4);
-          const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint32_t a = kk == 0 ? a4[i].x : kk == 1 ? a4[i].y : kk == 2 ? a4[i].z : a4[i].w;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_u32(a, b[j], acc[i][j]);
-          }
         }
       }
     }

@@ -12,9 +12,11 @@
 // (28 slice products; the dropped orders g >= 7 and the residuals are below
 // 2^-49 of the scaled magnitudes, which leaves room for the error growth of
 // Strassen levels above these leaves).  Each G_g is an integer: it
-// accumulates in its own TMEM accumulator over chunks of 64 k, where every
-// partial sum is an integer of magnitude < 2^21.2 (so the FP32 accumulation
-// is exact whatever its rounding), and drain warps move each chunk into two
+// accumulates in its own TMEM accumulator over chunks of 96 k, where every
+// partial sum is an integer of magnitude <= 96 * 36864 < 2^22 (per k, the
+// digit products of one order sum to at most 2 * 128 * 64 + 5 * 64 * 64), so
+// the FP32 accumulation is exact whatever its rounding, and drain warps move
+// each chunk into two
 // int64 registers per output (hi = G0 2^14 + G1 2^7 + G2, lo = G3 2^21 +
 // G4 2^14 + G5 2^7 + G6).  The epilogue forms 2^(E_i+F_j) (hi 2^-28 +
 // lo 2^-56) in FP64.  FP64 arithmetic is used only for that final sum and
@@ -34,7 +36,7 @@ namespace {
 __device__ int g_f64acc_status;
 
 constexpr int kSlices = 7, kDigitBits = 7, kGroups = 7;
-constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2, CHUNK = 2;  // CHUNK k-blocks per drain
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2, CHUNK = 3;  // CHUNK k-blocks per drain
 constexpr int kDrain = 8, kThreads = 64 + 32 * kDrain;
 constexpr uint32_t A_TILE = BM * BK * 2, B_TILE = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = kSlices * (A_TILE + B_TILE);
