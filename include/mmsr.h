@@ -215,9 +215,13 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   MM_OPT_MINPLUS_PACKED: 1 (default) lets (min,+) products run the exact
  *   packed 2 x 16-bit leaf when a device-side range scan finds every finite
  *   input <= 16383; 0 always runs the 32-bit leaf.  Results are identical.
+ *   MM_OPT_MINPLUS_STREAMK: 1 (default) lets an unsplit packed (min,+)
+ *   product whose tiles fill fewer than four waves run in the zero-workspace
+ *   k-parallel form (TAR-MM, Fig. tar-mm: register tiles merged into C by an
+ *   atomic min); 0 disables it.  Results are identical.
  * Returns MM_OK or MM_ERR_ARG.
  */
-typedef enum { MM_OPT_MINPLUS_PACKED = 1 } mm_option_t;
+typedef enum { MM_OPT_MINPLUS_PACKED = 1, MM_OPT_MINPLUS_STREAMK = 2 } mm_option_t;
 int mm_set_option(int option, int value);
 
 /* Static string for a status code. */

@@ -227,6 +227,10 @@ int mm_set_option(int option, int value) {
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_packed_mode = value;
       return MM_OK;
+    case MM_OPT_MINPLUS_STREAMK:
+      if (value != 0 && value != 1) return MM_ERR_ARG;
+      g_streamk_mode = value;
+      return MM_OK;
     default:
       return MM_ERR_ARG;
   }

@@ -98,6 +98,40 @@ __global__ void __launch_bounds__(PTHREADS, 2)
                  vec, (int)threadIdx.x, psmem, SyncCta());
 }
 
+// Zero-workspace k-parallel form (the TAR-MM of Fig. tar-mm: every worker
+// keeps a tile-sized temporary -- here the register tile -- and merges it
+// into C with an atomic (+), here min, which is exact and order-free).  The
+// persistent CTAs split the (tile, 16-wide k sub-block) units of the whole
+// product evenly (stream-K), so no wave of CTAs runs half empty; a segment
+// that covers a whole tile stores it, partial segments merge into C, which
+// a fill kernel sets to the sentinel first.
+__global__ void __launch_bounds__(PTHREADS, 2)
+    minplus16_streamk_kernel(int64_t m, int64_t n, int64_t k, const int32_t* __restrict__ A,
+                             const int32_t* __restrict__ B, int32_t* __restrict__ C, bool vec,
+                             int slot, int64_t units, int64_t nsub, int64_t tiles_n) {
+  if (pack_verdict(slot) != 1) return;
+  extern __shared__ __align__(16) uint32_t psmem[];
+  const int64_t G = gridDim.x;
+  int64_t u = units * blockIdx.x / G;
+  const int64_t end = units * (blockIdx.x + 1) / G;
+  while (u < end) {
+    const int64_t tile = u / nsub, s0 = u - tile * nsub;
+    const int64_t s1 = min(nsub, s0 + (end - u));
+    const bool whole = (s0 == 0 && s1 == nsub);
+    minplus16_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, (tile / tiles_n) * PBM, (tile % tiles_n) * PBN,
+                   s0 * PBK, min(k, s1 * PBK), vec, (int)threadIdx.x, psmem, SyncCta(), !whole);
+    __syncthreads();  // the next segment restages shared memory
+    u += s1 - s0;
+  }
+}
+
+__global__ void __launch_bounds__(256) fill_inf_kernel(int32_t* __restrict__ C, int64_t count, int slot) {
+  if (pack_verdict(slot) != 1) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    C[e] = kInf;
+}
+
 __global__ void __launch_bounds__(THREADS, 2)
     minplus_leaf_kernel(int64_t m, int64_t n, int64_t k, const int32_t* __restrict__ A,
                         const int32_t* __restrict__ B, int32_t* __restrict__ C,
@@ -153,6 +187,7 @@ __global__ void __launch_bounds__(256) min_reduce_kernel(int64_t count, int32_t*
 int minplus_tile_k() { return BK; }
 
 int g_packed_mode = 1;  // 1: use the packed path when the range scan allows, 0: never
+int g_streamk_mode = 1;  // 1: stream-K for unsplit packed products with few waves, 0: never
 
 cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* A,
                                 const int32_t* B, int32_t* C, int32_t* W, int s,
@@ -163,6 +198,9 @@ cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* 
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SMEM_BYTES));
     MMSR_CUDA_TRY(cudaFuncSetAttribute(minplus16_leaf_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PSMEM_BYTES));
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(minplus16_streamk_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)PSMEM_BYTES));
     configured = true;
@@ -183,9 +221,25 @@ cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* 
       range_scan_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m * k, B, k * n, slot, svec);
       MMSR_CUDA_TRY(cudaGetLastError());
     }
-    {
+    const int64_t tiles_m = (m + PBM - 1) / PBM, tiles_n = (n + PBN - 1) / PBN;
+    static int resident = 0;  // CTAs of the packed leaf that fit on the GPU at once
+    if (!resident) {
+      int dev = 0, sms = kNumSMs, per_sm = 2;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, minplus16_streamk_kernel, PTHREADS, PSMEM_BYTES);
+      resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    if (s == 1 && g_streamk_mode && tiles_m * tiles_n < 4 * (int64_t)resident) {
       TraceScope tr(kTrMinplus16Leaf, st);
-      dim3 pgrid((unsigned)((n + PBN - 1) / PBN), (unsigned)((m + PBM - 1) / PBM), (unsigned)s);
+      fill_inf_kernel<<<(unsigned)(kNumSMs * 4), 256, 0, st>>>(C, m * n, slot);
+      const int64_t nsub = (k + PBK - 1) / PBK;
+      minplus16_streamk_kernel<<<(unsigned)resident, PTHREADS, PSMEM_BYTES, st>>>(
+          m, n, k, A, B, C, vec, slot, tiles_m * tiles_n * nsub, nsub, tiles_n);
+      MMSR_CUDA_TRY(cudaGetLastError());
+    } else {
+      TraceScope tr(kTrMinplus16Leaf, st);
+      dim3 pgrid((unsigned)tiles_n, (unsigned)tiles_m, (unsigned)s);
       minplus16_leaf_kernel<<<pgrid, PTHREADS, PSMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice,
                                                                    vec, slot);
       MMSR_CUDA_TRY(cudaGetLastError());

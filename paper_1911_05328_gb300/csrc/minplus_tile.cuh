@@ -166,13 +166,16 @@ __device__ __forceinline__ void packed_store(const PackStage& r, uint32_t* As, u
 }
 
 // One 128 x 256 output tile of the packed leaf over k in [kbeg, kend),
-// executed by 256 threads (tid 0..255) that synchronise with `bar`.
+// executed by 256 threads (tid 0..255) that synchronise with `bar`.  With
+// `merge` the tile is folded into C by an atomic min (C must already hold
+// the semiring's 0 or another partial of the same product) instead of stored.
 template <class Bar>
 __device__ __forceinline__ void minplus16_tile(const int32_t* __restrict__ A, const int32_t* __restrict__ B,
                                                int32_t* __restrict__ C, int32_t* __restrict__ W, int z,
                                                int64_t m, int64_t n, int64_t k,
                                                int64_t i0, int64_t j0, int64_t kbeg, int64_t kend,
-                                               bool vec, int tid, uint32_t* psmem, Bar bar) {
+                                               bool vec, int tid, uint32_t* psmem, Bar bar,
+                                               bool merge = false) {
   uint32_t* As = psmem;                      // [2][PBK][PBM]
   uint32_t* Bs = psmem + 2 * PBK * PBM;      // [2][PBK][PBNP]
   const int tx = tid & 15, ty = tid >> 4;
@@ -230,7 +233,11 @@ __device__ __forceinline__ void minplus16_tile(const int32_t* __restrict__ A, co
         v[2 * p + 1] = hi >= kInf16 ? kInf : (int)hi;
       }
       int32_t* dst = out + gi * n + gj;
-      if (vec && gj + 8 <= n) {
+      if (merge) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (gj + e < n) atomicMin(reinterpret_cast<unsigned int*>(dst + e), (unsigned int)v[e]);
+      } else if (vec && gj + 8 <= n) {
         *reinterpret_cast<int4*>(dst) = make_int4(v[0], v[1], v[2], v[3]);
         *reinterpret_cast<int4*>(dst + 4) = make_int4(v[4], v[5], v[6], v[7]);
       } else {

@@ -174,7 +174,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  // Banded rasterisation: consecutive CTAs walk bands of 8 tile rows column
+  // by column, so a wave touches ~8 x 128 A rows and ~19 x 64 B rows (the
+  // minimum of rows_a * 128 + 152 / rows_a * 64) instead of one A panel
+  // and all of B.
+  int64_t i0, j0;
+  {
+    constexpr int kBand = 8;
+    const int tiles_n = gridDim.x, tiles_m = gridDim.y;
+    const int pid = blockIdx.y * tiles_n + blockIdx.x;
+    const int band = pid / (kBand * tiles_n);
+    const int first_m = band * kBand;
+    const int rows = min(kBand, tiles_m - first_m);
+    const int in_band = pid - band * kBand * tiles_n;
+    i0 = (int64_t)(first_m + in_band % rows) * BM;
+    j0 = (int64_t)(in_band / rows) * BN;
+  }
   // blockIdx.z = batch * kslices + k-slice; batch b uses rows [b*m, (b+1)*m)
   // of every A slice (and of E), rows [b*n, (b+1)*n) of every B^T slice
   const int z = blockIdx.z % kslices;

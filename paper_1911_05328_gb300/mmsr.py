@@ -26,6 +26,7 @@ MM_STRASSEN_PAPER = 0
 MM_STRASSEN_WINOGRAD = 1
 
 MM_OPT_MINPLUS_PACKED = 1
+MM_OPT_MINPLUS_STREAMK = 2
 
 MM_OK = 0
 MM_ERR_ARG = -1

@@ -3,7 +3,9 @@
     python -m paper_1911_05328_gb300.profile_case --case minplus4096 --reps 3
 
 Cases: minplus4096 (the (min,+) n=4096 product, budget 0 unless --budget),
-f32_<n> (FP32 mode, bf16x3 on tensor cores), f64_<n> (plain FP64 path).
+f32_<n> (FP32 mode, bf16x3 on tensor cores), f64acc_<n> (FP64-accuracy mode),
+f64_<n> (plain FP64 path), orand_<n> (boolean), batched512 (the 512-problem
+mixed batch in one persistent launch).
 Inputs come from the seeded generators; nothing is checked here.
 """
 import argparse
@@ -37,6 +39,30 @@ def main():
         A, B = inputs.normal_f32(n, n, n, seed=2)
         sr, dt = mmsr.MM_SR_PLUS_TIMES_F32, torch.float32
         acc = 4
+    elif a.case.startswith("f64acc_"):
+        n = int(a.case[7:])
+        A, B = inputs.uniform_f64(n, n, n, seed=3)
+        sr, dt = mmsr.MM_SR_PLUS_TIMES_F64ACC, torch.float64
+        acc = 8
+    elif a.case.startswith("orand_"):
+        n = int(a.case[6:])
+        A, B = inputs.boolean_u8(n, n, n, seed=6, density=0.01)
+        sr, dt = mmsr.MM_SR_OR_AND_U8, torch.uint8
+        acc = 1
+    elif a.case == "batched512":
+        probs = inputs.batched_problems(count=512, seed=4)
+        dA = [torch.from_numpy(p.A).cuda() for p in probs]
+        dB = [torch.from_numpy(p.B).cuda() for p in probs]
+        dC = [torch.empty((p.m, p.n), dtype=torch.float32 if p.semiring == mmsr.MM_SR_PLUS_TIMES_F32
+                          else torch.int32, device="cuda") for p in probs]
+        table = [(p.semiring, p.m, p.n, p.k, x, y, z) for p, x, y, z in zip(probs, dA, dB, dC)]
+        need = mmsr.mm_batched_query(table)
+        ws = torch.empty((need,), dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            mmsr.mm_batched(table, ws, need)
+        torch.cuda.synchronize()
+        print("done", a.case, "reps", a.reps)
+        return
     elif a.case.startswith("f64_"):
         n = int(a.case[4:])
         A, B = inputs.uniform_f64(n, n, n, seed=0)

@@ -127,3 +127,22 @@ def test_full_size_workload_all_budgets():
         assert canary_intact(ws, budget)
         np.testing.assert_array_equal(dC.cpu().numpy(), ref)
         del ws
+
+
+@pytest.mark.parametrize("m,n,k", [(4096, 4096, 4096), (333, 97, 4099), (1000, 700, 300), (129, 257, 17), (64, 64, 5000)])
+def test_streamk_zero_budget_matches(m, n, k):
+    # budget 0, few waves: the zero-workspace k-parallel form (register tiles
+    # merged into C by atomic min) must equal the oracle bit for bit, and
+    # equal the plain k-serial leaf
+    A, B = inputs.tropical_i32(m, k, n, seed=m + 2 * n + 3 * k)
+    mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_STREAMK, 1)
+    C1 = run(A, B)
+    mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_STREAMK, 0)
+    try:
+        C0 = run(A, B)
+    finally:
+        mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_STREAMK, 1)
+    ref = oracle.mm_minplus(A, B) if m * n * k <= 2 ** 33 else None
+    np.testing.assert_array_equal(C1, C0)
+    if ref is not None:
+        np.testing.assert_array_equal(C1, ref)
