@@ -219,9 +219,16 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   product whose tiles fill fewer than four waves run in the zero-workspace
  *   k-parallel form (TAR-MM, Fig. tar-mm: register tiles merged into C by an
  *   atomic min); 0 disables it.  Results are identical.
+ *   MM_OPT_TC_PAIR: 1 (default) runs the FP32-mode tensor-core leaf as
+ *   clusters of two CTAs that share (multicast) each B tile when the product
+ *   has at least two tile rows; 0 runs independent CTAs.  Results are identical.
  * Returns MM_OK or MM_ERR_ARG.
  */
-typedef enum { MM_OPT_MINPLUS_PACKED = 1, MM_OPT_MINPLUS_STREAMK = 2 } mm_option_t;
+typedef enum {
+  MM_OPT_MINPLUS_PACKED = 1,
+  MM_OPT_MINPLUS_STREAMK = 2,
+  MM_OPT_TC_PAIR = 3
+} mm_option_t;
 int mm_set_option(int option, int value);
 
 /* Static string for a status code. */

@@ -231,6 +231,10 @@ int mm_set_option(int option, int value) {
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_streamk_mode = value;
       return MM_OK;
+    case MM_OPT_TC_PAIR:
+      if (value != 0 && value != 1) return MM_ERR_ARG;
+      g_tc_pair_mode = value;
+      return MM_OK;
     default:
       return MM_ERR_ARG;
   }

@@ -80,6 +80,7 @@ cudaError_t launch_min_reduce(int64_t count, int32_t* C, const int32_t* W, int p
 int minplus_tile_k();
 extern int g_packed_mode;  // mm_set_option(MM_OPT_MINPLUS_PACKED, ...)
 extern int g_streamk_mode;  // mm_set_option(MM_OPT_MINPLUS_STREAMK, ...)
+extern int g_tc_pair_mode;  // mm_set_option(MM_OPT_TC_PAIR, ...)
 
 // FP64 DFMA leaf, same slicing contract with FP64 partials.
 cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, const double* B,

@@ -23,6 +23,8 @@ namespace {
 __device__ int g_tc_status;  // device status word of this translation unit
 }
 
+int g_tc_pair_mode = 1;  // 1: CTA pairs multicast B when the product has >= 2 tile rows
+
 // ------------------------------------------------------------ tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -61,7 +63,21 @@ cudaError_t make_tmap_2d_16bit(CUtensorMap* map, const void* base, int64_t rows,
 
 namespace {
 
-constexpr int BM = 128, BK = 64;
+constexpr int BM = 128, BK = 64;  // BK: k alignment of the split operands
+
+// GEMM k-block (64: 128-byte swizzled rows, 32: 64-byte rows), ring depth
+// and TMEM chunk length (in k-blocks).
+#ifndef MMSR_TC_BK
+#define MMSR_TC_BK 64
+#endif
+#ifndef MMSR_TC_STAGES
+#define MMSR_TC_STAGES 2
+#endif
+#ifndef MMSR_TC_CHUNK
+#define MMSR_TC_CHUNK 2
+#endif
+constexpr int kTcBK = MMSR_TC_BK;
+static_assert(BK % kTcBK == 0, "the GEMM k-block must divide the operand k alignment");
 
 // ----------------------------------------------------------- split kernels
 __device__ __forceinline__ void split1(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
@@ -136,17 +152,28 @@ constexpr int kDrainWarps = 8;
 constexpr int kGroupM = 16;  // tile rows per rasterisation band
 constexpr int kTcThreads = 64 + 32 * kDrainWarps;
 
+// Shared-memory descriptor for a K-major tile whose rows are KB bf16 wide.
+template <int KB>
+__device__ __forceinline__ uint64_t desc_kb(uint32_t saddr) {
+  return KB == 64 ? tc::desc_sw128(saddr) : tc::desc_sw64(saddr);
+}
+
 template <int BN, int STAGES>
 struct Bf16x3Cfg {
-  static constexpr uint32_t A_BYTES = BM * BK * 2;
-  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr int KB = kTcBK;
+  static constexpr uint32_t A_BYTES = BM * KB * 2;
+  static constexpr uint32_t B_BYTES = BN * KB * 2;
   static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
   static constexpr uint32_t TMEM_COLS = 2 * BN;  // double-buffered chunk accumulator
   static constexpr int COLS_PER_WARP = BN / 2;   // two drain warps share each lane quarter
 };
 
-template <int BN, int STAGES, int CHUNK>
+// MC: the kernel runs as clusters of two CTAs stacked along M that share one
+// B tile -- each CTA loads half of it and multicasts the half into both CTAs'
+// shared memory, so a CTA pair fetches B once instead of twice; each stage is
+// released by MMA-completion arrivals from both CTAs.
+template <int BN, int STAGES, int CHUNK, bool MC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAhi, const __grid_constant__ CUtensorMap tAlo,
                        const __grid_constant__ CUtensorMap tBhi, const __grid_constant__ CUtensorMap tBlo,
@@ -168,14 +195,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // column by column, so a wave shares its A and B panels through L2 instead
   // of streaming all of B once per band of rows.
   int64_t i0, j0;
+  const uint32_t rank = MC ? tc::cluster_ctarank() : 0u;  // position of this CTA in its pair
   {
-    const int tiles_n = gridDim.x, tiles_m = gridDim.y;
-    const int pid = blockIdx.y * tiles_n + blockIdx.x;
-    const int band = pid / (kGroupM * tiles_n);
-    const int first_m = band * kGroupM;
-    const int rows = min(kGroupM, tiles_m - first_m);
-    const int in_band = pid - band * kGroupM * tiles_n;
-    i0 = (int64_t)(first_m + in_band % rows) * BM;
+    // the unit of rasterisation is a CTA pair under MC, a CTA otherwise
+    const int per = MC ? 2 : 1;
+    const int tiles_n = gridDim.x, units_m = gridDim.y / per, band_h = kGroupM / per;
+    const int pid = (blockIdx.y / per) * tiles_n + blockIdx.x;
+    const int band = pid / (band_h * tiles_n);
+    const int first_m = band * band_h;
+    const int rows = min(band_h, units_m - first_m);
+    const int in_band = pid - band * band_h * tiles_n;
+    i0 = (int64_t)((first_m + in_band % rows) * per + (int)rank) * BM;
     j0 = (int64_t)(in_band / rows) * BN;
   }
   // blockIdx.z = batch * slices + k-slice; a batch is one independent product
@@ -191,7 +221,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], MC ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
@@ -204,6 +234,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  if (MC) tc::cluster_sync();  // the peer's barriers exist before any multicast lands
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
@@ -218,11 +249,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (it >= STAGES && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_tc_status)) break;
         tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
         uint8_t* st = smem + s * Cfg::STAGE_BYTES;
-        const int kx = (kb_begin + it) * BK;
+        const int kx = (kb_begin + it) * Cfg::KB;
         tc::tma_load_2d(st, &tAhi, &full[s], kx, ya);
         tc::tma_load_2d(st + Cfg::A_BYTES, &tAlo, &full[s], kx, ya);
-        tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, yb);
-        tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, yb);
+        if (MC) {
+          // this CTA's half of the B tile, into both CTAs of the pair
+          const uint32_t hb = Cfg::B_BYTES / 2;
+          const int yh = yb + (int)rank * (BN / 2);
+          tc::tma_load_2d_mc(st + 2 * Cfg::A_BYTES + rank * hb, &tBhi, &full[s], kx, yh, (uint16_t)3);
+          tc::tma_load_2d_mc(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + rank * hb, &tBlo, &full[s], kx, yh,
+                             (uint16_t)3);
+        } else {
+          tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, yb);
+          tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, yb);
+        }
+      }
+      if (MC) {
+        // wait until both CTAs have released the last stages, so no arrival
+        // from the peer is still in flight towards this CTA when it exits
+        for (int it = max(nkb, STAGES); it < nkb + STAGES; ++it) {
+          const int s = it % STAGES;
+          if (!tc::mbar_wait(&empty[s], ((uint32_t)(it / STAGES) - 1) & 1u, abort_flag, &g_tc_status)) break;
+        }
       }
     }
   } else if (warp == 1) {
@@ -243,16 +291,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc::fence_after_sync();
           const uint32_t base = smem_u32(smem + s * Cfg::STAGE_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t ahi = tc::desc_sw128(base + kk * 32);
-            const uint64_t alo = tc::desc_sw128(base + Cfg::A_BYTES + kk * 32);
-            const uint64_t bhi = tc::desc_sw128(base + 2 * Cfg::A_BYTES + kk * 32);
-            const uint64_t blo = tc::desc_sw128(base + 2 * Cfg::A_BYTES + Cfg::B_BYTES + kk * 32);
+          for (int kk = 0; kk < Cfg::KB / 16; ++kk) {
+            const uint64_t ahi = desc_kb<Cfg::KB>(base + kk * 32);
+            const uint64_t alo = desc_kb<Cfg::KB>(base + Cfg::A_BYTES + kk * 32);
+            const uint64_t bhi = desc_kb<Cfg::KB>(base + 2 * Cfg::A_BYTES + kk * 32);
+            const uint64_t blo = desc_kb<Cfg::KB>(base + 2 * Cfg::A_BYTES + Cfg::B_BYTES + kk * 32);
             tc::mma_f16(d, ahi, bhi, idesc, (first && kk == 0) ? 0u : 1u);
             tc::mma_f16(d, ahi, blo, idesc, 1);
             tc::mma_f16(d, alo, bhi, idesc, 1);
           }
-          tc::mma_commit(&empty[s]);
+          if (MC)
+            tc::mma_commit_mc(&empty[s], (uint16_t)3);  // releases the stage in both CTAs
+          else
+            tc::mma_commit(&empty[s]);
         }
         tc::mma_commit(&acc_full[b]);
         if (aborted) break;
@@ -305,6 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (MC) tc::cluster_sync();  // neither CTA leaves while the pair still shares smem traffic
   if (warp == 1) tc::tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
@@ -336,19 +388,40 @@ cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const 
                         const CUtensorMap& b_lo, float* C, float* W, int64_t m, int64_t n,
                         int kb_total, int kbs, int s, cudaStream_t st, int batches = 1,
                         int64_t a_batch_rows = 0, int64_t b_batch_rows = 0,
-                        int64_t c_batch_stride = 0) {
+                        int64_t c_batch_stride = 0, bool pair = false) {
   using Cfg = Bf16x3Cfg<BN, STAGES>;
   static bool configured = false;
   if (!configured) {
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK>,
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     configured = true;
   }
-  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)(s * batches));
+  const unsigned tiles_m = (unsigned)((m + BM - 1) / BM), tiles_n = (unsigned)((n + BN - 1) / BN);
   TraceScope tr(kTrTcBf16x3, st);
-  bf16x3_gemm_kernel<BN, STAGES, CHUNK><<<grid, kTcThreads, Cfg::SMEM, st>>>(
-      a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride);
-  return cudaGetLastError();
+  if (!pair) {
+    dim3 grid(tiles_n, tiles_m, (unsigned)(s * batches));
+    bf16x3_gemm_kernel<BN, STAGES, CHUNK, false><<<grid, kTcThreads, Cfg::SMEM, st>>>(
+        a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride);
+    return cudaGetLastError();
+  }
+  // pairs along M: an odd tile-row count gets one idle partner row, whose
+  // A rows lie past m (zero-filled by TMA, outputs discarded)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles_n, (tiles_m + 1) & ~1u, (unsigned)(s * batches));
+  cfg.blockDim = dim3(kTcThreads, 1, 1);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 2;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bf16x3_gemm_kernel<BN, STAGES, CHUNK, true>, a_hi, a_lo, b_hi, b_lo, C, W,
+                            m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride);
 }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -370,7 +443,7 @@ F32Layout f32_layout(int64_t m, int64_t n, int64_t k) {
   return L;
 }
 
-constexpr int kTcBN = 256, kTcStages = 2, kTcChunk = 2;
+constexpr int kTcBN = 256, kTcStages = MMSR_TC_STAGES, kTcChunk = MMSR_TC_CHUNK;
 
 }  // namespace
 
@@ -396,13 +469,14 @@ cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16*
                                   const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,
                                   int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st) {
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_hi, ahi, batches * m, Kp, Kp, BM, true));
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_lo, alo, batches * m, Kp, Kp, BM, true));
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_hi, bhi, batches * n, Kp, Kp, kTcBN, true));
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, batches * n, Kp, Kp, kTcBN, true));
-  const int kb_total = (int)(Kp / BK);
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_hi, ahi, batches * m, Kp, Kp, BM, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_lo, alo, batches * m, Kp, Kp, BM, true, kTcBK));
+  const bool pair = g_tc_pair_mode && m > BM;
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_hi, bhi, batches * n, Kp, Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, batches * n, Kp, Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK));
+  const int kb_total = (int)(Kp / kTcBK);
   return launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, P, nullptr, m, n,
-                                                 kb_total, kb_total, 1, st, batches, m, n, m * n);
+                                                 kb_total, kb_total, 1, st, batches, m, n, m * n, pair);
 }
 
 int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
@@ -410,7 +484,7 @@ int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
   const F32Layout L = f32_layout(m, n, k);
   p->tile_m = BM;
   p->tile_n = kTcBN;
-  p->tile_k = BK;
+  p->tile_k = kTcBK;
   p->kernel = 2;
   p->workspace_min = L.min_bytes;
   if (budget < (size_t)L.min_bytes) {
@@ -420,7 +494,7 @@ int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
   }
   int s = 1, kbs = 0;
   int64_t used = 0;
-  split_plan(m, n, L.Kp, BK, 4, budget - (size_t)L.min_bytes, &s, &kbs, &used);
+  split_plan(m, n, L.Kp, kTcBK, 4, budget - (size_t)L.min_bytes, &s, &kbs, &used);
   p->split_k = s;
   p->workspace_used = L.min_bytes + used;
   return MM_OK;
@@ -441,15 +515,17 @@ int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, flo
   cudaError_t e = launch_split_bf16(A, B, m, n, k, L.Kp, ahi, alo, bhi, blo, st);
   if (e != cudaSuccess) return MM_ERR_CUDA;
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-  if (make_tmap_2d_16bit(&ta_hi, ahi, m, L.Kp, L.Kp, BM, true) != cudaSuccess ||
-      make_tmap_2d_16bit(&ta_lo, alo, m, L.Kp, L.Kp, BM, true) != cudaSuccess ||
-      make_tmap_2d_16bit(&tb_hi, bhi, n, L.Kp, L.Kp, kTcBN, true) != cudaSuccess ||
-      make_tmap_2d_16bit(&tb_lo, blo, n, L.Kp, L.Kp, kTcBN, true) != cudaSuccess)
+  const bool pair = g_tc_pair_mode && m > BM;
+  if (make_tmap_2d_16bit(&ta_hi, ahi, m, L.Kp, L.Kp, BM, true, kTcBK) != cudaSuccess ||
+      make_tmap_2d_16bit(&ta_lo, alo, m, L.Kp, L.Kp, BM, true, kTcBK) != cudaSuccess ||
+      make_tmap_2d_16bit(&tb_hi, bhi, n, L.Kp, L.Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK) != cudaSuccess ||
+      make_tmap_2d_16bit(&tb_lo, blo, n, L.Kp, L.Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK) != cudaSuccess)
     return MM_ERR_CUDA;
-  const int kb_total = (int)(L.Kp / BK);
+  const int kb_total = (int)(L.Kp / kTcBK);
   const int s = p.split_k;
   const int kbs = (kb_total + s - 1) / s;
-  e = launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, C, part, m, n, kb_total, kbs, s, st);
+  e = launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, C, part, m, n, kb_total, kbs, s, st,
+                                              1, 0, 0, 0, pair);
   if (e == cudaSuccess && s > 1) {
     TraceScope tr(kTrSumReduceF32, st);
     const bool vec = aligned16(C) && aligned16(part) && (m * n) % 4 == 0;

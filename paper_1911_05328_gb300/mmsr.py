@@ -27,6 +27,7 @@ MM_STRASSEN_WINOGRAD = 1
 
 MM_OPT_MINPLUS_PACKED = 1
 MM_OPT_MINPLUS_STREAMK = 2
+MM_OPT_TC_PAIR = 3
 
 MM_OK = 0
 MM_ERR_ARG = -1
