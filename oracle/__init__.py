@@ -13,7 +13,8 @@ MM) with ``t`` ascending; ``rows`` selects which rows of C to compute.
 
 Parity pins: see ``tests/test_oracle_pins.py``.  All functions here are
 pinned (identity/zero invariants, closed forms, brute force, exact rationals,
-library routines, Strassen/Winograd agreement, Floyd-Warshall closure).
+library routines, Strassen/Winograd agreement, Floyd-Warshall closure,
+closures against scipy's graph search and the power series on tiny inputs).
 """
 from __future__ import annotations
 
@@ -57,6 +58,9 @@ def _load():
             lib.oracle_strassen_i64.restype = ctypes.c_int
             lib.oracle_floyd_warshall.argtypes = [i64, vp]
             lib.oracle_floyd_warshall.restype = ctypes.c_int
+            for name in ("oracle_closure_minplus", "oracle_closure_orand"):
+                getattr(lib, name).argtypes = [i64, vp]
+                getattr(lib, name).restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -132,6 +136,26 @@ def floyd_warshall(D) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("oracle_floyd_warshall failed with %d" % rc)
     return D
+
+
+def closure_minplus(A) -> np.ndarray:
+    """(min,+) closure A* = 1 (+) A (+) A^2 (+) ... (all-pairs shortest paths,
+    diagonal 0, sentinel 2^30 = unreachable) of a square int matrix, as int64."""
+    D = np.array(A, dtype=np.int64, copy=True, order="C")
+    rc = _load().oracle_closure_minplus(D.shape[0], _ptr(D))
+    if rc != 0:
+        raise RuntimeError("oracle_closure_minplus failed with %d" % rc)
+    return D
+
+
+def closure_orand(A) -> np.ndarray:
+    """(or, and) closure: reflexive-transitive reachability of a square 0/1
+    matrix (nonzero = arc), as uint8 0/1."""
+    R = np.array(A, dtype=np.uint8, copy=True, order="C")
+    rc = _load().oracle_closure_orand(R.shape[0], _ptr(R))
+    if rc != 0:
+        raise RuntimeError("oracle_closure_orand failed with %d" % rc)
+    return R
 
 
 def num_threads() -> int:

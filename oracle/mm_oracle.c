@@ -26,6 +26,13 @@
  * below exist only so the tests can pin the triple loop against independent
  * algorithms (Section 5 Strassen formulas; the bilinear generalisation that
  * names Strassen-Winograd).
+ *
+ * Closures.  A closed semiring (Section 2) has a closure A* = 1 (+) A (+) A^2
+ * (+) ... for square A.  For (min,+) on [0, 2^30] A* is the all-pairs
+ * shortest-path matrix (0 on the diagonal); for (or, and) it is reflexive
+ * reachability.  The oracle computes both by the textbook vertex-elimination
+ * algorithms (Floyd-Warshall, Warshall), which share nothing with the
+ * repeated squaring the GPU path uses.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -303,6 +310,31 @@ int oracle_floyd_warshall(int64_t n, int64_t* D) {
         if (s > ORACLE_INF) s = ORACLE_INF;
         if (s < D[i * n + j]) D[i * n + j] = s;
       }
+    }
+  return 0;
+}
+
+/* (min,+) closure A* = 1 (+) A (+) A^2 (+) ... of an n x n int64 matrix in
+ * place: the semiring's 1 (0 on the diagonal, the sentinel elsewhere) is
+ * folded in first, then Floyd-Warshall eliminates every vertex. */
+int oracle_closure_minplus(int64_t n, int64_t* D) {
+  if (n < 0) return -1;
+  for (int64_t i = 0; i < n; ++i)
+    if (D[i * n + i] > 0) D[i * n + i] = 0;
+  return oracle_floyd_warshall(n, D);
+}
+
+/* (or, and) closure of an n x n 0/1 matrix in place (nonzero input = true):
+ * reflexive diagonal, then Warshall's vertex elimination
+ * R[i][j] |= R[i][v] & R[v][j] for v = 0 .. n-1. */
+int oracle_closure_orand(int64_t n, uint8_t* R) {
+  if (n < 0) return -1;
+  for (int64_t e = 0; e < n * n; ++e) R[e] = R[e] ? 1 : 0;
+  for (int64_t i = 0; i < n; ++i) R[i * n + i] = 1;
+  for (int64_t v = 0; v < n; ++v)
+    for (int64_t i = 0; i < n; ++i) {
+      if (!R[i * n + v]) continue;
+      for (int64_t j = 0; j < n; ++j) R[i * n + j] |= R[v * n + j];
     }
   return 0;
 }

@@ -243,3 +243,73 @@ def test_orand_closure_equals_reachability():
         R = oracle.mm_orand(R, R)
     reach = np.isfinite(shortest_path(A.astype(np.float64), unweighted=True, directed=True)).astype(np.uint8)
     np.testing.assert_array_equal(R, reach)
+
+
+# ------------------------------------------------------------------ closures
+def _tropical_power_series(A):
+    # A* = 1 (+) A (+) A^2 (+) ... (+) A^(n-1), each power by numpy broadcasting
+    # (an independent min-plus product), summed with the semiring's min.
+    n = A.shape[0]
+    A = np.minimum(A.astype(np.int64), INF)
+    one = np.full((n, n), INF, dtype=np.int64)
+    np.fill_diagonal(one, 0)
+    X, P = one.copy(), one.copy()
+    for _ in range(max(n - 1, 0)):
+        P = np.minimum((P[:, :, None] + A[None, :, :]).min(axis=1), INF)
+        X = np.minimum(X, P)
+    return X
+
+
+def test_minplus_closure_equals_power_series_tiny():
+    # Brute force on tiny inputs, including a nonzero diagonal that only the
+    # semiring's 1 term of the closure clears.
+    for seed, nv in ((30, 1), (31, 2), (32, 5), (33, 9)):
+        D = inputs.graph_minplus(nv, seed=seed, density=0.4)
+        rng = np.random.default_rng(seed)
+        np.fill_diagonal(D, rng.integers(0, 50, size=nv))
+        np.testing.assert_array_equal(oracle.closure_minplus(D), _tropical_power_series(D))
+
+
+def test_minplus_closure_equals_scipy_dijkstra():
+    from scipy.sparse.csgraph import shortest_path
+
+    D = inputs.graph_minplus(70, seed=34, density=0.05)
+    W = np.where(D >= INF, 0, D).astype(np.float64)
+    sp = shortest_path(W, method="D", directed=True)
+    sp = np.where(np.isinf(sp), INF, sp).astype(np.int64)
+    np.testing.assert_array_equal(oracle.closure_minplus(D), sp)
+
+
+def test_minplus_closure_special_cases():
+    # no arcs: the closure is the semiring's 1; zero-weight complete graph: all 0.
+    n = 6
+    none = np.full((n, n), INF, dtype=np.int32)
+    one = np.full((n, n), INF, dtype=np.int64)
+    np.fill_diagonal(one, 0)
+    np.testing.assert_array_equal(oracle.closure_minplus(none), one)
+    np.testing.assert_array_equal(oracle.closure_minplus(np.zeros((n, n), np.int32)), np.zeros((n, n)))
+    # a directed path 0 -> 1 -> ... -> n-1 of unit arcs: C[i][j] = j - i above the diagonal.
+    path = np.full((n, n), INF, dtype=np.int32)
+    for i in range(n - 1):
+        path[i, i + 1] = 1
+    C = oracle.closure_minplus(path)
+    for i in range(n):
+        for j in range(n):
+            assert C[i, j] == (j - i if j >= i else INF)
+
+
+def test_orand_closure_equals_scipy_and_power_series():
+    from scipy.sparse.csgraph import shortest_path
+
+    for seed, nv, dens in ((35, 1, 0.5), (36, 7, 0.2), (37, 45, 0.04)):
+        A, _ = inputs.boolean_u8(nv, nv, 1, seed=seed, density=dens)
+        A = A * 3  # nonzero means true
+        reach = np.isfinite(shortest_path((A > 0).astype(np.float64), unweighted=True, directed=True))
+        R = oracle.closure_orand(A)
+        np.testing.assert_array_equal(R, reach.astype(np.uint8))
+        X = np.eye(nv, dtype=np.int64)
+        P = np.eye(nv, dtype=np.int64)
+        for _ in range(max(nv - 1, 0)):
+            P = ((P @ (A > 0).astype(np.int64)) > 0).astype(np.int64)
+            X |= P
+        np.testing.assert_array_equal(R, X.astype(np.uint8))
