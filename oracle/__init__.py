@@ -58,6 +58,8 @@ def _load():
             lib.oracle_strassen_i64.restype = ctypes.c_int
             lib.oracle_floyd_warshall.argtypes = [i64, vp]
             lib.oracle_floyd_warshall.restype = ctypes.c_int
+            lib.oracle_closure_minplus_rows.argtypes = [i64, vp, i64, vp, vp]
+            lib.oracle_closure_minplus_rows.restype = ctypes.c_int
             for name in ("oracle_closure_minplus", "oracle_closure_orand"):
                 getattr(lib, name).argtypes = [i64, vp]
                 getattr(lib, name).restype = ctypes.c_int
@@ -146,6 +148,20 @@ def closure_minplus(A) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("oracle_closure_minplus failed with %d" % rc)
     return D
+
+
+def closure_minplus_rows(A, rows) -> np.ndarray:
+    """Rows of the (min,+) closure by one dense Dijkstra per source row (int64)."""
+    D = np.ascontiguousarray(A, dtype=np.int32)
+    n = D.shape[0]
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    if rows.size and (rows.min() < 0 or rows.max() >= n):
+        raise ValueError("row index out of range")
+    out = np.empty((rows.size, n), dtype=np.int64)
+    rc = _load().oracle_closure_minplus_rows(n, _ptr(D), rows.size, _ptr(rows), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle_closure_minplus_rows failed with %d" % rc)
+    return out
 
 
 def closure_orand(A) -> np.ndarray:

@@ -339,6 +339,44 @@ int oracle_closure_orand(int64_t n, uint8_t* R) {
   return 0;
 }
 
+/* Rows `rows[0..nrows)` of the (min,+) closure of an n x n matrix with
+ * entries in [0, 2^30] (sentinel = no arc): one dense Dijkstra per source
+ * (nonnegative arc lengths), O(n^2) each, sums clamped to the sentinel.
+ * Writes out[r][j] = shortest distance rows[r] -> j (0 for j = rows[r]). */
+int oracle_closure_minplus_rows(int64_t n, const int32_t* D, int64_t nrows, const int64_t* rows,
+                                int64_t* out) {
+  if (n < 0 || nrows < 0) return -1;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < nrows; ++r) {
+    const int64_t src = rows[r];
+    int64_t* dist = out + r * n;
+    uint8_t* done = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!done) {
+      bad = 1;
+      continue;
+    }
+    for (int64_t j = 0; j < n; ++j) dist[j] = ORACLE_INF;
+    dist[src] = 0;
+    for (int64_t it = 0; it < n; ++it) {
+      int64_t u = -1;
+      for (int64_t j = 0; j < n; ++j)
+        if (!done[j] && (u < 0 || dist[j] < dist[u])) u = j;
+      if (u < 0 || dist[u] >= ORACLE_INF) break;
+      done[u] = 1;
+      for (int64_t j = 0; j < n; ++j) {
+        const int64_t w = D[u * n + j];
+        if (w >= ORACLE_INF || done[j]) continue;
+        int64_t d = dist[u] + w;
+        if (d > ORACLE_INF) d = ORACLE_INF;
+        if (d < dist[j]) dist[j] = d;
+      }
+    }
+    free(done);
+  }
+  return bad ? -2 : 0;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   extern int omp_get_max_threads(void);

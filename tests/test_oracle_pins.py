@@ -313,3 +313,15 @@ def test_orand_closure_equals_scipy_and_power_series():
             P = ((P @ (A > 0).astype(np.int64)) > 0).astype(np.int64)
             X |= P
         np.testing.assert_array_equal(R, X.astype(np.uint8))
+
+
+def test_minplus_closure_rows_dijkstra_matches_floyd_warshall():
+    # two independent algorithms for the same closure rows; zero-weight arcs,
+    # a nonzero diagonal and unreachable vertices included.
+    for seed, nv, dens in ((38, 1, 0.5), (39, 13, 0.2), (40, 90, 0.05)):
+        D = inputs.graph_minplus(nv, seed=seed, density=dens, hi=1000)
+        rng = np.random.default_rng(seed)
+        D[rng.random((nv, nv)) < 0.02] = 0
+        np.fill_diagonal(D, rng.integers(0, 9, size=nv))
+        rows = np.arange(nv)[:: max(1, nv // 7)]
+        np.testing.assert_array_equal(oracle.closure_minplus_rows(D, rows), oracle.closure_minplus(D)[rows])
