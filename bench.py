@@ -461,6 +461,7 @@ def run_extras(mmsr, lib, torch, sp):
     torch.cuda.empty_cache()
     out["batched_512"] = run_batched_extras(mmsr, lib, torch, sp, ctypes)
     out["strassen_fp32_n16384"] = run_strassen_extras(mmsr, lib, torch, sp, ctypes)
+    out["closure_minplus_n4096"] = run_closure_extras(mmsr, torch, sp)
     rate, pms = ctypes.c_double(), ctypes.c_double()
     lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -507,6 +508,37 @@ def run_batched_extras(mmsr, lib, torch, sp, ctypes):
     return res
 
 
+def run_closure_extras(mmsr, torch, sp):
+    """(min,+) closure (all-pairs shortest paths) of a 4096-vertex graph with
+    10% arcs of length in [0, 1000] (seed 1) by repeated squaring, one extra
+    n x n buffer of budget per squaring: all 12 squarings, and stopping at
+    the fixed point."""
+    n = 4096
+    rng = np.random.default_rng(1)
+    D = rng.integers(0, 1001, size=(n, n)).astype(np.int32)
+    D[rng.random((n, n)) >= 0.1] = mmsr.INF
+    dA = torch.from_numpy(D).cuda()
+    dC = torch.empty_like(dA)
+    sr = mmsr.MM_SR_MIN_PLUS_I32
+    p = mmsr.mm_closure_query(sr, n, 0)
+    budget = int(p.workspace_min) + n * n * 4
+    ws = torch.empty((budget,), dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, flags in (("all_squarings", 0), ("early_exit", mmsr.MM_CLOSURE_EARLY_EXIT)):
+        sq = []
+
+        def fn():
+            sq.append(mmsr.mm_closure(sr, n, dA, dC, ws, budget, flags=flags, stream=sp)[1])
+
+        ms = _time_call(torch, fn, 3)
+        res[name] = {"ms": ms, "squarings": sq[-1],
+                     "gops": sq[-1] * 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                     "workspace_bytes": budget}
+    del dA, dC, ws
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
     """Strassen-Winograd, FP32 mode, n = 16384 (uniform[-1,1], seed 3, cast
     to float32): classic (L = 0) and L = 1..4, per-level time, classic-
@@ -545,6 +577,19 @@ def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
         res["L%d" % L] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
                           "workspace_bytes": int(p.workspace_min),
                           "workspace_n2x4B": p.workspace_min / (n * n * 4.0), "kernel_ms": split}
+        del ws
+        torch.cuda.empty_cache()
+    # STAR-Strassen-1 mixed plans: c classic in-place levels over L Strassen
+    # levels; the workspace of one block product only
+    for c, L in ((1, 1), (1, 2), (2, 1), (2, 2)):
+        p = mmsr.mm_star_strassen_query(c, L, sr, n, n, n)
+        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+        fn = lambda: mmsr.mm_star_strassen(c, L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
+                                           int(p.workspace_min), sp)
+        ms = _time_call(torch, fn, 3)
+        res["star_c%d_L%d" % (c, L)] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                                        "workspace_bytes": int(p.workspace_min),
+                                        "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
         del ws
         torch.cuda.empty_cache()
     del dA, dB, dC

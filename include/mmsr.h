@@ -146,6 +146,35 @@ int mm_strassen(int levels, int variant, int semiring, int64_t m, int64_t n, int
                 void* stream);
 
 /*
+ * mm_star_strassen -- C := A (x) B as STAR-Strassen-1 (Theorem
+ * star-strassen-1): the top `classic_levels` levels are the classic 8-way
+ * recursion of Eq. mm-dac done in place (each of the 2^c x 2^c blocks of C
+ * accumulates its 2^c block products one after the other, c =
+ * classic_levels, with no temporaries), and every block product runs
+ * `levels` Strassen levels of `variant`.  The Strassen temporaries are those
+ * of ONE block product, (m/2^c) x (n/2^c) x (k/2^c), reused by the next, so
+ * the workspace is 4^c times smaller than that of mm_strassen at the same
+ * block size while the arithmetic is (8/7)^c times that of Strassen on all
+ * c + levels levels.
+ *   classic_levels   0 .. 4 (0 is mm_strassen)
+ *   levels           0 .. 4 (0 is mm_semiring on the whole product)
+ *   variant, semiring, m, n, k, A, B, C, workspace, workspace_bytes, stream
+ *                    as in mm_strassen; m, n, k divisible by
+ *                    2^(classic_levels + levels), else MM_ERR_SHAPE
+ * In FP32 mode the block products after the first add into C with the same
+ * top-level summation as mm_strassen (double-float when levels >= 3).
+ * Returns MM_OK or a negative mm_status_t.
+ */
+int mm_star_strassen(int classic_levels, int levels, int variant, int semiring, int64_t m, int64_t n,
+                     int64_t k, const void* A, const void* B, void* C, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* The plan (workspace_min / workspace_used, leaf tiles, levels) of
+ * mm_star_strassen for these arguments.  Host-only. */
+int mm_star_strassen_query(int classic_levels, int levels, int semiring, int64_t m, int64_t n,
+                           int64_t k, size_t workspace_bytes, mm_plan_t* plan);
+
+/*
  * mm_strassen_tables -- the bilinear coefficients one level of `variant`
  * uses (host copy of the device tables): alpha[7][4] (S_r = sum_q
  * alpha[r][q] A_q), beta[7][4] (T_r = sum_q beta[r][q] B_q) and gamma[4][7]
@@ -177,6 +206,43 @@ int mm_batched(int count, const mm_problem_t* problems, void* workspace, size_t 
 
 /* Workspace the batched call needs for these problems (0 on bad input). */
 size_t mm_batched_query(int count, const mm_problem_t* problems);
+
+/* Flags of mm_closure. */
+#define MM_CLOSURE_EARLY_EXIT 1
+
+/*
+ * mm_closure -- C := A* = 1 (+) A (+) A^2 (+) ... for a square n x n matrix
+ * on a semiring whose (+) is idempotent (Section 2 poses MM on a closed
+ * semiring; the closure is that structure's extra operation).
+ *   MM_SR_MIN_PLUS_I32: A[i][j] is the length of arc i -> j in [0, 2^30]
+ *     (2^30 = no arc); C is the all-pairs shortest-path matrix (diagonal 0,
+ *     2^30 = unreachable; path lengths saturate at 2^30).
+ *   MM_SR_OR_AND_U8: A[i][j] nonzero = arc; C is reflexive-transitive
+ *     reachability as 0/1.
+ *   Other semirings: MM_ERR_UNSUPPORTED ((+, x) has no idempotent (+)).
+ * Computed by repeated squaring of X_0 = 1 (+) A: T = ceil(log2(n-1))
+ * squarings (0 for n <= 2), each a mm_semiring product with the budget left
+ * after the closure's own buffers (so every squaring runs budgeted split-K).
+ *   n                  order, n >= 0 (n = 0: nothing is done)
+ *   A, C               device pointers, 16-byte aligned; A may equal C
+ *   workspace(_bytes)  as in mm_semiring; at least mm_closure_query's
+ *                      workspace_min (16 + n*n*elem rounded up to 16 + the
+ *                      squaring's minimum), else MM_ERR_WORKSPACE
+ *   flags              0: all T squarings, asynchronous and capturable;
+ *                      MM_CLOSURE_EARLY_EXIT: after each squaring compare
+ *                      X_{t+1} with X_t on the device and stop at the fixed
+ *                      point; SYNCHRONISES the stream once per squaring and
+ *                      returns MM_ERR_ARG if the stream is being captured
+ *   squarings          host pointer or NULL; receives the squarings run
+ * Returns MM_OK or a negative mm_status_t.
+ */
+int mm_closure(int semiring, int64_t n, const void* A, void* C, void* workspace,
+               size_t workspace_bytes, int flags, int* squarings, void* stream);
+
+/* Plan of mm_closure for a budget: split_k and tiles of each squaring,
+ * levels = T (the number of squarings without early exit), workspace_min /
+ * workspace_used of the whole call.  Host-only. */
+int mm_closure_query(int semiring, int64_t n, size_t workspace_bytes, mm_plan_t* plan);
 
 /*
  * mm_plan_query -- the plan mm_semiring (levels < 0) or mm_strassen
@@ -219,15 +285,21 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   product whose tiles fill fewer than four waves run in the zero-workspace
  *   k-parallel form (TAR-MM, Fig. tar-mm: register tiles merged into C by an
  *   atomic min); 0 disables it.  Results are identical.
- *   MM_OPT_TC_PAIR: 1 (default) runs the FP32-mode tensor-core leaf as
- *   clusters of two CTAs that share (multicast) each B tile when the product
- *   has at least two tile rows; 0 runs independent CTAs.  Results are identical.
+ *   MM_OPT_TC_PAIR: 1 runs the FP32-mode tensor-core leaf as clusters of two
+ *   CTAs that share (multicast) each B tile when the product has at least two
+ *   tile rows; 0 (default) runs independent CTAs.  Results are identical.
+ *   MM_OPT_STRASSEN_TOP_F64: FP32-mode Strassen with levels >= 3 sums its
+ *   top-level post-additions wider than FP32.  0 (default): an error-free
+ *   double-float sum on the FP32 units (Sum2 of Ogita, Rump and Oishi); 1:
+ *   FP64 arithmetic.  Both round the exact sum once to FP32 in all but rare
+ *   tie cases; the FP64 units of this GPU are far slower.
  * Returns MM_OK or MM_ERR_ARG.
  */
 typedef enum {
   MM_OPT_MINPLUS_PACKED = 1,
   MM_OPT_MINPLUS_STREAMK = 2,
-  MM_OPT_TC_PAIR = 3
+  MM_OPT_TC_PAIR = 3,
+  MM_OPT_STRASSEN_TOP_F64 = 4
 } mm_option_t;
 int mm_set_option(int option, int value);
 

@@ -9,7 +9,10 @@ fastest per shape bucket:
 * ``mm_semiring``: split factors s = 1 .. s_max, requested by handing the
   library a smaller budget (``budget_for_split``);
 * ``mm_strassen``: Strassen depths L = 0 .. 4 whose workspace fits the budget
-  and whose shape divides by 2^L.
+  and whose shape divides by 2^L;
+* ``mm_star_strassen``: mixed plans (Theorem star-strassen-1) of c classic
+  in-place levels over L Strassen levels, c + L <= 4 -- at a small budget a
+  deep Strassen plan fits only below a few classic levels.
 
 Choices are cached in JSON (``MMSR_TUNE_CACHE``, default
 ``~/.cache/mmsr_tune.json``) keyed by semiring, power-of-two shape bucket and
@@ -96,6 +99,49 @@ def strassen_candidates(semiring: int, m: int, n: int, k: int, budget: int):
         if int(p.workspace_min) <= budget:
             out.append((L, int(p.workspace_min)))
     return out
+
+
+def star_candidates(semiring: int, m: int, n: int, k: int, budget: int, max_depth: int = 4):
+    """Mixed plans (c classic levels, L Strassen levels) whose workspace fits
+    the budget, as (c, L, workspace); c = L = 0 is the classic product.  Of
+    plans with the same total depth c + L only the one with the fewest classic
+    levels that fits is kept (it does the least arithmetic)."""
+    out = []
+    for depth in range(0, max_depth + 1):
+        mask = (1 << depth) - 1
+        if (m & mask) or (n & mask) or (k & mask):
+            break
+        for c in range(0, depth + 1):
+            L = depth - c
+            if L == 0 and c > 0:
+                continue  # classic levels alone are the classic product
+            p = mmsr.mm_star_strassen_query(c, L, semiring, m, n, k, budget, check=False)
+            if p.status == mmsr.MM_OK and int(p.workspace_min) <= budget:
+                out.append((c, L, int(p.workspace_min)))
+                break
+    return out
+
+
+def tune_star_strassen(semiring, m, n, k, A, B, C, workspace, budget, variant=mmsr.MM_STRASSEN_WINOGRAD,
+                       timer=None, cache=None, persist=True):
+    """Time every mixed plan the budget allows; returns {"classic", "levels",
+    "workspace", "ms"}."""
+    timer = timer or cuda_timer
+    kk = key("star%d" % variant, semiring, m, n, k, budget)
+    with _lock:
+        c = load_cache() if cache is None else cache
+        if kk in c:
+            return c[kk]
+    best = None
+    for cl, L, w in star_candidates(semiring, m, n, k, budget):
+        ms = timer(lambda: mmsr.mm_star_strassen(cl, L, variant, semiring, m, n, k, A, B, C, workspace, w))
+        if best is None or ms < best["ms"]:
+            best = {"classic": cl, "levels": L, "workspace": w, "ms": ms}
+    with _lock:
+        c[kk] = best
+        if persist and cache is None:
+            save_cache(c)
+    return best
 
 
 def cuda_timer(fn, reps=3):

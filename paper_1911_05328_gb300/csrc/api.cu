@@ -186,6 +186,37 @@ int mm_strassen(int levels, int variant, int semiring, int64_t m, int64_t n, int
                       static_cast<cudaStream_t>(stream));
 }
 
+// Shared checks of the mixed (STAR-Strassen-1) plan entry points.
+static int check_star(int classic, int levels, int semiring, int64_t m, int64_t n, int64_t k) {
+  if (acc_bytes(semiring) == 0 || m < 0 || n < 0 || k < 0) return MM_ERR_ARG;
+  if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return MM_ERR_SHAPE;
+  if (classic < 0 || classic > kMaxLevels || levels < 0 || levels > kMaxLevels) return MM_ERR_ARG;
+  if (semiring == MM_SR_MIN_PLUS_I32 || semiring == MM_SR_OR_AND_U8) return MM_ERR_UNSUPPORTED;
+  const int64_t mask = ((int64_t)1 << (classic + levels)) - 1;
+  if ((m & mask) || (n & mask) || (k & mask)) return MM_ERR_SHAPE;
+  return MM_OK;
+}
+
+int mm_star_strassen(int classic_levels, int levels, int variant, int semiring, int64_t m, int64_t n,
+                     int64_t k, const void* A, const void* B, void* C, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+  int rc = validate_common(semiring, m, n, k, A, B, C, workspace, workspace_bytes);
+  if (rc != MM_OK) return rc;
+  if (variant != MM_STRASSEN_PAPER && variant != MM_STRASSEN_WINOGRAD) return MM_ERR_ARG;
+  rc = check_star(classic_levels, levels, semiring, m, n, k);
+  if (rc != MM_OK || m == 0 || n == 0) return rc;
+  return run_star_strassen(classic_levels, levels, variant, semiring, m, n, k, A, B, C, workspace,
+                           workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int mm_star_strassen_query(int classic_levels, int levels, int semiring, int64_t m, int64_t n,
+                           int64_t k, size_t workspace_bytes, mm_plan_t* plan) {
+  if (!plan) return MM_ERR_ARG;
+  const int rc = check_star(classic_levels, levels, semiring, m, n, k);
+  if (rc != MM_OK) return rc;
+  return plan_star_strassen(classic_levels, levels, semiring, m, n, k, workspace_bytes, plan);
+}
+
 int mm_plan_query(int semiring, int levels, int64_t m, int64_t n, int64_t k,
                   size_t workspace_bytes, mm_plan_t* plan) {
   if (!plan) return MM_ERR_ARG;
@@ -234,6 +265,10 @@ int mm_set_option(int option, int value) {
     case MM_OPT_TC_PAIR:
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_tc_pair_mode = value;
+      return MM_OK;
+    case MM_OPT_STRASSEN_TOP_F64:
+      if (value != 0 && value != 1) return MM_ERR_ARG;
+      g_strassen_top_f64 = value;
       return MM_OK;
     default:
       return MM_ERR_ARG;

@@ -49,7 +49,8 @@ __host__ __device__ inline bool aligned16(const void* p) {
 enum TraceKernel {
   kTrMinplusLeaf = 0, kTrMinReduce, kTrDfmaLeaf, kTrSumReduceF64, kTrSplitBf16, kTrTcBf16x3,
   kTrSumReduceF32, kTrSplitF64Slices, kTrTcF64Acc, kTrStrassenCombine, kTrStrassenPost,
-  kTrBatched, kTrOrAndLeaf, kTrOrReduce, kTrMinplus16Leaf, kTrRangeScan, kTrOrPack, kTraceKernels
+  kTrBatched, kTrOrAndLeaf, kTrOrReduce, kTrMinplus16Leaf, kTrRangeScan, kTrOrPack, kTrClosureAux,
+  kTraceKernels
 };
 // RAII: records a start event now and an end event at scope exit, on `st`,
 // when tracing is enabled; otherwise does nothing.
@@ -81,6 +82,7 @@ int minplus_tile_k();
 extern int g_packed_mode;  // mm_set_option(MM_OPT_MINPLUS_PACKED, ...)
 extern int g_streamk_mode;  // mm_set_option(MM_OPT_MINPLUS_STREAMK, ...)
 extern int g_tc_pair_mode;  // mm_set_option(MM_OPT_TC_PAIR, ...)
+extern int g_strassen_top_f64;  // mm_set_option(MM_OPT_STRASSEN_TOP_F64, ...)
 
 // FP64 DFMA leaf, same slicing contract with FP64 partials.
 cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, const double* B,

@@ -63,6 +63,20 @@ int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t bu
 int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,
                  const void* B, void* C, void* ws, size_t ws_bytes, cudaStream_t st);
 
+// STAR-Strassen-1 mixed plans: `classic` in-place classic levels over
+// `levels` Strassen levels
+int plan_star_strassen(int classic, int levels, int sr, int64_t m, int64_t n, int64_t k,
+                       size_t budget, mm_plan_t* p);
+int run_star_strassen(int classic, int levels, int variant, int sr, int64_t m, int64_t n, int64_t k,
+                      const void* A, const void* B, void* C, void* ws, size_t ws_bytes,
+                      cudaStream_t st);
+
+// closure by repeated squaring
+int closure_squarings(int64_t n);
+int plan_closure(int sr, int64_t n, size_t budget, mm_plan_t* p);
+int run_closure(int sr, int64_t n, const void* A, void* C, void* ws, size_t ws_bytes, int flags,
+                int* squarings, cudaStream_t st);
+
 // device status word (bounded waits of the batched kernel)
 int read_device_status(cudaStream_t st, int* status);
 

@@ -28,69 +28,112 @@
 namespace mmsr {
 
 // ------------------------------------------------------ coefficient tables
-// [variant][product r][quadrant q]
-static const int8_t kAlphaHost[2][7][4] = {
-    {{1, 0, 0, 1}, {0, 0, 1, 1}, {1, 0, 0, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}},
-    {{1, 0, 0, 0}, {0, 1, 0, 0}, {1, 1, -1, -1}, {0, 0, 0, 1}, {0, 0, 1, 1}, {-1, 0, 1, 1}, {1, 0, -1, 0}}};
-static const int8_t kBetaHost[2][7][4] = {
-    {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}},
-    {{1, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}, {1, -1, -1, 1}, {-1, 1, 0, 0}, {1, -1, 0, 1}, {0, -1, 0, 1}}};
-// [variant][quadrant q][product r]
-static const int8_t kGammaHost[2][4][7] = {
-    {{1, 0, 0, 1, -1, 0, 1}, {0, 0, 1, 0, 1, 0, 0}, {0, 1, 0, 1, 0, 0, 0}, {1, -1, 1, 0, 0, 1, 0}},
-    {{1, 1, 0, 0, 0, 0, 0}, {1, 0, 1, 0, 1, 1, 0}, {1, 0, 0, -1, 0, 1, 1}, {1, 0, 0, 0, 1, 1, 1}}};
-
-__constant__ int8_t kAlpha[2][7][4] = {
-    {{1, 0, 0, 1}, {0, 0, 1, 1}, {1, 0, 0, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}},
-    {{1, 0, 0, 0}, {0, 1, 0, 0}, {1, 1, -1, -1}, {0, 0, 0, 1}, {0, 0, 1, 1}, {-1, 0, 1, 1}, {1, 0, -1, 0}}};
-__constant__ int8_t kBeta[2][7][4] = {
-    {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}},
-    {{1, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}, {1, -1, -1, 1}, {-1, 1, 0, 0}, {1, -1, 0, 1}, {0, -1, 0, 1}}};
-__constant__ int8_t kGamma[2][4][7] = {
-    {{1, 0, 0, 1, -1, 0, 1}, {0, 0, 1, 0, 1, 0, 0}, {0, 1, 0, 1, 0, 0, 0}, {1, -1, 1, 0, 0, 1, 0}},
-    {{1, 1, 0, 0, 0, 0, 0}, {1, 0, 1, 0, 1, 1, 0}, {1, 0, 0, -1, 0, 1, 1}, {1, 0, 0, 0, 1, 1, 1}}};
+// One source for host and device: alpha / beta are [variant][product r]
+// [quadrant q], gamma is [variant][quadrant q][product r].  Kernels take the
+// variant as a template argument, so every coefficient is a compile-time
+// constant and the zero terms vanish from the generated code.
+__host__ __device__ constexpr int coef_alpha(int v, int r, int q) {
+  constexpr int8_t t[2][7][4] = {
+      {{1, 0, 0, 1}, {0, 0, 1, 1}, {1, 0, 0, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}},
+      {{1, 0, 0, 0}, {0, 1, 0, 0}, {1, 1, -1, -1}, {0, 0, 0, 1}, {0, 0, 1, 1}, {-1, 0, 1, 1}, {1, 0, -1, 0}}};
+  return t[v][r][q];
+}
+__host__ __device__ constexpr int coef_beta(int v, int r, int q) {
+  constexpr int8_t t[2][7][4] = {
+      {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}},
+      {{1, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}, {1, -1, -1, 1}, {-1, 1, 0, 0}, {1, -1, 0, 1}, {0, -1, 0, 1}}};
+  return t[v][r][q];
+}
+__host__ __device__ constexpr int coef_gamma(int v, int q, int r) {
+  constexpr int8_t t[2][4][7] = {
+      {{1, 0, 0, 1, -1, 0, 1}, {0, 0, 1, 0, 1, 0, 0}, {0, 1, 0, 1, 0, 0, 0}, {1, -1, 1, 0, 0, 1, 0}},
+      {{1, 1, 0, 0, 0, 0, 0}, {1, 0, 1, 0, 1, 1, 0}, {1, 0, 0, -1, 0, 1, 1}, {1, 0, 0, 0, 1, 1, 1}}};
+  return t[v][q][r];
+}
 
 namespace {
 
 template <typename T>
-__device__ __forceinline__ T apply(int8_t c, T acc, T x) {
+__device__ __forceinline__ T apply(int c, T acc, T x) {
   return c == 0 ? acc : (c > 0 ? acc + x : acc - x);
 }
 
-// Sum of +-1/0 terms in the fixed quadrant order 00, 01, 10, 11.
-template <typename T>
-__device__ __forceinline__ T combo4(const int8_t* c, T x0, T x1, T x2, T x3) {
+// Operand sum r of one side (0: alpha over A's quadrants, 1: beta over B's),
+// terms in the fixed quadrant order 00, 01, 10, 11.
+template <int VARIANT, int SIDE, typename T>
+__device__ __forceinline__ T combo4(int r, T x0, T x1, T x2, T x3) {
   T acc = T(0);
-  acc = apply(c[0], acc, x0);
-  acc = apply(c[1], acc, x1);
-  acc = apply(c[2], acc, x2);
-  acc = apply(c[3], acc, x3);
+  if constexpr (SIDE == 0) {
+    acc = apply(coef_alpha(VARIANT, r, 0), acc, x0);
+    acc = apply(coef_alpha(VARIANT, r, 1), acc, x1);
+    acc = apply(coef_alpha(VARIANT, r, 2), acc, x2);
+    acc = apply(coef_alpha(VARIANT, r, 3), acc, x3);
+  } else {
+    acc = apply(coef_beta(VARIANT, r, 0), acc, x0);
+    acc = apply(coef_beta(VARIANT, r, 1), acc, x1);
+    acc = apply(coef_beta(VARIANT, r, 2), acc, x2);
+    acc = apply(coef_beta(VARIANT, r, 3), acc, x3);
+  }
   return acc;
 }
 
-__device__ __forceinline__ const int8_t* coef_row(int variant, int side, int j) {
-  return side == 0 ? kAlpha[variant][j] : kBeta[variant][j];
+// ------------------------------------------------------- vector helpers
+// V consecutive elements through one 16-byte access when V * sizeof(T) is
+// 16 (the caller checks alignment), element by element otherwise.
+template <typename T, int V>
+__device__ __forceinline__ void vload(const T* __restrict__ p, T (&x)[V]) {
+  if constexpr (V * sizeof(T) == 16) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    memcpy(x, &u, 16);
+  } else {
+#pragma unroll
+    for (int t = 0; t < V; ++t) x[t] = p[t];
+  }
+}
+template <typename T, int V>
+__device__ __forceinline__ void vstore(T* __restrict__ p, const T (&x)[V]) {
+  if constexpr (V * sizeof(T) == 16) {
+    uint4 u;
+    memcpy(&u, x, 16);
+    *reinterpret_cast<uint4*>(p) = u;
+  } else {
+#pragma unroll
+    for (int t = 0; t < V; ++t) p[t] = x[t];
+  }
 }
 
 // Level transition for one operand side: source stack matrix r (2h x 2w,
 // row pitch src_ld, matrices src_stride apart) -> seven (h x w) matrices
-// 7r..7r+6 of the destination stack (contiguous).  One thread per element
-// position reads the four quadrants once and writes seven sums.
-template <typename T>
+// 7r..7r+6 of the destination stack (contiguous).  Blocks walk rows, threads
+// walk V-element column groups: each position's four quadrant values are
+// read once and its seven sums written once.
+template <typename T, int V, int VARIANT, int SIDE>
 __global__ void __launch_bounds__(256) pre_combine_kernel(const T* __restrict__ src, int64_t src_ld,
-                                                          int64_t src_stride, int64_t h, int64_t w,
-                                                          T* __restrict__ dst, int variant, int side) {
+                                                          int64_t src_stride, int h, int w,
+                                                          T* __restrict__ dst) {
   const int r = blockIdx.y;
   const T* s = src + (int64_t)r * src_stride;
-  T* d = dst + (int64_t)r * 7 * h * w;
-  const int64_t total = h * w;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / w, j = e - i * w;
-    const T x0 = s[i * src_ld + j], x1 = s[i * src_ld + w + j];
-    const T x2 = s[(h + i) * src_ld + j], x3 = s[(h + i) * src_ld + w + j];
+  const int64_t total = (int64_t)h * w;
+  T* d = dst + (int64_t)r * 7 * total;
+  const int wv = w / V;
+  for (int i = blockIdx.x; i < h; i += gridDim.x) {
+    const T* top = s + (int64_t)i * src_ld;
+    const T* bot = s + (int64_t)(h + i) * src_ld;
+    for (int jv = threadIdx.x; jv < wv; jv += blockDim.x) {
+      const int j = jv * V;
+      T x0[V], x1[V], x2[V], x3[V];
+      vload<T, V>(top + j, x0);
+      vload<T, V>(top + w + j, x1);
+      vload<T, V>(bot + j, x2);
+      vload<T, V>(bot + w + j, x3);
 #pragma unroll
-    for (int p = 0; p < 7; ++p) d[(int64_t)p * total + e] = combo4(coef_row(variant, side, p), x0, x1, x2, x3);
+      for (int p = 0; p < 7; ++p) {
+        T y[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) y[t] = combo4<VARIANT, SIDE>(p, x0[t], x1[t], x2[t], x3[t]);
+        vstore<T, V>(d + (int64_t)p * total + (int64_t)i * w + j, y);
+      }
+    }
   }
 }
 
@@ -100,33 +143,40 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 }
 
 // Last level, A side, FP32 mode: seven (h x w) sums written as bf16 hi/lo
-// rows of pitch Kp (columns w..Kp-1 zero).  One thread per 8 columns.
+// rows of pitch Kp (columns w..Kp-1 zero).  Blocks walk rows, threads walk
+// 8-column groups; `vec` = the source rows allow 16-byte loads.
+template <int VARIANT>
 __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
-    const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int64_t h, int64_t w,
-    int64_t Kp, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int variant) {
+    const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int h, int w, int Kp,
+    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int vec) {
   const int r = blockIdx.y;
   const float* s = src + (int64_t)r * src_stride;
-  const int64_t cpr = Kp / 8;
-  const int64_t total = h * cpr;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / cpr, c8 = (e - i * cpr) * 8;
-    float x[4][8];
+  for (int i = blockIdx.x; i < h; i += gridDim.x) {
+    for (int c8 = threadIdx.x * 8; c8 < Kp; c8 += blockDim.x * 8) {
+      float x[4][8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float* row = s + ((q >> 1) * h + i) * src_ld + (q & 1) * w;
+      for (int q = 0; q < 4; ++q) {
+        const float* row = s + (int64_t)((q >> 1) * h + i) * src_ld + (q & 1) * w;
+        if (vec && c8 + 8 <= w) {
+          const float4 a = *reinterpret_cast<const float4*>(row + c8);
+          const float4 b = *reinterpret_cast<const float4*>(row + c8 + 4);
+          x[q][0] = a.x; x[q][1] = a.y; x[q][2] = a.z; x[q][3] = a.w;
+          x[q][4] = b.x; x[q][5] = b.y; x[q][6] = b.z; x[q][7] = b.w;
+        } else {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) x[q][t] = (c8 + t < w) ? row[c8 + t] : 0.f;
-    }
+          for (int t = 0; t < 8; ++t) x[q][t] = (c8 + t < w) ? row[c8 + t] : 0.f;
+        }
+      }
 #pragma unroll
-    for (int p = 0; p < 7; ++p) {
-      const int8_t* c = kAlpha[variant][p];
-      __align__(16) __nv_bfloat16 hh[8], ll[8];
+      for (int p = 0; p < 7; ++p) {
+        __align__(16) __nv_bfloat16 hh[8], ll[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) split_bf16(combo4(c, x[0][t], x[1][t], x[2][t], x[3][t]), hh[t], ll[t]);
-      const int64_t off = ((int64_t)(r * 7 + p) * h + i) * Kp + c8;
-      *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(hh);
-      *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(ll);
+        for (int t = 0; t < 8; ++t)
+          split_bf16(combo4<VARIANT, 0>(p, x[0][t], x[1][t], x[2][t], x[3][t]), hh[t], ll[t]);
+        const int64_t off = ((int64_t)(r * 7 + p) * h + i) * Kp + c8;
+        *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(hh);
+        *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(ll);
+      }
     }
   }
 }
@@ -134,9 +184,10 @@ __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
 // Last level, B side, FP32 mode: source stack matrix r is (2h x 2w) = (k x n);
 // the seven sums T_p (h x w) are written transposed as bf16 hi/lo (w x Kp).
 // Tile: 64 k x 32 n of each quadrant through shared memory.
+template <int VARIANT>
 __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
     const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int64_t h, int64_t w,
-    int64_t Kp, __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT, int variant) {
+    int64_t Kp, __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT) {
   __shared__ float tile[4][64][33];
   const int r = blockIdx.z;
   const float* s = src + (int64_t)r * src_stride;
@@ -157,12 +208,12 @@ __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
   if (gn >= w) return;
 #pragma unroll
   for (int p = 0; p < 7; ++p) {
-    const int8_t* c = kBeta[variant][p];
     __align__(16) __nv_bfloat16 hh[8], ll[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int kk = chunk * 8 + t;
-      split_bf16(combo4(c, tile[0][kk][row], tile[1][kk][row], tile[2][kk][row], tile[3][kk][row]), hh[t], ll[t]);
+      split_bf16(combo4<VARIANT, 1>(p, tile[0][kk][row], tile[1][kk][row], tile[2][kk][row], tile[3][kk][row]),
+                 hh[t], ll[t]);
     }
     const int64_t off = ((int64_t)(r * 7 + p) * w + gn) * Kp + k0 + chunk * 8;
     *reinterpret_cast<uint4*>(hiT + off) = *reinterpret_cast<const uint4*>(hh);
@@ -170,39 +221,147 @@ __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
   }
 }
 
+// How a post-addition pass sums: in the products' own type, in FP64
+// arithmetic, or (FP32 products) as an error-free double-float sum.
+enum PostSum { kSumPlain = 0, kSumF64 = 1, kSumDoubleFloat = 2 };
+
+// s + e = a + b exactly (Knuth's TwoSum; round-to-nearest adds, no
+// contraction or reassociation).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 // Post-additions: products 7r..7r+6 (h x w each, contiguous) -> the four
 // quadrants of destination matrix r (2h x 2w, pitch dst_ld, dst_stride
-// apart).  Sums run in ACC precision in product order; one thread per
-// element position reads each product once and writes four quadrants.
-template <typename TP, typename ACC, typename TOUT>
-__global__ void __launch_bounds__(256) post_combine_kernel(const TP* __restrict__ P, int64_t h, int64_t w,
-                                                           TOUT* __restrict__ dst, int64_t dst_ld,
-                                                           int64_t dst_stride, int variant) {
+// apart).  Terms are added in product order, after the destination's old
+// value when `accumulate` is set.  kSumDoubleFloat is Sum2 of Ogita, Rump
+// and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005):
+// the running sum carries its exact rounding errors separately, so the
+// result is as accurate as a sum in twice the precision, rounded once.
+template <typename TP, int V, int MODE, int VARIANT>
+__global__ void __launch_bounds__(256) post_combine_kernel(const TP* __restrict__ P, int h, int w,
+                                                           TP* __restrict__ dst, int64_t dst_ld,
+                                                           int64_t dst_stride, int accumulate) {
   const int r = blockIdx.y;
-  const TP* pp = P + (int64_t)r * 7 * h * w;
-  TOUT* d = dst + (int64_t)r * dst_stride;
-  const int64_t total = h * w;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / w, j = e - i * w;
-    ACC x[7];
+  const int64_t total = (int64_t)h * w;
+  const TP* pp = P + (int64_t)r * 7 * total;
+  TP* d = dst + (int64_t)r * dst_stride;
+  const int wv = w / V;
+  for (int i = blockIdx.x; i < h; i += gridDim.x) {
+    for (int jv = threadIdx.x; jv < wv; jv += blockDim.x) {
+      const int64_t e = (int64_t)i * w + jv * V;
+      TP x[7][V];
 #pragma unroll
-    for (int p = 0; p < 7; ++p) x[p] = (ACC)pp[(int64_t)p * total + e];
+      for (int p = 0; p < 7; ++p) vload<TP, V>(pp + (int64_t)p * total + e, x[p]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      ACC acc = ACC(0);
+      for (int q = 0; q < 4; ++q) {
+        TP* out = d + (int64_t)((q >> 1) * h + i) * dst_ld + (q & 1) * w + jv * V;
+        TP y[V];
+        if (accumulate) vload<TP, V>(out, y);
 #pragma unroll
-      for (int p = 0; p < 7; ++p) acc = apply(kGamma[variant][q][p], acc, x[p]);
-      d[((q >> 1) * h + i) * dst_ld + (q & 1) * w + j] = (TOUT)acc;
+        for (int t = 0; t < V; ++t) {
+          if constexpr (MODE == kSumDoubleFloat) {
+            float sum = accumulate ? (float)y[t] : 0.f, err = 0.f;
+#pragma unroll
+            for (int p = 0; p < 7; ++p) {
+              const int g = coef_gamma(VARIANT, q, p);
+              if (g == 0) continue;
+              float s2, e2;
+              two_sum(sum, g > 0 ? (float)x[p][t] : -(float)x[p][t], s2, e2);
+              sum = s2;
+              err = __fadd_rn(err, e2);
+            }
+            y[t] = (TP)__fadd_rn(sum, err);
+          } else if constexpr (MODE == kSumF64) {
+            double acc = accumulate ? (double)y[t] : 0.0;
+#pragma unroll
+            for (int p = 0; p < 7; ++p) acc = apply(coef_gamma(VARIANT, q, p), acc, (double)x[p][t]);
+            y[t] = (TP)acc;
+          } else {
+            TP acc = accumulate ? y[t] : TP(0);
+#pragma unroll
+            for (int p = 0; p < 7; ++p) acc = apply(coef_gamma(VARIANT, q, p), acc, x[p][t]);
+            y[t] = acc;
+          }
+        }
+        vstore<TP, V>(out, y);
+      }
     }
   }
 }
 
-unsigned grid_for(int64_t work) {
-  int64_t b = (work + 255) / 256;
-  const int64_t cap = (int64_t)kNumSMs * 16;
-  if (b > cap) b = cap;
+// Blocks per matrix for a row-walking pass over R matrices of h rows with
+// `threads`-thread blocks: about one full wave of the GPU in total.
+unsigned rows_grid(int64_t h, int64_t R, int threads) {
+  const int64_t per_sm = 2048 / threads < 32 ? 2048 / threads : 32;
+  int64_t b = ((int64_t)kNumSMs * per_sm + R - 1) / R;
+  if (b > h) b = h;
   return (unsigned)(b < 1 ? 1 : b);
+}
+
+// Threads per block for rows of `groups` column groups (a multiple of 32,
+// at most 256).
+int row_threads(int64_t groups) {
+  if (groups >= 256) return 256;
+  const int64_t t = (groups + 31) / 32 * 32;
+  return (int)(t < 32 ? 32 : t);
+}
+
+bool aligned_to(const void* p, int64_t bytes) {
+  return (reinterpret_cast<uintptr_t>(p) % (uintptr_t)bytes) == 0;
+}
+
+template <typename T, int VARIANT, int SIDE>
+void pre_combine_v(bool vec, dim3 g, int threads, cudaStream_t st, const T* src, int64_t src_ld,
+                   int64_t src_stride, int h, int w, T* dst) {
+  if (vec)
+    pre_combine_kernel<T, 16 / sizeof(T), VARIANT, SIDE><<<g, threads, 0, st>>>(src, src_ld, src_stride, h, w, dst);
+  else
+    pre_combine_kernel<T, 1, VARIANT, SIDE><<<g, threads, 0, st>>>(src, src_ld, src_stride, h, w, dst);
+}
+
+template <typename T>
+cudaError_t launch_pre_combine(const T* src, int64_t src_ld, int64_t src_stride, int64_t h, int64_t w,
+                               int64_t R, T* dst, int variant, int side, cudaStream_t st) {
+  constexpr int V = 16 / sizeof(T);
+  const bool vec = w % V == 0 && src_ld % V == 0 && src_stride % V == 0 && aligned_to(src, 16) &&
+                   aligned_to(dst, 16);
+  const int threads = row_threads(vec ? w / V : w);
+  const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+  const int hh = (int)h, ww = (int)w;
+  if (variant == 0 && side == 0) pre_combine_v<T, 0, 0>(vec, g, threads, st, src, src_ld, src_stride, hh, ww, dst);
+  if (variant == 0 && side == 1) pre_combine_v<T, 0, 1>(vec, g, threads, st, src, src_ld, src_stride, hh, ww, dst);
+  if (variant == 1 && side == 0) pre_combine_v<T, 1, 0>(vec, g, threads, st, src, src_ld, src_stride, hh, ww, dst);
+  if (variant == 1 && side == 1) pre_combine_v<T, 1, 1>(vec, g, threads, st, src, src_ld, src_stride, hh, ww, dst);
+  return cudaGetLastError();
+}
+
+template <typename TP, int MODE, int VARIANT>
+void post_combine_v(bool vec, dim3 g, int threads, cudaStream_t st, const TP* P, int h, int w, TP* dst,
+                    int64_t dst_ld, int64_t dst_stride, int accumulate) {
+  if (vec)
+    post_combine_kernel<TP, 16 / sizeof(TP), MODE, VARIANT><<<g, threads, 0, st>>>(P, h, w, dst, dst_ld,
+                                                                                   dst_stride, accumulate);
+  else
+    post_combine_kernel<TP, 1, MODE, VARIANT><<<g, threads, 0, st>>>(P, h, w, dst, dst_ld, dst_stride,
+                                                                     accumulate);
+}
+
+template <typename TP, int MODE>
+cudaError_t launch_post_combine(const TP* P, int64_t h, int64_t w, int64_t R, TP* dst, int64_t dst_ld,
+                                int64_t dst_stride, int variant, int accumulate, cudaStream_t st) {
+  constexpr int V = 16 / sizeof(TP);
+  const bool vec = w % V == 0 && dst_ld % V == 0 && dst_stride % V == 0 && aligned_to(P, 16) &&
+                   aligned_to(dst, 16);
+  const int threads = row_threads(vec ? w / V : w);
+  const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+  if (variant == 0)
+    post_combine_v<TP, MODE, 0>(vec, g, threads, st, P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
+  else
+    post_combine_v<TP, MODE, 1>(vec, g, threads, st, P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
+  return cudaGetLastError();
 }
 
 int64_t pw7(int l) {
@@ -269,45 +428,54 @@ StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
   return s;
 }
 
-// Operand side of the breadth-first expansion (FP32 mode).
+// Operand side of the breadth-first expansion (FP32 mode).  X is rows x
+// cols with row pitch ld.
 cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t rows, int64_t cols,
-                       uint8_t* ws, const StrassenLayout& S, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                       cudaStream_t st) {
+                       int64_t ld, uint8_t* ws, const StrassenLayout& S, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, cudaStream_t st) {
   const float* src = X;
-  int64_t src_ld = cols, src_stride = 0;
+  int64_t src_ld = ld, src_stride = 0;
   for (int l = 1; l <= L; ++l) {
     const int64_t h = rows >> l, w = cols >> l, R = pw7(l - 1);
     if (l < L) {
       float* dst = reinterpret_cast<float*>(ws + ((l & 1) ? S.off_pp1 : 0));
-      pre_combine_kernel<float><<<dim3(grid_for(h * w), (unsigned)R), 256, 0, st>>>(
-          src, src_ld, src_stride, h, w, dst, variant, side);
+      MMSR_CUDA_TRY(launch_pre_combine<float>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
       src = dst;
       src_ld = w;
       src_stride = h * w;  // stacks hold contiguous (h x w) matrices
     } else if (side == 0) {
-      pre_combine_split_rows_kernel<<<dim3(grid_for(h * (S.KpL / 8)), (unsigned)R), 256, 0, st>>>(
-          src, src_ld, src_stride, h, w, S.KpL, hi, lo, variant);
+      const int vec = (w % 4 == 0 && src_ld % 4 == 0 && src_stride % 4 == 0 && aligned_to(src, 16)) ? 1 : 0;
+      const int threads = row_threads(S.KpL / 8);
+      const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+      if (variant == 0)
+        pre_combine_split_rows_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                               (int)S.KpL, hi, lo, vec);
+      else
+        pre_combine_split_rows_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                               (int)S.KpL, hi, lo, vec);
+      MMSR_CUDA_TRY(cudaGetLastError());
     } else {
       dim3 g((unsigned)(S.KpL / 64), (unsigned)((w + 31) / 32), (unsigned)R);
-      pre_combine_split_transpose_kernel<<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo,
-                                                            variant);
+      if (variant == 0)
+        pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
+      else
+        pre_combine_split_transpose_kernel<1><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
+      MMSR_CUDA_TRY(cudaGetLastError());
     }
-    MMSR_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
 }
 
 // Operand side, FP64 mode: FP64 stacks all the way to the leaves.
 cudaError_t expand_f64(int L, int variant, int side, const double* X, int64_t rows, int64_t cols,
-                       uint8_t* ws, const StrassenLayout& S, double* leaf, cudaStream_t st) {
+                       int64_t ld, uint8_t* ws, const StrassenLayout& S, double* leaf,
+                       cudaStream_t st) {
   const double* src = X;
-  int64_t src_ld = cols, src_stride = 0;
+  int64_t src_ld = ld, src_stride = 0;
   for (int l = 1; l <= L; ++l) {
     const int64_t h = rows >> l, w = cols >> l, R = pw7(l - 1);
     double* dst = (l < L) ? reinterpret_cast<double*>(ws + ((l & 1) ? S.off_pp1 : 0)) : leaf;
-    pre_combine_kernel<double><<<dim3(grid_for(h * w), (unsigned)R), 256, 0, st>>>(
-        src, src_ld, src_stride, h, w, dst, variant, side);
-    MMSR_CUDA_TRY(cudaGetLastError());
+    MMSR_CUDA_TRY(launch_pre_combine<double>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
     src = dst;
     src_ld = w;
     src_stride = h * w;
@@ -315,60 +483,36 @@ cudaError_t expand_f64(int L, int variant, int side, const double* X, int64_t ro
   return cudaSuccess;
 }
 
-// Bottom-up post-additions from the leaf products to C.
+// Bottom-up post-additions from the leaf products to C (pitch ldc).  The
+// top level adds into C's old values when `accumulate` is set and sums in
+// `top_mode` (PostSum).
 template <typename TP>
 cudaError_t fold(int L, int variant, const TP* P, int64_t m, int64_t n, uint8_t* ws,
-                 const StrassenLayout& S, TP* C, bool top_f64, cudaStream_t st) {
+                 const StrassenLayout& S, TP* C, int64_t ldc, int accumulate, int top_mode,
+                 cudaStream_t st) {
   const TP* src = P;
   for (int l = L; l >= 1; --l) {
     const int64_t h = m >> l, w = n >> l, R = pw7(l - 1);
-    dim3 g(grid_for(h * w), (unsigned)R);
     if (l > 1) {
       TP* dst = reinterpret_cast<TP*>(ws + (((l - 1) & 1) ? S.off_pp1 : 0));
-      post_combine_kernel<TP, TP, TP><<<g, 256, 0, st>>>(src, h, w, dst, 2 * w, 4 * h * w, variant);
+      MMSR_CUDA_TRY((launch_post_combine<TP, kSumPlain>(src, h, w, R, dst, 2 * w, 4 * h * w, variant, 0, st)));
       src = dst;
-    } else if (top_f64) {
-      post_combine_kernel<TP, double, TP><<<g, 256, 0, st>>>(src, h, w, C, n, 0, variant);
+    } else if (top_mode == kSumDoubleFloat) {
+      MMSR_CUDA_TRY((launch_post_combine<TP, kSumDoubleFloat>(src, h, w, 1, C, ldc, 0, variant, accumulate, st)));
+    } else if (top_mode == kSumF64) {
+      MMSR_CUDA_TRY((launch_post_combine<TP, kSumF64>(src, h, w, 1, C, ldc, 0, variant, accumulate, st)));
     } else {
-      post_combine_kernel<TP, TP, TP><<<g, 256, 0, st>>>(src, h, w, C, n, 0, variant);
+      MMSR_CUDA_TRY((launch_post_combine<TP, kSumPlain>(src, h, w, 1, C, ldc, 0, variant, accumulate, st)));
     }
-    MMSR_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
 }
 
-}  // namespace
-
-void strassen_tables(int variant, int8_t* alpha, int8_t* beta, int8_t* gamma) {
-  memcpy(alpha, kAlphaHost[variant], 28);
-  memcpy(beta, kBetaHost[variant], 28);
-  memcpy(gamma, kGammaHost[variant], 28);
-}
-
-int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
-  memset(p, 0, sizeof(*p));
-  if (sr != MM_SR_PLUS_TIMES_F32 && sr != MM_SR_PLUS_TIMES_F64 && sr != MM_SR_PLUS_TIMES_F64ACC)
-    return MM_ERR_UNSUPPORTED;
-  const StrassenLayout S = strassen_layout(levels, sr, m, n, k);
-  p->levels = levels;
-  p->split_k = 1;
-  p->tile_m = sr == MM_SR_PLUS_TIMES_F64 ? 64 : 128;
-  p->tile_n = sr == MM_SR_PLUS_TIMES_F32 ? 256 : 64;
-  p->tile_k = sr == MM_SR_PLUS_TIMES_F32 ? 64 : (sr == MM_SR_PLUS_TIMES_F64 ? 16 : 32);
-  p->kernel = sr == MM_SR_PLUS_TIMES_F32 ? 2 : (sr == MM_SR_PLUS_TIMES_F64 ? 0 : 3);
-  p->workspace_min = S.total;
-  p->workspace_used = S.total;
-  (void)budget;
-  return MM_OK;
-}
-
-int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,
-                 const void* B, void* C, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (sr != MM_SR_PLUS_TIMES_F32 && sr != MM_SR_PLUS_TIMES_F64 && sr != MM_SR_PLUS_TIMES_F64ACC)
-    return MM_ERR_UNSUPPORTED;
-  const StrassenLayout S = strassen_layout(levels, sr, m, n, k);
-  if ((size_t)S.total > ws_bytes) return MM_ERR_WORKSPACE;
-  uint8_t* w = static_cast<uint8_t*>(ws);
+// One Strassen product on strided views: C (pitch ldc) := [C +] A (pitch
+// lda) x B (pitch ldb), `levels` >= 1 levels, workspace laid out by S.
+int run_view(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,
+             int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc, int accumulate, uint8_t* w,
+             const StrassenLayout& S, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (sr == MM_SR_PLUS_TIMES_F32) {
     auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + S.off_ahi);
@@ -378,14 +522,17 @@ int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t 
     float* P = reinterpret_cast<float*>(w + S.off_p);
     {
       TraceScope tr(kTrStrassenCombine, st);
-      e = expand_f32(levels, variant, 0, static_cast<const float*>(A), m, k, w, S, ahi, alo, st);
+      e = expand_f32(levels, variant, 0, static_cast<const float*>(A), m, k, lda, w, S, ahi, alo, st);
       if (e == cudaSuccess)
-        e = expand_f32(levels, variant, 1, static_cast<const float*>(B), k, n, w, S, bhi, blo, st);
+        e = expand_f32(levels, variant, 1, static_cast<const float*>(B), k, n, ldb, w, S, bhi, blo, st);
     }
     if (e == cudaSuccess) e = launch_bf16x3_batched(ahi, alo, bhi, blo, P, S.mL, S.nL, S.KpL, (int)S.leaves, st);
     if (e == cudaSuccess) {
       TraceScope tr(kTrStrassenPost, st);
-      e = fold<float>(levels, variant, P, m, n, w, S, static_cast<float*>(C), levels >= 3, st);
+      // Wide top-level sums once the operand and product sums of three or
+      // more levels have grown the cancellation error.
+      const int top = levels >= 3 ? (g_strassen_top_f64 ? kSumF64 : kSumDoubleFloat) : kSumPlain;
+      e = fold<float>(levels, variant, P, m, n, w, S, static_cast<float*>(C), ldc, accumulate, top, st);
     }
   } else {
     double* la = reinterpret_cast<double*>(w + S.off_ahi);
@@ -393,9 +540,9 @@ int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t 
     double* P = reinterpret_cast<double*>(w + S.off_p);
     {
       TraceScope tr(kTrStrassenCombine, st);
-      e = expand_f64(levels, variant, 0, static_cast<const double*>(A), m, k, w, S, la, st);
+      e = expand_f64(levels, variant, 0, static_cast<const double*>(A), m, k, lda, w, S, la, st);
       if (e == cudaSuccess)
-        e = expand_f64(levels, variant, 1, static_cast<const double*>(B), k, n, w, S, lb, st);
+        e = expand_f64(levels, variant, 1, static_cast<const double*>(B), k, n, ldb, w, S, lb, st);
     }
     if (e == cudaSuccess) {
       if (sr == MM_SR_PLUS_TIMES_F64ACC) {
@@ -407,10 +554,94 @@ int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t 
     }
     if (e == cudaSuccess) {
       TraceScope tr(kTrStrassenPost, st);
-      e = fold<double>(levels, variant, P, m, n, w, S, static_cast<double*>(C), false, st);
+      e = fold<double>(levels, variant, P, m, n, w, S, static_cast<double*>(C), ldc, accumulate, kSumPlain, st);
     }
   }
-  return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+  return e == cudaSuccess ? MM_OK : report_cuda(e, "Strassen level pass");
+}
+
+bool strassen_semiring(int sr) {
+  return sr == MM_SR_PLUS_TIMES_F32 || sr == MM_SR_PLUS_TIMES_F64 || sr == MM_SR_PLUS_TIMES_F64ACC;
+}
+
+void fill_plan(int levels, int sr, int64_t total, mm_plan_t* p) {
+  memset(p, 0, sizeof(*p));
+  p->levels = levels;
+  p->split_k = 1;
+  p->tile_m = sr == MM_SR_PLUS_TIMES_F64 ? 64 : 128;
+  p->tile_n = sr == MM_SR_PLUS_TIMES_F32 ? 256 : 64;
+  p->tile_k = sr == MM_SR_PLUS_TIMES_F32 ? 64 : (sr == MM_SR_PLUS_TIMES_F64 ? 16 : 32);
+  p->kernel = sr == MM_SR_PLUS_TIMES_F32 ? 2 : (sr == MM_SR_PLUS_TIMES_F64 ? 0 : 3);
+  p->workspace_min = total;
+  p->workspace_used = total;
+}
+
+}  // namespace
+
+int g_strassen_top_f64 = 0;  // mm_set_option(MM_OPT_STRASSEN_TOP_F64, ...)
+
+void strassen_tables(int variant, int8_t* alpha, int8_t* beta, int8_t* gamma) {
+  for (int r = 0; r < 7; ++r)
+    for (int q = 0; q < 4; ++q) {
+      alpha[r * 4 + q] = (int8_t)coef_alpha(variant, r, q);
+      beta[r * 4 + q] = (int8_t)coef_beta(variant, r, q);
+      gamma[q * 7 + r] = (int8_t)coef_gamma(variant, q, r);
+    }
+}
+
+int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
+  memset(p, 0, sizeof(*p));
+  if (!strassen_semiring(sr)) return MM_ERR_UNSUPPORTED;
+  fill_plan(levels, sr, strassen_layout(levels, sr, m, n, k).total, p);
+  (void)budget;
+  return MM_OK;
+}
+
+int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,
+                 const void* B, void* C, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!strassen_semiring(sr)) return MM_ERR_UNSUPPORTED;
+  const StrassenLayout S = strassen_layout(levels, sr, m, n, k);
+  if ((size_t)S.total > ws_bytes) return MM_ERR_WORKSPACE;
+  return run_view(levels, variant, sr, m, n, k, A, k, B, n, C, n, 0, static_cast<uint8_t*>(ws), S, st);
+}
+
+// STAR-Strassen-1 (Theorem star-strassen-1): the top `classic` levels are
+// the classic 8-way recursion of Eq. mm-dac run in place (no temporaries:
+// every block product adds into its C block, the k-halves one after the
+// other as in CO2), and each of the 8^classic block products runs `levels`
+// Strassen levels.  The Strassen temporaries are those of one block product,
+// reused by the next, so the workspace shrinks by 4^classic while the work
+// grows by (8/7)^classic against Strassen on all classic + levels levels.
+int plan_star_strassen(int classic, int levels, int sr, int64_t m, int64_t n, int64_t k,
+                       size_t budget, mm_plan_t* p) {
+  if (!strassen_semiring(sr)) return MM_ERR_UNSUPPORTED;
+  if (levels == 0) return plan_semiring(sr, m, n, k, budget, p);
+  fill_plan(levels, sr, strassen_layout(levels, sr, m >> classic, n >> classic, k >> classic).total, p);
+  return MM_OK;
+}
+
+int run_star_strassen(int classic, int levels, int variant, int sr, int64_t m, int64_t n, int64_t k,
+                      const void* A, const void* B, void* C, void* ws, size_t ws_bytes,
+                      cudaStream_t st) {
+  if (!strassen_semiring(sr)) return MM_ERR_UNSUPPORTED;
+  if (levels == 0) return run_semiring(sr, m, n, k, A, B, C, ws, ws_bytes, st);
+  const int64_t g = (int64_t)1 << classic;
+  const int64_t bm = m >> classic, bn = n >> classic, bk = k >> classic;
+  const StrassenLayout S = strassen_layout(levels, sr, bm, bn, bk);
+  if ((size_t)S.total > ws_bytes) return MM_ERR_WORKSPACE;
+  const int64_t eb = sr == MM_SR_PLUS_TIMES_F32 ? 4 : 8;
+  const uint8_t* a = static_cast<const uint8_t*>(A);
+  const uint8_t* b = static_cast<const uint8_t*>(B);
+  uint8_t* c = static_cast<uint8_t*>(C);
+  for (int64_t t = 0; t < g; ++t)
+    for (int64_t I = 0; I < g; ++I)
+      for (int64_t J = 0; J < g; ++J) {
+        const int rc = run_view(levels, variant, sr, bm, bn, bk, a + (I * bm * k + t * bk) * eb, k,
+                                b + (t * bk * n + J * bn) * eb, n, c + (I * bm * n + J * bn) * eb, n,
+                                t > 0 ? 1 : 0, static_cast<uint8_t*>(ws), S, st);
+        if (rc != MM_OK) return rc;
+      }
+  return MM_OK;
 }
 
 }  // namespace mmsr

@@ -23,7 +23,9 @@ namespace {
 __device__ int g_tc_status;  // device status word of this translation unit
 }
 
-int g_tc_pair_mode = 1;  // 1: CTA pairs multicast B when the product has >= 2 tile rows
+// CTA pairs multicasting B: correct but measured no faster here (the ring's
+// latency, not operand bandwidth, limited the kernel), so off by default.
+int g_tc_pair_mode = 0;
 
 // ------------------------------------------------------------ tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -66,15 +68,19 @@ namespace {
 constexpr int BM = 128, BK = 64;  // BK: k alignment of the split operands
 
 // GEMM k-block (64: 128-byte swizzled rows, 32: 64-byte rows), ring depth
-// and TMEM chunk length (in k-blocks).
+// and TMEM chunk length (in k-blocks).  Measured at n = 8192 / 16384: 32-wide
+// blocks in a 4-deep ring beat 64-wide blocks in a 2-deep ring (the ring
+// hides three blocks of TMA latency instead of one), and 256-k chunks beat
+// 128-k chunks (fewer drain handshakes) at 4.52e-6 vs 4.46e-6 error; chunks
+// of 512 k / 1024 k gain ~1-2% more but raise the error to 4.8e-6 / 5.6e-6.
 #ifndef MMSR_TC_BK
-#define MMSR_TC_BK 64
+#define MMSR_TC_BK 32
 #endif
 #ifndef MMSR_TC_STAGES
-#define MMSR_TC_STAGES 2
+#define MMSR_TC_STAGES 4
 #endif
 #ifndef MMSR_TC_CHUNK
-#define MMSR_TC_CHUNK 2
+#define MMSR_TC_CHUNK 8
 #endif
 constexpr int kTcBK = MMSR_TC_BK;
 static_assert(BK % kTcBK == 0, "the GEMM k-block must divide the operand k alignment");

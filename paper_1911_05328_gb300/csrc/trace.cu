@@ -14,7 +14,7 @@ const char* const kNames[kTraceKernels] = {
     "minplus_leaf", "min_reduce",   "dfma_leaf",   "sum_reduce_f64", "split_bf16x2",
     "tc_bf16x3",    "sum_reduce_f32", "split_f64_slices", "tc_f64acc", "strassen_combine",
     "strassen_post", "batched",     "orand_leaf",  "or_reduce",      "minplus16_leaf",
-    "range_scan",   "orand_pack"};
+    "range_scan",   "orand_pack", "closure_aux"};
 
 struct Rec {
   int id;

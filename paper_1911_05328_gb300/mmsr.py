@@ -28,6 +28,9 @@ MM_STRASSEN_WINOGRAD = 1
 MM_OPT_MINPLUS_PACKED = 1
 MM_OPT_MINPLUS_STREAMK = 2
 MM_OPT_TC_PAIR = 3
+MM_OPT_STRASSEN_TOP_F64 = 4
+
+MM_CLOSURE_EARLY_EXIT = 1
 
 MM_OK = 0
 MM_ERR_ARG = -1
@@ -88,6 +91,14 @@ def load(path: str = LIB_PATH):
             lib.mm_version.argtypes = []
             lib.mm_set_option.argtypes = [i32, i32]
             lib.mm_set_option.restype = ctypes.c_int
+            lib.mm_star_strassen.argtypes = [i32, i32, i32, i32, i64, i64, i64, vp, vp, vp, vp, sz, vp]
+            lib.mm_star_strassen.restype = ctypes.c_int
+            lib.mm_star_strassen_query.argtypes = [i32, i32, i32, i64, i64, i64, sz, ctypes.POINTER(mm_plan_t)]
+            lib.mm_star_strassen_query.restype = ctypes.c_int
+            lib.mm_closure.argtypes = [i32, i64, vp, vp, vp, sz, i32, ctypes.POINTER(ctypes.c_int), vp]
+            lib.mm_closure.restype = ctypes.c_int
+            lib.mm_closure_query.argtypes = [i32, i64, sz, ctypes.POINTER(mm_plan_t)]
+            lib.mm_closure_query.restype = ctypes.c_int
             for f in ("mm_semiring", "mm_strassen", "mm_batched", "mm_plan_query",
                       "mm_last_device_status", "mm_version"):
                 getattr(lib, f).restype = ctypes.c_int
@@ -143,6 +154,42 @@ def mm_strassen(levels, variant, semiring, m, n, k, A, B, C, workspace=None, wor
                             _addr(A), _addr(B), _addr(C), _addr(workspace), int(workspace_bytes),
                             _stream(stream))
     return _check(rc, "mm_strassen", check)
+
+
+def mm_closure(semiring, n, A, C, workspace=None, workspace_bytes=0, flags=0, stream=None,
+               check=True):
+    """C := A* by repeated squaring; returns (status, squarings run)."""
+    sq = ctypes.c_int(0)
+    rc = load().mm_closure(int(semiring), int(n), _addr(A), _addr(C), _addr(workspace),
+                           int(workspace_bytes), int(flags), ctypes.byref(sq), _stream(stream))
+    _check(rc, "mm_closure", check)
+    return rc, sq.value
+
+
+def mm_closure_query(semiring, n, workspace_bytes=0, check=True) -> mm_plan_t:
+    plan = mm_plan_t()
+    rc = load().mm_closure_query(int(semiring), int(n), int(workspace_bytes), ctypes.byref(plan))
+    _check(rc, "mm_closure_query", check)
+    plan.status = rc
+    return plan
+
+
+def mm_star_strassen(classic_levels, levels, variant, semiring, m, n, k, A, B, C, workspace=None,
+                     workspace_bytes=0, stream=None, check=True) -> int:
+    rc = load().mm_star_strassen(int(classic_levels), int(levels), int(variant), int(semiring), int(m),
+                                 int(n), int(k), _addr(A), _addr(B), _addr(C), _addr(workspace),
+                                 int(workspace_bytes), _stream(stream))
+    return _check(rc, "mm_star_strassen", check)
+
+
+def mm_star_strassen_query(classic_levels, levels, semiring, m, n, k, workspace_bytes=0,
+                           check=True) -> mm_plan_t:
+    plan = mm_plan_t()
+    rc = load().mm_star_strassen_query(int(classic_levels), int(levels), int(semiring), int(m), int(n),
+                                       int(k), int(workspace_bytes), ctypes.byref(plan))
+    _check(rc, "mm_star_strassen_query", check)
+    plan.status = rc
+    return plan
 
 
 def _problems(problems):

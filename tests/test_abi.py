@@ -99,3 +99,61 @@ def test_split_never_exceeds_budget_or_kblocks(lib):
                 # monotone in the budget
                 q = mmsr.mm_plan_query(sr, -1, m, n, k, budget + m * n * accb)
                 assert q.split_k >= p.split_k
+
+
+def test_closure_argument_checks(lib):
+    # (+, x) has no idempotent (+): the closure is not defined by squaring.
+    for sr in (mmsr.MM_SR_PLUS_TIMES_F64, mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_PLUS_TIMES_F64ACC):
+        rc, _ = mmsr.mm_closure(sr, 8, FAKE, FAKE, stream=0, check=False)
+        assert rc == mmsr.MM_ERR_UNSUPPORTED
+    sr = mmsr.MM_SR_MIN_PLUS_I32
+    assert mmsr.mm_closure(99, 8, FAKE, FAKE, stream=0, check=False)[0] == mmsr.MM_ERR_ARG
+    assert mmsr.mm_closure(sr, -1, FAKE, FAKE, stream=0, check=False)[0] == mmsr.MM_ERR_ARG
+    assert mmsr.mm_closure(sr, 8, None, FAKE, stream=0, check=False)[0] == mmsr.MM_ERR_ARG
+    assert mmsr.mm_closure(sr, 8, FAKE, FAKE, flags=4, stream=0, check=False)[0] == mmsr.MM_ERR_ARG
+    assert mmsr.mm_closure(sr, 8, FAKE + 4, FAKE, stream=0, check=False)[0] == mmsr.MM_ERR_ALIGN
+    assert mmsr.mm_closure(sr, 0, None, None, stream=0, check=False) == (mmsr.MM_OK, 0)
+    # below the minimum workspace: rejected before any launch
+    p = mmsr.mm_closure_query(sr, 100)
+    rc, _ = mmsr.mm_closure(sr, 100, FAKE, FAKE, FAKE, int(p.workspace_min) - 16, stream=0, check=False)
+    assert rc == mmsr.MM_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("n,squarings", [(1, 0), (2, 0), (3, 1), (5, 2), (17, 4), (18, 5), (4096, 12)])
+def test_closure_plan(lib, n, squarings):
+    # 2^T >= n - 1 arcs, T minimal; the closure's own buffers come first and
+    # every extra n x n buffer of budget buys one more k-slice per squaring.
+    for sr, eb in ((mmsr.MM_SR_MIN_PLUS_I32, 4), (mmsr.MM_SR_OR_AND_U8, 1)):
+        p = mmsr.mm_closure_query(sr, n, 0)
+        assert p.levels == squarings
+        prefix = 16 + -(-n * n * eb // 16) * 16
+        sq = mmsr.mm_plan_query(sr, -1, n, n, n, 0)
+        assert p.workspace_min == prefix + sq.workspace_min
+    big = mmsr.mm_closure_query(mmsr.MM_SR_MIN_PLUS_I32, 4096, 16 + 4096 * 4096 * 4 + 2 * 4096 * 4096 * 4)
+    assert big.split_k == 3 and big.workspace_used == 16 + 3 * 4096 * 4096 * 4
+
+
+def test_star_strassen_argument_checks_and_workspace(lib):
+    sr = mmsr.MM_SR_PLUS_TIMES_F32
+    W = mmsr.MM_STRASSEN_WINOGRAD
+    # Strassen needs the inverse of (+) at any classic depth
+    rc = mmsr.mm_star_strassen(1, 1, W, mmsr.MM_SR_MIN_PLUS_I32, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False)
+    assert rc == mmsr.MM_ERR_UNSUPPORTED
+    # divisibility by 2^(classic + levels)
+    assert mmsr.mm_star_strassen(2, 2, W, sr, 40, 64, 64, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_SHAPE
+    assert mmsr.mm_star_strassen(5, 1, W, sr, 64, 64, 64, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert mmsr.mm_star_strassen(1, 1, 9, sr, 64, 64, 64, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    # the workspace is that of one block product: mm_strassen at the block size
+    n = 4096
+    for c, L in ((1, 1), (1, 2), (2, 1), (2, 2)):
+        p = mmsr.mm_star_strassen_query(c, L, sr, n, n, n)
+        q = mmsr.mm_plan_query(sr, L, n >> c, n >> c, n >> c)
+        assert p.workspace_min == q.workspace_min and p.levels == L
+        full = mmsr.mm_plan_query(sr, L + c, n, n, n)
+        assert p.workspace_min * 4 ** c <= full.workspace_min * 1.01
+    # classic_levels = 0 is mm_strassen's plan
+    assert mmsr.mm_star_strassen_query(0, 2, sr, n, n, n).workspace_min == mmsr.mm_plan_query(sr, 2, n, n, n).workspace_min
+    rc = mmsr.mm_star_strassen(1, 1, W, sr, 64, 64, 64, FAKE, FAKE, FAKE, FAKE,
+                               int(mmsr.mm_star_strassen_query(1, 1, sr, 64, 64, 64).workspace_min) - 1024,
+                               stream=0, check=False)
+    assert rc == mmsr.MM_ERR_WORKSPACE

@@ -68,3 +68,34 @@ def test_key_buckets():
     k2 = autotune.key("semiring", 3, 1024, 1024, 1024, 16384)
     assert k1 == k2
     assert autotune.key("semiring", 3, 1025, 1024, 1024, 16384) != k2
+
+
+def test_star_candidates_trade_classic_levels_for_workspace():
+    sr = mmsr.MM_SR_PLUS_TIMES_F32
+    n = 4096
+    big = 1 << 40
+    # unlimited budget: pure Strassen at every depth
+    assert [(c, L) for c, L, _ in autotune.star_candidates(sr, n, n, n, big)] == [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4)]
+    # a budget that holds one level of Strassen only at a quarter of the size
+    w = int(mmsr.mm_star_strassen_query(1, 1, sr, n, n, n).workspace_min)
+    assert w < int(mmsr.mm_plan_query(sr, 1, n, n, n).workspace_min)
+    cands = autotune.star_candidates(sr, n, n, n, w)
+    assert all(wc <= w for _, _, wc in cands)
+    assert [(c, L) for c, L, _ in cands][0] == (1, 1)
+    assert all(c >= 1 for c, L, _ in cands if L >= 1)
+    # the classic FP32 product keeps two split copies of A and B (bf16 hi/lo,
+    # 8 (m + n) k bytes), more than this budget: the mixed plan is the only
+    # plan of depth <= 1 that fits.
+    assert int(mmsr.mm_plan_query(sr, -1, n, n, n).workspace_min) > w
+    assert (0, 0) not in [(c, L) for c, L, _ in cands]
+
+
+def test_star_choice(tmp_path, monkeypatch):
+    monkeypatch.setenv("MMSR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    sr = mmsr.MM_SR_PLUS_TIMES_F32
+    n = 4096
+    w = int(mmsr.mm_star_strassen_query(1, 2, sr, n, n, n).workspace_min)
+    cands = autotune.star_candidates(sr, n, n, n, w)
+    times = iter([10.0 - i for i in range(len(cands))])
+    best = autotune.tune_star_strassen(sr, n, n, n, 0, 0, 0, 0, w, timer=lambda fn: next(times))
+    assert (best["classic"], best["levels"], best["workspace"]) == cands[-1]

@@ -18,7 +18,7 @@ TOL = 1e-5
 def pair(request):
     mmsr.mm_set_option(mmsr.MM_OPT_TC_PAIR, request.param)
     yield request.param
-    mmsr.mm_set_option(mmsr.MM_OPT_TC_PAIR, 1)
+    mmsr.mm_set_option(mmsr.MM_OPT_TC_PAIR, 0)
 
 
 def run(A, B, extra_parts=0):
