@@ -233,13 +233,46 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Running sum of one post-addition output in the pass's summation mode.
+// kSumDoubleFloat is Sum2 of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005): the running sum carries its exact
+// rounding errors separately, so the result is as accurate as a sum in twice
+// the precision, rounded once.  Zero coefficients add nothing.
+template <typename TP, int MODE>
+struct PostAcc {
+  TP v;
+  __device__ __forceinline__ void init(TP x0) { v = x0; }
+  __device__ __forceinline__ void add(int g, TP x) { v = apply(g, v, x); }
+  __device__ __forceinline__ TP get() const { return v; }
+};
+template <typename TP>
+struct PostAcc<TP, kSumF64> {
+  double v;
+  __device__ __forceinline__ void init(TP x0) { v = (double)x0; }
+  __device__ __forceinline__ void add(int g, TP x) { v = apply(g, v, (double)x); }
+  __device__ __forceinline__ TP get() const { return (TP)v; }
+};
+template <typename TP>
+struct PostAcc<TP, kSumDoubleFloat> {
+  float s, e;
+  __device__ __forceinline__ void init(TP x0) {
+    s = (float)x0;
+    e = 0.f;
+  }
+  __device__ __forceinline__ void add(int g, TP x) {
+    if (g == 0) return;
+    float s2, e2;
+    two_sum(s, g > 0 ? (float)x : -(float)x, s2, e2);
+    s = s2;
+    e = __fadd_rn(e, e2);
+  }
+  __device__ __forceinline__ TP get() const { return (TP)__fadd_rn(s, e); }
+};
+
 // Post-additions: products 7r..7r+6 (h x w each, contiguous) -> the four
 // quadrants of destination matrix r (2h x 2w, pitch dst_ld, dst_stride
 // apart).  Terms are added in product order, after the destination's old
-// value when `accumulate` is set.  kSumDoubleFloat is Sum2 of Ogita, Rump
-// and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005):
-// the running sum carries its exact rounding errors separately, so the
-// result is as accurate as a sum in twice the precision, rounded once.
+// value when `accumulate` is set.
 template <typename TP, int V, int MODE, int VARIANT>
 __global__ void __launch_bounds__(256) post_combine_kernel(const TP* __restrict__ P, int h, int w,
                                                            TP* __restrict__ dst, int64_t dst_ld,
@@ -262,32 +295,242 @@ __global__ void __launch_bounds__(256) post_combine_kernel(const TP* __restrict_
         if (accumulate) vload<TP, V>(out, y);
 #pragma unroll
         for (int t = 0; t < V; ++t) {
-          if constexpr (MODE == kSumDoubleFloat) {
-            float sum = accumulate ? (float)y[t] : 0.f, err = 0.f;
+          PostAcc<TP, MODE> acc;
+          acc.init(accumulate ? y[t] : TP(0));
 #pragma unroll
-            for (int p = 0; p < 7; ++p) {
-              const int g = coef_gamma(VARIANT, q, p);
-              if (g == 0) continue;
-              float s2, e2;
-              two_sum(sum, g > 0 ? (float)x[p][t] : -(float)x[p][t], s2, e2);
-              sum = s2;
-              err = __fadd_rn(err, e2);
-            }
-            y[t] = (TP)__fadd_rn(sum, err);
-          } else if constexpr (MODE == kSumF64) {
-            double acc = accumulate ? (double)y[t] : 0.0;
-#pragma unroll
-            for (int p = 0; p < 7; ++p) acc = apply(coef_gamma(VARIANT, q, p), acc, (double)x[p][t]);
-            y[t] = (TP)acc;
-          } else {
-            TP acc = accumulate ? y[t] : TP(0);
-#pragma unroll
-            for (int p = 0; p < 7; ++p) acc = apply(coef_gamma(VARIANT, q, p), acc, x[p][t]);
-            y[t] = acc;
-          }
+          for (int p = 0; p < 7; ++p) acc.add(coef_gamma(VARIANT, q, p), x[p][t]);
+          y[t] = acc.get();
         }
         vstore<TP, V>(out, y);
       }
+    }
+  }
+}
+
+// ------------------------------------------------- two levels in one pass
+// The 49 two-level operand sums at one element position: x[a][b] is the
+// (a, b) sub-block (a, b in 0..3) of a 4h x 4w source matrix, i.e. sub-
+// quadrant (a & 1, b & 1) of level-1 quadrant (a >> 1, b >> 1).  The level-1
+// sums S1 are formed in registers and never stored; every addition is the one
+// two single-level passes make, in the same order, so the results are
+// identical.  emit(7 r1 + r2, value) receives each level-2 sum.
+template <int VARIANT, int SIDE, typename T, typename Emit>
+__device__ __forceinline__ void combine2(const T (&x)[4][4], Emit&& emit) {
+#pragma unroll
+  for (int r1 = 0; r1 < 7; ++r1) {
+    T s1[4];
+#pragma unroll
+    for (int q2 = 0; q2 < 4; ++q2) {
+      const int u = q2 >> 1, v = q2 & 1;
+      s1[q2] = combo4<VARIANT, SIDE>(r1, x[u][v], x[u][2 + v], x[2 + u][v], x[2 + u][2 + v]);
+    }
+#pragma unroll
+    for (int r2 = 0; r2 < 7; ++r2) emit(7 * r1 + r2, combo4<VARIANT, SIDE>(r2, s1[0], s1[1], s1[2], s1[3]));
+  }
+}
+
+// Two operand levels: source matrix r (4h x 4w, pitch src_ld, src_stride
+// apart) -> matrices 49r..49r+48 (h x w, contiguous) of the stack two levels
+// down.  Blocks walk rows, threads walk columns.
+template <typename T, int VARIANT, int SIDE>
+__global__ void __launch_bounds__(256) pre_combine2_kernel(const T* __restrict__ src, int64_t src_ld,
+                                                           int64_t src_stride, int h, int w,
+                                                           T* __restrict__ dst) {
+  const int r = blockIdx.y;
+  const T* s = src + (int64_t)r * src_stride;
+  const int64_t total = (int64_t)h * w;
+  T* d = dst + (int64_t)r * 49 * total;
+  for (int i = blockIdx.x; i < h; i += gridDim.x) {
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+      T x[4][4];
+      const T* row = s + (int64_t)i * src_ld + j;
+#pragma unroll
+      for (int a = 0; a < 4; ++a, row += (int64_t)h * src_ld)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) x[a][b] = row[b * w];
+      // the 49 sums arrive in output order: one running pointer
+      T* o = d + (int64_t)i * w + j;
+      combine2<VARIANT, SIDE>(x, [&](int, T v) {
+        *o = v;
+        o += total;
+      });
+    }
+  }
+}
+
+// bf16 hi/lo of four consecutive values, as two 8-byte words.
+__device__ __forceinline__ void split4(const float (&v)[4], uint2& hi, uint2& lo) {
+  __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) split_bf16(v[t], h[t], l[t]);
+  memcpy(&hi, h, 8);
+  memcpy(&lo, l, 8);
+}
+
+// Two operand levels ending at the leaves, A side, FP32 mode: the 49 sums
+// are written as bf16 hi/lo rows of pitch Kp (columns w..Kp-1 zero).  Each
+// thread takes four consecutive columns (16-byte loads where `vec` allows,
+// 8-byte stores).
+template <int VARIANT>
+__global__ void __launch_bounds__(256) pre_combine2_split_rows_kernel(
+    const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int h, int w, int Kp,
+    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int vec) {
+  const int r = blockIdx.y;
+  const float* s = src + (int64_t)r * src_stride;
+  const int64_t step = (int64_t)h * Kp;  // one leaf operand
+  for (int i = blockIdx.x; i < h; i += gridDim.x) {
+    for (int j = threadIdx.x * 4; j < Kp; j += blockDim.x * 4) {
+      float x[4][4][4];  // [a][b][column]
+      const float* row = s + (int64_t)i * src_ld + j;
+#pragma unroll
+      for (int a = 0; a < 4; ++a, row += (int64_t)h * src_ld)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (vec && j + 4 <= w) {
+            const float4 q = *reinterpret_cast<const float4*>(row + b * w);
+            x[a][b][0] = q.x; x[a][b][1] = q.y; x[a][b][2] = q.z; x[a][b][3] = q.w;
+          } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[a][b][t] = j + t < w ? row[b * w + t] : 0.f;
+          }
+        }
+      int64_t off = ((int64_t)49 * r * h + i) * Kp + j;
+#pragma unroll
+      for (int r1 = 0; r1 < 7; ++r1) {
+        float s1[4][4];  // [q2][column]
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          const int u = q2 >> 1, v = q2 & 1;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            s1[q2][t] = combo4<VARIANT, 0>(r1, x[u][v][t], x[u][2 + v][t], x[2 + u][v][t], x[2 + u][2 + v][t]);
+        }
+#pragma unroll
+        for (int r2 = 0; r2 < 7; ++r2, off += step) {
+          float y[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) y[t] = combo4<VARIANT, 0>(r2, s1[0][t], s1[1][t], s1[2][t], s1[3][t]);
+          uint2 vh, vl;
+          split4(y, vh, vl);
+          *reinterpret_cast<uint2*>(hi + off) = vh;
+          *reinterpret_cast<uint2*>(lo + off) = vl;
+        }
+      }
+    }
+  }
+}
+
+// Two operand levels ending at the leaves, B side, FP32 mode: source matrix r
+// is (4h x 4w) = (k x n); the 49 sums (h x w) are written transposed as bf16
+// hi/lo (w x Kp).  A 32 k x 16 n tile of each of the 16 sub-blocks goes
+// through shared memory (reads run along n); each of the 128 threads then
+// takes four consecutive k of one column (8-byte stores along k).
+template <int VARIANT>
+__global__ void __launch_bounds__(128) pre_combine2_split_transpose_kernel(
+    const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int h, int w, int Kp,
+    __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT) {
+  __shared__ float tile[16][32][17];
+  const int r = blockIdx.z;
+  const float* s = src + (int64_t)r * src_stride;
+  const int k0 = blockIdx.x * 32, n0 = blockIdx.y * 16;
+  {
+    const int jj = threadIdx.x & 15;
+    const int gn = n0 + jj;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int kk = (threadIdx.x >> 4) + 8 * it;
+      const int gk = k0 + kk;
+      const bool in = gk < h && gn < w;
+      const float* p = s + (int64_t)gk * src_ld + gn;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) tile[a * 4 + b][kk][jj] = in ? p[(int64_t)a * h * src_ld + b * w] : 0.f;
+    }
+  }
+  __syncthreads();
+  const int kq = threadIdx.x & 7, jj = threadIdx.x >> 3;
+  const int gn = n0 + jj;
+  if (gn >= w) return;
+  float x[4][4][4];  // [a][b][k]
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) x[a][b][t] = tile[a * 4 + b][kq * 4 + t][jj];
+  const int64_t step = (int64_t)w * Kp;  // one leaf operand
+  int64_t off = ((int64_t)49 * r * w + gn) * Kp + k0 + kq * 4;
+#pragma unroll
+  for (int r1 = 0; r1 < 7; ++r1) {
+    float s1[4][4];
+#pragma unroll
+    for (int q2 = 0; q2 < 4; ++q2) {
+      const int u = q2 >> 1, v = q2 & 1;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        s1[q2][t] = combo4<VARIANT, 1>(r1, x[u][v][t], x[u][2 + v][t], x[2 + u][v][t], x[2 + u][2 + v][t]);
+    }
+#pragma unroll
+    for (int r2 = 0; r2 < 7; ++r2, off += step) {
+      float y[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) y[t] = combo4<VARIANT, 1>(r2, s1[0][t], s1[1][t], s1[2][t], s1[3][t]);
+      uint2 vh, vl;
+      split4(y, vh, vl);
+      *reinterpret_cast<uint2*>(hiT + off) = vh;
+      *reinterpret_cast<uint2*>(loT + off) = vl;
+    }
+  }
+}
+
+// Two post-addition levels: products 49r..49r+48 (h x w each, contiguous) ->
+// the 16 sub-blocks of destination matrix r (4h x 4w, pitch dst_ld,
+// dst_stride apart).  For each level-1 product r1 the level-2 sums T (four
+// values) are formed in registers in the order of a single-level pass, then
+// folded into the 16 outputs in r1 order, so the results equal two separate
+// passes (the second in the `MODE` summation, after the old value when
+// `accumulate` is set).
+template <typename TP, int MODE, int VARIANT>
+__global__ void __launch_bounds__(256) post_combine2_kernel(const TP* __restrict__ P, int h, int w,
+                                                            TP* __restrict__ dst, int64_t dst_ld,
+                                                            int64_t dst_stride, int accumulate) {
+  const int r = blockIdx.y;
+  const int64_t total = (int64_t)h * w;
+  const TP* pp = P + (int64_t)r * 49 * total;
+  TP* d = dst + (int64_t)r * dst_stride;
+  for (int i = blockIdx.x; i < h; i += gridDim.x) {
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+      PostAcc<TP, MODE> acc[4][4];  // [level-1 quadrant][level-2 quadrant]
+      // sub-block (a, b) of the destination = level-1 quadrant
+      // (a >> 1, b >> 1), level-2 quadrant (a & 1, b & 1)
+      TP* drow = d + (int64_t)i * dst_ld + j;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          acc[(a >> 1) * 2 + (b >> 1)][(a & 1) * 2 + (b & 1)].init(
+              accumulate ? drow[(int64_t)a * h * dst_ld + b * w] : TP(0));
+      const TP* src = pp + (int64_t)i * w + j;
+#pragma unroll
+      for (int r1 = 0; r1 < 7; ++r1) {
+        TP p7[7];
+#pragma unroll
+        for (int r2 = 0; r2 < 7; ++r2, src += total) p7[r2] = *src;
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          TP t = TP(0);
+#pragma unroll
+          for (int r2 = 0; r2 < 7; ++r2) t = apply(coef_gamma(VARIANT, q2, r2), t, p7[r2]);
+#pragma unroll
+          for (int q1 = 0; q1 < 4; ++q1) acc[q1][q2].add(coef_gamma(VARIANT, q1, r1), t);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          drow[(int64_t)a * h * dst_ld + b * w] = acc[(a >> 1) * 2 + (b >> 1)][(a & 1) * 2 + (b & 1)].get();
     }
   }
 }
@@ -428,6 +671,40 @@ StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
   return s;
 }
 
+// Level passes.  Two levels run as one pass wherever possible (half the
+// stack traffic of two single-level passes), paired where the stacks are
+// largest: operand expansion pairs the LAST levels ((L-1, L), (L-3, L-2),
+// ...; a single first level when L is odd), post-addition pairs the
+// deepest levels ((L, L-1), ...; a single top level when L is odd).
+template <typename T>
+cudaError_t launch_pre_combine2(const T* src, int64_t src_ld, int64_t src_stride, int64_t h, int64_t w,
+                                int64_t R, T* dst, int variant, int side, cudaStream_t st) {
+  const int threads = row_threads(w);
+  const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+  const int hh = (int)h, ww = (int)w;
+  if (variant == 0 && side == 0) pre_combine2_kernel<T, 0, 0><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, dst);
+  if (variant == 0 && side == 1) pre_combine2_kernel<T, 0, 1><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, dst);
+  if (variant == 1 && side == 0) pre_combine2_kernel<T, 1, 0><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, dst);
+  if (variant == 1 && side == 1) pre_combine2_kernel<T, 1, 1><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, dst);
+  return cudaGetLastError();
+}
+
+template <typename TP, int MODE>
+cudaError_t launch_post_combine2(const TP* P, int64_t h, int64_t w, int64_t R, TP* dst, int64_t dst_ld,
+                                 int64_t dst_stride, int variant, int accumulate, cudaStream_t st) {
+  const int threads = row_threads(w);
+  const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+  if (variant == 0)
+    post_combine2_kernel<TP, MODE, 0><<<g, threads, 0, st>>>(P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
+  else
+    post_combine2_kernel<TP, MODE, 1><<<g, threads, 0, st>>>(P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
+  return cudaGetLastError();
+}
+
+// First level of each operand pass: pairs (l, l+1) ending at L, a single
+// level 1 first when L is odd.
+inline int pass_first_level(int L, int l) { return (L & 1) && l == 1 ? 1 : 2; }
+
 // Operand side of the breadth-first expansion (FP32 mode).  X is rows x
 // cols with row pitch ld.
 cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t rows, int64_t cols,
@@ -435,33 +712,63 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
                        __nv_bfloat16* lo, cudaStream_t st) {
   const float* src = X;
   int64_t src_ld = ld, src_stride = 0;
-  for (int l = 1; l <= L; ++l) {
-    const int64_t h = rows >> l, w = cols >> l, R = pw7(l - 1);
-    if (l < L) {
-      float* dst = reinterpret_cast<float*>(ws + ((l & 1) ? S.off_pp1 : 0));
-      MMSR_CUDA_TRY(launch_pre_combine<float>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
+  int pass = 0;
+  for (int l = 1; l <= L;) {
+    const int span = pass_first_level(L, l);  // levels l .. l+span-1 in this pass
+    const int lend = l + span - 1;
+    const int64_t h = rows >> lend, w = cols >> lend, R = pw7(l - 1);
+    if (lend < L) {
+      float* dst = reinterpret_cast<float*>(ws + ((pass & 1) ? S.off_pp1 : 0));
+      if (span == 2)
+        MMSR_CUDA_TRY(launch_pre_combine2<float>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
+      else
+        MMSR_CUDA_TRY(launch_pre_combine<float>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
       src = dst;
       src_ld = w;
       src_stride = h * w;  // stacks hold contiguous (h x w) matrices
     } else if (side == 0) {
-      const int vec = (w % 4 == 0 && src_ld % 4 == 0 && src_stride % 4 == 0 && aligned_to(src, 16)) ? 1 : 0;
-      const int threads = row_threads(S.KpL / 8);
-      const dim3 g(rows_grid(h, R, threads), (unsigned)R);
-      if (variant == 0)
-        pre_combine_split_rows_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
-                                                               (int)S.KpL, hi, lo, vec);
-      else
-        pre_combine_split_rows_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
-                                                               (int)S.KpL, hi, lo, vec);
+      if (span == 2) {
+        const int vec = (w % 4 == 0 && src_ld % 4 == 0 && src_stride % 4 == 0 && aligned_to(src, 16)) ? 1 : 0;
+        const int threads = row_threads(S.KpL / 4);
+        const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+        if (variant == 0)
+          pre_combine2_split_rows_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                                  (int)S.KpL, hi, lo, vec);
+        else
+          pre_combine2_split_rows_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                                  (int)S.KpL, hi, lo, vec);
+      } else {
+        const int vec = (w % 4 == 0 && src_ld % 4 == 0 && src_stride % 4 == 0 && aligned_to(src, 16)) ? 1 : 0;
+        const int threads = row_threads(S.KpL / 8);
+        const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+        if (variant == 0)
+          pre_combine_split_rows_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                                 (int)S.KpL, hi, lo, vec);
+        else
+          pre_combine_split_rows_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                                 (int)S.KpL, hi, lo, vec);
+      }
       MMSR_CUDA_TRY(cudaGetLastError());
     } else {
-      dim3 g((unsigned)(S.KpL / 64), (unsigned)((w + 31) / 32), (unsigned)R);
-      if (variant == 0)
-        pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
-      else
-        pre_combine_split_transpose_kernel<1><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
+      if (span == 2) {
+        const dim3 g((unsigned)(S.KpL / 32), (unsigned)((w + 15) / 16), (unsigned)R);
+        if (variant == 0)
+          pre_combine2_split_transpose_kernel<0><<<g, 128, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                                   (int)S.KpL, hi, lo);
+        else
+          pre_combine2_split_transpose_kernel<1><<<g, 128, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
+                                                                   (int)S.KpL, hi, lo);
+      } else {
+        const dim3 g((unsigned)(S.KpL / 64), (unsigned)((w + 31) / 32), (unsigned)R);
+        if (variant == 0)
+          pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
+        else
+          pre_combine_split_transpose_kernel<1><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
+      }
       MMSR_CUDA_TRY(cudaGetLastError());
     }
+    l += span;
+    ++pass;
   }
   return cudaSuccess;
 }
@@ -472,38 +779,66 @@ cudaError_t expand_f64(int L, int variant, int side, const double* X, int64_t ro
                        cudaStream_t st) {
   const double* src = X;
   int64_t src_ld = ld, src_stride = 0;
-  for (int l = 1; l <= L; ++l) {
-    const int64_t h = rows >> l, w = cols >> l, R = pw7(l - 1);
-    double* dst = (l < L) ? reinterpret_cast<double*>(ws + ((l & 1) ? S.off_pp1 : 0)) : leaf;
-    MMSR_CUDA_TRY(launch_pre_combine<double>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
+  int pass = 0;
+  for (int l = 1; l <= L;) {
+    const int span = pass_first_level(L, l);
+    const int lend = l + span - 1;
+    const int64_t h = rows >> lend, w = cols >> lend, R = pw7(l - 1);
+    double* dst = (lend < L) ? reinterpret_cast<double*>(ws + ((pass & 1) ? S.off_pp1 : 0)) : leaf;
+    if (span == 2)
+      MMSR_CUDA_TRY(launch_pre_combine2<double>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
+    else
+      MMSR_CUDA_TRY(launch_pre_combine<double>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
     src = dst;
     src_ld = w;
     src_stride = h * w;
+    l += span;
+    ++pass;
   }
   return cudaSuccess;
 }
 
+template <typename TP>
+cudaError_t post_pass(int span, const TP* src, int64_t h, int64_t w, int64_t R, TP* dst, int64_t dst_ld,
+                      int64_t dst_stride, int variant, int accumulate, int mode, cudaStream_t st) {
+  if (span == 2) {
+    if (mode == kSumDoubleFloat)
+      return launch_post_combine2<TP, kSumDoubleFloat>(src, h, w, R, dst, dst_ld, dst_stride, variant, accumulate, st);
+    if (mode == kSumF64)
+      return launch_post_combine2<TP, kSumF64>(src, h, w, R, dst, dst_ld, dst_stride, variant, accumulate, st);
+    return launch_post_combine2<TP, kSumPlain>(src, h, w, R, dst, dst_ld, dst_stride, variant, accumulate, st);
+  }
+  if (mode == kSumDoubleFloat)
+    return launch_post_combine<TP, kSumDoubleFloat>(src, h, w, R, dst, dst_ld, dst_stride, variant, accumulate, st);
+  if (mode == kSumF64)
+    return launch_post_combine<TP, kSumF64>(src, h, w, R, dst, dst_ld, dst_stride, variant, accumulate, st);
+  return launch_post_combine<TP, kSumPlain>(src, h, w, R, dst, dst_ld, dst_stride, variant, accumulate, st);
+}
+
 // Bottom-up post-additions from the leaf products to C (pitch ldc).  The
 // top level adds into C's old values when `accumulate` is set and sums in
-// `top_mode` (PostSum).
+// `top_mode` (PostSum); lower levels sum plainly.
 template <typename TP>
 cudaError_t fold(int L, int variant, const TP* P, int64_t m, int64_t n, uint8_t* ws,
                  const StrassenLayout& S, TP* C, int64_t ldc, int accumulate, int top_mode,
                  cudaStream_t st) {
   const TP* src = P;
-  for (int l = L; l >= 1; --l) {
-    const int64_t h = m >> l, w = n >> l, R = pw7(l - 1);
-    if (l > 1) {
-      TP* dst = reinterpret_cast<TP*>(ws + (((l - 1) & 1) ? S.off_pp1 : 0));
-      MMSR_CUDA_TRY((launch_post_combine<TP, kSumPlain>(src, h, w, R, dst, 2 * w, 4 * h * w, variant, 0, st)));
+  int pass = 0;
+  for (int l = L; l >= 1;) {
+    const int span = l >= 2 ? 2 : 1;  // levels l .. l-span+1 in this pass
+    const int ltop = l - span + 1;
+    const int64_t h = m >> l, w = n >> l, R = pw7(ltop - 1);
+    const int64_t side = (int64_t)1 << span;  // destination matrices are side*h x side*w
+    if (ltop > 1) {
+      TP* dst = reinterpret_cast<TP*>(ws + ((pass & 1) ? S.off_pp1 : 0));
+      MMSR_CUDA_TRY(post_pass<TP>(span, src, h, w, R, dst, side * w, side * side * h * w, variant, 0,
+                                  kSumPlain, st));
       src = dst;
-    } else if (top_mode == kSumDoubleFloat) {
-      MMSR_CUDA_TRY((launch_post_combine<TP, kSumDoubleFloat>(src, h, w, 1, C, ldc, 0, variant, accumulate, st)));
-    } else if (top_mode == kSumF64) {
-      MMSR_CUDA_TRY((launch_post_combine<TP, kSumF64>(src, h, w, 1, C, ldc, 0, variant, accumulate, st)));
     } else {
-      MMSR_CUDA_TRY((launch_post_combine<TP, kSumPlain>(src, h, w, 1, C, ldc, 0, variant, accumulate, st)));
+      MMSR_CUDA_TRY(post_pass<TP>(span, src, h, w, R, C, ldc, 0, variant, accumulate, top_mode, st));
     }
+    l -= span;
+    ++pass;
   }
   return cudaSuccess;
 }

@@ -12,8 +12,8 @@
 // (28 slice products; the dropped orders g >= 7 and the residuals are below
 // 2^-49 of the scaled magnitudes, which leaves room for the error growth of
 // Strassen levels above these leaves).  Each G_g is an integer: it
-// accumulates in its own TMEM accumulator over chunks of 96 k, where every
-// partial sum is an integer of magnitude <= 96 * 36864 < 2^22 (per k, the
+// accumulates in its own TMEM accumulator over chunks of 256 k, where every
+// partial sum is an integer of magnitude <= 256 * 36864 < 2^24 (per k, the
 // digit products of one order sum to at most 2 * 128 * 64 + 5 * 64 * 64), so
 // the FP32 accumulation is exact whatever its rounding, and drain warps move
 // each chunk into two
@@ -24,6 +24,11 @@
 //
 // Tile 128 x 64, k-blocks of 32 (64-byte swizzled rows), 2-stage TMA ring of
 // the 14 slice tiles, 7 x 64 TMEM columns, warp roles as in the FP32 mode.
+// Each group accumulator has its own full / empty mbarrier pair: the drain
+// warps read group g as soon as its last product of a chunk has completed
+// (while the tensor core still works on groups g+1..6), and the MMA issuer
+// waits only for the group it is about to overwrite, so the drain runs
+// under the next chunk's products instead of between chunks.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -36,12 +41,14 @@ namespace {
 __device__ int g_f64acc_status;
 
 constexpr int kSlices = 7, kDigitBits = 7, kGroups = 7;
-constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2, CHUNK = 3;  // CHUNK k-blocks per drain
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2, CHUNK = 8;  // CHUNK k-blocks per drain
+static_assert((int64_t)CHUNK * BK * 36864 < (1 << 24), "chunk sums must stay exact in FP32");
 constexpr int kDrain = 8, kThreads = 64 + 32 * kDrain;
 constexpr uint32_t A_TILE = BM * BK * 2, B_TILE = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = kSlices * (A_TILE + B_TILE);
 constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
 constexpr uint32_t TMEM_COLS = 512;  // 7 groups x 64 columns used
+static_assert(BK == 32, "the MMA issue loop covers two 16-deep k-steps per k-block");
 
 // ----------------------------------------------------------- split kernels
 // Exponent E with max|x| < 2^E (0 for an all-zero line).
@@ -153,10 +160,9 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
 
 // ------------------------------------------------------------ GEMM kernel
 __device__ __forceinline__ int exact_int(uint32_t fbits) {
-  // fbits holds an integer-valued float of magnitude < 2^22; adding 1.5*2^23
-  // leaves the integer in the low mantissa bits exactly.
-  const float t = __uint_as_float(fbits) + 12582912.0f;
-  return (int)(__float_as_uint(t) - 0x4B400000u);
+  // fbits holds an integer-valued float of magnitude < 2^24: the conversion
+  // is exact in any rounding mode.
+  return __float2int_rn(__uint_as_float(fbits));
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -168,9 +174,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = tc::align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint64_t* acc_full = empty + STAGES;       // [kGroups]
+  uint64_t* acc_empty = acc_full + kGroups;   // [kGroups]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + kGroups);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,8 +211,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, kDrain);
+    for (int g = 0; g < kGroups; ++g) {
+      tc::mbar_init(&acc_full[g], 1);
+      tc::mbar_init(&acc_empty[g], kDrain);
+    }
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
@@ -238,36 +246,69 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_f16(BM, BN, 1);
+      constexpr uint32_t dhi = tc::desc_hi_sw64();
+      // The products are small (128 x 64 x 16, ~40 tensor-core cycles), so
+      // the issue loop is kept lean: descriptors are one 32-bit add of a
+      // compile-time offset to a per-stage base word.
+      auto issue_group = [&](uint32_t a_lo, uint32_t b_lo, int kk, int g, bool overwrite) {
+#pragma unroll
+        for (int sa = 0; sa <= g; ++sa) {
+          const uint32_t aoff = (uint32_t)(sa * A_TILE + kk * 32) >> 4;
+          const uint32_t boff = (uint32_t)((g - sa) * B_TILE + kk * 32) >> 4;
+          tc::mma_f16(tmem + (uint32_t)(g * BN), tc::desc_join(a_lo + aoff, dhi),
+                      tc::desc_join(b_lo + boff, dhi), idesc, (overwrite && sa == 0) ? 0u : 1u);
+        }
+      };
       int it = 0;
-      for (int c = 0; c < nchunks; ++c) {
-        if (c >= 1 && !tc::mbar_wait(acc_empty, (c - 1) & 1u, abort_flag, &g_f64acc_status)) break;
-        tc::fence_after_sync();
+      bool aborted = false;
+      for (int c = 0; c < nchunks && !aborted; ++c) {
+        const int first_it = it;
         const int last = min(nkb, (c + 1) * CHUNK);
-        bool aborted = false;
-        for (int first = 1; it < last; ++it, first = 0) {
+        for (; it < last && !aborted; ++it) {
           const int s = it % STAGES;
           const uint32_t round = (uint32_t)(it / STAGES);
-          if (!tc::mbar_wait(&full[s], round & 1u, abort_flag, &g_f64acc_status)) { aborted = true; break; }
+          if (!tc::mbar_wait(&full[s], round & 1u, abort_flag, &g_f64acc_status)) {
+            aborted = true;
+            break;
+          }
           tc::fence_after_sync();
           const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t a_lo = tc::desc_lo(base), b_lo = tc::desc_lo(base + kSlices * A_TILE);
+          if (it == first_it) {
+            // first k-block of a chunk: overwrite each group, after the
+            // drain has read the previous chunk's G_g
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) {
-#pragma unroll
-              for (int sa = 0; sa <= g; ++sa) {
-                const int sb = g - sa;
-                const uint64_t ad = tc::desc_sw64(base + sa * A_TILE + kk * 32);
-                const uint64_t bd = tc::desc_sw64(base + kSlices * A_TILE + sb * B_TILE + kk * 32);
-                tc::mma_f16(tmem + (uint32_t)(g * BN), ad, bd, idesc,
-                            (first && kk == 0 && sa == 0) ? 0u : 1u);
+              if (c >= 1 && !aborted) {
+                if (!tc::mbar_wait(&acc_empty[g], (c - 1) & 1u, abort_flag, &g_f64acc_status)) aborted = true;
+                tc::fence_after_sync();
               }
+              if (!aborted) issue_group(a_lo, b_lo, 0, g, true);
+            }
+            if (!aborted) {
+#pragma unroll
+              for (int g = 0; g < kGroups; ++g) {
+                issue_group(a_lo, b_lo, 1, g, false);
+                if (it == last - 1) tc::mma_commit(&acc_full[g]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 0, g, false);
+            if (it == last - 1) {
+              // the chunk's last product of group g is issued: signal it
+#pragma unroll
+              for (int g = 0; g < kGroups; ++g) {
+                issue_group(a_lo, b_lo, 1, g, false);
+                tc::mma_commit(&acc_full[g]);
+              }
+            } else {
+#pragma unroll
+              for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 1, g, false);
             }
           }
           tc::mma_commit(&empty[s]);
         }
-        tc::mma_commit(acc_full);
-        if (aborted) break;
       }
     }
   } else {
@@ -279,10 +320,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int e = 0; e < 32; ++e) hi[e] = lo[e] = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
-      ok = tc::mbar_wait(acc_full, c & 1u, abort_flag, &g_f64acc_status);
-      tc::fence_after_sync();
 #pragma unroll
       for (int g = 0; g < kGroups; ++g) {
+        // warp-uniform verdict: the __syncwarp below needs every lane
+        ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[g], c & 1u, abort_flag, &g_f64acc_status));
+        if (!ok) break;
+        tc::fence_after_sync();
         const long long wgt = g < 3 ? (1ll << (7 * (2 - g))) : (1ll << (7 * (6 - g)));
 #pragma unroll
         for (int half16 = 0; half16 < 2; ++half16) {
@@ -298,10 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               lo[half16 * 16 + e] += v;
           }
         }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acc_empty[g]);
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty);
     }
     double* out = (z == 0) ? C + ra * n : W + (int64_t)(z - 1) * m * n;
     const int64_t row = i0 + q * 32 + lane;

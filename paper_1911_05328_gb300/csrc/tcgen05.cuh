@@ -133,6 +133,19 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
          ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
+// The same descriptors split into 32-bit words: the start address occupies
+// the low 14 bits of the low word, so for any shared-memory address the
+// descriptor of (saddr + off) is {lo(saddr) + off / 16, hi} -- one 32-bit add
+// per descriptor in an MMA issue loop instead of a full re-encode.
+__device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) {
+  return ((saddr >> 4) & 0x3FFFu) | (1u << 16);
+}
+constexpr uint32_t desc_hi_sw128() { return (1024u >> 4) | (1u << 14) | (2u << 29); }
+constexpr uint32_t desc_hi_sw64() { return (512u >> 4) | (1u << 14) | (4u << 29); }
+__device__ __forceinline__ uint64_t desc_join(uint32_t lo, uint32_t hi) {
+  return ((uint64_t)hi << 32) | lo;
+}
+
 // Instruction descriptor, kind::f16: D fp32, A/B of `ab_fmt` (0 = f16,
 // 1 = bf16), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, uint32_t ab_fmt) {
