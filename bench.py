@@ -120,20 +120,25 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def ncu_traffic(kernel_file, key):
+def source_sha(files):
+    """Hash of the sources that define a kernel (csrc/ file names, in order)."""
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1911_05328_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_files, key):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed after the counters were taken."""
+    kernel's sources changed after the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(key)
     except (OSError, ValueError):
         return None
-    if not rec:
-        return None
-    src = os.path.join(ROOT, "paper_1911_05328_gb300", "csrc", kernel_file)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != h:
+    if not rec or rec.get("source_sha") != source_sha(kernel_files):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -286,7 +291,7 @@ def main():
     leaf_avg_ms = leaf["ms"] / (args.steps * len(BUDGETS))
     achieved_tops = ops_per_call / (leaf_avg_ms * 1e-3) / 1e12
     peak_tops = alu_peak_u16x2_tops if leaf_name == "minplus16_leaf" else alu_peak_tops
-    traffic = ncu_traffic("minplus.cu", leaf_name + "_n4096")
+    traffic = ncu_traffic(["minplus.cu", "minplus_tile.cuh"], leaf_name + "_n4096")
     per_budget = []
     for i, b in enumerate(BUDGETS):
         ms = per_budget_ms[i] / args.steps
@@ -548,8 +553,9 @@ def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
 
     n = 16384
     A, B = inputs.uniform_f64(n, n, n, seed=3)
-    dA = torch.from_numpy(A.astype(np.float32)).cuda()
-    dB = torch.from_numpy(B.astype(np.float32)).cuda()
+    dA64, dB64 = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dA = dA64.float()
+    dB = dB64.float()
     del A, B
     dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
     sr = mmsr.MM_SR_PLUS_TIMES_F32
@@ -590,6 +596,40 @@ def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
         res["star_c%d_L%d" % (c, L)] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
                                         "workspace_bytes": int(p.workspace_min),
                                         "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
+        del ws
+        torch.cuda.empty_cache()
+    del dC
+    # FP64-accuracy mode (28 digit-slice products per leaf) at the same size
+    dC64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    sr64 = mmsr.MM_SR_PLUS_TIMES_F64ACC
+    for L in range(0, 3):
+        p = mmsr.mm_plan_query(sr64, L, n, n, n, 0)
+        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+        fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr64, n, n, n, dA64, dB64, dC64, ws,
+                                      int(p.workspace_min), sp)
+        ms = _time_call(torch, fn, 2)
+        res["fp64acc_L%d" % L] = {"ms": ms, "gflops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                                  "workspace_bytes": int(p.workspace_min),
+                                  "workspace_n2x8B": p.workspace_min / (n * n * 8.0)}
+        del ws
+        torch.cuda.empty_cache()
+    del dA, dB, dA64, dB64, dC64
+    torch.cuda.empty_cache()
+    # the rectangular product m = 12288, k = 16384, n = 8192, FP32 mode
+    m, k, n2 = 12288, 16384, 8192
+    A, B = inputs.uniform_f64(m, k, n2, seed=3)
+    dA = torch.from_numpy(A.astype(np.float32)).cuda()
+    dB = torch.from_numpy(B.astype(np.float32)).cuda()
+    del A, B
+    dC = torch.empty((m, n2), dtype=torch.float32, device="cuda")
+    for L in range(0, 4):
+        p = mmsr.mm_plan_query(sr, L, m, n2, k, 0)
+        ws = torch.empty((max(int(p.workspace_min), 16),), dtype=torch.uint8, device="cuda")
+        fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, m, n2, k, dA, dB, dC, ws,
+                                      int(p.workspace_min), sp)
+        ms = _time_call(torch, fn, 3)
+        res["rect_12288x16384x8192_L%d" % L] = {"ms": ms, "gops_classic_equiv": 2.0 * m * n2 * k / (ms * 1e-3) / 1e9,
+                                               "workspace_bytes": int(p.workspace_min)}
         del ws
         torch.cuda.empty_cache()
     del dA, dB, dC

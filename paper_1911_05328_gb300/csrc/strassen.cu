@@ -78,13 +78,16 @@ __device__ __forceinline__ T combo4(int r, T x0, T x1, T x2, T x3) {
 }
 
 // ------------------------------------------------------- vector helpers
-// V consecutive elements through one 16-byte access when V * sizeof(T) is
-// 16 (the caller checks alignment), element by element otherwise.
+// V consecutive elements through one 16- or 8-byte access when V * sizeof(T)
+// is 16 or 8 (the caller checks alignment), element by element otherwise.
 template <typename T, int V>
 __device__ __forceinline__ void vload(const T* __restrict__ p, T (&x)[V]) {
   if constexpr (V * sizeof(T) == 16) {
     const uint4 u = *reinterpret_cast<const uint4*>(p);
     memcpy(x, &u, 16);
+  } else if constexpr (V * sizeof(T) == 8) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    memcpy(x, &u, 8);
   } else {
 #pragma unroll
     for (int t = 0; t < V; ++t) x[t] = p[t];
@@ -96,6 +99,10 @@ __device__ __forceinline__ void vstore(T* __restrict__ p, const T (&x)[V]) {
     uint4 u;
     memcpy(&u, x, 16);
     *reinterpret_cast<uint4*>(p) = u;
+  } else if constexpr (V * sizeof(T) == 8) {
+    uint2 u;
+    memcpy(&u, x, 8);
+    *reinterpret_cast<uint2*>(p) = u;
   } else {
 #pragma unroll
     for (int t = 0; t < V; ++t) p[t] = x[t];
@@ -490,8 +497,8 @@ __global__ void __launch_bounds__(128) pre_combine2_split_transpose_kernel(
 // values) are formed in registers in the order of a single-level pass, then
 // folded into the 16 outputs in r1 order, so the results equal two separate
 // passes (the second in the `MODE` summation, after the old value when
-// `accumulate` is set).
-template <typename TP, int MODE, int VARIANT>
+// `accumulate` is set).  Each thread takes V consecutive columns.
+template <typename TP, int V, int MODE, int VARIANT>
 __global__ void __launch_bounds__(256) post_combine2_kernel(const TP* __restrict__ P, int h, int w,
                                                             TP* __restrict__ dst, int64_t dst_ld,
                                                             int64_t dst_stride, int accumulate) {
@@ -499,38 +506,50 @@ __global__ void __launch_bounds__(256) post_combine2_kernel(const TP* __restrict
   const int64_t total = (int64_t)h * w;
   const TP* pp = P + (int64_t)r * 49 * total;
   TP* d = dst + (int64_t)r * dst_stride;
+  const int wv = w / V;
   for (int i = blockIdx.x; i < h; i += gridDim.x) {
-    for (int j = threadIdx.x; j < w; j += blockDim.x) {
-      PostAcc<TP, MODE> acc[4][4];  // [level-1 quadrant][level-2 quadrant]
+    for (int jv = threadIdx.x; jv < wv; jv += blockDim.x) {
+      const int j = jv * V;
+      PostAcc<TP, MODE> acc[4][4][V];  // [level-1 quadrant][level-2 quadrant][column]
       // sub-block (a, b) of the destination = level-1 quadrant
       // (a >> 1, b >> 1), level-2 quadrant (a & 1, b & 1)
       TP* drow = d + (int64_t)i * dst_ld + j;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-          acc[(a >> 1) * 2 + (b >> 1)][(a & 1) * 2 + (b & 1)].init(
-              accumulate ? drow[(int64_t)a * h * dst_ld + b * w] : TP(0));
+        for (int b = 0; b < 4; ++b) {
+          TP y[V];
+          if (accumulate) vload<TP, V>(drow + (int64_t)a * h * dst_ld + b * w, y);
+#pragma unroll
+          for (int t = 0; t < V; ++t)
+            acc[(a >> 1) * 2 + (b >> 1)][(a & 1) * 2 + (b & 1)][t].init(accumulate ? y[t] : TP(0));
+        }
       const TP* src = pp + (int64_t)i * w + j;
 #pragma unroll
       for (int r1 = 0; r1 < 7; ++r1) {
-        TP p7[7];
+        TP p7[7][V];
 #pragma unroll
-        for (int r2 = 0; r2 < 7; ++r2, src += total) p7[r2] = *src;
+        for (int r2 = 0; r2 < 7; ++r2, src += total) vload<TP, V>(src, p7[r2]);
 #pragma unroll
-        for (int q2 = 0; q2 < 4; ++q2) {
-          TP t = TP(0);
+        for (int q2 = 0; q2 < 4; ++q2)
 #pragma unroll
-          for (int r2 = 0; r2 < 7; ++r2) t = apply(coef_gamma(VARIANT, q2, r2), t, p7[r2]);
+          for (int t = 0; t < V; ++t) {
+            TP tq = TP(0);
 #pragma unroll
-          for (int q1 = 0; q1 < 4; ++q1) acc[q1][q2].add(coef_gamma(VARIANT, q1, r1), t);
-        }
+            for (int r2 = 0; r2 < 7; ++r2) tq = apply(coef_gamma(VARIANT, q2, r2), tq, p7[r2][t]);
+#pragma unroll
+            for (int q1 = 0; q1 < 4; ++q1) acc[q1][q2][t].add(coef_gamma(VARIANT, q1, r1), tq);
+          }
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-          drow[(int64_t)a * h * dst_ld + b * w] = acc[(a >> 1) * 2 + (b >> 1)][(a & 1) * 2 + (b & 1)].get();
+        for (int b = 0; b < 4; ++b) {
+          TP y[V];
+#pragma unroll
+          for (int t = 0; t < V; ++t) y[t] = acc[(a >> 1) * 2 + (b >> 1)][(a & 1) * 2 + (b & 1)][t].get();
+          vstore<TP, V>(drow + (int64_t)a * h * dst_ld + b * w, y);
+        }
     }
   }
 }
@@ -692,12 +711,14 @@ cudaError_t launch_pre_combine2(const T* src, int64_t src_ld, int64_t src_stride
 template <typename TP, int MODE>
 cudaError_t launch_post_combine2(const TP* P, int64_t h, int64_t w, int64_t R, TP* dst, int64_t dst_ld,
                                  int64_t dst_stride, int variant, int accumulate, cudaStream_t st) {
+  // One column per thread: with 49 product streams per thread, wider
+  // accesses measured slower (fewer threads in flight).
   const int threads = row_threads(w);
   const dim3 g(rows_grid(h, R, threads), (unsigned)R);
   if (variant == 0)
-    post_combine2_kernel<TP, MODE, 0><<<g, threads, 0, st>>>(P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
+    post_combine2_kernel<TP, 1, MODE, 0><<<g, threads, 0, st>>>(P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
   else
-    post_combine2_kernel<TP, MODE, 1><<<g, threads, 0, st>>>(P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
+    post_combine2_kernel<TP, 1, MODE, 1><<<g, threads, 0, st>>>(P, (int)h, (int)w, dst, dst_ld, dst_stride, accumulate);
   return cudaGetLastError();
 }
 
