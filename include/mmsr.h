@@ -196,10 +196,13 @@ typedef struct {
 
 /*
  * mm_batched -- C_p := A_p (x) B_p for `count` independent problems of
- * mixed shapes and semirings in one persistent launch over a cost-sorted
- * tile queue (the dynamic load balance of Section 6).  `problems` is a
- * HOST array read during the call.  Workspace holds the tile queue and the
- * split operands; mm_batched_query reports the minimum.
+ * mixed shapes and semirings in one call (the dynamic load balance of
+ * Section 6): FP32 (+, x) tiles run in a persistent tensor-core kernel that
+ * pops a cost-sorted tile queue, (min,+) tiles in a CUDA-core launch over a
+ * cost-sorted tile list.  Asynchronous and capturable in a CUDA graph.
+ * `problems` is a HOST array read during the call.  Workspace holds the
+ * tile counter, the per-problem range verdicts and the split FP32 operands;
+ * mm_batched_query reports the minimum.
  */
 int mm_batched(int count, const mm_problem_t* problems, void* workspace, size_t workspace_bytes,
                void* stream);

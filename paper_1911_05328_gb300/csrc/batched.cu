@@ -9,15 +9,22 @@
 // describe every FP32 problem of the batch); a second pre-pass decides, per
 // (min,+) problem, whether the exact packed 2 x 16-bit leaf applies.
 //
-// Device side: one CTA per SM pops tile indices from an atomic counter.  A
-// FP32 tile runs the tcgen05 pipeline (TMA producer warp, MMA warp, eight
-// drain warps, chunked TMEM accumulation); a (min,+) tile runs the CUDA-core
-// mainloop on the eight drain warps.  The shared-memory ring and the TMEM
-// accumulators persist across tiles with running phase counters, so no
-// barrier is ever re-initialised while an asynchronous arrive may be pending.
+// Device side: FP32 tiles run in one persistent tcgen05 kernel -- one CTA
+// per SM pops tile indices from an atomic counter and runs the pipeline
+// (TMA producer warp, MMA warp, eight drain warps, chunked TMEM
+// accumulation); the shared-memory ring and the TMEM accumulators persist
+// across tiles with running phase counters, so no barrier is ever
+// re-initialised while an asynchronous arrive may be pending.  (min,+) tiles
+// run in a second launch, one 128 x 256 packed tile per CTA and two CTAs per
+// SM: the packed mainloop needs sixteen warps per SM to keep the ALU pipe
+// busy, which does not fit beside the tensor pipeline's register budget
+// (inside the persistent kernel eight warps reached half its rate).  Both
+// lists run longest problem first; a 32-bit launch takes (min,+) problems
+// outside the packed range.  The whole call is capturable in one CUDA graph.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
 #include <numeric>
 #include <string.h>
 #include <vector>
@@ -32,21 +39,29 @@ namespace {
 __device__ int g_batched_status;
 
 constexpr int kMaxBatch = 512;
-constexpr int TBM = 128, TBN = 128, TBK = 64, TSTAGES = 3, TCHUNK = 2;
+// FP32 tiles: 128 x 128, 32-wide k-blocks (64-byte swizzled rows) in a
+// 6-deep TMA ring, TMEM chunks of 8 k-blocks (256 k) -- the k-pipeline
+// shape that measured fastest for the standalone FP32 GEMM.  Split operands
+// are padded to TKA columns.
+constexpr int TBM = 128, TBN = 128, TBK = 32, TSTAGES = 6, TCHUNK = 8, TKA = 64;
+static_assert(TKA % TBK == 0 && (TBK == 32 || TBK == 64), "k-block / swizzle");
 constexpr int kDrainW = 8, kBThreads = 64 + 32 * kDrainW;
 constexpr uint32_t TA_BYTES = TBM * TBK * 2, TB_BYTES = TBN * TBK * 2;
 constexpr uint32_t TSTAGE = 2 * TA_BYTES + 2 * TB_BYTES;
+constexpr int kTileQ = 4;  // tile indices the producer may claim ahead of the consumers
 constexpr size_t BSMEM = 1024 + (size_t)TSTAGES * TSTAGE + 256;
 constexpr uint32_t BTMEM_COLS = 2 * TBN;
 constexpr int MPN = 256;  // (min,+) tile: 128 x 256
 
 struct BatchTable {
   int count;
-  int total_tiles;
+  int total_tiles;  // FP32 tiles (persistent kernel)
   int kind[kMaxBatch];  // 0: FP32 (+,x) on tensor cores, 1: (min,+)
   int m[kMaxBatch], n[kMaxBatch], k[kMaxBatch];
-  int tile_start[kMaxBatch + 1];
+  int tile_start[kMaxBatch + 1];     // 128 x 128 tiles of FP32 problems
+  int mp16_tile_start[kMaxBatch + 1];  // 128 x 256 packed tiles of (min,+) problems
   int mp_tile_start[kMaxBatch + 1];  // 128 x 128 tiles of (min,+) problems, for the fallback
+  int mp16_total;
   int mp_total;
   int row0a[kMaxBatch];  // FP32: first row of this A in the stacked split buffers
   int row0b[kMaxBatch];  // FP32: first row of this B^T in the stacked split buffers
@@ -72,7 +87,7 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const __grid_constan
   const int p = blockIdx.y;
   if (T.kind[p] != 0) return;
   const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
-  const int64_t kp = (k + TBK - 1) / TBK * TBK;
+  const int64_t kp = (k + TKA - 1) / TKA * TKA;
   const float* A = static_cast<const float*>(T.A[p]);
   const float* B = static_cast<const float*>(T.B[p]);
   // A rows: one thread per 8 output columns
@@ -165,21 +180,53 @@ __global__ void __launch_bounds__(256, 2)
                      (int)threadIdx.x, fsmem, mp::SyncCta());
 }
 
+// Packed (min,+) tiles: one 128 x 256 tile per CTA over the compact list of
+// (min,+) problems' tiles (longest problem first); CTAs of problems outside
+// the packed range exit at once.
+__global__ void __launch_bounds__(256, 2)
+    batched_minplus16_kernel(const __grid_constant__ BatchTable T, const int* __restrict__ violation) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = T.count - 1;  // last p with mp16_tile_start[p] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (T.mp16_tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const int p = lo;
+  if (T.kind[p] != 1 || __ldcg(&violation[p]) != 0) return;
+  __shared__ __align__(16) uint32_t psmem[mp::PSMEM_BYTES / 4];
+  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+  const int local = t - T.mp16_tile_start[p];
+  const int tiles_n = (int)((n + MPN - 1) / MPN);
+  const int32_t* A = static_cast<const int32_t*>(T.A[p]);
+  const int32_t* B = static_cast<const int32_t*>(T.B[p]);
+  int32_t* C = static_cast<int32_t*>(T.C[p]);
+  const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
+  mp::minplus16_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, (int64_t)(local / tiles_n) * mp::PBM,
+                     (int64_t)(local % tiles_n) * MPN, (int64_t)0, k, vec, (int)threadIdx.x, psmem,
+                     mp::SyncCta());
+}
+
+// Shared-memory descriptor of a K-major operand tile with TBK-wide rows.
+__device__ __forceinline__ uint64_t kdesc(uint32_t saddr) {
+  return TBK == 64 ? tc::desc_sw128(saddr) : tc::desc_sw64(saddr);
+}
+
 // ------------------------------------------------------ persistent kernel
 __global__ void __launch_bounds__(kBThreads, 1)
     batched_kernel(const __grid_constant__ BatchTable T, const __grid_constant__ CUtensorMap tAhi,
                    const __grid_constant__ CUtensorMap tAlo, const __grid_constant__ CUtensorMap tBhi,
-                   const __grid_constant__ CUtensorMap tBlo, int* __restrict__ counter,
-                   const int* __restrict__ violation) {
+                   const __grid_constant__ CUtensorMap tBlo, int* __restrict__ counter) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + TSTAGES * TSTAGE);
   uint64_t* empty = full + TSTAGES;
   uint64_t* acc_full = empty + TSTAGES;
   uint64_t* acc_empty = acc_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* tile_full = acc_empty + 2;         // [kTileQ]
+  uint64_t* tile_empty = tile_full + kTileQ;   // [kTileQ]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_empty + kTileQ);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  int* s_tile = abort_flag + 1;
+  int* tile_q = abort_flag + 1;                // [kTileQ]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -191,6 +238,10 @@ __global__ void __launch_bounds__(kBThreads, 1)
       tc::mbar_init(&acc_full[b], 1);
       tc::mbar_init(&acc_empty[b], kDrainW);
     }
+    for (int q = 0; q < kTileQ; ++q) {
+      tc::mbar_init(&tile_full[q], 1);
+      tc::mbar_init(&tile_empty[q], 1 + kDrainW);  // the MMA thread and the drain warps
+    }
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
@@ -201,13 +252,30 @@ __global__ void __launch_bounds__(kBThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   // running positions of the TMA ring and of the TMEM chunk buffers; each
-  // role advances its own copy over the same sequence of tensor-core tiles
+  // role advances its own copy over the same sequence of tensor-core tiles.
+  // Tile indices travel through a small mbarrier queue instead of a CTA
+  // barrier: the producer claims tiles ahead (and starts their TMA loads)
+  // while the tensor core and the drain warps still work on earlier ones.
   uint32_t ring = 0, chunk = 0;
+  const bool active = warp >= 2 || lane == 0;  // warps 0 and 1 work through one lane
 
-  for (;;) {
-    if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1);
-    __syncthreads();
-    const int t = *s_tile;
+  for (uint32_t j = 0; active; ++j) {
+    const int slot = (int)(j % kTileQ);
+    const uint32_t ph = (j / kTileQ) & 1u;
+    int t = INT_MAX;
+    if (warp == 0) {
+      if (j < kTileQ || tc::mbar_wait(&tile_empty[slot], ph ^ 1u, abort_flag, &g_batched_status)) {
+        t = atomicAdd(counter, 1);
+        tile_q[slot] = t;
+        tc::mbar_arrive(&tile_full[slot]);  // release: the index is visible to the waiters
+      }
+    } else {
+      bool ok = tc::mbar_wait(&tile_full[slot], ph, abort_flag, &g_batched_status);
+      if (warp >= 2) ok = __all_sync(0xffffffffu, ok);
+      if (ok) t = *reinterpret_cast<volatile int*>(&tile_q[slot]);
+      if (warp >= 2) __syncwarp();
+      if (ok && lane == 0) tc::mbar_arrive(&tile_empty[slot]);
+    }
     if (t >= T.total_tiles) break;
     int lo = 0, hi = T.count - 1;  // last p with tile_start[p] <= t
     while (lo < hi) {
@@ -218,7 +286,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
     const int local = t - T.tile_start[p];
     const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
 
-    if (T.kind[p] == 0) {
+    {
       // ------------------------------------------------ FP32 tensor-core tile
       const int tiles_n = (int)((n + TBN - 1) / TBN);
       const int64_t i0 = (int64_t)(local / tiles_n) * TBM, j0 = (int64_t)(local % tiles_n) * TBN;
@@ -257,10 +325,10 @@ __global__ void __launch_bounds__(kBThreads, 1)
               const uint32_t base = smem_u32(smem + s * TSTAGE);
 #pragma unroll
               for (int kk = 0; kk < TBK / 16; ++kk) {
-                const uint64_t ahi = tc::desc_sw128(base + kk * 32);
-                const uint64_t alo = tc::desc_sw128(base + TA_BYTES + kk * 32);
-                const uint64_t bhi = tc::desc_sw128(base + 2 * TA_BYTES + kk * 32);
-                const uint64_t blo = tc::desc_sw128(base + 2 * TA_BYTES + TB_BYTES + kk * 32);
+                const uint64_t ahi = kdesc(base + kk * 32);
+                const uint64_t alo = kdesc(base + TA_BYTES + kk * 32);
+                const uint64_t bhi = kdesc(base + 2 * TA_BYTES + kk * 32);
+                const uint64_t blo = kdesc(base + 2 * TA_BYTES + TB_BYTES + kk * 32);
                 tc::mma_f16(d, ahi, bhi, idesc, (first && kk == 0) ? 0u : 1u);
                 tc::mma_f16(d, ahi, blo, idesc, 1);
                 tc::mma_f16(d, alo, bhi, idesc, 1);
@@ -279,7 +347,9 @@ __global__ void __launch_bounds__(kBThreads, 1)
         bool ok = true;
         for (int c = 0; c < nchunks; ++c, ++chunk) {
           const int b = chunk & 1;
-          if (ok) ok = tc::mbar_wait(&acc_full[b], (chunk >> 1) & 1u, abort_flag, &g_batched_status);
+          // warp-uniform verdict: the __syncwarp below needs every lane
+          ok = __all_sync(0xffffffffu, ok && tc::mbar_wait(&acc_full[b], (chunk >> 1) & 1u, abort_flag,
+                                                           &g_batched_status));
           tc::fence_after_sync();
 #pragma unroll
           for (int cc = 0; cc < TBN / 2; cc += 16) {
@@ -297,26 +367,24 @@ __global__ void __launch_bounds__(kBThreads, 1)
         const int64_t row = i0 + q * 32 + lane;
         if (row < m) {
           const int64_t c0 = j0 + half * (TBN / 2);
+          float* dst = C + row * n + c0;
+          // 16-byte stores where the row allows them (n % 4 == 0 keeps every
+          // row 16-byte aligned), element stores at the ragged edge
+          const bool vec = (n % 4 == 0) && aligned16(C);
 #pragma unroll
-          for (int e = 0; e < TBN / 2; ++e)
-            if (c0 + e < n) C[row * n + c0 + e] = ok ? sum[e] : 0.f;
+          for (int e = 0; e < TBN / 2; e += 4) {
+            if (vec && c0 + e + 4 <= n) {
+              *reinterpret_cast<float4*>(dst + e) =
+                  ok ? make_float4(sum[e], sum[e + 1], sum[e + 2], sum[e + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c0 + e + u < n) dst[e + u] = ok ? sum[e + u] : 0.f;
+            }
+          }
         }
       }
-    } else if (warp >= 2) {
-      // ------------------------------------------------ (min,+) CUDA-core tile
-      const int tiles_n = (int)((n + MPN - 1) / MPN);
-      const int64_t i0 = (int64_t)(local / tiles_n) * 128, j0 = (int64_t)(local % tiles_n) * MPN;
-      const int32_t* A = static_cast<const int32_t*>(T.A[p]);
-      const int32_t* B = static_cast<const int32_t*>(T.B[p]);
-      int32_t* C = static_cast<int32_t*>(T.C[p]);
-      const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
-      const int tid = threadIdx.x - 64;
-      // out-of-range problems are left to the 32-bit fallback launch
-      if (__ldcg(&violation[p]) == 0)
-        mp::minplus16_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, i0, j0, (int64_t)0, k, vec, tid,
-                           reinterpret_cast<uint32_t*>(smem), mp::SyncNamed256());
     }
-    __syncthreads();
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -352,7 +420,7 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     const double cb = (double)probs[b].m * probs[b].n * (double)std::max<int64_t>(probs[b].k, 1);
     return ca > cb;
   });
-  int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0;
+  int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0, mp16_tiles = 0;
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[order[i]];
     T.kind[i] = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : 1;
@@ -363,24 +431,28 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     T.B[i] = q.B;
     T.C[i] = q.C;
     T.tile_start[i] = (int)tiles;
+    T.mp16_tile_start[i] = (int)mp16_tiles;
     T.mp_tile_start[i] = (int)mp_tiles;
-    if (q.semiring == MM_SR_MIN_PLUS_I32 && q.m > 0 && q.n > 0)
+    if (q.semiring == MM_SR_MIN_PLUS_I32 && q.m > 0 && q.n > 0) {
       mp_tiles += ((q.m + mp::BM - 1) / mp::BM) * ((q.n + mp::BN - 1) / mp::BN);
-    const int64_t bn = T.kind[i] == 0 ? TBN : MPN;
-    if (q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + bn - 1) / bn);
+      mp16_tiles += ((q.m + mp::PBM - 1) / mp::PBM) * ((q.n + MPN - 1) / MPN);
+    }
+    if (T.kind[i] == 0 && q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN);
     if (T.kind[i] == 0) {
       T.row0a[i] = (int)ra;
       T.row0b[i] = (int)rb;
       ra += q.m;
       rb += q.n;
-      kp_max = std::max<int64_t>(kp_max, align_up(q.k > 0 ? q.k : 1, TBK));
+      kp_max = std::max<int64_t>(kp_max, align_up(q.k > 0 ? q.k : 1, TKA));
     }
   }
   if (tiles > (int64_t)1 << 30 || mp_tiles > (int64_t)1 << 30 || ra > (int64_t)1 << 30 ||
       rb > (int64_t)1 << 30)
     return MM_ERR_SHAPE;
   T.tile_start[count] = (int)tiles;
+  T.mp16_tile_start[count] = (int)mp16_tiles;
   T.mp_tile_start[count] = (int)mp_tiles;
+  T.mp16_total = (int)mp16_tiles;
   T.mp_total = (int)mp_tiles;
   T.count = count;
   T.total_tiles = (int)tiles;
@@ -421,7 +493,7 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   BatchPlan P;
   int rc = make_plan(count, problems, &P);
   if (rc != MM_OK) return rc;
-  if (count == 0 || P.T.total_tiles == 0) return MM_OK;
+  if (count == 0 || (P.T.total_tiles == 0 && P.T.mp_total == 0)) return MM_OK;
   if (!workspace) return MM_ERR_ARG;
   if (!aligned16(workspace)) return MM_ERR_ALIGN;
   if ((size_t)P.total > workspace_bytes) return MM_ERR_WORKSPACE;
@@ -442,11 +514,11 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   }
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
   const int64_t ra = std::max<int64_t>(P.rows_a, 1), rb = std::max<int64_t>(P.rows_b, 1);
-  const int64_t kp = std::max<int64_t>(P.KP, TBK);
-  MMSR_TRY_STATUS(make_tmap_2d_16bit(&ta_hi, ahi, ra, kp, kp, TBM, true));
-  MMSR_TRY_STATUS(make_tmap_2d_16bit(&ta_lo, alo, ra, kp, kp, TBM, true));
-  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_hi, bhi, rb, kp, kp, TBN, true));
-  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_lo, blo, rb, kp, kp, TBN, true));
+  const int64_t kp = std::max<int64_t>(P.KP, TKA);
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&ta_hi, ahi, ra, kp, kp, TBM, true, TBK));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&ta_lo, alo, ra, kp, kp, TBM, true, TBK));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_hi, bhi, rb, kp, kp, TBN, true, TBK));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_lo, blo, rb, kp, kp, TBN, true, TBK));
   static bool configured = false;
   if (!configured) {
     MMSR_TRY_STATUS(
@@ -456,10 +528,15 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   int dev = 0, sms = kNumSMs;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(sms, P.T.total_tiles);
-  {
+  if (P.T.total_tiles > 0) {
     TraceScope tr(kTrBatched, st);
-    batched_kernel<<<grid, kBThreads, BSMEM, st>>>(P.T, ta_hi, ta_lo, tb_hi, tb_lo, counter, violation);
+    const int grid = std::min(sms, P.T.total_tiles);
+    batched_kernel<<<grid, kBThreads, BSMEM, st>>>(P.T, ta_hi, ta_lo, tb_hi, tb_lo, counter);
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  if (P.T.mp16_total > 0) {
+    TraceScope tr(kTrMinplus16Leaf, st);
+    batched_minplus16_kernel<<<(unsigned)P.T.mp16_total, 256, 0, st>>>(P.T, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   if (P.T.mp_total > 0) {

@@ -107,3 +107,28 @@ def test_workload_512_problems():
     probs = inputs.batched_problems(count=512, seed=4)
     assert sum(p.semiring == F32 for p in probs) == 358
     _check(probs, _launch(probs))
+
+
+@pytest.mark.parametrize("only", [F32, MP])
+def test_single_semiring_batches(only):
+    # a batch with no (min,+) (or no FP32) problem skips that launch entirely
+    probs = [p for p in _mixed(30, seed=204, lo=20, hi=600) if p.semiring == only]
+    assert probs
+    _check(probs, _launch(probs))
+
+
+def test_k_zero_and_tiny_problems():
+    # k = 0 writes the semiring's 0; 1 x 1 x 1 problems of both kinds
+    rng = np.random.default_rng(205)
+    probs = []
+    for sr, m, n, k in ((F32, 3, 5, 0), (MP, 4, 6, 0), (F32, 1, 1, 1), (MP, 1, 1, 1), (F32, 130, 129, 257)):
+        if sr == F32:
+            A = rng.standard_normal((m, k)).astype(np.float32)
+            B = rng.standard_normal((k, n)).astype(np.float32)
+        else:
+            A = rng.integers(0, 1001, size=(m, k)).astype(np.int32)
+            B = rng.integers(0, 1001, size=(k, n)).astype(np.int32)
+        probs.append(inputs.Problem(sr, m, n, k, A, B))
+    outs = _launch(probs)
+    assert np.all(outs[0] == 0.0) and np.all(outs[1] == mmsr.INF)
+    _check(probs, outs)
