@@ -599,6 +599,17 @@ def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
                           "workspace_n2x4B": p.workspace_min / (n * n * 4.0), "kernel_ms": split}
         del ws
         torch.cuda.empty_cache()
+    # TAR-Strassen: one level, products added into C's quadrants by the leaf
+    # epilogue in conflict-free waves (no product temporaries)
+    p = mmsr.mm_strassen_tar_query(sr, n, n, n)
+    ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+    fn = lambda: mmsr.mm_strassen_tar(mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
+                                      int(p.workspace_min), sp)
+    ms = _time_call(torch, fn, 3)
+    res["tar_L1"] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                     "workspace_bytes": int(p.workspace_min), "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
+    del ws
+    torch.cuda.empty_cache()
     # STAR-Strassen-1 mixed plans: c classic in-place levels over L Strassen
     # levels; the workspace of one block product only
     for c, L in ((1, 1), (1, 2), (2, 1), (2, 2)):

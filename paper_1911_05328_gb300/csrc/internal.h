@@ -50,10 +50,23 @@ int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, i
                        int batches, void* ws, cudaStream_t st);
 int read_batched_status(int* status);
 
+// Leaf epilogue that adds each product into quadrants of C instead of
+// writing it out: batch entry b adds sign[b][d] x product into dst[b][d]
+// (d < 4, nullptr = unused; row pitch ld), overwriting where add[b][d] == 0.
+// entries == 0 selects the ordinary output.
+struct QuadOut {
+  float* dst[7][4];
+  int8_t sign[7][4];
+  int8_t add[7][4];
+  int64_t ld;
+  int entries;
+};
+
 // batched leaves (independent products on stacked operands)
 cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
                                   const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,
-                                  int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st);
+                                  int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st,
+                                  const QuadOut* quad = nullptr);
 cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int64_t m, int64_t n,
                                 int64_t k, int batches, cudaStream_t st);
 
@@ -70,6 +83,13 @@ int plan_star_strassen(int classic, int levels, int sr, int64_t m, int64_t n, in
 int run_star_strassen(int classic, int levels, int variant, int sr, int64_t m, int64_t n, int64_t k,
                       const void* A, const void* B, void* C, void* ws, size_t ws_bytes,
                       cudaStream_t st);
+
+// TAR-Strassen level: products added straight into the quadrants of C in
+// conflict-free waves (FP32 mode)
+int plan_strassen_tar(int sr, int64_t m, int64_t n, int64_t k, mm_plan_t* p);
+int run_strassen_tar(int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
+                     void* ws, size_t ws_bytes, cudaStream_t st);
+int strassen_tar_waves(int variant, int* wave_of_product);
 
 // closure by repeated squaring
 int closure_squarings(int64_t n);

@@ -149,13 +149,20 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// Output slot of each of the seven products (identity, or the wave order of
+// a TAR-Strassen level, whose waves must sit in consecutive slots).
+struct Slots7 {
+  int8_t s[7];
+};
+
 // Last level, A side, FP32 mode: seven (h x w) sums written as bf16 hi/lo
-// rows of pitch Kp (columns w..Kp-1 zero).  Blocks walk rows, threads walk
-// 8-column groups; `vec` = the source rows allow 16-byte loads.
+// rows of pitch Kp (columns w..Kp-1 zero), product p into slot slot.s[p].
+// Blocks walk rows, threads walk 8-column groups; `vec` = the source rows
+// allow 16-byte loads.
 template <int VARIANT>
 __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
     const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int h, int w, int Kp,
-    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int vec) {
+    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int vec, Slots7 slot) {
   const int r = blockIdx.y;
   const float* s = src + (int64_t)r * src_stride;
   for (int i = blockIdx.x; i < h; i += gridDim.x) {
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
 #pragma unroll
         for (int t = 0; t < 8; ++t)
           split_bf16(combo4<VARIANT, 0>(p, x[0][t], x[1][t], x[2][t], x[3][t]), hh[t], ll[t]);
-        const int64_t off = ((int64_t)(r * 7 + p) * h + i) * Kp + c8;
+        const int64_t off = ((int64_t)(r * 7 + slot.s[p]) * h + i) * Kp + c8;
         *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(hh);
         *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(ll);
       }
@@ -189,12 +196,13 @@ __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
 }
 
 // Last level, B side, FP32 mode: source stack matrix r is (2h x 2w) = (k x n);
-// the seven sums T_p (h x w) are written transposed as bf16 hi/lo (w x Kp).
-// Tile: 64 k x 32 n of each quadrant through shared memory.
+// the seven sums T_p (h x w) are written transposed as bf16 hi/lo (w x Kp),
+// product p into slot slot.s[p].  Tile: 64 k x 32 n of each quadrant
+// through shared memory.
 template <int VARIANT>
 __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
     const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int64_t h, int64_t w,
-    int64_t Kp, __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT) {
+    int64_t Kp, __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT, Slots7 slot) {
   __shared__ float tile[4][64][33];
   const int r = blockIdx.z;
   const float* s = src + (int64_t)r * src_stride;
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
       split_bf16(combo4<VARIANT, 1>(p, tile[0][kk][row], tile[1][kk][row], tile[2][kk][row], tile[3][kk][row]),
                  hh[t], ll[t]);
     }
-    const int64_t off = ((int64_t)(r * 7 + p) * w + gn) * Kp + k0 + chunk * 8;
+    const int64_t off = ((int64_t)(r * 7 + slot.s[p]) * w + gn) * Kp + k0 + chunk * 8;
     *reinterpret_cast<uint4*>(hiT + off) = *reinterpret_cast<const uint4*>(hh);
     *reinterpret_cast<uint4*>(loT + off) = *reinterpret_cast<const uint4*>(ll);
   }
@@ -730,7 +738,7 @@ inline int pass_first_level(int L, int l) { return (L & 1) && l == 1 ? 1 : 2; }
 // cols with row pitch ld.
 cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t rows, int64_t cols,
                        int64_t ld, uint8_t* ws, const StrassenLayout& S, __nv_bfloat16* hi,
-                       __nv_bfloat16* lo, cudaStream_t st) {
+                       __nv_bfloat16* lo, cudaStream_t st, Slots7 slot = {{0, 1, 2, 3, 4, 5, 6}}) {
   const float* src = X;
   int64_t src_ld = ld, src_stride = 0;
   int pass = 0;
@@ -764,10 +772,10 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
         const dim3 g(rows_grid(h, R, threads), (unsigned)R);
         if (variant == 0)
           pre_combine_split_rows_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
-                                                                 (int)S.KpL, hi, lo, vec);
+                                                                 (int)S.KpL, hi, lo, vec, slot);
         else
           pre_combine_split_rows_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
-                                                                 (int)S.KpL, hi, lo, vec);
+                                                                 (int)S.KpL, hi, lo, vec, slot);
       }
       MMSR_CUDA_TRY(cudaGetLastError());
     } else {
@@ -782,9 +790,11 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
       } else {
         const dim3 g((unsigned)(S.KpL / 64), (unsigned)((w + 31) / 32), (unsigned)R);
         if (variant == 0)
-          pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
+          pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo,
+                                                                  slot);
         else
-          pre_combine_split_transpose_kernel<1><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
+          pre_combine_split_transpose_kernel<1><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo,
+                                                                  slot);
       }
       MMSR_CUDA_TRY(cudaGetLastError());
     }
@@ -936,6 +946,7 @@ void fill_plan(int levels, int sr, int64_t total, mm_plan_t* p) {
 
 int g_strassen_top_f64 = 0;  // mm_set_option(MM_OPT_STRASSEN_TOP_F64, ...)
 
+
 void strassen_tables(int variant, int8_t* alpha, int8_t* beta, int8_t* gamma) {
   for (int r = 0; r < 7; ++r)
     for (int q = 0; q < 4; ++q) {
@@ -959,6 +970,113 @@ int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t 
   const StrassenLayout S = strassen_layout(levels, sr, m, n, k);
   if ((size_t)S.total > ws_bytes) return MM_ERR_WORKSPACE;
   return run_view(levels, variant, sr, m, n, k, A, k, B, n, C, n, 0, static_cast<uint8_t*>(ws), S, st);
+}
+
+// TAR-Strassen (the zero-temporary Strassen schedule the paper sketches in
+// Section 5): one level whose seven products are added straight into the
+// quadrants of C by the leaf epilogue -- no product temporaries.  Products
+// run in waves in which no two touch the same quadrant, so the read-modify-
+// writes of one launch never collide; a quadrant's first writer overwrites
+// it.  The waves are a greedy colouring of the gamma table in product order
+// (for the paper's formulas exactly the order P1; P2 || P5; P3 || P4;
+// P6 || P7).  FP32 mode only (the quadrant epilogue lives in the bf16x3
+// leaf).  Workspace: the operand sums only.
+struct TarWaves {
+  int count;
+  int size[7];
+  int member[7][7];
+};
+
+TarWaves tar_waves(int variant) {
+  TarWaves W;
+  memset(&W, 0, sizeof(W));
+  int used[7] = {0};  // quadrant mask per wave
+  for (int r = 0; r < 7; ++r) {
+    int mask = 0;
+    for (int q = 0; q < 4; ++q)
+      if (coef_gamma(variant, q, r) != 0) mask |= 1 << q;
+    int w = 0;
+    while (w < W.count && (used[w] & mask)) ++w;
+    if (w == W.count) ++W.count;
+    used[w] |= mask;
+    W.member[w][W.size[w]++] = r;
+  }
+  return W;
+}
+
+size_t tar_workspace(int64_t m, int64_t n, int64_t k) {
+  return (size_t)strassen_layout(1, MM_SR_PLUS_TIMES_F32, m, n, k).off_p;
+}
+
+int run_tar_view(int variant, int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B,
+                 int64_t ldb, float* C, int64_t ldc, uint8_t* w, cudaStream_t st) {
+  const StrassenLayout S = strassen_layout(1, MM_SR_PLUS_TIMES_F32, m, n, k);
+  const TarWaves W = tar_waves(variant);
+  Slots7 slot;
+  int next = 0;
+  for (int v = 0; v < W.count; ++v)
+    for (int i = 0; i < W.size[v]; ++i) slot.s[W.member[v][i]] = (int8_t)next++;
+  auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + S.off_ahi);
+  auto* alo = reinterpret_cast<__nv_bfloat16*>(w + S.off_alo);
+  auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + S.off_bhi);
+  auto* blo = reinterpret_cast<__nv_bfloat16*>(w + S.off_blo);
+  cudaError_t e;
+  {
+    TraceScope tr(kTrStrassenCombine, st);
+    e = expand_f32(1, variant, 0, A, m, k, lda, w, S, ahi, alo, st, slot);
+    if (e == cudaSuccess) e = expand_f32(1, variant, 1, B, k, n, ldb, w, S, bhi, blo, st, slot);
+  }
+  if (e != cudaSuccess) return report_cuda(e, "TAR-Strassen operand pass");
+  bool written[4] = {false, false, false, false};
+  int first_slot = 0;
+  for (int v = 0; v < W.count; ++v) {
+    QuadOut qo;
+    memset(&qo, 0, sizeof(qo));
+    qo.entries = W.size[v];
+    qo.ld = ldc;
+    bool wrote[4] = {false, false, false, false};
+    for (int i = 0; i < W.size[v]; ++i) {
+      const int r = W.member[v][i];
+      int d = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int g = coef_gamma(variant, q, r);
+        if (g == 0) continue;
+        qo.dst[i][d] = C + (q >> 1) * S.mL * ldc + (q & 1) * S.nL;
+        qo.sign[i][d] = (int8_t)g;
+        qo.add[i][d] = written[q] ? 1 : 0;
+        wrote[q] = true;
+        ++d;
+      }
+    }
+    for (int q = 0; q < 4; ++q) written[q] = written[q] || wrote[q];
+    e = launch_bf16x3_batched(ahi + (int64_t)first_slot * S.mL * S.KpL, alo + (int64_t)first_slot * S.mL * S.KpL,
+                              bhi + (int64_t)first_slot * S.nL * S.KpL, blo + (int64_t)first_slot * S.nL * S.KpL,
+                              nullptr, S.mL, S.nL, S.KpL, W.size[v], st, &qo);
+    if (e != cudaSuccess) return report_cuda(e, "TAR-Strassen leaf wave");
+    first_slot += W.size[v];
+  }
+  return MM_OK;
+}
+
+int plan_strassen_tar(int sr, int64_t m, int64_t n, int64_t k, mm_plan_t* p) {
+  if (sr != MM_SR_PLUS_TIMES_F32) return MM_ERR_UNSUPPORTED;
+  fill_plan(1, sr, (int64_t)tar_workspace(m, n, k), p);
+  return MM_OK;
+}
+
+int run_strassen_tar(int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
+                     void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (sr != MM_SR_PLUS_TIMES_F32) return MM_ERR_UNSUPPORTED;
+  if (tar_workspace(m, n, k) > ws_bytes) return MM_ERR_WORKSPACE;
+  return run_tar_view(variant, m, n, k, static_cast<const float*>(A), k, static_cast<const float*>(B), n,
+                      static_cast<float*>(C), n, static_cast<uint8_t*>(ws), st);
+}
+
+int strassen_tar_waves(int variant, int* wave_of_product) {
+  const TarWaves W = tar_waves(variant);
+  for (int v = 0; v < W.count; ++v)
+    for (int i = 0; i < W.size[v]; ++i) wave_of_product[W.member[v][i]] = v;
+  return W.count;
 }
 
 // STAR-Strassen-1 (Theorem star-strassen-1): the top `classic` levels are

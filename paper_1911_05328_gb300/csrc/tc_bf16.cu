@@ -179,13 +179,18 @@ struct Bf16x3Cfg {
 // B tile -- each CTA loads half of it and multicasts the half into both CTAs'
 // shared memory, so a CTA pair fetches B once instead of twice; each stage is
 // released by MMA-completion arrivals from both CTAs.
-template <int BN, int STAGES, int CHUNK, bool MC>
+// QUAD epilogue: instead of writing its tile to C, batch entry b adds
+// sign[b][d] x tile into up to four destinations dst[b][d] (row pitch ld),
+// overwriting where add[b][d] is 0 -- the leaf epilogue of a Strassen level
+// whose products go straight into the quadrants of C (no product
+// temporaries).  Entries of one launch must write disjoint destinations.
+template <int BN, int STAGES, int CHUNK, bool MC, bool QUAD>
 __global__ void __launch_bounds__(kTcThreads, 1)
     bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAhi, const __grid_constant__ CUtensorMap tAlo,
                        const __grid_constant__ CUtensorMap tBhi, const __grid_constant__ CUtensorMap tBlo,
                        float* __restrict__ C, float* __restrict__ W, int64_t m, int64_t n,
                        int kb_total, int kb_per_slice, int slices, int64_t a_batch_rows,
-                       int64_t b_batch_rows, int64_t c_batch_stride) {
+                       int64_t b_batch_rows, int64_t c_batch_stride, const __grid_constant__ QuadOut quad) {
   using Cfg = Bf16x3Cfg<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
@@ -341,7 +346,49 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     float* out = (z == 0) ? C + (int64_t)batch * c_batch_stride : W + (int64_t)(z - 1) * m * n;
     const int64_t row = i0 + q * 32 + lane;
-    if (row < m) {
+    if constexpr (QUAD) {
+      if (row < m) {
+      const int64_t c0 = j0 + half * Cfg::COLS_PER_WARP;
+      const int64_t cols_left = n - c0;
+      if (!ok) {
+#pragma unroll
+        for (int e = 0; e < Cfg::COLS_PER_WARP; ++e) sum[e] = 0.f;
+      }
+#pragma unroll 1
+      for (int d = 0; d < 4; ++d) {
+        float* base = quad.dst[batch][d];
+        if (base == nullptr) continue;
+        const float sg = (float)quad.sign[batch][d];
+        const bool add = quad.add[batch][d] != 0;
+        float* dst = base + row * quad.ld + c0;
+        if ((quad.ld % 4 == 0) && aligned16(base) && cols_left >= Cfg::COLS_PER_WARP) {
+          // four 16-byte reads in flight per round trip, then their stores
+#pragma unroll
+          for (int e0 = 0; e0 < Cfg::COLS_PER_WARP; e0 += 16) {
+            float4 o[4];
+            if (add) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) o[u] = *reinterpret_cast<const float4*>(dst + e0 + 4 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int e = e0 + 4 * u;
+              float4 v = make_float4(sg * sum[e], sg * sum[e + 1], sg * sum[e + 2], sg * sum[e + 3]);
+              if (add) {
+                v.x = __fadd_rn(o[u].x, v.x); v.y = __fadd_rn(o[u].y, v.y);
+                v.z = __fadd_rn(o[u].z, v.z); v.w = __fadd_rn(o[u].w, v.w);
+              }
+              *reinterpret_cast<float4*>(dst + e) = v;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < Cfg::COLS_PER_WARP; ++e)
+            if (e < cols_left) dst[e] = add ? __fadd_rn(dst[e], sg * sum[e]) : sg * sum[e];
+        }
+      }
+      }
+    } else if (row < m) {
       const int64_t c0 = j0 + half * Cfg::COLS_PER_WARP;
       float* dst = out + row * n + c0;
       const int64_t cols_left = n - c0;
@@ -394,22 +441,32 @@ cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const 
                         const CUtensorMap& b_lo, float* C, float* W, int64_t m, int64_t n,
                         int kb_total, int kbs, int s, cudaStream_t st, int batches = 1,
                         int64_t a_batch_rows = 0, int64_t b_batch_rows = 0,
-                        int64_t c_batch_stride = 0, bool pair = false) {
+                        int64_t c_batch_stride = 0, bool pair = false, const QuadOut* quad = nullptr) {
+  QuadOut qo;
+  if (quad) qo = *quad; else memset(&qo, 0, sizeof(qo));
   using Cfg = Bf16x3Cfg<BN, STAGES>;
   static bool configured = false;
   if (!configured) {
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false>,
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, true>,
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, true, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     configured = true;
   }
+  const bool q = qo.entries > 0;
+  if (q) pair = false;  // the quadrant epilogue runs on independent CTAs
   const unsigned tiles_m = (unsigned)((m + BM - 1) / BM), tiles_n = (unsigned)((n + BN - 1) / BN);
   TraceScope tr(kTrTcBf16x3, st);
   if (!pair) {
     dim3 grid(tiles_n, tiles_m, (unsigned)(s * batches));
-    bf16x3_gemm_kernel<BN, STAGES, CHUNK, false><<<grid, kTcThreads, Cfg::SMEM, st>>>(
-        a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride);
+    if (q)
+      bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, true><<<grid, kTcThreads, Cfg::SMEM, st>>>(
+          a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
+    else
+      bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, false><<<grid, kTcThreads, Cfg::SMEM, st>>>(
+          a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
     return cudaGetLastError();
   }
   // pairs along M: an odd tile-row count gets one idle partner row, whose
@@ -426,8 +483,8 @@ cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, bf16x3_gemm_kernel<BN, STAGES, CHUNK, true>, a_hi, a_lo, b_hi, b_lo, C, W,
-                            m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride);
+  return cudaLaunchKernelEx(&cfg, bf16x3_gemm_kernel<BN, STAGES, CHUNK, true, false>, a_hi, a_lo, b_hi, b_lo, C, W,
+                            m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
 }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -473,7 +530,8 @@ cudaError_t launch_split_bf16(const float* A, const float* B, int64_t m, int64_t
 // output P + b*m*n (row-major m x n each).
 cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
                                   const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,
-                                  int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st) {
+                                  int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st,
+                                  const QuadOut* quad) {
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
   MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_hi, ahi, batches * m, Kp, Kp, BM, true, kTcBK));
   MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_lo, alo, batches * m, Kp, Kp, BM, true, kTcBK));
@@ -482,7 +540,7 @@ cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16*
   MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, batches * n, Kp, Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK));
   const int kb_total = (int)(Kp / kTcBK);
   return launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, P, nullptr, m, n,
-                                                 kb_total, kb_total, 1, st, batches, m, n, m * n, pair);
+                                                 kb_total, kb_total, 1, st, batches, m, n, m * n, pair, quad);
 }
 
 int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {

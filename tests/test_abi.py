@@ -157,3 +157,37 @@ def test_star_strassen_argument_checks_and_workspace(lib):
                                int(mmsr.mm_star_strassen_query(1, 1, sr, 64, 64, 64).workspace_min) - 1024,
                                stream=0, check=False)
     assert rc == mmsr.MM_ERR_WORKSPACE
+
+
+def test_tar_strassen_waves_follow_the_papers_order(lib):
+    # Section 5's zero-temporary Strassen writes P1; then P2 and P5 together;
+    # then P3 and P4; then P6 and P7 (products numbered P1..P7 as printed).
+    count, wave = mmsr.mm_strassen_tar_waves(mmsr.MM_STRASSEN_PAPER)
+    assert count == 4
+    assert wave == [0, 1, 2, 2, 1, 3, 3]
+    for variant in (mmsr.MM_STRASSEN_PAPER, mmsr.MM_STRASSEN_WINOGRAD):
+        count, wave = mmsr.mm_strassen_tar_waves(variant)
+        _, _, gamma = mmsr.mm_strassen_tables(variant)
+        for w in range(count):
+            members = [r for r in range(7) if wave[r] == w]
+            assert members
+            touched = [q for r in members for q in range(4) if gamma[q, r] != 0]
+            assert len(touched) == len(set(touched)), (variant, w, members)
+
+
+def test_tar_strassen_argument_checks_and_workspace(lib):
+    W = mmsr.MM_STRASSEN_WINOGRAD
+    for sr in (mmsr.MM_SR_PLUS_TIMES_F64, mmsr.MM_SR_PLUS_TIMES_F64ACC, mmsr.MM_SR_MIN_PLUS_I32):
+        assert mmsr.mm_strassen_tar(W, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_UNSUPPORTED
+    sr = mmsr.MM_SR_PLUS_TIMES_F32
+    assert mmsr.mm_strassen_tar(W, sr, 9, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_SHAPE
+    assert mmsr.mm_strassen_tar(5, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    n = 4096
+    tar = mmsr.mm_strassen_tar_query(sr, n, n, n)
+    full = mmsr.mm_plan_query(sr, 1, n, n, n)
+    # exactly the product stack of one level is saved: 7 (n/2)^2 FP32 values
+    assert full.workspace_min - tar.workspace_min == 7 * (n // 2) ** 2 * 4
+    rc = mmsr.mm_strassen_tar(W, sr, 64, 64, 64, FAKE, FAKE, FAKE, FAKE,
+                              int(mmsr.mm_strassen_tar_query(sr, 64, 64, 64).workspace_min) - 1024, stream=0,
+                              check=False)
+    assert rc == mmsr.MM_ERR_WORKSPACE
