@@ -5,7 +5,8 @@
 Cases: minplus4096 (the (min,+) n=4096 product, budget 0 unless --budget),
 f32_<n> (FP32 mode, bf16x3 on tensor cores), f64acc_<n> (FP64-accuracy mode),
 f64_<n> (plain FP64 path), orand_<n> (boolean), batched512 (the 512-problem
-mixed batch in one persistent launch).
+mixed batch), strassen<L>_<n> (FP32-mode Strassen-Winograd, L levels,
+uniform[-1,1] inputs), tar_<n> (one TAR-Strassen level, FP32 mode).
 Inputs come from the seeded generators; nothing is checked here.
 """
 import argparse
@@ -60,6 +61,25 @@ def main():
         ws = torch.empty((need,), dtype=torch.uint8, device="cuda")
         for _ in range(a.reps):
             mmsr.mm_batched(table, ws, need)
+        torch.cuda.synchronize()
+        print("done", a.case, "reps", a.reps)
+        return
+    elif a.case.startswith("strassen") or a.case.startswith("tar_"):
+        tar = a.case.startswith("tar_")
+        L = 1 if tar else int(a.case[len("strassen"):a.case.index("_")])
+        n = int(a.case[a.case.index("_") + 1:])
+        A, B = inputs.uniform_f64(n, n, n, seed=3)
+        dA = torch.from_numpy(A.astype("float32")).cuda()
+        dB = torch.from_numpy(B.astype("float32")).cuda()
+        dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        sr = mmsr.MM_SR_PLUS_TIMES_F32
+        p = mmsr.mm_strassen_tar_query(sr, n, n, n) if tar else mmsr.mm_plan_query(sr, L, n, n, n, 0)
+        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            if tar:
+                mmsr.mm_strassen_tar(mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min))
+            else:
+                mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min))
         torch.cuda.synchronize()
         print("done", a.case, "reps", a.reps)
         return
