@@ -143,6 +143,13 @@ def ncu_traffic(kernel_files, key):
     return rec.get("dram_bytes_per_launch")
 
 
+def bench_config(world):
+    """The workload both arms report (the reference arm times a row sample of it)."""
+    return {"workload": "minplus_n4096_int32_inf10pct_seed1_budgets_0_1_2_4_8", "n": N,
+            "budgets_buffers": list(BUDGETS), "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 # --------------------------------------------------------------- reference
 def run_reference(args, rank):
     if rank != 0:
@@ -170,10 +177,10 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
         "data": "synthetic",
-        "config": {"workload": "minplus_n4096_int32_inf10pct_seed1", "n": N,
-                   "sample": "%d random rows of C per step" % rows_per_step},
+        "config": bench_config(args.gpus),
         "cpu_baseline": {"value": value, "unit": "GOp/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d rows x 4096 x 4096 per step" % rows_per_step},
+                         "sample": "%d random rows of C (x 4096 x 4096) per step; the oracle has no "
+                                   "budget, so every step is one product's row sample" % rows_per_step},
         "e2e": {"value": value, "unit": "GOp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -352,9 +359,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "GOp/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-        "config": {"workload": "minplus_n4096_int32_inf10pct_seed1_budgets_0_1_2_4_8", "n": N,
-                   "budgets_buffers": list(BUDGETS), "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": bench_config(world),
         "error": "bit-exact vs int64 oracle (tests); budgets agree: %s" % consistent,
         "pct_of_dtype_peak": 100.0 * (value / world) / (peak_tops * 1e3),
         "peak_workspace_bytes": int(max(p.workspace_used for p in plans)),
