@@ -2,7 +2,7 @@
 // one persistent launch (the dynamic load balancing a processor-oblivious
 // schedule relies on, Section 6: idle workers take the next available task).
 //
-// Host side: problems are sorted by cost (2 m n k, longest first) and cut
+// Host side: problems are sorted by tile cost (k, longest first) and cut
 // into output tiles; the sorted problem table travels by value as a kernel
 // parameter.  FP32 problems are split into bf16 hi/lo operands by one
 // pre-pass into stacked buffers with a common row pitch (so four tensor maps
@@ -56,7 +56,7 @@ constexpr int MPN = 256;  // (min,+) tile: 128 x 256
 struct BatchTable {
   int count;
   int total_tiles;  // FP32 tiles (persistent kernel)
-  int kind[kMaxBatch];  // 0: FP32 (+,x) on tensor cores, 1: (min,+)
+  int kind[kMaxBatch];  // 0: FP32 (+,x) on tensor cores, 1: (min,+) 256-wide tiles, 2: 128-wide
   int m[kMaxBatch], n[kMaxBatch], k[kMaxBatch];
   int tile_start[kMaxBatch + 1];     // 128 x 128 tiles of FP32 problems
   int mp16_tile_start[kMaxBatch + 1];  // 128 x 256 packed tiles of (min,+) problems
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const __grid_constan
 __global__ void __launch_bounds__(256) batched_range_kernel(const __grid_constant__ BatchTable T,
                                                             int* __restrict__ violation) {
   const int p = blockIdx.y;
-  if (T.kind[p] != 1) return;
+  if (T.kind[p] == 0) return;
   int bad = 0;
   const int64_t stride = (int64_t)gridDim.x * 256;
   const int64_t t0 = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256, 2)
     if (T.mp_tile_start[mid] <= t) lo = mid; else hi = mid - 1;
   }
   const int p = lo;
-  if (T.kind[p] != 1 || __ldcg(&violation[p]) == 0) return;
+  if (T.kind[p] == 0 || __ldcg(&violation[p]) == 0) return;
   extern __shared__ __align__(16) int32_t fsmem[];
   const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
   const int local = t - T.mp_tile_start[p];
@@ -180,9 +180,24 @@ __global__ void __launch_bounds__(256, 2)
                      (int)threadIdx.x, fsmem, mp::SyncCta());
 }
 
-// Packed (min,+) tiles: one 128 x 256 tile per CTA over the compact list of
-// (min,+) problems' tiles (longest problem first); CTAs of problems outside
+// Packed (min,+) tiles: one tile per CTA over the compact list of (min,+)
+// problems' tiles (longest first); a problem uses 128 x 256 tiles, or
+// 128 x 128 tiles where that pads its width less.  CTAs of problems outside
 // the packed range exit at once.
+template <int NP>
+__device__ __forceinline__ void batched_packed_tile(const BatchTable& T, int p, int local, uint32_t* psmem) {
+  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+  constexpr int TN = mp::PackTile<NP>::TN;
+  const int tiles_n = (int)((n + TN - 1) / TN);
+  const int32_t* A = static_cast<const int32_t*>(T.A[p]);
+  const int32_t* B = static_cast<const int32_t*>(T.B[p]);
+  int32_t* C = static_cast<int32_t*>(T.C[p]);
+  const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
+  mp::minplus16_tile<mp::SyncCta, NP>(A, B, C, (int32_t*)nullptr, 0, m, n, k, (int64_t)(local / tiles_n) * mp::PBM,
+                                      (int64_t)(local % tiles_n) * TN, (int64_t)0, k, vec, (int)threadIdx.x,
+                                      psmem, mp::SyncCta());
+}
+
 __global__ void __launch_bounds__(256, 2)
     batched_minplus16_kernel(const __grid_constant__ BatchTable T, const int* __restrict__ violation) {
   const int t = blockIdx.x;
@@ -192,18 +207,13 @@ __global__ void __launch_bounds__(256, 2)
     if (T.mp16_tile_start[mid] <= t) lo = mid; else hi = mid - 1;
   }
   const int p = lo;
-  if (T.kind[p] != 1 || __ldcg(&violation[p]) != 0) return;
+  if (T.kind[p] == 0 || __ldcg(&violation[p]) != 0) return;
   __shared__ __align__(16) uint32_t psmem[mp::PSMEM_BYTES / 4];
-  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
   const int local = t - T.mp16_tile_start[p];
-  const int tiles_n = (int)((n + MPN - 1) / MPN);
-  const int32_t* A = static_cast<const int32_t*>(T.A[p]);
-  const int32_t* B = static_cast<const int32_t*>(T.B[p]);
-  int32_t* C = static_cast<int32_t*>(T.C[p]);
-  const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
-  mp::minplus16_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, (int64_t)(local / tiles_n) * mp::PBM,
-                     (int64_t)(local % tiles_n) * MPN, (int64_t)0, k, vec, (int)threadIdx.x, psmem,
-                     mp::SyncCta());
+  if (T.kind[p] == 1)
+    batched_packed_tile<8>(T, p, local, psmem);
+  else
+    batched_packed_tile<4>(T, p, local, psmem);
 }
 
 // Shared-memory descriptor of a K-major operand tile with TBK-wide rows.
@@ -414,16 +424,19 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     if (q.m > 0 && q.n > 0 && (!q.C || (q.k > 0 && (!q.A || !q.B)))) return MM_ERR_ARG;
     if (!aligned16(q.C) || !aligned16(q.A) || !aligned16(q.B)) return MM_ERR_ALIGN;
   }
-  // longest first (cost 2 m n k), ties by index for determinism
+  // Longest tiles first: every tile of a problem costs ~k (tiles have a fixed
+  // size), so descending k is longest-processing-time order for the tile
+  // queues; ties by m n (more tiles first), then by index for determinism.
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    const double ca = (double)probs[a].m * probs[a].n * (double)std::max<int64_t>(probs[a].k, 1);
-    const double cb = (double)probs[b].m * probs[b].n * (double)std::max<int64_t>(probs[b].k, 1);
-    return ca > cb;
+    if (probs[a].k != probs[b].k) return probs[a].k > probs[b].k;
+    return (double)probs[a].m * probs[a].n > (double)probs[b].m * probs[b].n;
   });
   int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0, mp16_tiles = 0;
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[order[i]];
-    T.kind[i] = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : 1;
+    // (min,+): 128-wide tiles where they pad the width less than 256-wide ones
+    const bool narrow = ((q.n + 127) / 128) * 128 < ((q.n + 255) / 256) * 256;
+    T.kind[i] = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : (narrow ? 2 : 1);
     T.m[i] = (int)q.m;
     T.n[i] = (int)q.n;
     T.k[i] = (int)q.k;
@@ -435,7 +448,8 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     T.mp_tile_start[i] = (int)mp_tiles;
     if (q.semiring == MM_SR_MIN_PLUS_I32 && q.m > 0 && q.n > 0) {
       mp_tiles += ((q.m + mp::BM - 1) / mp::BM) * ((q.n + mp::BN - 1) / mp::BN);
-      mp16_tiles += ((q.m + mp::PBM - 1) / mp::PBM) * ((q.n + MPN - 1) / MPN);
+      const int64_t tn = T.kind[i] == 2 ? 128 : MPN;
+      mp16_tiles += ((q.m + mp::PBM - 1) / mp::PBM) * ((q.n + tn - 1) / tn);
     }
     if (T.kind[i] == 0 && q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN);
     if (T.kind[i] == 0) {

@@ -96,19 +96,36 @@ constexpr size_t PSMEM_BYTES = 2 * (size_t)(PBK * PBM + PBK * PBNP) * sizeof(uin
 
 __device__ __forceinline__ uint32_t to16(int v) { return min((uint32_t)v, kInf16); }
 
+// Tile shapes of the packed leaf: 128 rows x 32 NP columns, each of the 256
+// threads holding 8 rows x NP column pairs.  NP = 8 (256 columns) is the
+// standard tile; NP = 4 (128 columns) serves narrow products.
+template <int NP>
+struct PackTile {
+  static_assert(NP == 4 || NP == 8, "column pairs per thread");
+  static constexpr int TN = 32 * NP;   // output columns
+  static constexpr int TNP = TN / 2;   // packed column pairs
+  static constexpr int BQ = NP / 2;    // 16-byte B loads per thread and k sub-block
+  static constexpr int BROW = TN / 4;  // 16-byte chunks per B row
+  static constexpr int BROW_LOG2 = NP == 8 ? 6 : 5;
+  static constexpr size_t SMEM = 2 * (size_t)(PBK * PBM + PBK * TNP) * sizeof(uint32_t);
+};
+
+template <int NP>
 struct PackStage {
   int4 a[2];
-  int4 b[4];
+  int4 b[NP / 2];
 };
 
 // Loads the 16-wide k sub-block at k0; columns at or past `kend` (the end
 // of this CTA's k-slice, or k) read as the sentinel.
-__device__ __forceinline__ void packed_load(PackStage& r, const int32_t* __restrict__ A,
+template <int NP>
+__device__ __forceinline__ void packed_load(PackStage<NP>& r, const int32_t* __restrict__ A,
                                             const int32_t* __restrict__ B, int64_t m, int64_t n,
                                             int64_t k, int64_t kend, int64_t i0, int64_t j0,
                                             int64_t k0, bool vec, int tid) {
+  using T = PackTile<NP>;
   const bool a_full = vec && (i0 + PBM <= m) && (k0 + PBK <= kend);
-  const bool b_full = vec && (k0 + PBK <= kend) && (j0 + PBN <= n);
+  const bool b_full = vec && (k0 + PBK <= kend) && (j0 + T::TN <= n);
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int row = tid & 127, c4 = (tid >> 7) + 2 * q;
@@ -125,9 +142,9 @@ __device__ __forceinline__ void packed_load(PackStage& r, const int32_t* __restr
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < T::BQ; ++q) {
     const int idx = tid + q * PTHREADS;
-    const int row = idx >> 6, c4 = idx & 63;
+    const int row = idx >> T::BROW_LOG2, c4 = idx & (T::BROW - 1);
     if (b_full) {
       r.b[q] = __ldg(reinterpret_cast<const int4*>(B + (k0 + row) * n + j0 + c4 * 4));
     } else {
@@ -144,7 +161,9 @@ __device__ __forceinline__ void packed_load(PackStage& r, const int32_t* __restr
 
 // A goes to smem k-major with each value duplicated into both halves; B as
 // packed (even, odd) column pairs.
-__device__ __forceinline__ void packed_store(const PackStage& r, uint32_t* As, uint32_t* Bs, int tid) {
+template <int NP>
+__device__ __forceinline__ void packed_store(const PackStage<NP>& r, uint32_t* As, uint32_t* Bs, int tid) {
+  using T = PackTile<NP>;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int row = tid & 127, c4 = (tid >> 7) + 2 * q;
@@ -156,62 +175,72 @@ __device__ __forceinline__ void packed_store(const PackStage& r, uint32_t* As, u
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < T::BQ; ++q) {
     const int idx = tid + q * PTHREADS;
-    const int row = idx >> 6, c4 = idx & 63;
+    const int row = idx >> T::BROW_LOG2, c4 = idx & (T::BROW - 1);
     const uint32_t p0 = to16(r.b[q].x) | (to16(r.b[q].y) << 16);
     const uint32_t p1 = to16(r.b[q].z) | (to16(r.b[q].w) << 16);
-    *reinterpret_cast<uint2*>(Bs + row * PBNP + c4 * 2) = make_uint2(p0, p1);
+    *reinterpret_cast<uint2*>(Bs + row * T::TNP + c4 * 2) = make_uint2(p0, p1);
   }
 }
 
-// One 128 x 256 output tile of the packed leaf over k in [kbeg, kend),
+// One 128 x 32 NP output tile of the packed leaf over k in [kbeg, kend),
 // executed by 256 threads (tid 0..255) that synchronise with `bar`.  With
 // `merge` the tile is folded into C by an atomic min (C must already hold
 // the semiring's 0 or another partial of the same product) instead of stored.
-template <class Bar>
+template <class Bar, int NP = 8>
 __device__ __forceinline__ void minplus16_tile(const int32_t* __restrict__ A, const int32_t* __restrict__ B,
                                                int32_t* __restrict__ C, int32_t* __restrict__ W, int z,
                                                int64_t m, int64_t n, int64_t k,
                                                int64_t i0, int64_t j0, int64_t kbeg, int64_t kend,
                                                bool vec, int tid, uint32_t* psmem, Bar bar,
                                                bool merge = false) {
+  using T = PackTile<NP>;
   uint32_t* As = psmem;                      // [2][PBK][PBM]
-  uint32_t* Bs = psmem + 2 * PBK * PBM;      // [2][PBK][PBNP]
+  uint32_t* Bs = psmem + 2 * PBK * PBM;      // [2][PBK][TNP]
   const int tx = tid & 15, ty = tid >> 4;
   const int nkb = kend > kbeg ? (int)((kend - kbeg + PBK - 1) / PBK) : 0;
 
-  uint32_t acc[8][8];
+  uint32_t acc[8][NP];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = kInf16 | (kInf16 << 16);
+    for (int j = 0; j < NP; ++j) acc[i][j] = kInf16 | (kInf16 << 16);
 
-  PackStage stg;
+  PackStage<NP> stg;
   if (nkb > 0) {
-    packed_load(stg, A, B, m, n, k, kend, i0, j0, kbeg, vec, tid);
-    packed_store(stg, As, Bs, tid);
+    packed_load<NP>(stg, A, B, m, n, k, kend, i0, j0, kbeg, vec, tid);
+    packed_store<NP>(stg, As, Bs, tid);
   }
   bar();
   for (int kb = 0; kb < nkb; ++kb) {
     const int cur = kb & 1;
-    if (kb + 1 < nkb) packed_load(stg, A, B, m, n, k, kend, i0, j0, kbeg + (int64_t)(kb + 1) * PBK, vec, tid);
+    if (kb + 1 < nkb)
+      packed_load<NP>(stg, A, B, m, n, k, kend, i0, j0, kbeg + (int64_t)(kb + 1) * PBK, vec, tid);
     const uint32_t* as = As + cur * PBK * PBM;
-    const uint32_t* bs = Bs + cur * PBK * PBNP;
+    const uint32_t* bs = Bs + cur * PBK * T::TNP;
 #pragma unroll
     for (int kk = 0; kk < PBK; ++kk) {
       const uint4 a0 = *reinterpret_cast<const uint4*>(as + kk * PBM + ty * 4);
       const uint4 a1 = *reinterpret_cast<const uint4*>(as + kk * PBM + 64 + ty * 4);
-      const uint4 b0 = *reinterpret_cast<const uint4*>(bs + kk * PBNP + tx * 4);
-      const uint4 b1 = *reinterpret_cast<const uint4*>(bs + kk * PBNP + 64 + tx * 4);
       const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const uint4 b0 = *reinterpret_cast<const uint4*>(bs + kk * T::TNP + tx * 4);
+      if constexpr (NP == 8) {
+        const uint4 b1 = *reinterpret_cast<const uint4*>(bs + kk * T::TNP + 64 + tx * 4);
+        const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_u16x2(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_u16x2(a[i], b[j], acc[i][j]);
+      } else {
+        const uint32_t b[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = __viaddmin_u16x2(a[i], b[j], acc[i][j]);
+      }
     }
-    if (kb + 1 < nkb) packed_store(stg, As + (cur ^ 1) * PBK * PBM, Bs + (cur ^ 1) * PBK * PBNP, tid);
+    if (kb + 1 < nkb) packed_store<NP>(stg, As + (cur ^ 1) * PBK * PBM, Bs + (cur ^ 1) * PBK * T::TNP, tid);
     bar();
   }
 
@@ -222,7 +251,7 @@ __device__ __forceinline__ void minplus16_tile(const int32_t* __restrict__ A, co
     const int64_t gi = i0 + ((i < 4) ? (ty * 4 + i) : (64 + ty * 4 + (i - 4)));
     if (gi >= m) continue;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NP / 4; ++h) {
       const int64_t gj = j0 + 2 * (h * 64 + tx * 4);  // 8 consecutive output columns
       int v[8];
 #pragma unroll
