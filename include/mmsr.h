@@ -289,8 +289,11 @@ int mm_plan_query(int semiring, int levels, int64_t m, int64_t n, int64_t k,
 /*
  * mm_last_device_status -- synchronises `stream` and returns, in *status,
  * the device-side status word written by kernels that can fail on the
- * device (bounded waits of the batched kernel); the word is then cleared.
- * Returns MM_OK or MM_ERR_CUDA.
+ * device: the tensor-core pipelines (FP32 mode, FP64-accuracy mode, the
+ * batched kernel) bound every mbarrier wait (2 s) and, on expiry, record
+ * MM_ERR_TIMEOUT, stop their CTA cleanly (TMEM freed) and leave its outputs
+ * zero.  The words of all three are read and cleared; MM_OK when none was
+ * set.  Returns MM_OK or MM_ERR_CUDA.
  */
 int mm_last_device_status(void* stream, int* status);
 

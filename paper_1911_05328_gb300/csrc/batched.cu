@@ -533,12 +533,8 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&ta_lo, alo, ra, kp, kp, TBM, true, TBK));
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_hi, bhi, rb, kp, kp, TBN, true, TBK));
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_lo, blo, rb, kp, kp, TBN, true, TBK));
-  static bool configured = false;
-  if (!configured) {
-    MMSR_TRY_STATUS(
-        cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BSMEM));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  MMSR_TRY_STATUS(smem_limit_once(batched_kernel, BSMEM, configured));
   int dev = 0, sms = kNumSMs;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -555,13 +551,8 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   }
   if (P.T.mp_total > 0) {
     TraceScope tr(kTrMinplusLeaf, st);
-    static bool fb_configured = false;
-    if (!fb_configured) {
-      MMSR_TRY_STATUS(cudaFuncSetAttribute(batched_minplus32_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)mp::SMEM_BYTES));
-      fb_configured = true;
-    }
+    static std::atomic<uint64_t> fb_configured{0};
+    MMSR_TRY_STATUS(smem_limit_once(batched_minplus32_kernel, mp::SMEM_BYTES, fb_configured));
     batched_minplus32_kernel<<<(unsigned)P.T.mp_total, 256, mp::SMEM_BYTES, st>>>(P.T, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }

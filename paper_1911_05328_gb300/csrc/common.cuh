@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/mmsr.h"
 
 namespace mmsr {
@@ -26,6 +28,20 @@ int report_cuda(cudaError_t e, const char* where);
     cudaError_t err_ = (expr);                                           \
     if (err_ != cudaSuccess) return ::mmsr::report_cuda(err_, #expr);    \
   } while (0)
+
+// Raises a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the device's context); concurrent first calls from
+// several threads only repeat an idempotent call.
+template <typename F>
+inline cudaError_t smem_limit_once(F* func, size_t bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  MMSR_CUDA_TRY(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  MMSR_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done.fetch_or(bit, std::memory_order_release);
+  return cudaSuccess;
+}
 
 // ---------------------------------------------------------------- cp.async
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -217,13 +217,8 @@ int dfma_tile_k() { return BK; }
 
 cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, const double* B,
                              double* C, double* W, int s, int kb_per_slice, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(dfma_leaf_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BYTES));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  MMSR_CUDA_TRY(smem_limit_once(dfma_leaf_kernel, SMEM_BYTES, configured));
   const bool vec = (k % 2 == 0) && (n % 2 == 0) && aligned16(A) && aligned16(B) && aligned16(C) &&
                    (W == nullptr || aligned16(W));
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
@@ -240,13 +235,8 @@ cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, c
 
 cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int64_t m, int64_t n,
                                 int64_t k, int batches, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(dfma_leaf_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BYTES));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  MMSR_CUDA_TRY(smem_limit_once(dfma_leaf_kernel, SMEM_BYTES, configured));
   const bool vec = (k % 2 == 0) && (n % 2 == 0) && aligned16(A) && aligned16(B) && aligned16(C) &&
                    ((m * k) % 2 == 0) && ((k * n) % 2 == 0) && ((m * n) % 2 == 0);
   const int kb = (int)((k + BK - 1) / BK);

@@ -445,16 +445,10 @@ cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const 
   QuadOut qo;
   if (quad) qo = *quad; else memset(&qo, 0, sizeof(qo));
   using Cfg = Bf16x3Cfg<BN, STAGES>;
-  static bool configured = false;
-  if (!configured) {
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, true, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-    configured = true;
-  }
+  static std::atomic<uint64_t> conf_plain{0}, conf_pair{0}, conf_quad{0};
+  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, false>, Cfg::SMEM, conf_plain));
+  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, true, false>, Cfg::SMEM, conf_pair));
+  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, true>, Cfg::SMEM, conf_quad));
   const bool q = qo.entries > 0;
   if (q) pair = false;  // the quadrant epilogue runs on independent CTAs
   const unsigned tiles_m = (unsigned)((m + BM - 1) / BM), tiles_n = (unsigned)((n + BN - 1) / BN);

@@ -439,12 +439,8 @@ int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* 
   CUtensorMap tA, tB;
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&tA, SA, kSlices * rows_a, L.Kp, L.Kp, BM, true, BK));
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&tB, SB, kSlices * (int64_t)batches * n, L.Kp, L.Kp, BN, true, BK));
-  static bool configured = false;
-  if (!configured) {
-    MMSR_TRY_STATUS(cudaFuncSetAttribute(f64acc_gemm_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  MMSR_TRY_STATUS(smem_limit_once(f64acc_gemm_kernel, SMEM, configured));
   const int kb_total = (int)(L.Kp / BK);
   const int kbs = (kb_total + s - 1) / s;
   {
