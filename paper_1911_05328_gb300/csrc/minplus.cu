@@ -59,8 +59,21 @@ __global__ void __launch_bounds__(256) range_scan_kernel(const int32_t* __restri
     const int32_t* X = pass ? B : A;
     const int64_t cnt = pass ? nb : na;
     if (vec) {
-      for (int64_t v = t0; v < cnt / 4; v += stride) {
-        const int4 q = __ldcs(reinterpret_cast<const int4*>(X) + v);
+      // four 16-byte loads in flight per thread
+      const int4* X4 = reinterpret_cast<const int4*>(X);
+      const int64_t nv = cnt / 4;
+      int64_t v = t0;
+      for (; v + 3 * stride < nv; v += 4 * stride) {
+        int4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = __ldcs(X4 + v + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          bad |= out_of_pack_range(q[u].x) | out_of_pack_range(q[u].y) | out_of_pack_range(q[u].z) |
+                 out_of_pack_range(q[u].w);
+      }
+      for (; v < nv; v += stride) {
+        const int4 q = __ldcs(X4 + v);
         bad |= out_of_pack_range(q.x) | out_of_pack_range(q.y) | out_of_pack_range(q.z) |
                out_of_pack_range(q.w);
       }
@@ -192,19 +205,10 @@ int g_streamk_mode = 1;  // 1: stream-K for unsplit packed products with few wav
 cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* A,
                                 const int32_t* B, int32_t* C, int32_t* W, int s,
                                 int kb_per_slice, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(minplus_leaf_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BYTES));
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(minplus16_leaf_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PSMEM_BYTES));
-    MMSR_CUDA_TRY(cudaFuncSetAttribute(minplus16_streamk_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PSMEM_BYTES));
-    configured = true;
-  }
+  static std::atomic<uint64_t> conf32{0}, conf16{0}, conf16s{0};
+  MMSR_CUDA_TRY(smem_limit_once(minplus_leaf_kernel, SMEM_BYTES, conf32));
+  MMSR_CUDA_TRY(smem_limit_once(minplus16_leaf_kernel, PSMEM_BYTES, conf16));
+  MMSR_CUDA_TRY(smem_limit_once(minplus16_streamk_kernel, PSMEM_BYTES, conf16s));
   const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C) &&
                    (W == nullptr || aligned16(W));
   int slot = -1;
@@ -216,19 +220,23 @@ cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* 
       TraceScope tr(kTrRangeScan, st);
       const bool svec = aligned16(A) && aligned16(B) && ((m * k) % 4 == 0) && ((k * n) % 4 == 0);
       int64_t blocks = ((m * k + k * n) / (svec ? 4 : 1) + 255) / 256;
-      if (blocks > (int64_t)kNumSMs * 4) blocks = (int64_t)kNumSMs * 4;
+      if (blocks > (int64_t)kNumSMs * 8) blocks = (int64_t)kNumSMs * 8;
       if (blocks < 1) blocks = 1;
       range_scan_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m * k, B, k * n, slot, svec);
       MMSR_CUDA_TRY(cudaGetLastError());
     }
     const int64_t tiles_m = (m + PBM - 1) / PBM, tiles_n = (n + PBN - 1) / PBN;
-    static int resident = 0;  // CTAs of the packed leaf that fit on the GPU at once
+    // CTAs of the packed leaf that fit on the GPU at once (the same for every
+    // GB300 of the process; a racing first computation stores the same value)
+    static std::atomic<int> resident_cache{0};
+    int resident = resident_cache.load(std::memory_order_relaxed);
     if (!resident) {
       int dev = 0, sms = kNumSMs, per_sm = 2;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, minplus16_streamk_kernel, PTHREADS, PSMEM_BYTES);
       resident = sms * (per_sm > 0 ? per_sm : 1);
+      resident_cache.store(resident, std::memory_order_relaxed);
     }
     if (s == 1 && g_streamk_mode && tiles_m * tiles_n < 4 * (int64_t)resident) {
       TraceScope tr(kTrMinplus16Leaf, st);
