@@ -291,9 +291,12 @@ int mm_plan_query(int semiring, int levels, int64_t m, int64_t n, int64_t k,
  * the device-side status word written by kernels that can fail on the
  * device: the tensor-core pipelines (FP32 mode, FP64-accuracy mode, the
  * batched kernel) bound every mbarrier wait (2 s) and, on expiry, record
- * MM_ERR_TIMEOUT, stop their CTA cleanly (TMEM freed) and leave its outputs
- * zero.  The words of all three are read and cleared; MM_OK when none was
- * set.  Returns MM_OK or MM_ERR_CUDA.
+ * MM_ERR_TIMEOUT and stop their CTA cleanly: the CTA lets its own TMA loads
+ * and tensor-core products in flight land (bounded waits), frees its TMEM
+ * and writes zeros for the output tile it was working on.  After a timeout
+ * the outputs of the call are not valid (other tiles and split-K sums may
+ * be partial).  The words of all three are read and cleared; MM_OK when
+ * none was set.  Returns MM_OK or MM_ERR_CUDA.
  */
 int mm_last_device_status(void* stream, int* status);
 
@@ -329,13 +332,21 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   double-float sum on the FP32 units (Sum2 of Ogita, Rump and Oishi); 1:
  *   FP64 arithmetic.  Both round the exact sum once to FP32 in all but rare
  *   tie cases; the FP64 units of this GPU are far slower.
- * Returns MM_OK or MM_ERR_ARG.
+ *   MM_OPT_TEST_SKIP_SIGNAL (testing the timeout path): 1, 2 or 3 arms a
+ *   one-shot switch for the next launch of the FP32-mode GEMM kernel, the
+ *   FP64-accuracy GEMM kernel or the batched FP32 kernel: that launch's first
+ *   CTA skips the arrival and loads of its first pipeline stage, so its MMA
+ *   wait runs out after 2 s and the call records MM_ERR_TIMEOUT (read with
+ *   mm_last_device_status).  No fault is raised; the CTA quiesces and exits.
+ *   0 disarms all three.  Needs a device (writes a device word).
+ * Returns MM_OK, MM_ERR_ARG, or MM_ERR_CUDA (arming the switch failed).
  */
 typedef enum {
   MM_OPT_MINPLUS_PACKED = 1,
   MM_OPT_MINPLUS_STREAMK = 2,
   MM_OPT_TC_PAIR = 3,
-  MM_OPT_STRASSEN_TOP_F64 = 4
+  MM_OPT_STRASSEN_TOP_F64 = 4,
+  MM_OPT_TEST_SKIP_SIGNAL = 5
 } mm_option_t;
 int mm_set_option(int option, int value);
 

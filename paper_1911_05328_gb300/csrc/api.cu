@@ -297,6 +297,13 @@ int mm_set_option(int option, int value) {
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_strassen_top_f64 = value;
       return MM_OK;
+    case MM_OPT_TEST_SKIP_SIGNAL: {
+      if (value < 0 || value > 3) return MM_ERR_ARG;
+      int r = arm_tc_skip_signal(value == 1);
+      if (r == MM_OK) r = arm_f64acc_skip_signal(value == 2);
+      if (r == MM_OK) r = arm_batched_skip_signal(value == 3);
+      return r;
+    }
     default:
       return MM_ERR_ARG;
   }

@@ -37,6 +37,9 @@ namespace mmsr {
 namespace {
 
 __device__ int g_batched_status;
+// One-shot test switch: the CTA that claims tile 0 in the next launch skips
+// the arrival and loads of its first ring position, so its MMA wait runs out.
+__device__ int g_batched_skip_signal;
 
 constexpr int kMaxBatch = 512;
 // FP32 tiles: 128 x 128, 32-wide k-blocks (64-byte swizzled rows) in a
@@ -234,7 +237,8 @@ __global__ void __launch_bounds__(kBThreads, 1)
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* tile_full = acc_empty + 2;         // [kTileQ]
   uint64_t* tile_empty = tile_full + kTileQ;   // [kTileQ]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_empty + kTileQ);
+  uint64_t* quiesce = tile_empty + kTileQ;     // after an abort: all issued MMAs done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(quiesce + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* tile_q = abort_flag + 1;                // [kTileQ]
 
@@ -252,6 +256,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
       tc::mbar_init(&tile_full[q], 1);
       tc::mbar_init(&tile_empty[q], 1 + kDrainW);  // the MMA thread and the drain warps
     }
+    tc::mbar_init(quiesce, 1);
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
@@ -268,6 +273,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
   // while the tensor core and the drain warps still work on earlier ones.
   uint32_t ring = 0, chunk = 0;
   const bool active = warp >= 2 || lane == 0;  // warps 0 and 1 work through one lane
+  bool skipped = false;  // producer: the test switch took ring position 0 out
 
   for (uint32_t j = 0; active; ++j) {
     const int slot = (int)(j % kTileQ);
@@ -276,6 +282,8 @@ __global__ void __launch_bounds__(kBThreads, 1)
     if (warp == 0) {
       if (j < kTileQ || tc::mbar_wait(&tile_empty[slot], ph ^ 1u, abort_flag, &g_batched_status)) {
         t = atomicAdd(counter, 1);
+        // tile 0 is always its CTA's first claim, so the ring is at position 0
+        if (t == 0) skipped = atomicExch(&g_batched_skip_signal, 0) != 0;
         tile_q[slot] = t;
         tc::mbar_arrive(&tile_full[slot]);  // release: the index is visible to the waiters
       }
@@ -310,6 +318,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
             const int s = ring % TSTAGES;
             const uint32_t round = ring / TSTAGES;
             if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_batched_status)) break;
+            if (ring == 0 && skipped) continue;
             tc::mbar_expect_tx(&full[s], TSTAGE);
             uint8_t* st = smem + s * TSTAGE;
             tc::tma_load_2d(st, &tAhi, &full[s], it * TBK, ya);
@@ -328,9 +337,13 @@ __global__ void __launch_bounds__(kBThreads, 1)
             tc::fence_after_sync();
             const uint32_t d = tmem + (uint32_t)(b * TBN);
             const int last = min(nkb, (c + 1) * TCHUNK);
+            bool aborted = false;
             for (int first = 1; it < last; ++it, ++ring, first = 0) {
               const int s = ring % TSTAGES;
-              if (!tc::mbar_wait(&full[s], (ring / TSTAGES) & 1u, abort_flag, &g_batched_status)) break;
+              if (!tc::mbar_wait(&full[s], (ring / TSTAGES) & 1u, abort_flag, &g_batched_status)) {
+                aborted = true;
+                break;
+              }
               tc::fence_after_sync();
               const uint32_t base = smem_u32(smem + s * TSTAGE);
 #pragma unroll
@@ -345,6 +358,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
               }
               tc::mma_commit(&empty[s]);
             }
+            if (aborted) break;  // no chunk signal: the drain must not read a partial chunk
             tc::mma_commit(&acc_full[b]);
           }
         }
@@ -360,6 +374,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
           // warp-uniform verdict: the __syncwarp below needs every lane
           ok = __all_sync(0xffffffffu, ok && tc::mbar_wait(&acc_full[b], (chunk >> 1) & 1u, abort_flag,
                                                            &g_batched_status));
+          if (!ok) break;
           tc::fence_after_sync();
 #pragma unroll
           for (int cc = 0; cc < TBN / 2; cc += 16) {
@@ -398,7 +413,23 @@ __global__ void __launch_bounds__(kBThreads, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tmem, BTMEM_COLS);
+  if (*reinterpret_cast<volatile int*>(abort_flag)) {
+    // Aborted: let this CTA's own TMA loads (the last ring round issued) and
+    // issued MMAs land before shared memory and TMEM are released; both waits
+    // are bounded and ignore the abort flag.
+    if (warp == 0 && lane == 0)
+      for (uint32_t r = ring > (uint32_t)TSTAGES ? ring - TSTAGES : 0u; r < ring; ++r)
+        if (!(r == 0 && skipped)) tc::mbar_wait_quiesce(&full[r % TSTAGES], (r / TSTAGES) & 1u);
+    if (warp == 1 && lane == 0) {
+      tc::mma_commit(quiesce);
+      tc::mbar_wait_quiesce(quiesce, 0);
+    }
+    __syncwarp();
+  }
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, BTMEM_COLS);
+  }
 }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -482,6 +513,10 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
 }
 
 }  // namespace
+
+int arm_batched_skip_signal(int on) {
+  return cudaMemcpyToSymbol(g_batched_skip_signal, &on, sizeof(int)) == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}
 
 int read_batched_status(int* status) {
   int v = 0;

@@ -49,6 +49,12 @@ size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches);
 int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, int64_t n, int64_t k,
                        int batches, void* ws, cudaStream_t st);
 int read_batched_status(int* status);
+// Test switches (one-shot): the first CTA of the next launch of the FP32
+// GEMM / FP64-accuracy GEMM / batched FP32 kernel skips its first ring
+// stage's arrival, so a bounded wait runs out.  on = 0 disarms.
+int arm_tc_skip_signal(int on);
+int arm_f64acc_skip_signal(int on);
+int arm_batched_skip_signal(int on);
 
 // Leaf epilogue that adds each product into quadrants of C instead of
 // writing it out: batch entry b adds sign[b][d] x product into dst[b][d]

@@ -21,6 +21,10 @@ namespace mmsr {
 
 namespace {
 __device__ int g_tc_status;  // device status word of this translation unit
+// One-shot test switch: when set, the first CTA of the next GEMM launch skips
+// the arrival and loads of its first ring stage, so its MMA wait runs out
+// (the bounded-wait timeout path, exercised without any fault).
+__device__ int g_tc_skip_signal;
 }
 
 // CTA pairs multicasting B: correct but measured no faster here (the ring's
@@ -198,8 +202,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;  // [2]: chunk accumulated (MMA -> drain)
   uint64_t* acc_empty = acc_full + 2;   // [2]: chunk drained (drain -> MMA)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* quiesce = acc_empty + 2;    // after an abort: all issued MMAs done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(quiesce + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  // producer state read after an abort (shared, so that no register stays
+  // live through the other roles): [0] k-blocks issued, [1] k-block 0 skipped
+  int* prod_state = abort_flag + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Grouped rasterisation: consecutive CTAs walk a band of kGroupM tile rows
@@ -238,7 +246,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::mbar_init(&acc_full[b], 1);
       tc::mbar_init(&acc_empty[b], kDrainWarps);
     }
+    tc::mbar_init(quiesce, 1);
     *abort_flag = 0;
+    prod_state[0] = prod_state[1] = 0;
     tc::mbar_init_fence();
   }
   if (warp == 1) tc::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
@@ -254,10 +264,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::tma_prefetch(&tAlo);
       tc::tma_prefetch(&tBhi);
       tc::tma_prefetch(&tBlo);
-      for (int it = 0; it < nkb; ++it) {
+      bool skipped = false;  // the test switch took k-block 0 out
+      int issued = 0;        // k-blocks whose loads were issued
+      if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && nkb > 0)
+        skipped = atomicExch(&g_tc_skip_signal, 0) != 0;
+      for (int it = 0; it < nkb; ++it, issued = it) {
         const int s = it % STAGES;
         const uint32_t round = (uint32_t)(it / STAGES);
         if (it >= STAGES && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_tc_status)) break;
+        if (it == 0 && skipped) continue;
         tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
         uint8_t* st = smem + s * Cfg::STAGE_BYTES;
         const int kx = (kb_begin + it) * Cfg::KB;
@@ -275,6 +290,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, yb);
         }
       }
+      prod_state[0] = issued;
+      prod_state[1] = skipped ? 1 : 0;
       if (MC) {
         // wait until both CTAs have released the last stages, so no arrival
         // from the peer is still in flight towards this CTA when it exits
@@ -316,8 +333,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           else
             tc::mma_commit(&empty[s]);
         }
+        if (aborted) break;  // no chunk signal: the drain must not read a partial chunk
         tc::mma_commit(&acc_full[b]);
-        if (aborted) break;
       }
     }
   } else {
@@ -330,7 +347,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       const int b = c & 1;
-      ok = tc::mbar_wait(&acc_full[b], (c >> 1) & 1u, abort_flag, &g_tc_status);
+      // warp-uniform verdict: the TMEM loads below are warp-collective (after
+      // an abort they read a discarded chunk; the tile is written as zeros)
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[b], (c >> 1) & 1u, abort_flag, &g_tc_status));
       tc::fence_after_sync();
 #pragma unroll
       for (int cc = 0; cc < Cfg::COLS_PER_WARP; cc += 32) {
@@ -409,8 +428,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (*reinterpret_cast<volatile int*>(abort_flag)) {
+    // Aborted: before shared memory and TMEM are released, let this CTA's
+    // own asynchronous work land -- the TMA loads of the last ring round the
+    // producer issued and every MMA the issuer started.  Both waits are
+    // bounded and ignore the abort flag.
+    if (warp == 0 && lane == 0) {
+      const int issued = prod_state[0], skipped = prod_state[1];
+      for (int it = max(0, issued - STAGES); it < issued; ++it)
+        if (!(it == 0 && skipped)) tc::mbar_wait_quiesce(&full[it % STAGES], (uint32_t)(it / STAGES) & 1u);
+    }
+    if (warp == 1 && lane == 0) {
+      tc::mma_commit(quiesce);
+      tc::mbar_wait_quiesce(quiesce, 0);
+    }
+    __syncwarp();
+  }
   if (MC) tc::cluster_sync();  // neither CTA leaves while the pair still shares smem traffic
-  if (warp == 1) tc::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
 }
 
 __global__ void __launch_bounds__(256) sum_reduce_f32_kernel(int64_t count, float* __restrict__ C,
@@ -593,6 +631,10 @@ int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, flo
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}
+
+int arm_tc_skip_signal(int on) {
+  return cudaMemcpyToSymbol(g_tc_skip_signal, &on, sizeof(int)) == cudaSuccess ? MM_OK : MM_ERR_CUDA;
 }
 
 int read_tc_status(int* status) {

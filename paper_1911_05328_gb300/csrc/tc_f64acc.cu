@@ -39,6 +39,9 @@ namespace mmsr {
 namespace {
 
 __device__ int g_f64acc_status;
+// One-shot test switch: the first CTA of the next launch skips the arrival
+// and loads of its first ring stage, so its MMA wait runs out.
+__device__ int g_f64acc_skip_signal;
 
 constexpr int kSlices = 7, kDigitBits = 7, kGroups = 7;
 constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2, CHUNK = 8;  // CHUNK k-blocks per drain
@@ -176,8 +179,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;       // [kGroups]
   uint64_t* acc_empty = acc_full + kGroups;   // [kGroups]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + kGroups);
+  uint64_t* quiesce = acc_empty + kGroups;    // after an abort: all issued MMAs done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(quiesce + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  // producer state read after an abort (shared, so that no register stays
+  // live through the other roles): [0] k-blocks issued, [1] k-block 0 skipped
+  int* prod_state = abort_flag + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Banded rasterisation: consecutive CTAs walk bands of 8 tile rows column
@@ -215,7 +222,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&acc_full[g], 1);
       tc::mbar_init(&acc_empty[g], kDrain);
     }
+    tc::mbar_init(quiesce, 1);
     *abort_flag = 0;
+    prod_state[0] = prod_state[1] = 0;
     tc::mbar_init_fence();
   }
   if (warp == 1) tc::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -228,10 +237,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       tc::tma_prefetch(&tA);
       tc::tma_prefetch(&tB);
-      for (int it = 0; it < nkb; ++it) {
+      bool skipped = false;  // the test switch took k-block 0 out
+      int issued = 0;        // k-blocks whose loads were issued
+      if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && nkb > 0)
+        skipped = atomicExch(&g_f64acc_skip_signal, 0) != 0;
+      for (int it = 0; it < nkb; ++it, issued = it) {
         const int s = it % STAGES;
         const uint32_t round = (uint32_t)(it / STAGES);
         if (it >= STAGES && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_f64acc_status)) break;
+        if (it == 0 && skipped) continue;
         tc::mbar_expect_tx(&full[s], STAGE_BYTES);
         uint8_t* st = smem + s * STAGE_BYTES;
         const int kx = (kb_begin + it) * BK;
@@ -242,6 +256,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                           (int)(sl * b_slice_rows + rb + j0));
         }
       }
+      prod_state[0] = issued;
+      prod_state[1] = skipped ? 1 : 0;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -361,7 +377,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
+  if (*reinterpret_cast<volatile int*>(abort_flag)) {
+    // Aborted: let this CTA's own TMA loads (the last ring round issued) and
+    // issued MMAs land before shared memory and TMEM are released; both waits
+    // are bounded and ignore the abort flag.
+    if (warp == 0 && lane == 0) {
+      const int issued = prod_state[0], skipped = prod_state[1];
+      for (int it = max(0, issued - STAGES); it < issued; ++it)
+        if (!(it == 0 && skipped)) tc::mbar_wait_quiesce(&full[it % STAGES], (uint32_t)(it / STAGES) & 1u);
+    }
+    if (warp == 1 && lane == 0) {
+      tc::mma_commit(quiesce);
+      tc::mbar_wait_quiesce(quiesce, 0);
+    }
+    __syncwarp();
+  }
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, TMEM_COLS);
+  }
 }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -473,6 +507,10 @@ int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, i
                        int batches, void* ws, cudaStream_t st) {
   const F64AccLayout L = layout(m, n, k, batches);
   return f64acc_core(m, n, k, A, B, C, static_cast<uint8_t*>(ws), L, batches, 1, nullptr, st);
+}
+
+int arm_f64acc_skip_signal(int on) {
+  return cudaMemcpyToSymbol(g_f64acc_skip_signal, &on, sizeof(int)) == cudaSuccess ? MM_OK : MM_ERR_CUDA;
 }
 
 int read_f64acc_status(int* status) {

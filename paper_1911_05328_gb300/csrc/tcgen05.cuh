@@ -64,6 +64,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* a
   }
 }
 
+// Bounded wait that ignores the abort flag: used after an abort, to let the
+// CTA's own copies and products in flight land before it frees shared memory
+// and TMEM.  Returns false if the limit expired.
+__device__ __forceinline__ bool mbar_wait_quiesce(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = global_timer();
+  while (!mbar_try_wait(bar, parity))
+    if (global_timer() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
 // ------------------------------------------------------------------ TMA
 __device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
