@@ -111,6 +111,18 @@ def gpu_uuid():
         return None
 
 
+def sm_max_mhz():
+    """Maximum SM clock of this GPU (nvidia-smi), 2070 MHz when unavailable."""
+    try:
+        cmd = ["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"]
+        u = gpu_uuid()
+        if u:
+            cmd += ["-i", u]
+        return float(subprocess.run(cmd, capture_output=True, text=True, timeout=20).stdout.split()[0])
+    except Exception:
+        return 2070.0
+
+
 # ------------------------------------------------------------ measured peaks
 def measured_peaks():
     try:
@@ -414,6 +426,25 @@ def main():
     return 0
 
 
+def _probe(lib, sp, kind, iters):
+    """Measured rate (ops/s) of one instruction kind on every SM: a short
+    warm-up launch, then the timed one (mm_probe_peak, include/mmsr_probe.h)."""
+    import ctypes
+
+    rate, pms = ctypes.c_double(), ctypes.c_double()
+    lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.mm_probe_peak(kind, max(iters // 10, 1), sp, ctypes.byref(rate), ctypes.byref(pms))
+    lib.mm_probe_peak(kind, iters, sp, ctypes.byref(rate), ctypes.byref(pms))
+    return rate.value
+
+
+def _roof(bound, achieved, peak, unit, peak_source):
+    """Roofline record of one kernel or call: achieved vs peak in `unit`."""
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if peak else None, "peak_source": peak_source}
+
+
 def _time_call(torch, fn, reps):
     fn()
     torch.cuda.synchronize()
@@ -435,19 +466,38 @@ def run_extras(mmsr, lib, torch, sp):
     lib.mm_trace_summary.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
 
     out = {}
+    # roofline denominators of the CUDA-core rows: measured probes (bf16
+    # tensor peaks come from the measured-peaks file)
+    peaks, src = measured_peaks()
+    u16_peak = _probe(lib, sp, 1, 20000) / 1e12
+    # boolean leaf: one three-input logic op covers 32 terms (32 ANDs + 32
+    # ORs) and issues on the same ALU pipe as the packed add-min, whose probe
+    # issues exactly one ALU instruction per step: ALU rate x 64 ops
+    lop_peak = u16_peak / 4 * 64
+    # FP64: 2 FMA lanes per SM per clock (the nominal 1.25 TFLOP/s at the
+    # maximum clock); the FMA-chain probe reaches ~89% of it
+    mhz = sm_max_mhz()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp64_peak = sms * 2 * 2 * mhz * 1e6 / 1e12
+    fp64_src = "derived: %d SMs x 2 FP64 FMA/clk x 2 FLOP x %.0f MHz" % (sms, mhz)
+    bf16_src = "%s: bf16 dense burst (cuBLAS)" % src
     # FP64 classic n=256, uniform[-1,1], seed 0, budget 0 (plain FP64 path)
     A, B = inputs.uniform_f64(256, 256, 256, seed=0)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((256, 256), dtype=torch.float64, device="cuda")
     ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC, None, 0, sp), 50)
-    out["fp64_n256_budget0"] = {"ms": ms, "gops": 2 * 256 ** 3 / (ms * 1e-3) / 1e9}
+    out["fp64_n256_budget0"] = {"ms": ms, "gops": 2 * 256 ** 3 / (ms * 1e-3) / 1e9,
+                                "roofline": _roof("fp64", 2 * 256 ** 3 / (ms * 1e-3) / 1e12, fp64_peak,
+                                                  "TFLOP/s", fp64_src)}
     # FP64 DFMA path at n=8192 (comparator of the FP32 split-precision path)
     n = 8192
     A, B = inputs.uniform_f64(n, n, n, seed=2)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
     ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, n, n, n, dA, dB, dC, None, 0, sp), 2)
-    out["fp64_dfma_n8192"] = {"ms": ms, "gops": 2 * n ** 3 / (ms * 1e-3) / 1e9}
+    out["fp64_dfma_n8192"] = {"ms": ms, "gops": 2 * n ** 3 / (ms * 1e-3) / 1e9,
+                              "roofline": _roof("fp64", 2 * n ** 3 / (ms * 1e-3) / 1e12, fp64_peak,
+                                                "TFLOP/s", fp64_src)}
     del dA, dB, dC
     # FP32 mode n=8192, normal(0,1), seed 2: bf16x3 split products on tcgen05
     A, B = inputs.normal_f32(n, n, n, seed=2)
@@ -462,11 +512,11 @@ def run_extras(mmsr, lib, torch, sp):
     cnt, tot = ctypes.c_int64(), ctypes.c_double()
     lib.mm_trace_summary(5, ctypes.byref(cnt), ctypes.byref(tot))  # tc_bf16x3
     gemm_ms = tot.value / max(cnt.value, 1)
-    peaks, src = measured_peaks()
     issued = 3 * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12
     out["fp32_bf16x3_n8192"] = {
         "ms": ms, "gops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms,
         "tensor_tflops_issued": issued, "frac_of_bf16_peak": issued / peaks["bf16_tflops"],
+        "roofline": _roof("tensor", issued, peaks["bf16_tflops"], "TFLOP/s", bf16_src),
         "peak_source": src, "workspace_bytes": wmin,
         "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms,
         "error": "rel. Frobenius vs FP64 oracle on 512 sampled rows <= 1e-5 (tests)"}
@@ -493,27 +543,25 @@ def run_extras(mmsr, lib, torch, sp):
     out["fp64acc_n8192"] = {
         "ms": ms, "gflops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms,
         "tensor_tflops_issued_28_slice_products": issued, "frac_of_bf16_peak": issued / peaks["bf16_tflops"],
+        "roofline": _roof("tensor", issued, peaks["bf16_tflops"], "TFLOP/s", bf16_src),
         "workspace_bytes": wmin, "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms,
         "error": "rel. Frobenius vs FP64 oracle <= 1e-12 (tests; 4.6e-15 at n=16384)"}
     del dA, dB, dC, ws
     torch.cuda.empty_cache()
-    out["batched_512"] = run_batched_extras(mmsr, lib, torch, sp, ctypes)
-    out["strassen_fp32_n16384"] = run_strassen_extras(mmsr, lib, torch, sp, ctypes)
-    out["closure_minplus_n4096"] = run_closure_extras(mmsr, torch, sp)
-    rate, pms = ctypes.c_double(), ctypes.c_double()
-    lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
-                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
-    lib.mm_probe_peak(2, 2000, sp, ctypes.byref(rate), ctypes.byref(pms))
-    out["fp64_fma_probe_tflops"] = rate.value / 1e12
-    lib.mm_probe_peak(1, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
-    out["addmin_u16x2_probe_tops"] = rate.value / 1e12
-    lib.mm_probe_peak(3, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
-    out["fp32_fma_probe_tflops"] = rate.value / 1e12
+    out["batched_512"] = run_batched_extras(mmsr, lib, torch, sp, ctypes, peaks["bf16_tflops"], u16_peak, bf16_src)
+    out["strassen_fp32_n16384"] = run_strassen_extras(mmsr, lib, torch, sp, ctypes, peaks["bf16_tflops"], bf16_src)
+    out["closure_minplus_n4096"] = run_closure_extras(mmsr, torch, sp, u16_peak)
+    out["orand_n4096"] = run_orand_extras(mmsr, lib, torch, sp, ctypes, lop_peak)
+    out["fp64_fma_probe_tflops"] = _probe(lib, sp, 2, 2000) / 1e12
+    out["fp64_peak_derived_tflops"] = fp64_peak
+    out["addmin_u16x2_probe_tops"] = u16_peak
+    out["orand_peak_derived_tops"] = lop_peak
+    out["fp32_fma_probe_tflops"] = _probe(lib, sp, 3, 20000) / 1e12
     torch.cuda.empty_cache()
     return out
 
 
-def run_batched_extras(mmsr, lib, torch, sp, ctypes):
+def run_batched_extras(mmsr, lib, torch, sp, ctypes, bf16_peak, u16_peak, bf16_src):
     """512 problems (m, n, k log-uniform in [64, 2048], 70% FP32 (+,x) with
     normal(0,1) entries, 30% (min,+) with integers in [0, 1000], seed 4) in
     one persistent launch, captured once in a CUDA graph and replayed."""
@@ -550,7 +598,13 @@ def run_batched_extras(mmsr, lib, torch, sp, ctypes):
         lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
         if cnt.value:
             split[lib.mm_trace_kernel_name(kid).decode()] = tot.value / 3
+    # ideal time: every FP32 product's three bf16 split products at the tensor
+    # peak plus every (min,+) product at the packed add-min peak
+    ideal_ms = (3 * ops_fp32 / (bf16_peak * 1e12) + (ops - ops_fp32) / (u16_peak * 1e12)) * 1e3
     res = {"ms": ms, "gops": ops / (ms * 1e-3) / 1e9, "ops": ops, "fp32_share_of_ops": ops_fp32 / ops,
+           "roofline": _roof("tensor (FP32 tiles) + alu ((min,+) tiles)", ops / (ms * 1e-3) / 1e12,
+                             ops / (ideal_ms * 1e-3) / 1e12, "TOp/s",
+                             bf16_src + "; measured packed add-min probe"),
            "kernel_ms_eager": split,
            "workspace_bytes": int(need), "launch": "one CUDA graph: memset + 2 pre-passes + persistent tcgen05 kernel (FP32 tiles) + "
                      "packed (min,+) tile launch + 32-bit (min,+) launch (exits at once when unused)",
@@ -560,7 +614,43 @@ def run_batched_extras(mmsr, lib, torch, sp, ctypes):
     return res
 
 
-def run_closure_extras(mmsr, torch, sp):
+def run_orand_extras(mmsr, lib, torch, sp, ctypes, lop_peak):
+    """(or, and) semiring, n = 4096, 0/1 entries with density 1% (seed 6):
+    the bit-packed leaf, budget = the plan's minimum (packing buffers)."""
+    from paper_1911_05328_gb300 import inputs
+
+    n = 4096
+    A, B = inputs.boolean_u8(n, n, n, seed=6, density=0.01)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((n, n), dtype=torch.uint8, device="cuda")
+    sr = mmsr.MM_SR_OR_AND_U8
+    w = int(mmsr.mm_plan_query(sr, -1, n, n, n, 0).workspace_min)
+    ws = torch.empty((max(w, 16),), dtype=torch.uint8, device="cuda")
+    fn = lambda: mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, w, sp)
+    ms = _time_call(torch, fn, 20)
+    lib.mm_trace_enable(1)
+    for _ in range(5):
+        fn()
+    torch.cuda.synchronize()
+    lib.mm_trace_enable(0)
+    lib.mm_trace_kernel_name.restype = ctypes.c_char_p
+    split = {}
+    for kid in range(lib.mm_trace_kernel_count()):
+        cnt, tot = ctypes.c_int64(), ctypes.c_double()
+        lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
+        if cnt.value:
+            split[lib.mm_trace_kernel_name(kid).decode()] = tot.value / 5
+    res = {"ms": ms, "gops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "workspace_bytes": w, "kernel_ms": split,
+           "roofline": _roof("alu", 2.0 * n ** 3 / (ms * 1e-3) / 1e12, lop_peak, "TOp/s",
+                             "derived: measured ALU-pipe rate (packed add-min probe / 4) x 64 ops per "
+                             "32-bit and-or"),
+           "error": "bit-exact vs oracle (tests)"}
+    del dA, dB, dC, ws
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_closure_extras(mmsr, torch, sp, u16_peak):
     """(min,+) closure (all-pairs shortest paths) of a 4096-vertex graph with
     10% arcs of length in [0, 1000] (seed 1) by repeated squaring, one extra
     n x n buffer of budget per squaring: all 12 squarings, and stopping at
@@ -585,13 +675,15 @@ def run_closure_extras(mmsr, torch, sp):
         ms = _time_call(torch, fn, 3)
         res[name] = {"ms": ms, "squarings": sq[-1],
                      "gops": sq[-1] * 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
-                     "workspace_bytes": budget}
+                     "workspace_bytes": budget,
+                     "roofline": _roof("alu", sq[-1] * 2.0 * n ** 3 / (ms * 1e-3) / 1e12, u16_peak, "TOp/s",
+                                       "measured: mm_probe_peak packed add-min, all SMs")}
     del dA, dC, ws
     torch.cuda.empty_cache()
     return res
 
 
-def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
+def run_strassen_extras(mmsr, lib, torch, sp, ctypes, bf16_peak, bf16_src):
     """Strassen-Winograd, FP32 mode, n = 16384 (uniform[-1,1], seed 3, cast
     to float32): classic (L = 0) and L = 1..4, per-level time, classic-
     equivalent GOp/s, workspace as a multiple of n^2 * 4 bytes and the time
@@ -630,6 +722,12 @@ def run_strassen_extras(mmsr, lib, torch, sp, ctypes):
         res["L%d" % L] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
                           "workspace_bytes": int(p.workspace_min),
                           "workspace_n2x4B": p.workspace_min / (n * n * 4.0), "kernel_ms": split}
+        leaf_ms = split.get("tc_bf16x3", 0.0)
+        if leaf_ms > 0:
+            # 7^L leaf products of size n / 2^L, three bf16 split products each
+            leaf_tf = 3 * 2.0 * (n >> L) ** 3 * 7 ** L / (leaf_ms * 1e-3) / 1e12
+            res["L%d" % L]["leaf_roofline"] = _roof("tensor", leaf_tf, bf16_peak, "TFLOP/s", bf16_src)
+            res["L%d" % L]["leaf_share_of_time"] = leaf_ms / ms
         del ws
         torch.cuda.empty_cache()
     # TAR-Strassen: one level, products added into C's quadrants by the leaf

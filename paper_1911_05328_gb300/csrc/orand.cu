@@ -16,46 +16,92 @@ namespace mmsr {
 namespace {
 
 constexpr int OBM = 128, OBN = 128, OBW = 32;  // tile rows, cols, words per stage (1024 k)
-constexpr int OLD = OBW + 1;                   // padded smem row (words)
+// Shared tiles are stored k-major ([word][row]) with a 132-word pitch: a
+// thread's four consecutive rows are one 16-byte load, and the staging
+// stores (4 rows x 8 words per warp) fall in 32 distinct banks.
+constexpr int OLD = OBM + 4;
+
+// Four bytes -> four bits: bit b of the result is set iff byte b of v is
+// nonzero.  The 0/1 flags sit at bits 0, 8, 16, 24; the multiplier copies
+// them to bits 21..24 without overlapping partial products (no carries).
+__device__ __forceinline__ uint32_t nonzero_nibble(uint32_t v) {
+  const uint32_t f = __vcmpne4(v, 0u) & 0x01010101u;
+  return ((f * 0x204081u) >> 21) & 0xFu;
+}
 
 __global__ void __launch_bounds__(256) pack_rows_kernel(const uint8_t* __restrict__ A, int64_t m,
                                                         int64_t k, int64_t KW,
-                                                        uint32_t* __restrict__ P) {
+                                                        uint32_t* __restrict__ P, bool vec) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * KW;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / KW, w = e - i * KW;
     uint32_t word = 0;
     const int64_t t0 = w * 32;
-    for (int b = 0; b < 32; ++b) {
-      const int64_t t = t0 + b;
-      if (t < k && A[i * k + t]) word |= 1u << b;
+    if (vec && t0 + 32 <= k) {
+      // rows are 16-byte aligned (k % 16 == 0): two 16-byte loads per word
+      const uint4* src = reinterpret_cast<const uint4*>(A + i * k + t0);
+      const uint4 lo = __ldcs(src), hi = __ldcs(src + 1);
+      const uint32_t v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) word |= nonzero_nibble(v[q]) << (4 * q);
+    } else {
+      for (int b = 0; b < 32; ++b) {
+        const int64_t t = t0 + b;
+        if (t < k && A[i * k + t]) word |= 1u << b;
+      }
     }
     P[e] = word;
   }
 }
 
-// B (k x n) -> bits of B^T (n x KW); threads over columns read 32 rows each.
+// B (k x n) -> bits of B^T (n x KW).  A block covers 32 columns and 8 words
+// (256 rows of B); warp q takes word w = 8 * blockIdx.y + q: lane l loads the
+// 32 bytes of row 32 w + l, and one ballot per column gathers that column's
+// word (bit l = row 32 w + l).  The words go through shared memory so that
+// each column's 8 words are stored as one 32-byte run.
 __global__ void __launch_bounds__(256) pack_cols_kernel(const uint8_t* __restrict__ B, int64_t k,
                                                         int64_t n, int64_t KW,
-                                                        uint32_t* __restrict__ P) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t w = blockIdx.y;
-  if (j >= n) return;
-  uint32_t word = 0;
-  const int64_t t0 = w * 32;
-  for (int b = 0; b < 32; ++b) {
-    const int64_t t = t0 + b;
-    if (t < k && B[t * n + j]) word |= 1u << b;
+                                                        uint32_t* __restrict__ P, bool vec) {
+  __shared__ uint32_t words[32][9];
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t j0 = (int64_t)blockIdx.x * 32;
+  const int64_t w = (int64_t)blockIdx.y * 8 + q;
+  const int64_t t = w * 32 + lane;
+  uint32_t v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = 0u;
+  if (w < KW && t < k) {
+    const uint8_t* row = B + t * n + j0;
+    if (vec && j0 + 32 <= n) {
+      // rows are 16-byte aligned (n % 16 == 0) and j0 is a multiple of 32
+      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(row));
+      const uint4 b = __ldcs(reinterpret_cast<const uint4*>(row) + 1);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (j0 + c < n) v[c >> 2] |= (uint32_t)row[c] << (8 * (c & 3));
+    }
   }
-  P[j * KW + w] = word;
+  uint32_t mine = 0;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const uint32_t bits = __ballot_sync(0xffffffffu, ((v[c >> 2] >> (8 * (c & 3))) & 0xFFu) != 0u);
+    if (lane == c) mine = bits;
+  }
+  words[lane][q] = mine;  // column j0 + lane, word w
+  __syncthreads();
+  const int col = threadIdx.x >> 3, wi = threadIdx.x & 7;
+  const int64_t jj = j0 + col, ww = (int64_t)blockIdx.y * 8 + wi;
+  if (jj < n && ww < KW) P[jj * KW + ww] = words[col][wi];
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     orand_leaf_kernel(int64_t m, int64_t n, int64_t KW, const uint32_t* __restrict__ PA,
                       const uint32_t* __restrict__ PB, uint8_t* __restrict__ C,
                       uint8_t* __restrict__ W, int words_per_slice) {
-  __shared__ uint32_t As[OBM][OLD];
-  __shared__ uint32_t Bs[OBN][OLD];
+  __shared__ __align__(16) uint32_t As[OBW][OLD];
+  __shared__ __align__(16) uint32_t Bs[OBW][OLD];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.y * OBM, j0 = (int64_t)blockIdx.x * OBN;
   const int z = blockIdx.z;
@@ -67,25 +113,26 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0u;
   for (int64_t w0 = wb; w0 < we; w0 += OBW) {
-    // 128 rows x 32 words of each operand, 16 per thread
+    // 128 rows x 32 words of each operand, 16 per thread; a warp reads 4
+    // rows x 8 consecutive words (whole 32-byte sectors)
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int e = tid + 256 * q;
-      const int r = e >> 5, c = e & 31;
+      const int lane = e & 31, wq = e >> 5;
+      const int r = (wq >> 2) * 4 + (lane >> 3), c = (wq & 3) * 8 + (lane & 7);
       const int64_t gw = w0 + c;
       const int64_t ga = i0 + r, gb = j0 + r;
-      As[r][c] = (ga < m && gw < we) ? PA[ga * KW + gw] : 0u;
-      Bs[r][c] = (gb < n && gw < we) ? PB[gb * KW + gw] : 0u;
+      As[c][r] = (ga < m && gw < we) ? PA[ga * KW + gw] : 0u;
+      Bs[c][r] = (gb < n && gw < we) ? PB[gb * KW + gw] : 0u;
     }
     __syncthreads();
 #pragma unroll 4
     for (int c = 0; c < OBW; ++c) {
       uint32_t a[8], b[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        a[i] = As[(i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4)][c];
-        b[i] = Bs[(i < 4) ? (tx * 4 + i) : (64 + tx * 4 + i - 4)][c];
-      }
+      *reinterpret_cast<uint4*>(a) = *reinterpret_cast<const uint4*>(&As[c][ty * 4]);
+      *reinterpret_cast<uint4*>(a + 4) = *reinterpret_cast<const uint4*>(&As[c][64 + ty * 4]);
+      *reinterpret_cast<uint4*>(b) = *reinterpret_cast<const uint4*>(&Bs[c][tx * 4]);
+      *reinterpret_cast<uint4*>(b + 4) = *reinterpret_cast<const uint4*>(&Bs[c][64 + tx * 4]);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -177,8 +224,9 @@ int run_orand(int64_t m, int64_t n, int64_t k, const uint8_t* A, const uint8_t* 
   {
     TraceScope tr(kTrOrPack, st);
     if (L.KW > 0) {
-      pack_rows_kernel<<<grid_for(m * L.KW), 256, 0, st>>>(A, m, k, L.KW, PA);
-      pack_cols_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)L.KW), 256, 0, st>>>(B, k, n, L.KW, PB);
+      pack_rows_kernel<<<grid_for(m * L.KW), 256, 0, st>>>(A, m, k, L.KW, PA, aligned16(A) && k % 16 == 0);
+      pack_cols_kernel<<<dim3((unsigned)((n + 31) / 32), (unsigned)((L.KW + 7) / 8)), 256, 0, st>>>(
+          B, k, n, L.KW, PB, aligned16(B) && n % 16 == 0);
     }
     MMSR_TRY_STATUS(cudaGetLastError());
   }

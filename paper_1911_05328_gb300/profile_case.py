@@ -6,7 +6,8 @@ Cases: minplus4096 (the (min,+) n=4096 product, budget 0 unless --budget),
 f32_<n> (FP32 mode, bf16x3 on tensor cores), f64acc_<n> (FP64-accuracy mode),
 f64_<n> (plain FP64 path), orand_<n> (boolean), batched512 (the 512-problem
 mixed batch), strassen<L>_<n> (FP32-mode Strassen-Winograd, L levels,
-uniform[-1,1] inputs), tar_<n> (one TAR-Strassen level, FP32 mode).
+uniform[-1,1] inputs), tar_<n> (one TAR-Strassen level, FP32 mode), probes (one
+launch of each instruction-throughput probe, kinds 0..3).
 Inputs come from the seeded generators; nothing is checked here.
 """
 import argparse
@@ -30,6 +31,18 @@ def main():
 
     __graft_entry__.build()
     torch.cuda.set_device(0)
+    if a.case == "probes":
+        import ctypes
+
+        lib = mmsr.load()
+        lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        rate, ms = ctypes.c_double(), ctypes.c_double()
+        for kind, iters in ((0, 20000), (1, 20000), (2, 2000), (3, 20000)):
+            for _ in range(a.reps):
+                lib.mm_probe_peak(kind, iters, None, ctypes.byref(rate), ctypes.byref(ms))
+            print("probe kind %d: %.2f Tops/s" % (kind, rate.value / 1e12))
+        return
     if a.case.startswith("minplus"):
         n = int(a.case[len("minplus"):] or 4096)
         A, B = inputs.tropical_i32(n, n, n, seed=1)

@@ -28,15 +28,24 @@ def run(A, B, extra_parts=0):
 
 
 @pytest.mark.parametrize("m,n,k,density", [(1, 1, 1, 0.5), (7, 5, 3, 0.5), (128, 128, 1024, 0.002),
-                                           (129, 131, 33, 0.05), (500, 300, 4000, 0.001), (1000, 1000, 1000, 0.003)])
+                                           (129, 131, 33, 0.05), (500, 300, 4000, 0.001), (1000, 1000, 1000, 0.003),
+                                           # k % 16 == 0 (16-byte row loads), last word partial or whole
+                                           (70, 90, 48, 0.1), (200, 130, 1008, 0.01), (256, 256, 4096, 0.5),
+                                           # n % 16 == 0: 16-byte column loads, last column block partial
+                                           (64, 1008, 100, 0.05), (33, 48, 300, 0.02)])
 def test_matches_oracle(m, n, k, density):
     A, B = inputs.boolean_u8(m, k, n, seed=m + k, density=density)
     np.testing.assert_array_equal(run(A, B), oracle.mm_orand(A, B))
 
 
-def test_nonzero_bytes_are_true():
-    A, B = inputs.boolean_u8(64, 100, 64, seed=3, density=0.05)
-    A2, B2 = A * 7, B * 200
+@pytest.mark.parametrize("k", [100, 96])
+def test_nonzero_bytes_are_true(k):
+    # every nonzero byte value counts as true, on both the byte-wise and the
+    # 16-byte packing paths
+    A, B = inputs.boolean_u8(64, k, 64, seed=3, density=0.05)
+    rng = np.random.default_rng(k)
+    A2 = A * rng.integers(1, 256, size=A.shape).astype(np.uint8)
+    B2 = B * rng.integers(1, 256, size=B.shape).astype(np.uint8)
     np.testing.assert_array_equal(run(A2, B2), oracle.mm_orand(A, B))
 
 
