@@ -12,6 +12,7 @@
 namespace mmsr {
 
 constexpr int kInf = 1 << 30;  // +infinity of the (min,+) semiring on [0, 2^30]
+constexpr int64_t kMaxGridY = 65535;  // grid y / z extent limit; larger extents loop in-kernel
 constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
 #define MMSR_CUDA_TRY(expr)                                   \

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(THREADS)
     dfma_leaf_kernel(int64_t m, int64_t n, int64_t k, const double* __restrict__ A,
                      const double* __restrict__ B, double* __restrict__ C,
                      double* __restrict__ W, int kb_per_slice, bool vec, int slices,
-                     int64_t a_bs, int64_t b_bs, int64_t c_bs) {
+                     int64_t a_bs, int64_t b_bs, int64_t c_bs, int64_t flat_tiles_n) {
   extern __shared__ __align__(16) double smem_d[];
   // blockIdx.z = batch * slices + k-slice (batches: independent products)
   const int batch = blockIdx.z / slices;
@@ -71,7 +71,14 @@ __global__ void __launch_bounds__(THREADS)
   double* Bs = smem_d + SMEM_A;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  // tile (row, column) = (blockIdx.y, blockIdx.x); with flat_tiles_n > 0 the
+  // tiles run along x alone (more row tiles than a grid's y extent allows)
+  int64_t tile_r = blockIdx.y, tile_c = blockIdx.x;
+  if (flat_tiles_n > 0) {
+    tile_r = (int64_t)blockIdx.x / flat_tiles_n;
+    tile_c = (int64_t)blockIdx.x - tile_r * flat_tiles_n;
+  }
+  const int64_t i0 = tile_r * BM, j0 = tile_c * BN;
   const int z = blockIdx.z % slices;
   const int64_t kb_total = (k + BK - 1) / BK;
   const int64_t kb_begin = (int64_t)z * kb_per_slice;
@@ -229,7 +236,14 @@ cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, c
     dfma_small_kernel<<<sg, 256, 0, st>>>(m, n, k, A, B, C, W, kb_per_slice);
     return cudaGetLastError();
   }
-  dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec, s, 0, 0, 0);
+  if (grid.y > kMaxGridY) {
+    const int64_t tiles_n = grid.x;
+    dim3 flat((unsigned)(tiles_n * grid.y), 1, (unsigned)s);
+    dfma_leaf_kernel<<<flat, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec, s, 0, 0, 0,
+                                                        tiles_n);
+    return cudaGetLastError();
+  }
+  dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec, s, 0, 0, 0, 0);
   return cudaGetLastError();
 }
 
@@ -243,7 +257,7 @@ cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)batches);
   TraceScope tr(kTrDfmaLeaf, st);
   dfma_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, nullptr, kb > 0 ? kb : 1, vec, 1,
-                                                      m * k, k * n, m * n);
+                                                      m * k, k * n, m * n, 0);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include <cuda_bf16.h>
 
 #include "../../include/mmsr.h"

@@ -207,7 +207,10 @@ __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
   const int r = blockIdx.z;
   const float* s = src + (int64_t)r * src_stride;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t k0 = (int64_t)blockIdx.x * 64, n0 = (int64_t)blockIdx.y * 32;
+  const int64_t k0 = (int64_t)blockIdx.x * 64;
+  // n-tiles with stride gridDim.y (the grid's y extent is capped at 65535)
+  for (int64_t n0 = (int64_t)blockIdx.y * 32; n0 < w; n0 += (int64_t)gridDim.y * 32) {
+  __syncthreads();  // the previous n-tile's readers are done with `tile`
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
 #pragma unroll
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
   __syncthreads();
   const int row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
   const int64_t gn = n0 + row;
-  if (gn >= w) return;
+  if (gn >= w) continue;
 #pragma unroll
   for (int p = 0; p < 7; ++p) {
     __align__(16) __nv_bfloat16 hh[8], ll[8];
@@ -233,6 +236,7 @@ __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
     const int64_t off = ((int64_t)(r * 7 + slot.s[p]) * w + gn) * Kp + k0 + chunk * 8;
     *reinterpret_cast<uint4*>(hiT + off) = *reinterpret_cast<const uint4*>(hh);
     *reinterpret_cast<uint4*>(loT + off) = *reinterpret_cast<const uint4*>(ll);
+  }
   }
 }
 
@@ -447,7 +451,10 @@ __global__ void __launch_bounds__(128) pre_combine2_split_transpose_kernel(
   __shared__ float tile[16][32][17];
   const int r = blockIdx.z;
   const float* s = src + (int64_t)r * src_stride;
-  const int k0 = blockIdx.x * 32, n0 = blockIdx.y * 16;
+  const int k0 = blockIdx.x * 32;
+  // n-tiles with stride gridDim.y (the grid's y extent is capped at 65535)
+  for (int n0 = blockIdx.y * 16; n0 < w; n0 += gridDim.y * 16) {
+  __syncthreads();  // the previous n-tile's readers are done with `tile`
   {
     const int jj = threadIdx.x & 15;
     const int gn = n0 + jj;
@@ -466,7 +473,7 @@ __global__ void __launch_bounds__(128) pre_combine2_split_transpose_kernel(
   __syncthreads();
   const int kq = threadIdx.x & 7, jj = threadIdx.x >> 3;
   const int gn = n0 + jj;
-  if (gn >= w) return;
+  if (gn >= w) continue;
   float x[4][4][4];  // [a][b][k]
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -496,6 +503,7 @@ __global__ void __launch_bounds__(128) pre_combine2_split_transpose_kernel(
       *reinterpret_cast<uint2*>(hiT + off) = vh;
       *reinterpret_cast<uint2*>(loT + off) = vl;
     }
+  }
   }
 }
 
@@ -780,7 +788,7 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
       MMSR_CUDA_TRY(cudaGetLastError());
     } else {
       if (span == 2) {
-        const dim3 g((unsigned)(S.KpL / 32), (unsigned)((w + 15) / 16), (unsigned)R);
+        const dim3 g((unsigned)(S.KpL / 32), (unsigned)std::min<int64_t>((w + 15) / 16, kMaxGridY), (unsigned)R);
         if (variant == 0)
           pre_combine2_split_transpose_kernel<0><<<g, 128, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
                                                                    (int)S.KpL, hi, lo);
@@ -788,7 +796,7 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
           pre_combine2_split_transpose_kernel<1><<<g, 128, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
                                                                    (int)S.KpL, hi, lo);
       } else {
-        const dim3 g((unsigned)(S.KpL / 64), (unsigned)((w + 31) / 32), (unsigned)R);
+        const dim3 g((unsigned)(S.KpL / 64), (unsigned)std::min<int64_t>((w + 31) / 32, kMaxGridY), (unsigned)R);
         if (variant == 0)
           pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo,
                                                                   slot);

@@ -140,7 +140,11 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
   B += b * k * n;
   F += b * n;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t k0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
+  const int64_t k0 = (int64_t)blockIdx.x * 32;
+  const int64_t slice = (int64_t)batches * n * Kp;
+  // n-tiles with stride gridDim.y (the grid's y extent is capped at 65535)
+  for (int64_t n0 = (int64_t)blockIdx.y * 32; n0 < n; n0 += (int64_t)gridDim.y * 32) {
+  __syncthreads();  // the previous n-tile's readers are done with `tile`
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const int kk = ty + 8 * it;
@@ -148,7 +152,6 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
     tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.0;
   }
   __syncthreads();
-  const int64_t slice = (int64_t)batches * n * Kp;
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const int nn = ty + 8 * it;
@@ -158,6 +161,7 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
     digits7(tile[tx][nn], F[gn], d);
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) S[s * slice + (b * n + gn) * Kp + gk] = d[s];
+  }
   }
 }
 
@@ -466,7 +470,7 @@ int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* 
                      st>>>(B, k, n, Fmax);
     col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
     digits_rows_kernel<<<grid_for(rows_a * L.Kp), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA);
-    dim3 g((unsigned)(L.Kp / 32), (unsigned)((n + 31) / 32), (unsigned)batches);
+    dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>((n + 31) / 32, kMaxGridY), (unsigned)batches);
     digits_cols_kernel<<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
