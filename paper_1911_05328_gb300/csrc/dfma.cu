@@ -155,30 +155,35 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 // Small-tile variant for products whose 64 x 64 grid would leave most SMs
-// idle (n = 256 gives 16 CTAs): a 16 x 16 tile per CTA, one output per
-// thread, k staged through shared memory in blocks of 32.
-constexpr int SBM = 16, SBK = 32;
+// idle (n = 256 gives 16 CTAs): an SB x SB tile per CTA, one output per
+// thread, k staged through shared memory in blocks of 32.  The FP64 pipe
+// (2 FMA per SM per clock) bounds these products, so an SM's time grows with
+// the CTAs it holds: SB = 8 gives n = 256 1024 CTAs (6 or 7 per SM) where
+// SB = 16 gave 256 (1 or 2 per SM).
+constexpr int SBK = 32;
 
-__global__ void __launch_bounds__(256)
+template <int SB>
+__global__ void __launch_bounds__(SB * SB)
     dfma_small_kernel(int64_t m, int64_t n, int64_t k, const double* __restrict__ A,
                       const double* __restrict__ B, double* __restrict__ C, double* __restrict__ W,
                       int kb_per_slice) {
-  __shared__ double As[SBM][SBK + 1];
-  __shared__ double Bs[SBK][SBM + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t i0 = (int64_t)blockIdx.y * SBM, j0 = (int64_t)blockIdx.x * SBM;
+  constexpr int T = SB * SB, PER = SBK * SB / T;  // staged elements per thread and operand
+  __shared__ double As[SB][SBK + 1];
+  __shared__ double Bs[SBK][SB + 1];
+  const int tx = threadIdx.x % SB, ty = threadIdx.x / SB;
+  const int64_t i0 = (int64_t)blockIdx.y * SB, j0 = (int64_t)blockIdx.x * SB;
   const int z = blockIdx.z;
   // slices are counted in the 16-wide k-blocks of the 64 x 64 leaf
   const int64_t kbeg = (int64_t)z * kb_per_slice * BK;
   const int64_t kend = min(k, kbeg + (int64_t)kb_per_slice * BK);
   double acc = 0.0;
   for (int64_t k0 = kbeg; k0 < kend; k0 += SBK) {
-    // 512 elements of each operand block, two per thread
+    // SB x 32 elements of each operand block, PER per thread
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      const int ar = e >> 5, ac = e & 31;   // A block 16 x 32
-      const int br = e >> 4, bc = e & 15;   // B block 32 x 16
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + T * q;
+      const int ar = e / SBK, ac = e % SBK;  // A block SB x 32
+      const int br = e / SB, bc = e % SB;    // B block 32 x SB
       const int64_t ga = i0 + ar, gk = k0 + ac;
       As[ar][ac] = (ga < m && gk < kend) ? A[ga * k + gk] : 0.0;
       const int64_t gkb = k0 + br, gb = j0 + bc;
@@ -231,9 +236,16 @@ cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, c
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
   TraceScope tr(kTrDfmaLeaf, st);
   if ((int64_t)grid.x * grid.y * s < 2 * kNumSMs) {
-    // too few 64 x 64 tiles to occupy the GPU: 16 x 16 tiles instead
-    dim3 sg((unsigned)((n + SBM - 1) / SBM), (unsigned)((m + SBM - 1) / SBM), (unsigned)s);
-    dfma_small_kernel<<<sg, 256, 0, st>>>(m, n, k, A, B, C, W, kb_per_slice);
+    // too few 64 x 64 tiles to occupy the GPU: 16 x 16 tiles, or 8 x 8 when
+    // 16 x 16 tiles would still leave fewer than four CTAs per SM
+    const int64_t tiles16 = ((n + 15) / 16) * ((m + 15) / 16) * s;
+    if (tiles16 < 4 * (int64_t)kNumSMs) {
+      dim3 sg((unsigned)((n + 7) / 8), (unsigned)((m + 7) / 8), (unsigned)s);
+      dfma_small_kernel<8><<<sg, 64, 0, st>>>(m, n, k, A, B, C, W, kb_per_slice);
+    } else {
+      dim3 sg((unsigned)((n + 15) / 16), (unsigned)((m + 15) / 16), (unsigned)s);
+      dfma_small_kernel<16><<<sg, 256, 0, st>>>(m, n, k, A, B, C, W, kb_per_slice);
+    }
     return cudaGetLastError();
   }
   if (grid.y > kMaxGridY) {
