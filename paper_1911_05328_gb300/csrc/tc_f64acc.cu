@@ -54,12 +54,26 @@ constexpr uint32_t TMEM_COLS = 512;  // 7 groups x 64 columns used
 static_assert(BK == 32, "the MMA issue loop covers two 16-deep k-steps per k-block");
 
 // ----------------------------------------------------------- split kernels
-// Exponent E with max|x| < 2^E (0 for an all-zero line).
-__device__ __forceinline__ int line_exponent(double maxabs) {
-  if (!(maxabs > 0.0)) return 0;
-  int e;
-  frexp(maxabs, &e);  // maxabs = f 2^e, f in [0.5, 1)
-  return e;
+// The split passes work on the bit patterns of the (finite) FP64 inputs in
+// integer arithmetic: this GPU's FP64 pipe retires about 2 operations per
+// clock per SM, so maxima, exponents and the scaled rounding are read from
+// the exponent and significand fields instead.
+
+// |x| as a bit pattern: for finite doubles the unsigned order of these
+// patterns is the numeric order of |x|.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Exponent E with max|x| < 2^E, from the bit pattern of max|x| (0 for an
+// all-zero line): frexp's exponent, max|x| = f 2^E with f in [0.5, 1) --
+// the exponent field minus 1022 for a normal number, the position of the
+// leading significand bit for a subnormal one (value = b 2^-1074).
+__device__ __forceinline__ int line_exponent(unsigned long long b) {
+  if (b == 0) return 0;
+  const int ex = (int)(b >> 52);
+  if (ex != 0) return ex - 1022;
+  return (63 - __clzll((long long)b)) - 1073;
 }
 
 // Row maxima of A (one warp per row), stored as the exponent E of the row.
@@ -68,16 +82,15 @@ __global__ void __launch_bounds__(256) row_exponent_kernel(const double* __restr
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
-  double mx = 0.0;
-  for (int64_t t = lane; t < k; t += 32) mx = fmax(mx, fabs(A[row * k + t]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  unsigned long long mx = 0;
+  for (int64_t t = lane; t < k; t += 32) mx = max(mx, abs_bits(A[row * k + t]));
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) E[row] = line_exponent(mx);
 }
 
 // Column maxima of B (k x n, batch blockIdx.z of a contiguous stack): each
-// thread scans 256 rows of one column and folds its maximum into Fmax with
-// an atomic max on the bit pattern (for non-negative doubles the unsigned
-// bit order is the numeric order; Fmax starts at +0.0).
+// thread scans 256 rows of one column and folds the bit pattern of its
+// maximum |x| into Fmax with an atomic max (Fmax starts at 0 = +0.0).
 __global__ void __launch_bounds__(256) col_max_kernel(const double* __restrict__ B, int64_t k,
                                                       int64_t n, unsigned long long* __restrict__ Fmax) {
   B += (int64_t)blockIdx.z * k * n;
@@ -85,23 +98,52 @@ __global__ void __launch_bounds__(256) col_max_kernel(const double* __restrict__
   const int64_t col = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (col >= n) return;
   const int64_t r0 = (int64_t)blockIdx.y * 256, r1 = min(k, r0 + 256);
-  double mx = 0.0;
-  for (int64_t t = r0; t < r1; ++t) mx = fmax(mx, fabs(B[t * n + col]));
-  if (mx > 0.0) atomicMax(&Fmax[col], (unsigned long long)__double_as_longlong(mx));
+  unsigned long long mx = 0;
+  for (int64_t t = r0; t < r1; ++t) mx = max(mx, abs_bits(B[t * n + col]));
+  if (mx) atomicMax(&Fmax[col], mx);
 }
 
 __global__ void __launch_bounds__(256) col_exponent_kernel(const unsigned long long* __restrict__ Fmax,
                                                            int64_t count, int* __restrict__ F) {
   const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (j < count) F[j] = line_exponent(__longlong_as_double((long long)Fmax[j]));
+  if (j < count) F[j] = line_exponent(Fmax[j]);
+}
+
+// x 2^(49-E) rounded to the nearest integer, ties to even, for finite x with
+// |x| < 2^E.  x = sig 2^e2 exactly (sig the significand with its implicit
+// bit), so the scaling by a power of two is an exponent shift and the one
+// rounding is a right shift of sig with round-half-even; |result| < 2^49.
+__device__ __forceinline__ long long scaled_round(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long sig = b & 0xFFFFFFFFFFFFFull;
+  int e2;
+  if (ex) {
+    sig |= 1ull << 52;
+    e2 = ex - 1075;
+  } else {
+    e2 = -1074;
+  }
+  const int sh = e2 + kDigitBits * kSlices - E;
+  long long M;
+  if (sh >= 0) {
+    M = (long long)(sig << sh);  // sig 2^sh < 2^49 since |x| < 2^E
+  } else if (sh <= -54) {
+    M = 0;  // |x 2^(49-E)| < 2^53 2^-54 = 1/2
+  } else {
+    const int r = -sh;
+    const unsigned long long q = sig >> r, rem = sig & ((1ull << r) - 1), half = 1ull << (r - 1);
+    M = (long long)(q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0));
+  }
+  return (b >> 63) ? -M : M;
 }
 
 // Seven digits of x * 2^-E: one rounding of x * 2^(49-E) to an integer M
 // (|M| < 2^49, residual below 2^-50 of 2^E), then balanced base-128 digits
-// by integer arithmetic (FP64 throughput is the scarce resource here):
+// by integer arithmetic:
 // M = sum_s d_s 128^(6-s) with d_1..d_6 in [-64, 63] and |d_0| <= 128.
 __device__ __forceinline__ void digits7(double x, int E, __nv_bfloat16 (&d)[kSlices]) {
-  long long M = __double2ll_rn(ldexp(x, kDigitBits * kSlices - E));
+  long long M = scaled_round(x, E);
 #pragma unroll
   for (int s = kSlices - 1; s >= 1; --s) {
     const int ds = (int)(((M + 64) & 127) - 64);
@@ -112,17 +154,18 @@ __device__ __forceinline__ void digits7(double x, int E, __nv_bfloat16 (&d)[kSli
 }
 
 // A (m x k) -> seven digit slices, slice s at S + s*m*Kp (row pitch Kp, zero pad).
+// blockIdx.x covers 256 columns, blockIdx.y rows with the grid's y stride.
 __global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restrict__ A, int64_t m,
                                                           int64_t k, int64_t Kp,
                                                           const int* __restrict__ E,
                                                           __nv_bfloat16* __restrict__ S) {
-  const int64_t total = m * Kp;
   const int64_t slice = m * Kp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / Kp, t = e - i * Kp;
+  const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (t >= Kp) return;
+  for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
     __nv_bfloat16 d[kSlices];
     digits7(t < k ? A[i * k + t] : 0.0, E[i], d);
+    const int64_t e = i * Kp + t;
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) S[s * slice + e] = d[s];
   }
@@ -422,12 +465,6 @@ F64AccLayout layout(int64_t m, int64_t n, int64_t k, int64_t batches = 1) {
   return L;
 }
 
-unsigned grid_for(int64_t work, int per_sm = 16) {
-  int64_t b = (work + 255) / 256;
-  if (b > (int64_t)kNumSMs * per_sm) b = (int64_t)kNumSMs * per_sm;
-  return (unsigned)(b < 1 ? 1 : b);
-}
-
 }  // namespace
 
 int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
@@ -469,7 +506,9 @@ int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* 
     col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256, 0,
                      st>>>(B, k, n, Fmax);
     col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
-    digits_rows_kernel<<<grid_for(rows_a * L.Kp), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA);
+    digits_rows_kernel<<<dim3((unsigned)std::max<int64_t>(1, (L.Kp + 255) / 256),
+                              (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows_a, kMaxGridY))),
+                         256, 0, st>>>(A, rows_a, k, L.Kp, E, SA);
     dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>((n + 31) / 32, kMaxGridY), (unsigned)batches);
     digits_cols_kernel<<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
     MMSR_TRY_STATUS(cudaGetLastError());
