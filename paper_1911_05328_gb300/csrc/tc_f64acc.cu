@@ -140,40 +140,55 @@ __device__ __forceinline__ long long scaled_round(double x, int E) {
 
 // Seven digits of x * 2^-E: one rounding of x * 2^(49-E) to an integer M
 // (|M| < 2^49, residual below 2^-50 of 2^E), then balanced base-128 digits
-// by integer arithmetic:
 // M = sum_s d_s 128^(6-s) with d_1..d_6 in [-64, 63] and |d_0| <= 128.
-__device__ __forceinline__ void digits7(double x, int E, __nv_bfloat16 (&d)[kSlices]) {
-  long long M = scaled_round(x, E);
-#pragma unroll
-  for (int s = kSlices - 1; s >= 1; --s) {
-    const int ds = (int)(((M + 64) & 127) - 64);
-    d[s] = __int2bfloat16_rn(ds);  // |ds| <= 64: exact
-    M = (M - ds) >> kDigitBits;    // exact: M - ds is a multiple of 128
-  }
-  d[0] = __int2bfloat16_rn((int)M);  // |M| <= 128 here: exact
+// Adding K = 64 (1 + 128 + ... + 128^5) makes them plain digits: for s >= 1,
+// d_s + 64 is the 7-bit field 6-s of M + K, and d_0 = (M + K) >> 42.  The
+// fields come from the two 32-bit halves of M + K, and each digit becomes an
+// exact float by the 2^23 trick (2^23 + u has u as its low mantissa bits).
+constexpr long long kDigitOffset = 64LL * (((1LL << 42) - 1) / 127);
+__device__ __forceinline__ float field_digit(uint32_t u, float bias) {
+  return __int_as_float(0x4B000000 | (int)u) - bias;  // (2^23 + u) - (2^23 + offset), exact
+}
+__device__ __forceinline__ void digits7(double x, int E, float (&d)[kSlices]) {
+  const long long Mk = scaled_round(x, E) + kDigitOffset;
+  const uint32_t lo = (uint32_t)Mk, hi = (uint32_t)(Mk >> 32);
+  constexpr float kB64 = 8388608.0f + 64.0f, kB128 = 8388608.0f + 128.0f;
+  d[6] = field_digit(lo & 127u, kB64);
+  d[5] = field_digit((lo >> 7) & 127u, kB64);
+  d[4] = field_digit((lo >> 14) & 127u, kB64);
+  d[3] = field_digit((lo >> 21) & 127u, kB64);
+  d[2] = field_digit(__funnelshift_r(lo, hi, 28) & 127u, kB64);
+  d[1] = field_digit((hi >> 3) & 127u, kB64);
+  d[0] = field_digit((uint32_t)(((int)hi >> 10) + 128), kB128);  // d_0 + 128 in [0, 256]
 }
 
-// A (m x k) -> seven digit slices, slice s at S + s*m*Kp (row pitch Kp, zero pad).
-// blockIdx.x covers 256 columns, blockIdx.y rows with the grid's y stride.
+// A (m x k) -> seven digit slices, slice s at S + s*m*Kp (row pitch Kp, zero
+// pad).  Each thread converts two adjacent columns and stores one bf16 pair
+// per slice; blockIdx.x covers 512 columns, blockIdx.y rows with the grid's
+// y stride.
 __global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restrict__ A, int64_t m,
                                                           int64_t k, int64_t Kp,
                                                           const int* __restrict__ E,
                                                           __nv_bfloat16* __restrict__ S) {
   const int64_t slice = m * Kp;
-  const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 2;  // Kp is even: t + 1 < Kp
   if (t >= Kp) return;
   for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
-    __nv_bfloat16 d[kSlices];
-    digits7(t < k ? A[i * k + t] : 0.0, E[i], d);
+    float d0[kSlices], d1[kSlices];
+    const int Ei = E[i];
+    digits7(t < k ? A[i * k + t] : 0.0, Ei, d0);
+    digits7(t + 1 < k ? A[i * k + t + 1] : 0.0, Ei, d1);
     const int64_t e = i * Kp + t;
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) S[s * slice + e] = d[s];
+    for (int s = 0; s < kSlices; ++s)
+      *reinterpret_cast<__nv_bfloat162*>(S + s * slice + e) = __floats2bfloat162_rn(d0[s], d1[s]);
   }
 }
 
 // B (k x n, batch blockIdx.z of a contiguous stack of `batches`) -> seven
 // digit slices of B^T: slice s holds batches*n rows of pitch Kp, batch b at
-// rows [b*n, (b+1)*n).  Via a 32 x 32 shared tile.
+// rows [b*n, (b+1)*n).  Via a 32 x 32 shared tile; each thread converts two
+// adjacent k of one column and stores one bf16 pair per slice.
 __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restrict__ B, int64_t k,
                                                           int64_t n, int64_t Kp,
                                                           const int* __restrict__ F,
@@ -183,28 +198,33 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
   B += b * k * n;
   F += b * n;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int pk = threadIdx.x & 15, pn = threadIdx.x >> 4;  // k pair, n row (of 16) when storing
   const int64_t k0 = (int64_t)blockIdx.x * 32;
   const int64_t slice = (int64_t)batches * n * Kp;
   // n-tiles with stride gridDim.y (the grid's y extent is capped at 65535)
   for (int64_t n0 = (int64_t)blockIdx.y * 32; n0 < n; n0 += (int64_t)gridDim.y * 32) {
-  __syncthreads();  // the previous n-tile's readers are done with `tile`
+    __syncthreads();  // the previous n-tile's readers are done with `tile`
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    const int kk = ty + 8 * it;
-    const int64_t gk = k0 + kk, gn = n0 + tx;
-    tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.0;
-  }
-  __syncthreads();
+    for (int it = 0; it < 4; ++it) {
+      const int kk = ty + 8 * it;
+      const int64_t gk = k0 + kk, gn = n0 + tx;
+      tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.0;
+    }
+    __syncthreads();
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    const int nn = ty + 8 * it;
-    const int64_t gn = n0 + nn, gk = k0 + tx;
-    if (gn >= n || gk >= Kp) continue;
-    __nv_bfloat16 d[kSlices];
-    digits7(tile[tx][nn], F[gn], d);
+    for (int it = 0; it < 2; ++it) {
+      const int nn = pn + 16 * it;
+      const int64_t gn = n0 + nn, gk = k0 + 2 * pk;  // k0 + 32 <= Kp: gk + 1 < Kp
+      if (gn >= n) continue;
+      float d0[kSlices], d1[kSlices];
+      const int Fj = F[gn];
+      digits7(tile[2 * pk][nn], Fj, d0);
+      digits7(tile[2 * pk + 1][nn], Fj, d1);
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) S[s * slice + (b * n + gn) * Kp + gk] = d[s];
-  }
+      for (int s = 0; s < kSlices; ++s)
+        *reinterpret_cast<__nv_bfloat162*>(S + s * slice + (b * n + gn) * Kp + gk) =
+            __floats2bfloat162_rn(d0[s], d1[s]);
+    }
   }
 }
 
@@ -506,7 +526,7 @@ int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* 
     col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256, 0,
                      st>>>(B, k, n, Fmax);
     col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
-    digits_rows_kernel<<<dim3((unsigned)std::max<int64_t>(1, (L.Kp + 255) / 256),
+    digits_rows_kernel<<<dim3((unsigned)std::max<int64_t>(1, (L.Kp + 511) / 512),
                               (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows_a, kMaxGridY))),
                          256, 0, st>>>(A, rows_a, k, L.Kp, E, SA);
     dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>((n + 31) / 32, kMaxGridY), (unsigned)batches);
