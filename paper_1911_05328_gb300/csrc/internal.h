@@ -40,7 +40,7 @@ int plan_orand(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
 int run_orand(int64_t m, int64_t n, int64_t k, const uint8_t* A, const uint8_t* B, uint8_t* C,
               void* ws, size_t ws_bytes, cudaStream_t st);
 
-// FP64-accuracy mode: six 7-bit digit slices per operand on tcgen05
+// FP64-accuracy mode: seven 7-bit digit slices per operand on tcgen05
 int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
 int run_f64acc(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
                void* ws, size_t ws_bytes, cudaStream_t st);
