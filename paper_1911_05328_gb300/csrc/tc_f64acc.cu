@@ -163,25 +163,39 @@ __device__ __forceinline__ void digits7(double x, int E, float (&d)[kSlices]) {
 }
 
 // A (m x k) -> seven digit slices, slice s at S + s*m*Kp (row pitch Kp, zero
-// pad).  Each thread converts two adjacent columns and stores one bf16 pair
-// per slice; blockIdx.x covers 512 columns, blockIdx.y rows with the grid's
-// y stride.
+// pad).  Each thread converts four adjacent columns and stores 8 bytes per
+// slice; blockIdx.x covers 1024 columns, blockIdx.y takes rows with the
+// grid's y stride (a few thousand blocks in all, each walking many rows).
 __global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restrict__ A, int64_t m,
                                                           int64_t k, int64_t Kp,
                                                           const int* __restrict__ E,
-                                                          __nv_bfloat16* __restrict__ S) {
+                                                          __nv_bfloat16* __restrict__ S, bool vec) {
   const int64_t slice = m * Kp;
-  const int64_t t = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 2;  // Kp is even: t + 1 < Kp
+  const int64_t t = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;  // Kp % 32 == 0: t + 3 < Kp
   if (t >= Kp) return;
   for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
-    float d0[kSlices], d1[kSlices];
+    double x[4];
+    const double* src = A + i * k + t;
+    if (vec && t + 4 <= k) {  // rows 16-byte aligned (k even, A 16-byte aligned)
+      const double2 a = __ldcs(reinterpret_cast<const double2*>(src));
+      const double2 b = __ldcs(reinterpret_cast<const double2*>(src) + 1);
+      x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = t + u < k ? __ldcs(src + u) : 0.0;
+    }
     const int Ei = E[i];
-    digits7(t < k ? A[i * k + t] : 0.0, Ei, d0);
-    digits7(t + 1 < k ? A[i * k + t + 1] : 0.0, Ei, d1);
+    float d[4][kSlices];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) digits7(x[u], Ei, d[u]);
     const int64_t e = i * Kp + t;
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s)
-      *reinterpret_cast<__nv_bfloat162*>(S + s * slice + e) = __floats2bfloat162_rn(d0[s], d1[s]);
+    for (int s = 0; s < kSlices; ++s) {
+      const __nv_bfloat162 p0 = __floats2bfloat162_rn(d[0][s], d[1][s]);
+      const __nv_bfloat162 p1 = __floats2bfloat162_rn(d[2][s], d[3][s]);
+      *reinterpret_cast<uint2*>(S + s * slice + e) =
+          make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+    }
   }
 }
 
@@ -526,10 +540,17 @@ int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* 
     col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256, 0,
                      st>>>(B, k, n, Fmax);
     col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
-    digits_rows_kernel<<<dim3((unsigned)std::max<int64_t>(1, (L.Kp + 511) / 512),
-                              (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows_a, kMaxGridY))),
-                         256, 0, st>>>(A, rows_a, k, L.Kp, E, SA);
-    dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>((n + 31) / 32, kMaxGridY), (unsigned)batches);
+    {
+      const int64_t gx = std::max<int64_t>(1, (L.Kp + 1023) / 1024);
+      const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(rows_a, std::max<int64_t>(1, 4096 / gx)));
+      digits_rows_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA,
+                                                                          aligned16(A) && k % 2 == 0);
+    }
+    // n-tiles per block: enough blocks to fill the GPU a few times over, each
+    // walking several tiles
+    const int64_t tiles_n = (n + 31) / 32;
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 8192 / (L.Kp / 32 * batches))));
+    dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>(gy, kMaxGridY), (unsigned)batches);
     digits_cols_kernel<<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
