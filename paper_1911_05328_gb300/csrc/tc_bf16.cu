@@ -557,7 +557,10 @@ cudaError_t launch_split_bf16(const float* A, const float* B, int64_t m, int64_t
   if (blocks > (int64_t)kNumSMs * 16) blocks = (int64_t)kNumSMs * 16;
   if (blocks < 1) blocks = 1;
   split_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, Kp, ahi, alo, vec);
-  dim3 g((unsigned)(Kp / 64), (unsigned)std::min<int64_t>((n + 31) / 32, kMaxGridY));
+  // a few thousand blocks, each walking several n-tiles
+  const int64_t tiles_n = (n + 31) / 32;
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 4096 / (Kp / 64))));
+  dim3 g((unsigned)(Kp / 64), (unsigned)std::min<int64_t>(gy, kMaxGridY));
   split_transpose_kernel<<<g, 256, 0, st>>>(B, k, n, Kp, bhi, blo);
   return cudaGetLastError();
 }
