@@ -96,59 +96,95 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const uint8_t* __restric
   if (jj < n && ww < KW) P[jj * KW + ww] = words[col][wi];
 }
 
+// 4-byte asynchronous copy global -> shared; a word outside the operand is
+// zero-filled (src-size 0: nothing is read, the address is only a valid one).
+__device__ __forceinline__ void cp_async4_zfill(uint32_t* smem, const uint32_t* gmem, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(valid ? 4 : 0));
+}
+
+// Shared memory: two stages x (A, B) x OBW words x OLD rows; the next stage's
+// words are copied asynchronously while the current one is consumed.
+constexpr size_t kOrSmem = (size_t)2 * 2 * OBW * OLD * sizeof(uint32_t);
+
 __global__ void __launch_bounds__(256, 2)
     orand_leaf_kernel(int64_t m, int64_t n, int64_t KW, const uint32_t* __restrict__ PA,
                       const uint32_t* __restrict__ PB, uint8_t* __restrict__ C,
-                      uint8_t* __restrict__ W, int words_per_slice) {
-  __shared__ __align__(16) uint32_t As[OBW][OLD];
-  __shared__ __align__(16) uint32_t Bs[OBW][OLD];
+                      uint8_t* __restrict__ W, int words_per_slice, bool vec_out) {
+  extern __shared__ __align__(16) uint32_t osm[];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.y * OBM, j0 = (int64_t)blockIdx.x * OBN;
   const int z = blockIdx.z;
   const int64_t wb = (int64_t)z * words_per_slice;
   const int64_t we = min(KW, wb + words_per_slice);
+  const int nblk = we > wb ? (int)((we - wb + OBW - 1) / OBW) : 0;
+  // staging map: a warp copies 4 rows x 8 consecutive words (whole 32-byte
+  // sectors); this thread's word column c is fixed, its rows are r0 + 8 q
+  const int lane = tid & 31, wrp = tid >> 5;
+  const int c = (wrp & 3) * 8 + (lane & 7);
+  const int r0 = 4 * (wrp >> 2) + (lane >> 3);
+  auto issue = [&](int b) {
+    uint32_t* As = osm + (size_t)(b & 1) * 2 * OBW * OLD;
+    uint32_t* Bs = As + OBW * OLD;
+    const int64_t gw = wb + (int64_t)b * OBW + c;
+    const bool wok = gw < we;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int r = r0 + 8 * q;
+      const int64_t ga = i0 + r, gb = j0 + r;
+      const bool va = wok && ga < m, vb = wok && gb < n;
+      cp_async4_zfill(&As[c * OLD + r], va ? PA + ga * KW + gw : PA, va);
+      cp_async4_zfill(&Bs[c * OLD + r], vb ? PB + gb * KW + gw : PB, vb);
+    }
+  };
   uint32_t acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0u;
-  for (int64_t w0 = wb; w0 < we; w0 += OBW) {
-    // 128 rows x 32 words of each operand, 16 per thread; a warp reads 4
-    // rows x 8 consecutive words (whole 32-byte sectors)
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int e = tid + 256 * q;
-      const int lane = e & 31, wq = e >> 5;
-      const int r = (wq >> 2) * 4 + (lane >> 3), c = (wq & 3) * 8 + (lane & 7);
-      const int64_t gw = w0 + c;
-      const int64_t ga = i0 + r, gb = j0 + r;
-      As[c][r] = (ga < m && gw < we) ? PA[ga * KW + gw] : 0u;
-      Bs[c][r] = (gb < n && gw < we) ? PB[gb * KW + gw] : 0u;
-    }
-    __syncthreads();
+  if (nblk > 0) issue(0);
+  cp_async_commit();
+  for (int b = 0; b < nblk; ++b) {
+    if (b + 1 < nblk) issue(b + 1);  // into the stage read in iteration b - 1
+    cp_async_commit();
+    cp_async_wait<1>();  // this thread's copies of stage b have landed
+    __syncthreads();     // ... and every other thread's
+    const uint32_t* As = osm + (size_t)(b & 1) * 2 * OBW * OLD;
+    const uint32_t* Bs = As + OBW * OLD;
 #pragma unroll 4
-    for (int c = 0; c < OBW; ++c) {
-      uint32_t a[8], b[8];
-      *reinterpret_cast<uint4*>(a) = *reinterpret_cast<const uint4*>(&As[c][ty * 4]);
-      *reinterpret_cast<uint4*>(a + 4) = *reinterpret_cast<const uint4*>(&As[c][64 + ty * 4]);
-      *reinterpret_cast<uint4*>(b) = *reinterpret_cast<const uint4*>(&Bs[c][tx * 4]);
-      *reinterpret_cast<uint4*>(b + 4) = *reinterpret_cast<const uint4*>(&Bs[c][64 + tx * 4]);
+    for (int cc = 0; cc < OBW; ++cc) {
+      uint32_t a[8], bb[8];
+      *reinterpret_cast<uint4*>(a) = *reinterpret_cast<const uint4*>(&As[cc * OLD + ty * 4]);
+      *reinterpret_cast<uint4*>(a + 4) = *reinterpret_cast<const uint4*>(&As[cc * OLD + 64 + ty * 4]);
+      *reinterpret_cast<uint4*>(bb) = *reinterpret_cast<const uint4*>(&Bs[cc * OLD + tx * 4]);
+      *reinterpret_cast<uint4*>(bb + 4) = *reinterpret_cast<const uint4*>(&Bs[cc * OLD + 64 + tx * 4]);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] |= a[i] & b[j];
+        for (int j = 0; j < 8; ++j) acc[i][j] |= a[i] & bb[j];
     }
-    __syncthreads();
+    __syncthreads();  // stage b is read out before iteration b + 1 refills it
   }
+  cp_async_wait<0>();
   uint8_t* out = (z == 0) ? C : W + (int64_t)(z - 1) * m * n;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t gi = i0 + ((i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4));
     if (gi >= m) continue;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int64_t gj = j0 + ((j < 4) ? (tx * 4 + j) : (64 + tx * 4 + j - 4));
-      if (gj < n) out[gi * n + gj] = acc[i][j] ? 1 : 0;
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gj = j0 + h * 64 + tx * 4;  // four consecutive outputs
+      uint8_t* dst = out + gi * n + gj;
+      if (vec_out && gj + 4 <= n) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v |= (acc[i][h * 4 + j] ? 1u : 0u) << (8 * j);
+        *reinterpret_cast<uint32_t*>(dst) = v;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (gj + j < n) dst[j] = acc[i][h * 4 + j] ? 1 : 0;
+      }
     }
   }
 }
@@ -233,7 +269,12 @@ int run_orand(int64_t m, int64_t n, int64_t k, const uint8_t* A, const uint8_t* 
   {
     TraceScope tr(kTrOrAndLeaf, st);
     dim3 grid((unsigned)((n + OBN - 1) / OBN), (unsigned)((m + OBM - 1) / OBM), (unsigned)s);
-    orand_leaf_kernel<<<grid, 256, 0, st>>>(m, n, L.KW, PA, PB, C, part, words_per_slice > 0 ? words_per_slice : OBW);
+    static std::atomic<uint64_t> configured{0};
+    MMSR_TRY_STATUS(smem_limit_once(orand_leaf_kernel, kOrSmem, configured));
+    // 4-byte output stores need n % 4 == 0 and 4-byte aligned outputs
+    const bool vec_out = n % 4 == 0 && ((uintptr_t)C % 4 == 0) && (part == nullptr || (uintptr_t)part % 4 == 0);
+    orand_leaf_kernel<<<grid, 256, kOrSmem, st>>>(m, n, L.KW, PA, PB, C, part,
+                                                  words_per_slice > 0 ? words_per_slice : OBW, vec_out);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   if (s > 1) {
