@@ -124,33 +124,37 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float* __restrict
 }
 
 // B (k x n fp32, row-major) -> hiT, loT (n x ld bf16): transposed so both
-// MMA operands are K-major.  Tile: 64 k x 32 n through shared memory; the
-// blocks of one grid row walk the n-tiles with stride gridDim.y (the grid's
-// y extent is capped at 65535).
+// MMA operands are K-major.  Tile: 64 k x 64 n through shared memory (256-byte
+// row segments read, 128-byte row segments written); the blocks of one grid
+// row walk the n-tiles with stride gridDim.y.
 __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __restrict__ Bm,
                                                               int64_t k, int64_t n, int64_t ld,
                                                               __nv_bfloat16* __restrict__ hiT,
                                                               __nv_bfloat16* __restrict__ loT) {
-  __shared__ float tile[64][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  __shared__ float tile[64][65];
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t k0 = (int64_t)blockIdx.x * 64;
-  for (int64_t n0 = (int64_t)blockIdx.y * 32; n0 < n; n0 += (int64_t)gridDim.y * 32) {
+  for (int64_t n0 = (int64_t)blockIdx.y * 64; n0 < n; n0 += (int64_t)gridDim.y * 64) {
     __syncthreads();  // the previous n-tile's readers are done with `tile`
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int kk = ty + 8 * i;
+    for (int i = 0; i < 16; ++i) {
+      const int kk = ty + 4 * i;
       const int64_t gk = k0 + kk, gn = n0 + tx;
       tile[kk][tx] = (gk < k && gn < n) ? __ldcs(Bm + gk * n + gn) : 0.f;
     }
     __syncthreads();
-    const int row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
-    const int64_t gn = n0 + row;
-    if (gn < n) {
-      __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], h[e], l[e]);
-      *reinterpret_cast<uint4*>(hiT + gn * ld + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(h);
-      *reinterpret_cast<uint4*>(loT + gn * ld + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(l);
+    for (int h = 0; h < 2; ++h) {
+      const int item = threadIdx.x + 256 * h;
+      const int row = item >> 3, chunk = item & 7;
+      const int64_t gn = n0 + row;
+      if (gn < n) {
+        __align__(16) __nv_bfloat16 hv[8], lv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], hv[e], lv[e]);
+        *reinterpret_cast<uint4*>(hiT + gn * ld + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(hv);
+        *reinterpret_cast<uint4*>(loT + gn * ld + k0 + chunk * 8) = *reinterpret_cast<const uint4*>(lv);
+      }
     }
   }
 }
@@ -558,7 +562,7 @@ cudaError_t launch_split_bf16(const float* A, const float* B, int64_t m, int64_t
   if (blocks < 1) blocks = 1;
   split_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, Kp, ahi, alo, vec);
   // a few thousand blocks, each walking several n-tiles
-  const int64_t tiles_n = (n + 31) / 32;
+  const int64_t tiles_n = (n + 63) / 64;
   const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 4096 / (Kp / 64))));
   dim3 g((unsigned)(Kp / 64), (unsigned)std::min<int64_t>(gy, kMaxGridY));
   split_transpose_kernel<<<g, 256, 0, st>>>(B, k, n, Kp, bhi, blo);
