@@ -19,14 +19,17 @@ GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "go
 
 
 # ----------------------------------------------------------------- (+,x) FP64
-def test_f64_identity_and_zero_exact():
+# Each pin is a function of the implementation under test (the oracle by
+# default), so that tests/test_oracle_mutations.py can show that planted
+# mistakes fail them.
+def pin_f64_identity_and_zero(mm=oracle.mm_f64):
     A, B = inputs.uniform_f64(7, 5, 9, seed=11)
-    np.testing.assert_array_equal(oracle.mm_f64(A, np.eye(5)), A)
-    np.testing.assert_array_equal(oracle.mm_f64(np.eye(9)[:7, :7], A), A)
-    np.testing.assert_array_equal(oracle.mm_f64(A, np.zeros((5, 3))), np.zeros((7, 3)))
+    np.testing.assert_array_equal(mm(A, np.eye(5)), A)
+    np.testing.assert_array_equal(mm(np.eye(9)[:7, :7], A), A)
+    np.testing.assert_array_equal(mm(A, np.zeros((5, 3))), np.zeros((7, 3)))
 
 
-def test_f64_rank1_closed_form_nonsquare():
+def pin_f64_rank1_closed_form(mm=oracle.mm_f64):
     # (u v^T)(w x^T) = (v . w) u x^T ; distinct m, k, n catch a transposed operand.
     rng = np.random.default_rng(3)
     u, v = rng.integers(-9, 10, 6), rng.integers(-9, 10, 4)
@@ -34,14 +37,14 @@ def test_f64_rank1_closed_form_nonsquare():
     A = np.outer(u, v).astype(np.float64)
     B = np.outer(w, x).astype(np.float64)
     expect = float(np.dot(v, w)) * np.outer(u, x).astype(np.float64)
-    np.testing.assert_array_equal(oracle.mm_f64(A, B), expect)
+    np.testing.assert_array_equal(mm(A, B), expect)
 
 
-def test_f64_exact_rational_error_bound():
+def pin_f64_exact_rational_error_bound(mm=oracle.mm_f64):
     # Exact rational sum of exact rational products; the oracle must sit
     # within the classical recursive-summation bound gamma_k * sum|a||b|.
     A, B = inputs.uniform_f64(5, 37, 6, seed=4)
-    C = oracle.mm_f64(A, B)
+    C = mm(A, B)
     u = 2.0 ** -53
     g = 37 * u / (1 - 37 * u)
     for i in range(5):
@@ -49,6 +52,18 @@ def test_f64_exact_rational_error_bound():
             exact = sum(Fraction(A[i, t]) * Fraction(B[t, j]) for t in range(37))
             bound = g * sum(abs(A[i, t] * B[t, j]) for t in range(37))
             assert abs(Fraction(C[i, j]) - exact) <= Fraction(bound)
+
+
+def test_f64_identity_and_zero_exact():
+    pin_f64_identity_and_zero()
+
+
+def test_f64_rank1_closed_form_nonsquare():
+    pin_f64_rank1_closed_form()
+
+
+def test_f64_exact_rational_error_bound():
+    pin_f64_exact_rational_error_bound()
 
 
 def test_f64_ascending_order_bitwise():
@@ -156,35 +171,47 @@ def _tropical_identity(n):
     return E
 
 
-def test_minplus_identity_and_zero():
+def pin_minplus_identity_and_zero(mm=oracle.mm_minplus):
     A, _ = inputs.tropical_i32(9, 6, 1, seed=13)
-    np.testing.assert_array_equal(oracle.mm_minplus(A, _tropical_identity(6)), A)
-    np.testing.assert_array_equal(oracle.mm_minplus(_tropical_identity(9), A), A)
+    np.testing.assert_array_equal(mm(A, _tropical_identity(6)), A)
+    np.testing.assert_array_equal(mm(_tropical_identity(9), A), A)
     Z = np.full((6, 4), INF, dtype=np.int32)
-    np.testing.assert_array_equal(oracle.mm_minplus(A, Z), np.full((9, 4), INF, dtype=np.int32))
+    np.testing.assert_array_equal(mm(A, Z), np.full((9, 4), INF, dtype=np.int32))
 
 
-def test_minplus_sentinel_saturates_without_wrap():
+def pin_minplus_sentinel_saturates_without_wrap(mm=oracle.mm_minplus):
     A = np.full((3, 4), INF, dtype=np.int32)
     B = np.full((4, 5), INF, dtype=np.int32)
-    np.testing.assert_array_equal(oracle.mm_minplus(A, B), np.full((3, 5), INF, dtype=np.int32))
+    np.testing.assert_array_equal(mm(A, B), np.full((3, 5), INF, dtype=np.int32))
     A[1, 2] = 7
     B[2, 3] = INF - 3  # finite sum 2^30 + 4 clamps to the sentinel
-    C = oracle.mm_minplus(A, B)
+    C = mm(A, B)
     assert C[1, 3] == INF
 
 
-def test_minplus_two_hop_paths_enumerated():
+def pin_minplus_two_hop_paths_enumerated(mm=oracle.mm_minplus):
     # (D (x) D)[i][j] is the cheapest walk of exactly two edges (with the 0
     # diagonal, at most two): enumerate every walk explicitly.
     D = inputs.graph_minplus(5, seed=14, density=0.5, hi=20)
-    C = oracle.mm_minplus(D, D)
+    C = mm(D, D)
     for i, j in itertools.product(range(5), repeat=2):
         best = INF
         for v in range(5):
             if D[i, v] < INF and D[v, j] < INF:
                 best = min(best, int(D[i, v]) + int(D[v, j]))
         assert C[i, j] == best
+
+
+def test_minplus_identity_and_zero():
+    pin_minplus_identity_and_zero()
+
+
+def test_minplus_sentinel_saturates_without_wrap():
+    pin_minplus_sentinel_saturates_without_wrap()
+
+
+def test_minplus_two_hop_paths_enumerated():
+    pin_minplus_two_hop_paths_enumerated()
 
 
 def test_minplus_squaring_equals_floyd_warshall_and_scipy():
@@ -226,12 +253,16 @@ def test_minplus_k_zero_gives_sentinel():
 
 
 # ------------------------------------------------------------------- boolean
-def test_orand_exhaustive_2x2():
+def pin_orand_exhaustive_2x2(mm=oracle.mm_orand):
     mats = [np.array(bits, dtype=np.uint8).reshape(2, 2) for bits in itertools.product((0, 1), repeat=4)]
     for A in mats:
         for B in mats:
             ref = ((A.astype(np.int64) @ B.astype(np.int64)) > 0).astype(np.uint8)
-            np.testing.assert_array_equal(oracle.mm_orand(A, B), ref)
+            np.testing.assert_array_equal(mm(A, B), ref)
+
+
+def test_orand_exhaustive_2x2():
+    pin_orand_exhaustive_2x2()
 
 
 def test_orand_closure_equals_reachability():
