@@ -1,0 +1,65 @@
+"""Host-side pieces of the benchmark, on the CPU: the committed DRAM-traffic
+record is used only while the kernel's sources still hash to the captured
+value, and the clock sampler's parser reports the median SM clock and every
+throttle reason it saw."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_committed_leaf_traffic_matches_current_sources():
+    files = ["minplus.cu", "minplus_tile.cuh"]
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)["minplus16_leaf_n4096"]
+    if rec["source_sha"] == bench.source_sha(files):
+        assert bench.ncu_traffic(files, "minplus16_leaf_n4096") == rec["dram_bytes_per_launch"]
+    else:  # the leaf changed after the capture: the bench must report no traffic
+        assert bench.ncu_traffic(files, "minplus16_leaf_n4096") is None
+
+
+def test_traffic_dropped_when_sources_change(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1911_05328_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cu").write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.source_sha(["k.cu"])
+    (tmp_path / "profiles" / "traffic.json").write_text(
+        json.dumps({"k_case": {"source_sha": sha, "dram_bytes_per_launch": 1234}}))
+    assert bench.ncu_traffic(["k.cu"], "k_case") == 1234
+    (csrc / "k.cu").write_text("kernel v2")
+    assert bench.ncu_traffic(["k.cu"], "k_case") is None
+    assert bench.ncu_traffic(["k.cu"], "missing_case") is None
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_parser(tmp_path):
+    path = tmp_path / "clocks.csv"
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+        "0, 1500, 2070, 1200.0, 0x8, Active, Not Active, Not Active, Not Active",
+    ]
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.path = str(path)
+    s.f = open(s.path, "w")
+    s.f.write("\n".join(rows) + "\n")
+    s.p = _Done()
+    out = s.stop()
+    assert out["samples"] == 4
+    assert out["sm_mhz"] == 2025.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert not os.path.exists(s.path)
