@@ -201,3 +201,17 @@ def test_option_argument_checks(lib):
         assert mmsr.mm_set_option(opt, 2, check=False) == mmsr.MM_ERR_ARG
     assert mmsr.mm_set_option(mmsr.MM_OPT_TEST_SKIP_SIGNAL, 4, check=False) == mmsr.MM_ERR_ARG
     assert mmsr.mm_set_option(mmsr.MM_OPT_TEST_SKIP_SIGNAL, -1, check=False) == mmsr.MM_ERR_ARG
+
+
+def test_noalloc_host_checks(lib):
+    """The allocation-free (min,+) entry point checks its arguments and the
+    size of its static scratch before any device call."""
+    f = mmsr.mm_minplus_noalloc
+    assert f(4, 4, 4, FAKE, FAKE, FAKE, 0, stream=0, check=False) == mmsr.MM_ERR_ARG  # split_k < 1
+    assert f(-1, 4, 4, FAKE, FAKE, FAKE, 1, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert f(4, 4, 4, None, FAKE, FAKE, 1, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert f(4, 4, 4, FAKE + 4, FAKE, FAKE, 1, stream=0, check=False) == mmsr.MM_ERR_ALIGN
+    assert f(4, 4, (1 << 22) + 1, FAKE, FAKE, FAKE, 1, stream=0, check=False) == mmsr.MM_ERR_SHAPE
+    assert f(0, 4, 4, None, None, None, 1, stream=0, check=False) == mmsr.MM_OK
+    # s = 3 needs 2 partial slices of 4096 x 4096 int32 = 128 MiB > the 64 MiB scratch
+    assert f(4096, 4096, 4096, FAKE, FAKE, FAKE, 3, stream=0, check=False) == mmsr.MM_ERR_WORKSPACE
