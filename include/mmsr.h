@@ -98,6 +98,13 @@ typedef struct {
  *   workspace_bytes  budget, see the conventions above
  *   stream           cudaStream_t
  * Returns MM_OK or a negative mm_status_t.
+ * (min,+) calls keep a small verdict record (whether the inputs fit the
+ * exact 16-bit path) in library device memory.  Calls made outside stream
+ * capture reuse 4096 records round-robin; each captured call owns a record
+ * of its own, so a graph's replays never share one with other calls, but
+ * two replays of one graph (like any two calls given one workspace) must
+ * not overlap on the GPU.  After 4096 captured (min,+) calls in a process,
+ * later captures run the 32-bit leaf (same results, about half the rate).
  */
 int mm_semiring(int semiring, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
                 void* C, void* workspace, size_t workspace_bytes, void* stream);
@@ -324,9 +331,8 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   product whose tiles fill fewer than four waves run in the zero-workspace
  *   k-parallel form (TAR-MM, Fig. tar-mm: register tiles merged into C by an
  *   atomic min); 0 disables it.  Results are identical.
- *   MM_OPT_TC_PAIR: 1 runs the FP32-mode tensor-core leaf as clusters of two
- *   CTAs that share (multicast) each B tile when the product has at least two
- *   tile rows; 0 (default) runs independent CTAs.  Results are identical.
+ *   Option 3 is retired (it selected a CTA-pair variant of the FP32-mode
+ *   leaf that is no longer built) and returns MM_ERR_ARG.
  *   MM_OPT_STRASSEN_TOP_F64: FP32-mode Strassen with levels >= 3 sums its
  *   top-level post-additions wider than FP32.  0 (default): an error-free
  *   double-float sum on the FP32 units (Sum2 of Ogita, Rump and Oishi); 1:
@@ -344,7 +350,6 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
 typedef enum {
   MM_OPT_MINPLUS_PACKED = 1,
   MM_OPT_MINPLUS_STREAMK = 2,
-  MM_OPT_TC_PAIR = 3,
   MM_OPT_STRASSEN_TOP_F64 = 4,
   MM_OPT_TEST_SKIP_SIGNAL = 5
 } mm_option_t;

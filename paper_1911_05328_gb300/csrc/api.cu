@@ -18,6 +18,20 @@
 
 namespace mmsr {
 
+int num_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);  // racing stores write the same value
+  return sms;
+}
+
 static int acc_bytes(int sr) {
   switch (sr) {
     case MM_SR_PLUS_TIMES_F64: return 8;
@@ -288,10 +302,6 @@ int mm_set_option(int option, int value) {
     case MM_OPT_MINPLUS_STREAMK:
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_streamk_mode = value;
-      return MM_OK;
-    case MM_OPT_TC_PAIR:
-      if (value != 0 && value != 1) return MM_ERR_ARG;
-      g_tc_pair_mode = value;
       return MM_OK;
     case MM_OPT_STRASSEN_TOP_F64:
       if (value != 0 && value != 1) return MM_ERR_ARG;

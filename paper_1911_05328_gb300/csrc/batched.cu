@@ -581,9 +581,7 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&tb_lo, blo, rb, kp, kp, TBN, true, TBK));
   static std::atomic<uint64_t> configured{0};
   MMSR_TRY_STATUS(smem_limit_once(batched_kernel, BSMEM, configured));
-  int dev = 0, sms = kNumSMs;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = num_sms();
   if (P.T.total_tiles > 0) {
     TraceScope tr(kTrBatched, st);
     const int grid = std::min(sms, P.T.total_tiles);

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) closure_diff_kernel(const uint8_t* __rest
 
 unsigned stream_grid(int64_t work) {
   int64_t b = (work + 255) / 256;
-  const int64_t cap = (int64_t)kNumSMs * 8;
+  const int64_t cap = (int64_t)num_sms() * 8;
   if (b > cap) b = cap;
   return (unsigned)(b < 1 ? 1 : b);
 }

@@ -13,7 +13,10 @@ namespace mmsr {
 
 constexpr int kInf = 1 << 30;  // +infinity of the (min,+) semiring on [0, 2^30]
 constexpr int64_t kMaxGridY = 65535;  // grid y / z extent limit; larger extents loop in-kernel
-constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (queried at run time where it matters)
+// Streaming multiprocessors of the current device, queried once per device
+// and cached; grid sizes are multiples of it.  Returns 1 when no device
+// answers (a launch would then fail on its own).
+int num_sms();
 
 #define MMSR_CUDA_TRY(expr)                                   \
   do {                                                        \
@@ -98,7 +101,6 @@ cudaError_t launch_min_reduce(int64_t count, int32_t* C, const int32_t* W, int p
 int minplus_tile_k();
 extern int g_packed_mode;  // mm_set_option(MM_OPT_MINPLUS_PACKED, ...)
 extern int g_streamk_mode;  // mm_set_option(MM_OPT_MINPLUS_STREAMK, ...)
-extern int g_tc_pair_mode;  // mm_set_option(MM_OPT_TC_PAIR, ...)
 extern int g_strassen_top_f64;  // mm_set_option(MM_OPT_STRASSEN_TOP_F64, ...)
 
 // FP64 DFMA leaf, same slicing contract with FP64 partials.

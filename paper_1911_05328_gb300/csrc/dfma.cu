@@ -235,11 +235,11 @@ cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, c
                    (W == nullptr || aligned16(W));
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
   TraceScope tr(kTrDfmaLeaf, st);
-  if ((int64_t)grid.x * grid.y * s < 2 * kNumSMs) {
+  if ((int64_t)grid.x * grid.y * s < 2 * (int64_t)num_sms()) {
     // too few 64 x 64 tiles to occupy the GPU: 16 x 16 tiles, or 8 x 8 when
     // 16 x 16 tiles would still leave fewer than four CTAs per SM
     const int64_t tiles16 = ((n + 15) / 16) * ((m + 15) / 16) * s;
-    if (tiles16 < 4 * (int64_t)kNumSMs) {
+    if (tiles16 < 4 * (int64_t)num_sms()) {
       dim3 sg((unsigned)((n + 7) / 8), (unsigned)((m + 7) / 8), (unsigned)s);
       dfma_small_kernel<8><<<sg, 64, 0, st>>>(m, n, k, A, B, C, W, kb_per_slice);
     } else {
@@ -279,7 +279,7 @@ cudaError_t launch_sum_reduce_f64(int64_t count, double* C, const double* W, int
   const bool vec = aligned16(C) && aligned16(W) && (count % 2 == 0);
   const int64_t work = vec ? count / 2 : count;
   int64_t blocks = (work + 255) / 256;
-  const int64_t cap = (int64_t)kNumSMs * 8;
+  const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   TraceScope tr(kTrSumReduceF64, st);

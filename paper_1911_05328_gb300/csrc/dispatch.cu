@@ -1,5 +1,6 @@
-// stubs.cu -- dispatch of the semirings served by the tensor-core and
-// boolean engines, plus engines not built yet (MM_ERR_UNSUPPORTED).
+// dispatch.cu -- routes mm_semiring's plan and run to the engines of the
+// tensor-core semirings (FP32 bf16x3, FP64-accuracy) and the boolean
+// semiring, and gathers the device status words of the bounded waits.
 #include <string.h>
 
 #include "internal.h"

@@ -35,7 +35,13 @@ using namespace mp;
 // 32767 therefore means +inf and maps back to 2^30.  One __viaddmin_u16x2
 // computes two outputs, twice the 32-bit rate.  A range scan decides the path
 // on the device (no host round trip); the loser kernel exits at once.
-constexpr int kPackSlots = 4096;
+// Slots 0 .. kEagerSlots-1 are reused round-robin by calls made outside
+// stream capture; each captured call gets a slot of its own from the rest,
+// never reused, so a replayed graph cannot share its slot with a later eager
+// call (replays of one graph still share theirs, like their workspace).
+// Once the captured slots run out, captured calls take the 32-bit leaf.
+constexpr int kEagerSlots = 4096, kCapturedSlots = 4096;
+constexpr int kPackSlots = kEagerSlots + kCapturedSlots;
 
 struct PackSlot {
   int viol;
@@ -214,13 +220,22 @@ cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* 
   int slot = -1;
   if (g_packed_mode && k > 0) {
     // the packed tile and the 32-bit tile split k into the same 32-wide blocks
-    static std::atomic<unsigned> counter{0};
-    slot = (int)(counter.fetch_add(1u) % (unsigned)kPackSlots);
+    static std::atomic<unsigned> eager{0}, captured{0};
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MMSR_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      slot = (int)(eager.fetch_add(1u) % (unsigned)kEagerSlots);
+    } else {
+      const unsigned c = captured.fetch_add(1u);
+      slot = c < (unsigned)kCapturedSlots ? kEagerSlots + (int)c : -1;
+    }
+  }
+  if (slot >= 0) {
     {
       TraceScope tr(kTrRangeScan, st);
       const bool svec = aligned16(A) && aligned16(B) && ((m * k) % 4 == 0) && ((k * n) % 4 == 0);
       int64_t blocks = ((m * k + k * n) / (svec ? 4 : 1) + 255) / 256;
-      if (blocks > (int64_t)kNumSMs * 8) blocks = (int64_t)kNumSMs * 8;
+      if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
       if (blocks < 1) blocks = 1;
       range_scan_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m * k, B, k * n, slot, svec);
       MMSR_CUDA_TRY(cudaGetLastError());
@@ -231,16 +246,15 @@ cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* 
     static std::atomic<int> resident_cache{0};
     int resident = resident_cache.load(std::memory_order_relaxed);
     if (!resident) {
-      int dev = 0, sms = kNumSMs, per_sm = 2;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      int per_sm = 2;
+      const int sms = num_sms();
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, minplus16_streamk_kernel, PTHREADS, PSMEM_BYTES);
       resident = sms * (per_sm > 0 ? per_sm : 1);
       resident_cache.store(resident, std::memory_order_relaxed);
     }
     if (s == 1 && g_streamk_mode && tiles_m * tiles_n < 4 * (int64_t)resident) {
       TraceScope tr(kTrMinplus16Leaf, st);
-      fill_inf_kernel<<<(unsigned)(kNumSMs * 4), 256, 0, st>>>(C, m * n, slot);
+      fill_inf_kernel<<<(unsigned)(num_sms() * 4), 256, 0, st>>>(C, m * n, slot);
       const int64_t nsub = (k + PBK - 1) / PBK;
       minplus16_streamk_kernel<<<(unsigned)resident, PTHREADS, PSMEM_BYTES, st>>>(
           m, n, k, A, B, C, vec, slot, tiles_m * tiles_n * nsub, nsub, tiles_n);
@@ -266,7 +280,7 @@ cudaError_t launch_min_reduce(int64_t count, int32_t* C, const int32_t* W, int p
   const bool vec = aligned16(C) && aligned16(W) && (count % 4 == 0);
   const int64_t work = vec ? count / 4 : count;
   int64_t blocks = (work + 255) / 256;
-  const int64_t cap = (int64_t)kNumSMs * 8;
+  const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   TraceScope tr(kTrMinReduce, st);

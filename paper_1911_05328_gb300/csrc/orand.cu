@@ -203,7 +203,7 @@ int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 unsigned grid_for(int64_t work) {
   int64_t b = (work + 255) / 256;
-  if (b > (int64_t)kNumSMs * 16) b = (int64_t)kNumSMs * 16;
+  if (b > (int64_t)num_sms() * 16) b = (int64_t)num_sms() * 16;
   return (unsigned)(b < 1 ? 1 : b);
 }
 

@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(256) post_combine2_kernel(const TP* __restrict
 // `threads`-thread blocks: about one full wave of the GPU in total.
 unsigned rows_grid(int64_t h, int64_t R, int threads) {
   const int64_t per_sm = 2048 / threads < 32 ? 2048 / threads : 32;
-  int64_t b = ((int64_t)kNumSMs * per_sm + R - 1) / R;
+  int64_t b = ((int64_t)num_sms() * per_sm + R - 1) / R;
   if (b > h) b = h;
   return (unsigned)(b < 1 ? 1 : b);
 }

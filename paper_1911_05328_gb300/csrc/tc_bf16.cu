@@ -27,10 +27,6 @@ __device__ int g_tc_status;  // device status word of this translation unit
 __device__ int g_tc_skip_signal;
 }
 
-// CTA pairs multicasting B: correct but measured no faster here (the ring's
-// latency, not operand bandwidth, limited the kernel), so off by default.
-int g_tc_pair_mode = 0;
-
 // ------------------------------------------------------------ tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -188,16 +184,12 @@ struct Bf16x3Cfg {
   static constexpr int COLS_PER_WARP = BN / 2;   // two drain warps share each lane quarter
 };
 
-// MC: the kernel runs as clusters of two CTAs stacked along M that share one
-// B tile -- each CTA loads half of it and multicasts the half into both CTAs'
-// shared memory, so a CTA pair fetches B once instead of twice; each stage is
-// released by MMA-completion arrivals from both CTAs.
 // QUAD epilogue: instead of writing its tile to C, batch entry b adds
 // sign[b][d] x tile into up to four destinations dst[b][d] (row pitch ld),
 // overwriting where add[b][d] is 0 -- the leaf epilogue of a Strassen level
 // whose products go straight into the quadrants of C (no product
 // temporaries).  Entries of one launch must write disjoint destinations.
-template <int BN, int STAGES, int CHUNK, bool MC, bool QUAD>
+template <int BN, int STAGES, int CHUNK, bool QUAD>
 __global__ void __launch_bounds__(kTcThreads, 1)
     bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAhi, const __grid_constant__ CUtensorMap tAlo,
                        const __grid_constant__ CUtensorMap tBhi, const __grid_constant__ CUtensorMap tBlo,
@@ -223,17 +215,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // column by column, so a wave shares its A and B panels through L2 instead
   // of streaming all of B once per band of rows.
   int64_t i0, j0;
-  const uint32_t rank = MC ? tc::cluster_ctarank() : 0u;  // position of this CTA in its pair
   {
-    // the unit of rasterisation is a CTA pair under MC, a CTA otherwise
-    const int per = MC ? 2 : 1;
-    const int tiles_n = gridDim.x, units_m = gridDim.y / per, band_h = kGroupM / per;
-    const int pid = (blockIdx.y / per) * tiles_n + blockIdx.x;
+    const int tiles_n = gridDim.x, units_m = gridDim.y, band_h = kGroupM;
+    const int pid = blockIdx.y * tiles_n + blockIdx.x;
     const int band = pid / (band_h * tiles_n);
     const int first_m = band * band_h;
     const int rows = min(band_h, units_m - first_m);
     const int in_band = pid - band * band_h * tiles_n;
-    i0 = (int64_t)((first_m + in_band % rows) * per + (int)rank) * BM;
+    i0 = (int64_t)(first_m + in_band % rows) * BM;
     j0 = (int64_t)(in_band / rows) * BN;
   }
   // blockIdx.z = batch * slices + k-slice; a batch is one independent product
@@ -249,7 +238,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], MC ? 2 : 1);
+      tc::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
@@ -264,7 +253,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (MC) tc::cluster_sync();  // the peer's barriers exist before any multicast lands
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
@@ -287,28 +275,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int kx = (kb_begin + it) * Cfg::KB;
         tc::tma_load_2d(st, &tAhi, &full[s], kx, ya);
         tc::tma_load_2d(st + Cfg::A_BYTES, &tAlo, &full[s], kx, ya);
-        if (MC) {
-          // this CTA's half of the B tile, into both CTAs of the pair
-          const uint32_t hb = Cfg::B_BYTES / 2;
-          const int yh = yb + (int)rank * (BN / 2);
-          tc::tma_load_2d_mc(st + 2 * Cfg::A_BYTES + rank * hb, &tBhi, &full[s], kx, yh, (uint16_t)3);
-          tc::tma_load_2d_mc(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES + rank * hb, &tBlo, &full[s], kx, yh,
-                             (uint16_t)3);
-        } else {
-          tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, yb);
-          tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, yb);
-        }
+        tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, yb);
+        tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, yb);
       }
       prod_state[0] = issued;
       prod_state[1] = skipped ? 1 : 0;
-      if (MC) {
-        // wait until both CTAs have released the last stages, so no arrival
-        // from the peer is still in flight towards this CTA when it exits
-        for (int it = max(nkb, STAGES); it < nkb + STAGES; ++it) {
-          const int s = it % STAGES;
-          if (!tc::mbar_wait(&empty[s], ((uint32_t)(it / STAGES) - 1) & 1u, abort_flag, &g_tc_status)) break;
-        }
-      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -337,10 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc::mma_f16(d, ahi, blo, idesc, 1);
             tc::mma_f16(d, alo, bhi, idesc, 1);
           }
-          if (MC)
-            tc::mma_commit_mc(&empty[s], (uint16_t)3);  // releases the stage in both CTAs
-          else
-            tc::mma_commit(&empty[s]);
+          tc::mma_commit(&empty[s]);
         }
         if (aborted) break;  // no chunk signal: the drain must not read a partial chunk
         tc::mma_commit(&acc_full[b]);
@@ -453,7 +421,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     __syncwarp();
   }
-  if (MC) tc::cluster_sync();  // neither CTA leaves while the pair still shares smem traffic
   if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, Cfg::TMEM_COLS);
@@ -488,44 +455,24 @@ cudaError_t launch_gemm(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const 
                         const CUtensorMap& b_lo, float* C, float* W, int64_t m, int64_t n,
                         int kb_total, int kbs, int s, cudaStream_t st, int batches = 1,
                         int64_t a_batch_rows = 0, int64_t b_batch_rows = 0,
-                        int64_t c_batch_stride = 0, bool pair = false, const QuadOut* quad = nullptr) {
+                        int64_t c_batch_stride = 0, const QuadOut* quad = nullptr) {
   QuadOut qo;
   if (quad) qo = *quad; else memset(&qo, 0, sizeof(qo));
   using Cfg = Bf16x3Cfg<BN, STAGES>;
-  static std::atomic<uint64_t> conf_plain{0}, conf_pair{0}, conf_quad{0};
-  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, false>, Cfg::SMEM, conf_plain));
-  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, true, false>, Cfg::SMEM, conf_pair));
-  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, true>, Cfg::SMEM, conf_quad));
+  static std::atomic<uint64_t> conf_plain{0}, conf_quad{0};
+  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, false>, Cfg::SMEM, conf_plain));
+  MMSR_CUDA_TRY(smem_limit_once(bf16x3_gemm_kernel<BN, STAGES, CHUNK, true>, Cfg::SMEM, conf_quad));
   const bool q = qo.entries > 0;
-  if (q) pair = false;  // the quadrant epilogue runs on independent CTAs
   const unsigned tiles_m = (unsigned)((m + BM - 1) / BM), tiles_n = (unsigned)((n + BN - 1) / BN);
   TraceScope tr(kTrTcBf16x3, st);
-  if (!pair) {
-    dim3 grid(tiles_n, tiles_m, (unsigned)(s * batches));
-    if (q)
-      bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, true><<<grid, kTcThreads, Cfg::SMEM, st>>>(
-          a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
-    else
-      bf16x3_gemm_kernel<BN, STAGES, CHUNK, false, false><<<grid, kTcThreads, Cfg::SMEM, st>>>(
-          a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
-    return cudaGetLastError();
-  }
-  // pairs along M: an odd tile-row count gets one idle partner row, whose
-  // A rows lie past m (zero-filled by TMA, outputs discarded)
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(tiles_n, (tiles_m + 1) & ~1u, (unsigned)(s * batches));
-  cfg.blockDim = dim3(kTcThreads, 1, 1);
-  cfg.dynamicSmemBytes = Cfg::SMEM;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1;
-  attr[0].val.clusterDim.y = 2;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, bf16x3_gemm_kernel<BN, STAGES, CHUNK, true, false>, a_hi, a_lo, b_hi, b_lo, C, W,
-                            m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
+  dim3 grid(tiles_n, tiles_m, (unsigned)(s * batches));
+  if (q)
+    bf16x3_gemm_kernel<BN, STAGES, CHUNK, true><<<grid, kTcThreads, Cfg::SMEM, st>>>(
+        a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
+  else
+    bf16x3_gemm_kernel<BN, STAGES, CHUNK, false><<<grid, kTcThreads, Cfg::SMEM, st>>>(
+        a_hi, a_lo, b_hi, b_lo, C, W, m, n, kb_total, kbs, s, a_batch_rows, b_batch_rows, c_batch_stride, qo);
+  return cudaGetLastError();
 }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -558,7 +505,7 @@ cudaError_t launch_split_bf16(const float* A, const float* B, int64_t m, int64_t
   TraceScope tr(kTrSplitBf16, st);
   const bool vec = (k % 4 == 0) && aligned16(A);
   int64_t blocks = (m * (Kp / 8) + 255) / 256;
-  if (blocks > (int64_t)kNumSMs * 16) blocks = (int64_t)kNumSMs * 16;
+  if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
   if (blocks < 1) blocks = 1;
   split_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, Kp, ahi, alo, vec);
   // a few thousand blocks, each walking several n-tiles
@@ -579,12 +526,11 @@ cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16*
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
   MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_hi, ahi, batches * m, Kp, Kp, BM, true, kTcBK));
   MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_lo, alo, batches * m, Kp, Kp, BM, true, kTcBK));
-  const bool pair = g_tc_pair_mode && m > BM;
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_hi, bhi, batches * n, Kp, Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK));
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, batches * n, Kp, Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_hi, bhi, batches * n, Kp, Kp, kTcBN, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, batches * n, Kp, Kp, kTcBN, true, kTcBK));
   const int kb_total = (int)(Kp / kTcBK);
   return launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, P, nullptr, m, n,
-                                                 kb_total, kb_total, 1, st, batches, m, n, m * n, pair, quad);
+                                                 kb_total, kb_total, 1, st, batches, m, n, m * n, quad);
 }
 
 int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
@@ -623,22 +569,20 @@ int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, flo
   cudaError_t e = launch_split_bf16(A, B, m, n, k, L.Kp, ahi, alo, bhi, blo, st);
   if (e != cudaSuccess) return MM_ERR_CUDA;
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-  const bool pair = g_tc_pair_mode && m > BM;
   if (make_tmap_2d_16bit(&ta_hi, ahi, m, L.Kp, L.Kp, BM, true, kTcBK) != cudaSuccess ||
       make_tmap_2d_16bit(&ta_lo, alo, m, L.Kp, L.Kp, BM, true, kTcBK) != cudaSuccess ||
-      make_tmap_2d_16bit(&tb_hi, bhi, n, L.Kp, L.Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK) != cudaSuccess ||
-      make_tmap_2d_16bit(&tb_lo, blo, n, L.Kp, L.Kp, pair ? kTcBN / 2 : kTcBN, true, kTcBK) != cudaSuccess)
+      make_tmap_2d_16bit(&tb_hi, bhi, n, L.Kp, L.Kp, kTcBN, true, kTcBK) != cudaSuccess ||
+      make_tmap_2d_16bit(&tb_lo, blo, n, L.Kp, L.Kp, kTcBN, true, kTcBK) != cudaSuccess)
     return MM_ERR_CUDA;
   const int kb_total = (int)(L.Kp / kTcBK);
   const int s = p.split_k;
   const int kbs = (kb_total + s - 1) / s;
-  e = launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, C, part, m, n, kb_total, kbs, s, st,
-                                              1, 0, 0, 0, pair);
+  e = launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, C, part, m, n, kb_total, kbs, s, st);
   if (e == cudaSuccess && s > 1) {
     TraceScope tr(kTrSumReduceF32, st);
     const bool vec = aligned16(C) && aligned16(part) && (m * n) % 4 == 0;
     int64_t blocks = ((vec ? m * n / 4 : m * n) + 255) / 256;
-    if (blocks > (int64_t)kNumSMs * 8) blocks = (int64_t)kNumSMs * 8;
+    if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
     sum_reduce_f32_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(m * n, C, part, s - 1, vec);
     e = cudaGetLastError();
   }

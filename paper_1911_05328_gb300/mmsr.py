@@ -27,7 +27,6 @@ MM_STRASSEN_WINOGRAD = 1
 
 MM_OPT_MINPLUS_PACKED = 1
 MM_OPT_MINPLUS_STREAMK = 2
-MM_OPT_TC_PAIR = 3
 MM_OPT_STRASSEN_TOP_F64 = 4
 MM_OPT_TEST_SKIP_SIGNAL = 5
 

@@ -196,9 +196,11 @@ def test_tar_strassen_argument_checks_and_workspace(lib):
 def test_option_argument_checks(lib):
     """Out-of-range options and values are refused on the host (no device call)."""
     assert mmsr.mm_set_option(99, 0, check=False) == mmsr.MM_ERR_ARG
-    for opt in (mmsr.MM_OPT_MINPLUS_PACKED, mmsr.MM_OPT_MINPLUS_STREAMK, mmsr.MM_OPT_TC_PAIR,
-                mmsr.MM_OPT_STRASSEN_TOP_F64):
+    for opt in (mmsr.MM_OPT_MINPLUS_PACKED, mmsr.MM_OPT_MINPLUS_STREAMK, mmsr.MM_OPT_STRASSEN_TOP_F64):
         assert mmsr.mm_set_option(opt, 2, check=False) == mmsr.MM_ERR_ARG
+    # option 3 is retired: every value is refused
+    for v in (0, 1):
+        assert mmsr.mm_set_option(3, v, check=False) == mmsr.MM_ERR_ARG
     assert mmsr.mm_set_option(mmsr.MM_OPT_TEST_SKIP_SIGNAL, 4, check=False) == mmsr.MM_ERR_ARG
     assert mmsr.mm_set_option(mmsr.MM_OPT_TEST_SKIP_SIGNAL, -1, check=False) == mmsr.MM_ERR_ARG
 

@@ -14,13 +14,6 @@ SR = mmsr.MM_SR_PLUS_TIMES_F32
 TOL = 1e-5
 
 
-@pytest.fixture(params=[1, 0], ids=["cta-pairs", "single-ctas"])
-def pair(request):
-    mmsr.mm_set_option(mmsr.MM_OPT_TC_PAIR, request.param)
-    yield request.param
-    mmsr.mm_set_option(mmsr.MM_OPT_TC_PAIR, 0)
-
-
 def run(A, B, extra_parts=0):
     import torch
 
@@ -44,20 +37,20 @@ def test_tiny_integer_tile_exact():
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (128, 256, 64), (129, 257, 65), (300, 200, 1000), (256, 512, 2048),
                                    (389, 300, 500)])
-def test_integer_inputs_exact(m, n, k, pair):
+def test_integer_inputs_exact(m, n, k):
     A, B = inputs.small_int(m, k, n, seed=m + n + k, bound=4, dtype=np.float32)
     np.testing.assert_array_equal(run(A, B), oracle.mm_f64(A, B).astype(np.float32))
 
 
 @pytest.mark.parametrize("m,n,k", [(128, 256, 64), (200, 300, 777), (512, 512, 4096), (1000, 1100, 1200)])
-def test_normal_inputs_tolerance(m, n, k, pair):
+def test_normal_inputs_tolerance(m, n, k):
     A, B = inputs.normal_f32(m, k, n, seed=m * 3 + k)
     err = rel_fro(run(A, B), oracle.mm_f64(A, B))
     assert err <= TOL, err
 
 
 @pytest.mark.parametrize("parts", [1, 2, 5])
-def test_split_k(parts, pair):
+def test_split_k(parts):
     m, n, k = 256, 384, 2048
     A, B = inputs.normal_f32(m, k, n, seed=60 + parts)
     err = rel_fro(run(A, B, extra_parts=parts), oracle.mm_f64(A, B))
