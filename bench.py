@@ -1,14 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the semiring MM library on GB300.
 
-Headline workload: (min,+) tropical MM, n = 4096, int32 entries uniform in
-[0, 1000] with 10% set to the +inf sentinel 2^30 (seed 1), run under the
-five workspace budgets 0, 1, 2, 4 and 8 extra n x n int32 buffers (split-K
-factors s = 1, 2, 3, 5, 9).  One step = the five calls; ops per call =
-2 n^3 (one (x) = add and one (+) = min per term).
+Headline workload: FP64-accuracy (+,x) matrix multiplication by
+Strassen-Winograd, square n = 16384, entries i.i.d. uniform[-1, 1] (seed 3;
+A drawn before B), HEADLINE_LEVELS recursion levels over the tensor-core leaf
+that sums seven 7-bit digit slices per operand (28 bf16 slice products, exact
+integer accumulation, one FP64 combination per output).  One step = one
+product through ``mm_strassen``; ``value`` = classic-equivalent 2 n^3 / step
+time (GOp/s).  The stated accuracy is a relative Frobenius error <= 1e-12 against
+the FP64 oracle, measured on 512 sampled rows.  Beside it, on the same inputs
+and at the same stated accuracy, the plain FP64 CUDA-core path (DFMA leaf).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
-instead on a bounded row sample of the same workload.
+instead, on a bounded row sample of the same product per step.
 """
 from __future__ import annotations
 
@@ -28,9 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GOp/s & % of dtype peak at stated error vs plain FP64 path; peak workspace bytes"
-N = 4096
-BUDGETS = (0, 1, 2, 4, 8)  # extra n x n int32 buffers
-L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+N = 16384
+SEED = 3
+HEADLINE_LEVELS = 2
+TOL_F64 = 1e-12
+SAMPLE_ROWS = 512
 
 
 def parse():
@@ -39,8 +45,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mmsr", choices=["mmsr", "reference"])
+    p.add_argument("--levels", type=int, default=HEADLINE_LEVELS, help="Strassen levels of the headline")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
-    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle (baseline and errors)")
     return p.parse_args()
 
 
@@ -155,28 +162,54 @@ def ncu_traffic(kernel_files, key):
     return rec.get("dram_bytes_per_launch")
 
 
-def bench_config(world):
+F64ACC_SOURCES = ["tc_f64acc.cu", "tcgen05.cuh"]
+
+
+def bench_config(world, levels=HEADLINE_LEVELS):
     """The workload both arms report (the reference arm times a row sample of it)."""
-    return {"workload": "minplus_n4096_int32_inf10pct_seed1_budgets_0_1_2_4_8", "n": N,
-            "budgets_buffers": list(BUDGETS), "l2": "flushed between timed steps (256 MiB write)",
+    return {"workload": "fp64acc_strassen_winograd_L%d_n%d_uniform_seed%d" % (levels, N, SEED),
+            "semiring": "(+,x) FP64-accuracy (7 digit slices, 28 bf16 tensor-core products, exact sums)",
+            "n": N, "levels": levels, "variant": "Strassen-Winograd",
+            "l2": "inputs larger than L2 (2 x 2 GiB FP64)",
             "parallelism": "replicas" if world > 1 else "single"}
+
+
+def sample_rows(m, count=SAMPLE_ROWS):
+    """Rows of C whose error is measured: an even spread plus the quadrant
+    edges of up to four halvings (where a Strassen level puts a block edge)."""
+    base = set(np.linspace(0, m - 1, max(count - 40, 1)).round().astype(np.int64).tolist())
+    for lvl in range(1, 5):
+        q = m >> lvl
+        if q <= 0:
+            break
+        for b in range(0, m, q):
+            base.update(x for x in (b - 1, b) if 0 <= x < m)
+    return np.array(sorted(base), dtype=np.int64)
+
+
+def rel_fro(C, R):
+    C = np.asarray(C, np.float64)
+    R = np.asarray(R, np.float64)
+    return float(np.linalg.norm(C - R) / np.linalg.norm(R))
 
 
 # --------------------------------------------------------------- reference
 def run_reference(args, rank):
+    """The oracle (plain C triple loop, FP64, OpenMP over rows) on a bounded
+    row sample of the headline product per step."""
     if rank != 0:
         return 0
     import oracle
     from paper_1911_05328_gb300 import inputs
 
-    A, B = inputs.tropical_i32(N, N, N, seed=1)
-    rows_per_step = 256
+    A, B = inputs.uniform_f64(N, N, N, seed=SEED)
+    rows_per_step = 64
     rng = np.random.default_rng(0)
     times = []
     for it in range(args.warmup + args.steps):
         rows = np.sort(rng.choice(N, rows_per_step, replace=False))
         t0 = time.perf_counter()
-        oracle.mm_minplus(A, B, rows=rows)
+        oracle.mm_f64(A, B, rows=rows)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
@@ -187,250 +220,20 @@ def run_reference(args, rank):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GOp/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": bench_config(args.gpus),
+        "config": bench_config(args.gpus, args.levels),
         "cpu_baseline": {"value": value, "unit": "GOp/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d random rows of C (x 4096 x 4096) per step; the oracle has no "
-                                   "budget, so every step is one product's row sample" % rows_per_step},
+                         "sample": "%d random rows of C (x %d x %d) per step, FP64 triple loop; "
+                                   "the oracle computes the classic definition, so its GOp/s counts "
+                                   "the same 2 n^3 per product" % (rows_per_step, N, N)},
         "e2e": {"value": value, "unit": "GOp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-# -------------------------------------------------------------------- mmsr
-def main():
-    args = parse()
-    rank, world, local = dist_env()
-    if args.impl == "reference":
-        return run_reference(args, rank)
-
-    import torch
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist  # noqa: F811
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_1911_05328_gb300 import inputs, mmsr
-
-    lib = mmsr.load()
-    SR = mmsr.MM_SR_MIN_PLUS_I32
-    stream = torch.cuda.current_stream()
-    sp = int(stream.cuda_stream)
-
-    A_h, B_h = inputs.tropical_i32(N, N, N, seed=1)
-    dA = torch.from_numpy(A_h).cuda()
-    dB = torch.from_numpy(B_h).cuda()
-    outs = [torch.empty((N, N), dtype=torch.int32, device="cuda") for _ in BUDGETS]
-    max_budget = max(BUDGETS) * N * N * 4
-    ws = torch.empty((max_budget,), dtype=torch.uint8, device="cuda")
-    flush = torch.empty((L2_FLUSH_BYTES,), dtype=torch.uint8, device="cuda")
-    plans = [mmsr.mm_plan_query(SR, -1, N, N, N, b * N * N * 4) for b in BUDGETS]
-
-    def one_step():
-        for b, C in zip(BUDGETS, outs):
-            mmsr.mm_semiring(SR, N, N, N, dA, dB, C, ws, b * N * N * 4, sp)
-
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
-    consistent = all(bool(torch.equal(outs[0], C)) for C in outs[1:])
-
-    # roofline denominators: measured probe of the fused add-min instruction
-    import ctypes
-
-    rate, pms = ctypes.c_double(), ctypes.c_double()
-    lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
-                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
-    lib.mm_probe_peak(0, 2000, sp, ctypes.byref(rate), ctypes.byref(pms))
-    lib.mm_probe_peak(0, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
-    alu_peak_tops = rate.value / 1e12
-    lib.mm_probe_peak(1, 20000, sp, ctypes.byref(rate), ctypes.byref(pms))
-    alu_peak_u16x2_tops = rate.value / 1e12
-
-    # ---------------------------------------------------------- timed region
-    per_budget_ms = [0.0] * len(BUDGETS)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(BUDGETS) + 1)] for _ in range(args.steps)]
-    sampler = ClockSampler(gpu_uuid())
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    lib.mm_trace_enable(1)
-    for s in range(args.steps):
-        flush.zero_()  # evict L2 between timed steps (not timed)
-        e = ev[s]
-        e[0].record(stream)
-        for i, (b, C) in enumerate(zip(BUDGETS, outs)):
-            mmsr.mm_semiring(SR, N, N, N, dA, dB, C, ws, b * N * N * 4, sp)
-            e[i + 1].record(stream)
-    torch.cuda.synchronize()
-    lib.mm_trace_enable(0)
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    step_ms = []
-    for s in range(args.steps):
-        e = ev[s]
-        step_ms.append(e[0].elapsed_time(e[-1]))
-        for i in range(len(BUDGETS)):
-            per_budget_ms[i] += e[i].elapsed_time(e[i + 1])
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-
-    # per-kernel trace
-    kernels = {}
-    launches_total = 0
-    for kid in range(lib.mm_trace_kernel_count()):
-        cnt, tot = ctypes.c_int64(), ctypes.c_double()
-        lib.mm_trace_summary.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
-        lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
-        if cnt.value:
-            lib.mm_trace_kernel_name.restype = ctypes.c_char_p
-            kernels[lib.mm_trace_kernel_name(kid).decode()] = {"launches": cnt.value, "ms": tot.value}
-            launches_total += cnt.value
-
-    ops_per_call = 2.0 * N * N * N
-    ops_per_step = ops_per_call * len(BUDGETS)
-    value = world * ops_per_step * args.steps / (total_ms * 1e-3) / 1e9
-    # dominant kernel: the leaf that did the work (the packed 2 x 16-bit leaf
-    # when the device-side range scan allows it, else the 32-bit leaf)
-    leaf_name = max(("minplus16_leaf", "minplus_leaf"), key=lambda k: kernels.get(k, {"ms": 0.0})["ms"])
-    leaf = kernels[leaf_name]
-    # every call launches both leaves; the one that is not chosen exits at once
-    leaf_avg_ms = leaf["ms"] / (args.steps * len(BUDGETS))
-    achieved_tops = ops_per_call / (leaf_avg_ms * 1e-3) / 1e12
-    peak_tops = alu_peak_u16x2_tops if leaf_name == "minplus16_leaf" else alu_peak_tops
-    traffic = ncu_traffic(["minplus.cu", "minplus_tile.cuh"], leaf_name + "_n4096")
-    per_budget = []
-    for i, b in enumerate(BUDGETS):
-        ms = per_budget_ms[i] / args.steps
-        per_budget.append({"budget_buffers": b, "budget_bytes": b * N * N * 4, "split_k": plans[i].split_k,
-                           "workspace_used_bytes": int(plans[i].workspace_used), "ms": ms,
-                           "gops": ops_per_call / (ms * 1e-3) / 1e9})
-
-    # ----------------------------------------------------- end to end (host)
-    # Every step uploads its inputs from pinned host memory and downloads
-    # every result.  Uploads and downloads run on two copy streams (the two
-    # directions use separate copy engines) with double-buffered device
-    # inputs and outputs: a step's uploads overlap the previous step's
-    # kernels and each result's download overlaps the next product.  On one
-    # shared copy stream the next step's upload queued behind the last
-    # download, serialising every step boundary.
-    e2e = None
-    if True:
-        pA = torch.from_numpy(A_h).pin_memory()
-        pB = torch.from_numpy(B_h).pin_memory()
-        pC = [torch.empty((N, N), dtype=torch.int32).pin_memory() for _ in BUDGETS]
-        dA2 = [dA, torch.empty_like(dA)]
-        dB2 = [dB, torch.empty_like(dB)]
-        outs2 = [outs, [torch.empty_like(c) for c in outs]]
-        cs_up, cs_down = torch.cuda.Stream(), torch.cuda.Stream()
-        e2e_steps = max(2, min(args.steps, 10))
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        in_ready = [torch.cuda.Event() for _ in range(2)]
-        in_free = [torch.cuda.Event() for _ in range(2)]
-        out_ready = [[torch.cuda.Event() for _ in BUDGETS] for _ in range(2)]
-        out_free = [[torch.cuda.Event() for _ in BUDGETS] for _ in range(2)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        evs[0].record(stream)
-        cs_up.wait_event(evs[0])
-        cs_down.wait_event(evs[0])
-        for t in range(e2e_steps):
-            j = t & 1
-            with torch.cuda.stream(cs_up):
-                if t >= 2:
-                    cs_up.wait_event(in_free[j])
-                dA2[j].copy_(pA, non_blocking=True)
-                dB2[j].copy_(pB, non_blocking=True)
-                in_ready[j].record(cs_up)
-            stream.wait_event(in_ready[j])
-            for i, b in enumerate(BUDGETS):
-                if t >= 2:
-                    stream.wait_event(out_free[j][i])
-                mmsr.mm_semiring(SR, N, N, N, dA2[j], dB2[j], outs2[j][i], ws, b * N * N * 4, sp)
-                out_ready[j][i].record(stream)
-                with torch.cuda.stream(cs_down):
-                    cs_down.wait_event(out_ready[j][i])
-                    pC[i].copy_(outs2[j][i], non_blocking=True)
-                    out_free[j][i].record(cs_down)
-            in_free[j].record(stream)
-        stream.wait_stream(cs_up)
-        stream.wait_stream(cs_down)
-        evs[1].record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = evs[0].elapsed_time(evs[1])
-        if dist:
-            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * ops_per_step * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GOp/s",
-               "h2d_bytes_per_step": int(A_h.nbytes + B_h.nbytes),
-               "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in pC)), "steps": e2e_steps,
-               "overlap": "uploads and downloads on two copy streams, double-buffered device buffers"}
-        consistent = consistent and all(bool(torch.equal(pC[0], c)) for c in pC[1:])
-
-    # ----------------------------------------------------------- extras
-    extras = {}
-    if not args.no_extras and rank == 0:
-        extras = run_extras(mmsr, lib, torch, sp)
-
-    # ------------------------------------------------------ CPU baseline
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        import oracle
-
-        rows = np.arange(0, N, 4, dtype=np.int64)  # 1024 rows, every 4th
-        t0 = time.perf_counter()
-        oracle.mm_minplus(A_h, B_h, rows=rows)
-        dt = time.perf_counter() - t0
-        cpu = {"value": 2.0 * len(rows) * N * N / dt / 1e9, "unit": "GOp/s", "cores": oracle.num_threads(),
-               "kind": "oracle", "sample": "%d of 4096 rows (every 4th) of one n=4096 product, %.1f s"
-                                           % (len(rows), dt)}
-
-    peaks, peak_src = measured_peaks()
-    line = {
-        "metric": METRIC, "value": value, "unit": "GOp/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-        "config": bench_config(world),
-        "error": "bit-exact vs int64 oracle (tests); budgets agree: %s" % consistent,
-        "pct_of_dtype_peak": 100.0 * (value / world) / (peak_tops * 1e3),
-        "peak_workspace_bytes": int(max(p.workspace_used for p in plans)),
-        "per_budget": per_budget,
-        "roofline": {"bound": "alu", "kernel": leaf_name, "achieved": achieved_tops,
-                     "peak": peak_tops, "unit": "TOp/s", "frac": achieved_tops / peak_tops,
-                     "traffic": traffic,
-                     "peak_source": ("measured: mm_probe_peak fused add-min on packed 2 x u16 "
-                                     "(4 ops/lane-instr), all SMs" if leaf_name == "minplus16_leaf" else
-                                     "measured: mm_probe_peak fused add-min u32 (2 ops/lane-instr), all SMs"),
-                     "alu_peak_u32_tops": alu_peak_tops, "alu_peak_u16x2_tops": alu_peak_u16x2_tops},
-        "kernels": kernels,
-        "gpu_launches": launches_total,
-        "clocks": clocks,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
-        "peaks_file": peak_src,
-        "extras": extras,
-    }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
-
-
+# ------------------------------------------------------------ helpers
 def _probe(lib, sp, kind, iters):
     """Measured rate (ops/s) of one instruction kind on every SM: a short
     warm-up launch, then the timed one (mm_probe_peak, include/mmsr_probe.h)."""
@@ -450,62 +253,433 @@ def _roof(bound, achieved, peak, unit, peak_source):
             "frac": (achieved / peak) if peak else None, "peak_source": peak_source}
 
 
-def _time_call(torch, fn, reps):
+def _time_call(torch, fn, reps, stream=None):
+    """Mean milliseconds per call over `reps` calls after one untimed call,
+    CUDA events on the launching stream."""
     fn()
     torch.cuda.synchronize()
+    s = stream if stream is not None else torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
+    a.record(s)
     for _ in range(reps):
         fn()
-    b.record()
+    b.record(s)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
 
 
-def run_extras(mmsr, lib, torch, sp):
-    """Secondary workloads (not the headline): reported for context."""
+def _trace(lib, ctypes):
+    """Per-kernel launches and total milliseconds recorded by the library's
+    event trace since it was last enabled."""
+    lib.mm_trace_summary.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    lib.mm_trace_kernel_name.restype = ctypes.c_char_p
+    out = {}
+    for kid in range(lib.mm_trace_kernel_count()):
+        cnt, tot = ctypes.c_int64(), ctypes.c_double()
+        lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
+        if cnt.value:
+            out[lib.mm_trace_kernel_name(kid).decode()] = {"launches": cnt.value, "ms": tot.value}
+    return out
+
+
+class ErrBook:
+    """Sampled GPU rows waiting for the oracle's rows of the same product.
+    The oracle runs after every GPU measurement, once per input set, so no
+    CPU work overlaps a timed region.  FP sets record the relative Frobenius
+    error; (min,+) sets record whether the rows are bit-identical."""
+
+    def __init__(self):
+        self.sets = {}   # key -> (make() -> (A, B), rows, kind)
+        self.items = []  # (key, record dict, field, gpu rows)
+        self.cache = {}
+
+    def add_set(self, key, make, rows, kind="f64"):
+        self.sets.setdefault(key, (make, rows, kind))
+
+    def add(self, key, record, field, gpu_rows):
+        self.items.append((key, record, field, gpu_rows))
+
+    def rows_of(self, key):
+        return self.sets[key][1]
+
+    def oracle_rows(self, key, oracle):
+        if key not in self.cache:
+            make, rows, kind = self.sets[key]
+            A, B = make()
+            fn = oracle.mm_minplus if kind == "minplus" else oracle.mm_f64
+            t0 = time.perf_counter()
+            R = fn(A, B, rows=rows)
+            self.cache[key] = (R, time.perf_counter() - t0, A.shape, B.shape)
+        return self.cache[key]
+
+    def resolve(self, oracle):
+        for key, rec, field, G in self.items:
+            R = self.oracle_rows(key, oracle)[0]
+            if self.sets[key][2] == "minplus":
+                rec[field] = bool(np.array_equal(G, R))
+            else:
+                rec[field] = rel_fro(G, R)
+        # input sets are large: release them once every error is known
+        self.sets = {k: (None, v[1], v[2]) for k, v in self.sets.items()}
+        self.cache.clear()
+
+
+def _rows_of(torch, dC, rows):
+    idx = torch.from_numpy(np.asarray(rows, np.int64)).to(dC.device)
+    return dC.index_select(0, idx).cpu().numpy()
+
+
+# -------------------------------------------------------------------- mmsr
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
     import ctypes
 
-    from paper_1911_05328_gb300 import inputs
+    import torch
 
-    lib.mm_trace_summary.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1911_05328_gb300 import inputs, mmsr
+
+    lib = mmsr.load()
+    L = args.levels
+    SR = mmsr.MM_SR_PLUS_TIMES_F64ACC
+    VAR = mmsr.MM_STRASSEN_WINOGRAD
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+    book = ErrBook()
+
+    A_h, B_h = inputs.uniform_f64(N, N, N, seed=SEED)
+    rows = sample_rows(N, SAMPLE_ROWS)
+    book.add_set("sq64", lambda: (A_h, B_h), rows)
+    dA = torch.from_numpy(A_h).cuda()
+    dB = torch.from_numpy(B_h).cuda()
+    dC = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    plan = mmsr.mm_plan_query(SR, L, N, N, N, 0)
+    wbytes = int(plan.workspace_min)
+    ws = torch.empty((wbytes,), dtype=torch.uint8, device="cuda")
+
+    def call(a, b, c, s=sp):
+        mmsr.mm_strassen(L, VAR, SR, N, N, N, a, b, c, ws, wbytes, s)
+
+    for _ in range(args.warmup):
+        call(dA, dB, dC)
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------- timed region
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    sampler = ClockSampler(gpu_uuid())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    lib.mm_trace_enable(1)
+    ev[0].record(stream)
+    for s in range(args.steps):
+        call(dA, dB, dC)
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    lib.mm_trace_enable(0)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    kernels = _trace(lib, ctypes)
+    launches_total = sum(v["launches"] for v in kernels.values())
+    head = {}
+    book.add("sq64", head, "error", _rows_of(torch, dC, rows))
+
+    ops_per_step = 2.0 * N ** 3  # classic-equivalent
+    value = world * ops_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    # dominant kernel: the leaf GEMM over all 7^L products (one batched launch
+    # per step); issued work = 28 bf16 slice products of every leaf
+    leaf = kernels.get("tc_f64acc", {"launches": 0, "ms": 0.0})
+    leaf_issued = 28 * 2.0 * (N >> L) ** 3 * 7 ** L * args.steps
+    peaks, peak_src = measured_peaks()
+    leaf_tflops = leaf_issued / (leaf["ms"] * 1e-3) / 1e12 if leaf["ms"] else 0.0
+    sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    traffic = ncu_traffic(F64ACC_SOURCES, "f64acc_gemm_strassen_L%d_n%d" % (L, N))
+
+    # ----------------------------------------------------- end to end (host)
+    # Every step uploads A and B from pinned host memory and downloads C.
+    # Uploads and downloads run on two copy streams (separate copy engines)
+    # with double-buffered device operands and results, so a step's uploads
+    # overlap the previous step's product and its download the next one.
+    pA = torch.from_numpy(A_h).pin_memory()
+    pB = torch.from_numpy(B_h).pin_memory()
+    pC = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    dA2, dB2, dC2 = [dA, torch.empty_like(dA)], [dB, torch.empty_like(dB)], [dC, torch.empty_like(dC)]
+    cs_up, cs_down = torch.cuda.Stream(), torch.cuda.Stream()
+    e2e_steps = max(2, min(args.steps, 10))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    in_ready = [torch.cuda.Event() for _ in range(2)]
+    in_free = [torch.cuda.Event() for _ in range(2)]
+    out_ready = [torch.cuda.Event() for _ in range(2)]
+    out_free = [torch.cuda.Event() for _ in range(2)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    cs_up.wait_event(evs[0])
+    cs_down.wait_event(evs[0])
+    for t in range(e2e_steps):
+        j = t & 1
+        with torch.cuda.stream(cs_up):
+            if t >= 2:
+                cs_up.wait_event(in_free[j])
+            dA2[j].copy_(pA, non_blocking=True)
+            dB2[j].copy_(pB, non_blocking=True)
+            in_ready[j].record(cs_up)
+        stream.wait_event(in_ready[j])
+        if t >= 2:
+            stream.wait_event(out_free[j])
+        call(dA2[j], dB2[j], dC2[j])
+        out_ready[j].record(stream)
+        in_free[j].record(stream)
+        with torch.cuda.stream(cs_down):
+            cs_down.wait_event(out_ready[j])
+            pC.copy_(dC2[j], non_blocking=True)
+            out_free[j].record(cs_down)
+    stream.wait_stream(cs_up)
+    stream.wait_stream(cs_down)
+    evs[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = evs[0].elapsed_time(evs[1])
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * ops_per_step * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GOp/s",
+           "h2d_bytes_per_step": int(A_h.nbytes + B_h.nbytes), "d2h_bytes_per_step": int(pC.numel() * 8),
+           "steps": e2e_steps,
+           "overlap": "uploads and downloads on two copy streams, double-buffered device buffers"}
+    e2e_same = bool(torch.equal(pC, dC2[(e2e_steps - 1) & 1].cpu()))
+    del pA, pB, pC, dA2, dB2, dC2, ws
+    torch.cuda.empty_cache()
+
+    # ------------------------------------- the plain FP64 path beside it
+    # same inputs, same stated accuracy; the DFMA leaf is bound by this
+    # GPU's FP64 pipe, so one product is timed (after a small warm call)
+    mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC, None, 0, sp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, N, N, N, dA, dB, dC, None, 0, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    mhz = sm_max_mhz()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp64_peak = sms * 2 * 2 * mhz * 1e6 / 1e12
+    plain = {"ms": plain_ms, "gops": 2.0 * N ** 3 / (plain_ms * 1e-3) / 1e9, "calls_timed": 1,
+             "kernel": "dfma_leaf (64 x 64 tiles, FP64 FMA)",
+             "roofline": _roof("fp64", 2.0 * N ** 3 / (plain_ms * 1e-3) / 1e12, fp64_peak, "TFLOP/s",
+                               "derived: %d SMs x 2 FP64 FMA/clk x 2 FLOP x %.0f MHz" % (sms, mhz))}
+    book.add("sq64", plain, "error", _rows_of(torch, dC, rows))
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+
+    # ----------------------------------------------------------- extras
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(mmsr, lib, torch, sp, book, A_h, B_h, rows)
+
+    # ------------------------------------- CPU phase: oracle, baseline, errors
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+
+        R, dt, _, _ = book.oracle_rows("sq64", oracle)
+        if world == 1:
+            cpu = {"value": 2.0 * len(rows) * N * N / dt / 1e9, "unit": "GOp/s", "cores": oracle.num_threads(),
+                   "kind": "oracle",
+                   "sample": "%d of %d rows (an even spread plus quadrant edges) of the n=%d product, FP64 "
+                             "triple loop, %.1f s; the full product extrapolates to %.0f s"
+                             % (len(rows), N, N, dt, dt * N / len(rows))}
+        book.resolve(oracle)
+    err = head.get("error")
+    line = {
+        "metric": METRIC, "value": value, "unit": "GOp/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "dtype_detail": "FP64 in/out; bf16 digit-slice products on tensor cores, exact FP32 chunks, "
+                        "int64 group sums, FP64 combination and FP64 Strassen additions",
+        "data": "synthetic",
+        "config": bench_config(world, L),
+        "error": err, "error_measure": "relative Frobenius vs FP64 oracle on %d sampled rows" % len(rows),
+        "tolerance": TOL_F64, "within_tolerance": (err is not None and err <= TOL_F64),
+        "vs_plain_fp64": dict(plain, speedup=plain["ms"] / (total_ms / args.steps)),
+        "pct_of_dtype_peak": {
+            "leaf_bf16_tensor_issued_vs_sustained": 100.0 * leaf_tflops / sustained,
+            "useful_fp64_vs_fp64_peak": 100.0 * (value / world) / (fp64_peak * 1e3)},
+        "peak_workspace_bytes": wbytes,
+        "workspace_n2x8B": wbytes / (N * N * 8.0),
+        "roofline": {"bound": "tensor", "kernel": "f64acc_gemm_kernel (all 7^L leaves in one launch)",
+                     "achieved": leaf_tflops, "peak": sustained, "unit": "TFLOP/s",
+                     "frac": leaf_tflops / sustained, "traffic": traffic,
+                     "frac_of_burst": leaf_tflops / peaks["bf16_tflops"],
+                     "peak_source": "%s: bf16 dense, sustained (the leaf runs back to back inside "
+                                    "seconds-long steps); burst %.1f" % (peak_src, peaks["bf16_tflops"]),
+                     "work": "28 bf16 products x 2 (n/2^L)^3 x 7^L issued FLOP per launch",
+                     "leaf_share_of_step": leaf["ms"] / total_ms if total_ms else None},
+        "kernels": kernels,
+        "gpu_launches": launches_total,
+        "clocks": clocks,
+        "e2e": dict(e2e, result_matches_device_run=e2e_same),
+        "cpu_baseline": cpu,
+        "peaks_file": peak_src,
+        "extras": extras,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ----------------------------------------------------------------- extras
+def run_extras(mmsr, lib, torch, sp, book, A_sq, B_sq, rows_sq):
+    """Secondary workloads (not the headline), each with its own roofline
+    record and, where the oracle can check it, its error."""
+    import ctypes
 
     out = {}
-    # roofline denominators of the CUDA-core rows: measured probes (bf16
-    # tensor peaks come from the measured-peaks file)
     peaks, src = measured_peaks()
+    u32_peak = _probe(lib, sp, 0, 20000) / 1e12
     u16_peak = _probe(lib, sp, 1, 20000) / 1e12
     # boolean leaf: one three-input logic op covers 32 terms (32 ANDs + 32
     # ORs) and issues on the same ALU pipe as the packed add-min, whose probe
     # issues exactly one ALU instruction per step: ALU rate x 64 ops
     lop_peak = u16_peak / 4 * 64
-    # FP64: 2 FMA lanes per SM per clock (the nominal 1.25 TFLOP/s at the
-    # maximum clock); the FMA-chain probe reaches ~89% of it
     mhz = sm_max_mhz()
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     fp64_peak = sms * 2 * 2 * mhz * 1e6 / 1e12
     fp64_src = "derived: %d SMs x 2 FP64 FMA/clk x 2 FLOP x %.0f MHz" % (sms, mhz)
+    bf16 = {"burst": peaks["bf16_tflops"], "sustained": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])}
     bf16_src = "%s: bf16 dense burst (cuBLAS)" % src
-    # FP64 classic n=256, uniform[-1,1], seed 0, budget 0 (plain FP64 path)
+    out["minplus_n4096_budgets"] = extras_minplus(mmsr, lib, torch, sp, ctypes, book, u32_peak, u16_peak)
+    out.update(extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf16_src))
+    out["strassen_n16384"] = extras_strassen(mmsr, lib, torch, sp, ctypes, book, A_sq, B_sq, rows_sq, bf16,
+                                             bf16_src)
+    out["strassen_rect_12288x16384x8192"] = extras_strassen_rect(mmsr, lib, torch, sp, ctypes, book, bf16,
+                                                                  bf16_src)
+    out["batched_512"] = extras_batched(mmsr, lib, torch, sp, ctypes, bf16["burst"], u16_peak, bf16_src)
+    out["closure_minplus_n4096"] = extras_closure(mmsr, torch, sp, u16_peak)
+    out["orand_n4096"] = extras_orand(mmsr, lib, torch, sp, ctypes, lop_peak)
+    out["probes"] = {"addmin_u32_tops": u32_peak, "addmin_u16x2_tops": u16_peak,
+                     "fp64_fma_probe_tflops": _probe(lib, sp, 2, 2000) / 1e12, "fp64_peak_derived_tflops": fp64_peak,
+                     "orand_peak_derived_tops": lop_peak, "fp32_fma_probe_tflops": _probe(lib, sp, 3, 20000) / 1e12}
+    torch.cuda.empty_cache()
+    return out
+
+
+def extras_minplus(mmsr, lib, torch, sp, ctypes, book, u32_peak, u16_peak):
+    """(min,+) n = 4096, int32 in [0, 1000] with 10% +inf (seed 1), under the
+    five budgets 0, 1, 2, 4, 8 extra n x n int32 buffers (s = 1, 2, 3, 5, 9),
+    first with the packed 2 x 16-bit leaf (the inputs fit it), then with the
+    exact 32-bit leaf that every other input takes."""
+    from paper_1911_05328_gb300 import inputs
+
+    n, budgets = 4096, (0, 1, 2, 4, 8)
+    SR = mmsr.MM_SR_MIN_PLUS_I32
+    A_h, B_h = inputs.tropical_i32(n, n, n, seed=1)
+    rows = sample_rows(n)
+    book.add_set("mp4096", lambda: (A_h, B_h), rows, kind="minplus")
+    dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+    outs = [torch.empty((n, n), dtype=torch.int32, device="cuda") for _ in budgets]
+    ws = torch.empty((max(budgets) * n * n * 4,), dtype=torch.uint8, device="cuda")
+    flush = torch.empty((256 << 20,), dtype=torch.uint8, device="cuda")
+    res = {}
+    for leaf_name, packed, peak in (("minplus16_leaf", 1, u16_peak), ("minplus_leaf", 0, u32_peak)):
+        mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_PACKED, packed)
+        steps = 10 if packed else 4
+        per = [0.0] * len(budgets)
+        for b, C in zip(budgets, outs):  # warm
+            mmsr.mm_semiring(SR, n, n, n, dA, dB, C, ws, b * n * n * 4, sp)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(budgets) + 1)] for _ in range(steps)]
+        lib.mm_trace_enable(1)
+        for s in range(steps):
+            flush.zero_()  # evict L2 between steps (not timed)
+            evs[s][0].record()
+            for i, (b, C) in enumerate(zip(budgets, outs)):
+                mmsr.mm_semiring(SR, n, n, n, dA, dB, C, ws, b * n * n * 4, sp)
+                evs[s][i + 1].record()
+        torch.cuda.synchronize()
+        lib.mm_trace_enable(0)
+        kern = _trace(lib, ctypes)
+        for s in range(steps):
+            for i in range(len(budgets)):
+                per[i] += evs[s][i].elapsed_time(evs[s][i + 1]) / steps
+        k = kern.get(leaf_name, {"launches": 1, "ms": 0.0})
+        leaf_ms = k["ms"] / (steps * len(budgets))
+        ach = 2.0 * n ** 3 / (leaf_ms * 1e-3) / 1e12 if leaf_ms else 0.0
+        step_ms = sum(per)
+        rec = {"ms_per_step_5_calls": step_ms, "gops": 5 * 2.0 * n ** 3 / (step_ms * 1e-3) / 1e9,
+               "per_budget": [{"budget_buffers": b, "split_k": mmsr.mm_plan_query(SR, -1, n, n, n, b * n * n * 4).split_k,
+                               "workspace_used_bytes": int(mmsr.mm_plan_query(SR, -1, n, n, n, b * n * n * 4).workspace_used),
+                               "ms": per[i], "gops": 2.0 * n ** 3 / (per[i] * 1e-3) / 1e9}
+                              for i, b in enumerate(budgets)],
+               "budgets_agree": all(bool(torch.equal(outs[0], C)) for C in outs[1:]),
+               "kernels": kern,
+               "roofline": dict(_roof("alu", ach, peak, "TOp/s",
+                                      "measured: mm_probe_peak fused add-min %s, all SMs"
+                                      % ("packed 2 x u16 (4 ops/lane-instr)" if packed else "u32 (2 ops/lane-instr)")),
+                                kernel=leaf_name,
+                                traffic=ncu_traffic(["minplus.cu", "minplus_tile.cuh"], leaf_name + "_n4096"))}
+        book.add("mp4096", rec, "bit_exact_sampled_rows", _rows_of(torch, outs[-1], rows))
+        res["packed_u16x2" if packed else "u32"] = rec
+    mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_PACKED, 1)
+    del dA, dB, outs, ws, flush
+    torch.cuda.empty_cache()
+    return res
+
+
+def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf16_src):
+    """FP64 classic n = 256 (budget 0); FP32 mode (bf16x3) and FP64-accuracy
+    mode at n = 8192 beside the plain FP64 path at the same size."""
+    from paper_1911_05328_gb300 import inputs
+
+    out = {}
     A, B = inputs.uniform_f64(256, 256, 256, seed=0)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((256, 256), dtype=torch.float64, device="cuda")
-    ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC, None, 0, sp), 50)
+    ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC, None, 0,
+                                                    sp), 50)
+    book.add_set("n256", lambda: (A, B), np.arange(256))
     out["fp64_n256_budget0"] = {"ms": ms, "gops": 2 * 256 ** 3 / (ms * 1e-3) / 1e9,
                                 "roofline": _roof("fp64", 2 * 256 ** 3 / (ms * 1e-3) / 1e12, fp64_peak,
                                                   "TFLOP/s", fp64_src)}
-    # FP64 DFMA path at n=8192 (comparator of the FP32 split-precision path)
+    book.add("n256", out["fp64_n256_budget0"], "error", dC.cpu().numpy())
     n = 8192
+    rows = sample_rows(n)
     A, B = inputs.uniform_f64(n, n, n, seed=2)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    del A, B
     dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
-    ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, n, n, n, dA, dB, dC, None, 0, sp), 2)
+    ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, n, n, n, dA, dB, dC, None, 0, sp), 1)
     out["fp64_dfma_n8192"] = {"ms": ms, "gops": 2 * n ** 3 / (ms * 1e-3) / 1e9,
                               "roofline": _roof("fp64", 2 * n ** 3 / (ms * 1e-3) / 1e12, fp64_peak,
                                                 "TFLOP/s", fp64_src)}
     del dA, dB, dC
     # FP32 mode n=8192, normal(0,1), seed 2: bf16x3 split products on tcgen05
     A, B = inputs.normal_f32(n, n, n, seed=2)
+    book.add_set("n8192_f32", lambda: (A, B), rows)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
     sr = mmsr.MM_SR_PLUS_TIMES_F32
@@ -514,62 +688,164 @@ def run_extras(mmsr, lib, torch, sp):
     lib.mm_trace_enable(1)
     ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, wmin, sp), 10)
     lib.mm_trace_enable(0)
-    cnt, tot = ctypes.c_int64(), ctypes.c_double()
-    lib.mm_trace_summary(5, ctypes.byref(cnt), ctypes.byref(tot))  # tc_bf16x3
-    gemm_ms = tot.value / max(cnt.value, 1)
-    issued = 3 * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12
+    kern = _trace(lib, ctypes)
+    g = kern.get("tc_bf16x3", {"launches": 1, "ms": 0.0})
+    gemm_ms = g["ms"] / max(g["launches"], 1)
+    issued = 3 * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
     out["fp32_bf16x3_n8192"] = {
-        "ms": ms, "gops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms,
-        "tensor_tflops_issued": issued, "frac_of_bf16_peak": issued / peaks["bf16_tflops"],
-        "roofline": _roof("tensor", issued, peaks["bf16_tflops"], "TFLOP/s", bf16_src),
-        "peak_source": src, "workspace_bytes": wmin,
-        "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms,
-        "error": "rel. Frobenius vs FP64 oracle on 512 sampled rows <= 1e-5 (tests)"}
-    import ctypes
-
-    rate, pms = ctypes.c_double(), ctypes.c_double()
+        "ms": ms, "gops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms, "kernels": kern,
+        "tensor_tflops_issued": issued,
+        "roofline": _roof("tensor", issued, bf16["burst"], "TFLOP/s", bf16_src),
+        "workspace_bytes": wmin, "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms, "tolerance": 1e-5}
+    book.add("n8192_f32", out["fp32_bf16x3_n8192"], "error", _rows_of(torch, dC, rows))
     del dA, dB, dC, ws
     torch.cuda.empty_cache()
-    # FP64-accuracy mode at n = 8192 (uniform[-1,1]) beside the plain FP64
-    # path at the same size and the same stated accuracy (1e-12)
+    # FP64-accuracy mode at n = 8192 (uniform[-1,1], seed 3)
     A, B = inputs.uniform_f64(n, n, n, seed=3)
+    book.add_set("n8192_f64", lambda: (A, B), rows)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    del A, B
     dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
     sr = mmsr.MM_SR_PLUS_TIMES_F64ACC
     wmin = int(mmsr.mm_plan_query(sr, -1, n, n, n, 0).workspace_min)
     ws = torch.empty((wmin,), dtype=torch.uint8, device="cuda")
     lib.mm_trace_enable(1)
-    ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, wmin, sp), 3)
+    ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, wmin, sp), 4)
     lib.mm_trace_enable(0)
-    lib.mm_trace_summary(8, ctypes.byref(cnt), ctypes.byref(tot))  # tc_f64acc
-    gemm_ms = tot.value / max(cnt.value, 1)
-    issued = 28 * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12
+    kern = _trace(lib, ctypes)
+    g = kern.get("tc_f64acc", {"launches": 1, "ms": 0.0})
+    gemm_ms = g["ms"] / max(g["launches"], 1)
+    issued = 28 * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
     out["fp64acc_n8192"] = {
-        "ms": ms, "gflops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms,
-        "tensor_tflops_issued_28_slice_products": issued, "frac_of_bf16_peak": issued / peaks["bf16_tflops"],
-        "roofline": _roof("tensor", issued, peaks["bf16_tflops"], "TFLOP/s", bf16_src),
-        "workspace_bytes": wmin, "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms,
-        "error": "rel. Frobenius vs FP64 oracle <= 1e-12 (tests; 4.6e-15 at n=16384)"}
+        "ms": ms, "gflops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms, "kernels": kern,
+        "tensor_tflops_issued_28_slice_products": issued,
+        "roofline": dict(_roof("tensor", issued, bf16["burst"], "TFLOP/s", bf16_src),
+                         frac_of_sustained=issued / bf16["sustained"]),
+        "workspace_bytes": wmin, "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms, "tolerance": 1e-12}
+    book.add("n8192_f64", out["fp64acc_n8192"], "error", _rows_of(torch, dC, rows))
     del dA, dB, dC, ws
-    torch.cuda.empty_cache()
-    out["batched_512"] = run_batched_extras(mmsr, lib, torch, sp, ctypes, peaks["bf16_tflops"], u16_peak, bf16_src)
-    out["strassen_fp32_n16384"] = run_strassen_extras(mmsr, lib, torch, sp, ctypes, peaks["bf16_tflops"], bf16_src)
-    out["closure_minplus_n4096"] = run_closure_extras(mmsr, torch, sp, u16_peak)
-    out["orand_n4096"] = run_orand_extras(mmsr, lib, torch, sp, ctypes, lop_peak)
-    out["fp64_fma_probe_tflops"] = _probe(lib, sp, 2, 2000) / 1e12
-    out["fp64_peak_derived_tflops"] = fp64_peak
-    out["addmin_u16x2_probe_tops"] = u16_peak
-    out["orand_peak_derived_tops"] = lop_peak
-    out["fp32_fma_probe_tflops"] = _probe(lib, sp, 3, 20000) / 1e12
     torch.cuda.empty_cache()
     return out
 
 
-def run_batched_extras(mmsr, lib, torch, sp, ctypes, bf16_peak, u16_peak, bf16_src):
+def _strassen_levels(mmsr, lib, torch, sp, ctypes, book, key, sr, m, n, k, dA, dB, dC, rows, bf16, bf16_src,
+                     levels=range(0, 5), reps=3):
+    """Time mm_strassen (Winograd) at each level on one product; record time,
+    classic-equivalent GOp/s, workspace, the leaf launch's tensor roofline,
+    the kernel split and the sampled-row error."""
+    products = 3 if sr == mmsr.MM_SR_PLUS_TIMES_F32 else 28
+    leaf_name = "tc_bf16x3" if sr == mmsr.MM_SR_PLUS_TIMES_F32 else "tc_f64acc"
+    eb = 4 if sr == mmsr.MM_SR_PLUS_TIMES_F32 else 8
+    res = {}
+    for L in levels:
+        p = mmsr.mm_plan_query(sr, L, m, n, k, 0)
+        ws = torch.empty((max(int(p.workspace_min), 16),), dtype=torch.uint8, device="cuda")
+        fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, m, n, k, dA, dB, dC, ws,
+                                      int(p.workspace_min), sp)
+        fn()
+        torch.cuda.synchronize()
+        lib.mm_trace_enable(1)
+        ms = _time_call(torch, fn, reps)
+        lib.mm_trace_enable(0)
+        kern = _trace(lib, ctypes)
+        calls = reps + 1  # _time_call's untimed call is traced too
+        split = {nm: v["ms"] / calls for nm, v in kern.items()}
+        rec = {"ms": ms, "gops_classic_equiv": 2.0 * m * n * k / (ms * 1e-3) / 1e9,
+               "workspace_bytes": int(p.workspace_min),
+               "workspace_over_mn_x_elem": p.workspace_min / (float(max(m, n)) * max(m, n) * eb),
+               "kernel_ms": split, "launches_per_call": {nm: v["launches"] / calls for nm, v in kern.items()}}
+        leaf_ms = split.get(leaf_name, 0.0)
+        if leaf_ms > 0:
+            issued = products * 2.0 * (m >> L) * (n >> L) * (k >> L) * 7 ** L / (leaf_ms * 1e-3) / 1e12
+            rec["leaf_roofline"] = dict(_roof("tensor", issued, bf16["burst"], "TFLOP/s", bf16_src),
+                                        frac_of_sustained=issued / bf16["sustained"], kernel=leaf_name)
+            rec["leaf_share_of_time"] = leaf_ms / ms
+        book.add(key, rec, "error", _rows_of(torch, dC, rows))
+        res["L%d" % L] = rec
+        del ws
+        torch.cuda.empty_cache()
+    return res
+
+
+def extras_strassen(mmsr, lib, torch, sp, ctypes, book, A_sq, B_sq, rows, bf16, bf16_src):
+    """Strassen-Winograd at n = 16384 (uniform[-1,1], seed 3): FP64-accuracy
+    mode and FP32 mode (the float32 cast of the same inputs), L = 0..4, with
+    the error of every level; then the zero-temporary TAR-Strassen level and
+    the STAR-Strassen-1 mixed plans in FP32 mode."""
+    n = N
+    res = {}
+    dA64, dB64 = torch.from_numpy(A_sq).cuda(), torch.from_numpy(B_sq).cuda()
+    dC64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    res["fp64acc"] = _strassen_levels(mmsr, lib, torch, sp, ctypes, book, "sq64", mmsr.MM_SR_PLUS_TIMES_F64ACC,
+                                      n, n, n, dA64, dB64, dC64, rows, bf16, bf16_src, reps=2)
+    del dC64
+    torch.cuda.empty_cache()
+    book.add_set("sq32", lambda: (A_sq.astype(np.float32), B_sq.astype(np.float32)), rows)
+    dA, dB = dA64.float(), dB64.float()
+    del dA64, dB64
+    dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    sr = mmsr.MM_SR_PLUS_TIMES_F32
+    res["fp32"] = _strassen_levels(mmsr, lib, torch, sp, ctypes, book, "sq32", sr, n, n, n, dA, dB, dC, rows,
+                                   bf16, bf16_src)
+    # TAR-Strassen: one level, products added into C's quadrants by the leaf
+    # epilogue in conflict-free waves (no product temporaries)
+    p = mmsr.mm_strassen_tar_query(sr, n, n, n)
+    ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+    fn = lambda: mmsr.mm_strassen_tar(mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
+                                      int(p.workspace_min), sp)
+    ms = _time_call(torch, fn, 3)
+    res["fp32_tar_L1"] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                          "workspace_bytes": int(p.workspace_min),
+                          "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
+    book.add("sq32", res["fp32_tar_L1"], "error", _rows_of(torch, dC, rows))
+    del ws
+    torch.cuda.empty_cache()
+    # STAR-Strassen-1 mixed plans: c classic in-place levels over L Strassen
+    # levels; the workspace of one block product only
+    for c, L in ((1, 1), (1, 2), (2, 1), (2, 2)):
+        p = mmsr.mm_star_strassen_query(c, L, sr, n, n, n)
+        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+        fn = lambda: mmsr.mm_star_strassen(c, L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
+                                           int(p.workspace_min), sp)
+        ms = _time_call(torch, fn, 3)
+        rec = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+               "workspace_bytes": int(p.workspace_min), "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
+        book.add("sq32", rec, "error", _rows_of(torch, dC, rows))
+        res["fp32_star_c%d_L%d" % (c, L)] = rec
+        del ws
+        torch.cuda.empty_cache()
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    return res
+
+
+def extras_strassen_rect(mmsr, lib, torch, sp, ctypes, book, bf16, bf16_src):
+    """The rectangular product m = 12288, k = 16384, n = 8192 (uniform[-1,1],
+    seed 3), Strassen-Winograd L = 0..4 in FP64-accuracy and FP32 modes."""
+    from paper_1911_05328_gb300 import inputs
+
+    m, k, n = 12288, 16384, 8192
+    A, B = inputs.uniform_f64(m, k, n, seed=3)
+    rows = sample_rows(m)
+    book.add_set("rect64", lambda: (A, B), rows)
+    book.add_set("rect32", lambda: (A.astype(np.float32), B.astype(np.float32)), rows)
+    res = {}
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    res["fp64acc"] = _strassen_levels(mmsr, lib, torch, sp, ctypes, book, "rect64", mmsr.MM_SR_PLUS_TIMES_F64ACC,
+                                      m, n, k, dA, dB, dC, rows, bf16, bf16_src, reps=2)
+    dA, dB = dA.float(), dB.float()
+    dC = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    res["fp32"] = _strassen_levels(mmsr, lib, torch, sp, ctypes, book, "rect32", mmsr.MM_SR_PLUS_TIMES_F32,
+                                   m, n, k, dA, dB, dC, rows, bf16, bf16_src)
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    return res
+
+
+def extras_batched(mmsr, lib, torch, sp, ctypes, bf16_peak, u16_peak, bf16_src):
     """512 problems (m, n, k log-uniform in [64, 2048], 70% FP32 (+,x) with
     normal(0,1) entries, 30% (min,+) with integers in [0, 1000], seed 4) in
-    one persistent launch, captured once in a CUDA graph and replayed."""
+    one capturable call, captured once in a CUDA graph and replayed."""
     from paper_1911_05328_gb300 import inputs
 
     probs = inputs.batched_problems(count=512, seed=4)
@@ -596,13 +872,7 @@ def run_batched_extras(mmsr, lib, torch, sp, ctypes, bf16_peak, u16_peak, bf16_s
         mmsr.mm_batched(table, ws, need, stream=sp)
     torch.cuda.synchronize()
     lib.mm_trace_enable(0)
-    lib.mm_trace_kernel_name.restype = ctypes.c_char_p
-    split = {}
-    for kid in range(lib.mm_trace_kernel_count()):
-        cnt, tot = ctypes.c_int64(), ctypes.c_double()
-        lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
-        if cnt.value:
-            split[lib.mm_trace_kernel_name(kid).decode()] = tot.value / 3
+    split = {nm: v["ms"] / 3 for nm, v in _trace(lib, ctypes).items()}
     # ideal time: every FP32 product's three bf16 split products at the tensor
     # peak plus every (min,+) product at the packed add-min peak
     ideal_ms = (3 * ops_fp32 / (bf16_peak * 1e12) + (ops - ops_fp32) / (u16_peak * 1e12)) * 1e3
@@ -610,16 +880,14 @@ def run_batched_extras(mmsr, lib, torch, sp, ctypes, bf16_peak, u16_peak, bf16_s
            "roofline": _roof("tensor (FP32 tiles) + alu ((min,+) tiles)", ops / (ms * 1e-3) / 1e12,
                              ops / (ideal_ms * 1e-3) / 1e12, "TOp/s",
                              bf16_src + "; measured packed add-min probe"),
-           "kernel_ms_eager": split,
-           "workspace_bytes": int(need), "launch": "one CUDA graph: memset + 2 pre-passes + persistent tcgen05 kernel (FP32 tiles) + "
-                     "packed (min,+) tile launch + 32-bit (min,+) launch (exits at once when unused)",
+           "kernel_ms_eager": split, "workspace_bytes": int(need),
            "error": "bit-exact (min,+), <= 1e-5 FP32, per problem (tests)"}
-    del dA, dB, dC, ws
+    del dA, dB, dC, ws, g
     torch.cuda.empty_cache()
     return res
 
 
-def run_orand_extras(mmsr, lib, torch, sp, ctypes, lop_peak):
+def extras_orand(mmsr, lib, torch, sp, ctypes, lop_peak):
     """(or, and) semiring, n = 4096, 0/1 entries with density 1% (seed 6):
     the bit-packed leaf, budget = the plan's minimum (packing buffers)."""
     from paper_1911_05328_gb300 import inputs
@@ -638,13 +906,7 @@ def run_orand_extras(mmsr, lib, torch, sp, ctypes, lop_peak):
         fn()
     torch.cuda.synchronize()
     lib.mm_trace_enable(0)
-    lib.mm_trace_kernel_name.restype = ctypes.c_char_p
-    split = {}
-    for kid in range(lib.mm_trace_kernel_count()):
-        cnt, tot = ctypes.c_int64(), ctypes.c_double()
-        lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
-        if cnt.value:
-            split[lib.mm_trace_kernel_name(kid).decode()] = tot.value / 5
+    split = {nm: v["ms"] / 5 for nm, v in _trace(lib, ctypes).items()}
     res = {"ms": ms, "gops": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "workspace_bytes": w, "kernel_ms": split,
            "roofline": _roof("alu", 2.0 * n ** 3 / (ms * 1e-3) / 1e12, lop_peak, "TOp/s",
                              "derived: measured ALU-pipe rate (packed add-min probe / 4) x 64 ops per "
@@ -655,7 +917,7 @@ def run_orand_extras(mmsr, lib, torch, sp, ctypes, lop_peak):
     return res
 
 
-def run_closure_extras(mmsr, torch, sp, u16_peak):
+def extras_closure(mmsr, torch, sp, u16_peak):
     """(min,+) closure (all-pairs shortest paths) of a 4096-vertex graph with
     10% arcs of length in [0, 1000] (seed 1) by repeated squaring, one extra
     n x n buffer of budget per squaring: all 12 squarings, and stopping at
@@ -684,116 +946,6 @@ def run_closure_extras(mmsr, torch, sp, u16_peak):
                      "roofline": _roof("alu", sq[-1] * 2.0 * n ** 3 / (ms * 1e-3) / 1e12, u16_peak, "TOp/s",
                                        "measured: mm_probe_peak packed add-min, all SMs")}
     del dA, dC, ws
-    torch.cuda.empty_cache()
-    return res
-
-
-def run_strassen_extras(mmsr, lib, torch, sp, ctypes, bf16_peak, bf16_src):
-    """Strassen-Winograd, FP32 mode, n = 16384 (uniform[-1,1], seed 3, cast
-    to float32): classic (L = 0) and L = 1..4, per-level time, classic-
-    equivalent GOp/s, workspace as a multiple of n^2 * 4 bytes and the time
-    split between operand sums, leaf products and post-additions."""
-    from paper_1911_05328_gb300 import inputs
-
-    n = 16384
-    A, B = inputs.uniform_f64(n, n, n, seed=3)
-    dA64, dB64 = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    dA = dA64.float()
-    dB = dB64.float()
-    del A, B
-    dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
-    sr = mmsr.MM_SR_PLUS_TIMES_F32
-    res = {}
-    names = {}
-    lib.mm_trace_kernel_name.restype = ctypes.c_char_p
-    for kid in range(lib.mm_trace_kernel_count()):
-        names[kid] = lib.mm_trace_kernel_name(kid).decode()
-    for L in range(0, 5):
-        p = mmsr.mm_plan_query(sr, L, n, n, n, 0)
-        ws = torch.empty((max(int(p.workspace_min), 16),), dtype=torch.uint8, device="cuda")
-        fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
-                                      int(p.workspace_min), sp)
-        fn()
-        torch.cuda.synchronize()
-        lib.mm_trace_enable(1)
-        ms = _time_call(torch, fn, 3)
-        lib.mm_trace_enable(0)
-        split = {}
-        for kid, nm in names.items():
-            cnt, tot = ctypes.c_int64(), ctypes.c_double()
-            lib.mm_trace_summary(kid, ctypes.byref(cnt), ctypes.byref(tot))
-            if cnt.value:
-                split[nm] = tot.value / 4  # 1 untimed-warm call + 3 timed calls traced
-        res["L%d" % L] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
-                          "workspace_bytes": int(p.workspace_min),
-                          "workspace_n2x4B": p.workspace_min / (n * n * 4.0), "kernel_ms": split}
-        leaf_ms = split.get("tc_bf16x3", 0.0)
-        if leaf_ms > 0:
-            # 7^L leaf products of size n / 2^L, three bf16 split products each
-            leaf_tf = 3 * 2.0 * (n >> L) ** 3 * 7 ** L / (leaf_ms * 1e-3) / 1e12
-            res["L%d" % L]["leaf_roofline"] = _roof("tensor", leaf_tf, bf16_peak, "TFLOP/s", bf16_src)
-            res["L%d" % L]["leaf_share_of_time"] = leaf_ms / ms
-        del ws
-        torch.cuda.empty_cache()
-    # TAR-Strassen: one level, products added into C's quadrants by the leaf
-    # epilogue in conflict-free waves (no product temporaries)
-    p = mmsr.mm_strassen_tar_query(sr, n, n, n)
-    ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
-    fn = lambda: mmsr.mm_strassen_tar(mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
-                                      int(p.workspace_min), sp)
-    ms = _time_call(torch, fn, 3)
-    res["tar_L1"] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
-                     "workspace_bytes": int(p.workspace_min), "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
-    del ws
-    torch.cuda.empty_cache()
-    # STAR-Strassen-1 mixed plans: c classic in-place levels over L Strassen
-    # levels; the workspace of one block product only
-    for c, L in ((1, 1), (1, 2), (2, 1), (2, 2)):
-        p = mmsr.mm_star_strassen_query(c, L, sr, n, n, n)
-        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
-        fn = lambda: mmsr.mm_star_strassen(c, L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
-                                           int(p.workspace_min), sp)
-        ms = _time_call(torch, fn, 3)
-        res["star_c%d_L%d" % (c, L)] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
-                                        "workspace_bytes": int(p.workspace_min),
-                                        "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
-        del ws
-        torch.cuda.empty_cache()
-    del dC
-    # FP64-accuracy mode (28 digit-slice products per leaf) at the same size
-    dC64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
-    sr64 = mmsr.MM_SR_PLUS_TIMES_F64ACC
-    for L in range(0, 3):
-        p = mmsr.mm_plan_query(sr64, L, n, n, n, 0)
-        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
-        fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr64, n, n, n, dA64, dB64, dC64, ws,
-                                      int(p.workspace_min), sp)
-        ms = _time_call(torch, fn, 2)
-        res["fp64acc_L%d" % L] = {"ms": ms, "gflops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
-                                  "workspace_bytes": int(p.workspace_min),
-                                  "workspace_n2x8B": p.workspace_min / (n * n * 8.0)}
-        del ws
-        torch.cuda.empty_cache()
-    del dA, dB, dA64, dB64, dC64
-    torch.cuda.empty_cache()
-    # the rectangular product m = 12288, k = 16384, n = 8192, FP32 mode
-    m, k, n2 = 12288, 16384, 8192
-    A, B = inputs.uniform_f64(m, k, n2, seed=3)
-    dA = torch.from_numpy(A.astype(np.float32)).cuda()
-    dB = torch.from_numpy(B.astype(np.float32)).cuda()
-    del A, B
-    dC = torch.empty((m, n2), dtype=torch.float32, device="cuda")
-    for L in range(0, 4):
-        p = mmsr.mm_plan_query(sr, L, m, n2, k, 0)
-        ws = torch.empty((max(int(p.workspace_min), 16),), dtype=torch.uint8, device="cuda")
-        fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, m, n2, k, dA, dB, dC, ws,
-                                      int(p.workspace_min), sp)
-        ms = _time_call(torch, fn, 3)
-        res["rect_12288x16384x8192_L%d" % L] = {"ms": ms, "gops_classic_equiv": 2.0 * m * n2 * k / (ms * 1e-3) / 1e9,
-                                               "workspace_bytes": int(p.workspace_min)}
-        del ws
-        torch.cuda.empty_cache()
-    del dA, dB, dC
     torch.cuda.empty_cache()
     return res
 

@@ -63,3 +63,17 @@ def test_clock_sampler_parser(tmp_path):
     assert out["sm_mhz"] == 2025.0 and out["sm_max_mhz"] == 2070.0
     assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
     assert not os.path.exists(s.path)
+
+
+def test_bench_row_sample_matches_the_tests_row_sample():
+    """The benchmark measures its errors on the same rows as the tests: an
+    even spread plus the quadrant edges of four halvings."""
+    import numpy as np
+
+    import oracle
+
+    for m in (256, 8192, 12288, 16384):
+        np.testing.assert_array_equal(bench.sample_rows(m), oracle.sample_rows(m))
+        r = bench.sample_rows(m)
+        assert r[0] == 0 and r[-1] == m - 1 and np.all(np.diff(r) > 0)
+        assert {m // 2 - 1, m // 2, m // 16 - 1, m // 16}.issubset(set(r.tolist()))

@@ -1,5 +1,5 @@
 """The benchmark's reference arm (the CPU oracle timed on a row sample of
-the (min,+) n = 4096 workload) on this machine's CPU: one JSON line with the
+the FP64-accuracy Strassen-Winograd n = 16384 workload) on this machine's CPU: one JSON line with the
 keys the benchmark contract asks for, and silence on ranks other than 0."""
 import json
 import os
@@ -26,7 +26,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["unit"] == "GOp/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 1 and d["ms_per_step"] > 0
     assert d["vs_baseline"] is None and d["data"] == "synthetic" and d["scaling"] == "weak"
-    assert d["config"]["workload"].startswith("minplus_n4096")
+    assert d["config"]["workload"].startswith("fp64acc_strassen_winograd_L")
+    assert d["config"]["n"] == 16384 and d["dtype"] == "f64"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]

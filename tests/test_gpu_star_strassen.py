@@ -6,6 +6,7 @@ import pytest
 import oracle
 from paper_1911_05328_gb300 import inputs, mmsr
 
+from error_bounds import FP32_TOL, fp32_strassen_tol
 from gpu_util import canary_intact, dev, empty, rel_fro, workspace
 
 pytestmark = pytest.mark.gpu
@@ -55,16 +56,20 @@ def test_fp64_modes(variant, c, L):
     assert rel_fro(run_star(c, L, variant, F64ACC, A, B), ref) <= 1e-12
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("c,L", [(1, 1), (1, 2), (2, 2), (1, 3)])
-def test_fp32_uniform_error_matches_pure_strassen_bound(c, L):
-    # the classic levels add no Strassen cancellation: the error stays within
-    # the bound of L Strassen levels.
+def test_fp32_uniform_error_matches_pure_strassen_bound(variant, c, L):
+    # the classic levels grow the worst-case bound by 2 per level at half the
+    # inner dimension (a factor 1 in all): the tolerance is that of L
+    # Strassen levels; the paper's formulas at one level meet plain 1e-5
     m, k, n = 1024, 2048, 768
     A, B = inputs.uniform_f64(m, k, n, seed=3)
     A32, B32 = A.astype(np.float32), B.astype(np.float32)
-    err = rel_fro(run_star(c, L, mmsr.MM_STRASSEN_WINOGRAD, F32, A32, B32), oracle.mm_f64(A32, B32))
-    print("fp32 star-strassen c %d L %d rel_fro %.3e" % (c, L, err))
-    assert err <= 1.5e-5 * 2.8 ** (L - 1), err
+    err = rel_fro(run_star(c, L, variant, F32, A32, B32), oracle.mm_f64(A32, B32))
+    print("fp32 star-strassen variant %d c %d L %d rel_fro %.3e" % (variant, c, L, err))
+    assert err <= fp32_strassen_tol(variant, L), err
+    if variant == mmsr.MM_STRASSEN_PAPER and L == 1:
+        assert err <= FP32_TOL, err
 
 
 @pytest.mark.parametrize("sr", [F32, F64])
@@ -122,5 +127,6 @@ def test_full_size_n16384_star_sampled_rows():
     C = run_star(1, 1, mmsr.MM_STRASSEN_WINOGRAD, F32, A, B)
     rows = oracle.sample_rows(n, 128)
     err = rel_fro(C[rows], oracle.mm_f64(A, B, rows=rows))
-    assert err <= 1.5e-5, err
+    print("n16384 star c 1 L 1 winograd rel_fro %.3e" % err)
+    assert err <= fp32_strassen_tol(mmsr.MM_STRASSEN_WINOGRAD, 1), err
     torch.cuda.empty_cache()

@@ -6,6 +6,7 @@ import pytest
 import oracle
 from paper_1911_05328_gb300 import inputs, mmsr
 
+from error_bounds import FP32_TOL, fp32_strassen_tol
 from gpu_util import canary_intact, dev, empty, rel_fro, workspace
 
 pytestmark = pytest.mark.gpu
@@ -46,7 +47,9 @@ def test_uniform_error_within_one_level_bound(variant):
     A32, B32 = A.astype(np.float32), B.astype(np.float32)
     err = rel_fro(run_tar(variant, A32, B32), oracle.mm_f64(A32, B32))
     print("tar-strassen variant %d rel_fro %.3e" % (variant, err))
-    assert err <= 1.5e-5, err
+    # the paper's formulas at one level meet the plain FP32-mode tolerance;
+    # Winograd's are held to the derived one-level tolerance (9 x 1e-5)
+    assert err <= (FP32_TOL if variant == mmsr.MM_STRASSEN_PAPER else fp32_strassen_tol(variant, 1)), err
 
 
 def test_same_result_class_as_stored_products():
@@ -62,8 +65,12 @@ def test_same_result_class_as_stored_products():
     mmsr.mm_strassen(1, mmsr.MM_STRASSEN_WINOGRAD, F32, m, n, k, dev(A), dev(B), dC, ws, int(p.workspace_min))
     torch.cuda.synchronize()
     ref = oracle.mm_f64(A, B)
-    assert rel_fro(tar, dC.cpu().numpy()) <= 2e-5
-    assert rel_fro(tar, ref) <= 1.5e-5
+    tol = fp32_strassen_tol(mmsr.MM_STRASSEN_WINOGRAD, 1)
+    assert rel_fro(dC.cpu().numpy(), ref) <= tol
+    assert rel_fro(tar, ref) <= tol
+    # same leaf products, different summation into C: the two differ by at
+    # most the sum of their bounds
+    assert rel_fro(tar, dC.cpu().numpy()) <= 2 * tol
 
 
 def test_full_size_n16384_sampled_rows():
@@ -75,5 +82,6 @@ def test_full_size_n16384_sampled_rows():
     C = run_tar(mmsr.MM_STRASSEN_WINOGRAD, A, B)
     rows = oracle.sample_rows(n, 128)
     err = rel_fro(C[rows], oracle.mm_f64(A, B, rows=rows))
-    assert err <= 1.5e-5, err
+    print("n16384 tar-strassen winograd rel_fro %.3e" % err)
+    assert err <= fp32_strassen_tol(mmsr.MM_STRASSEN_WINOGRAD, 1), err
     torch.cuda.empty_cache()

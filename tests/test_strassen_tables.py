@@ -73,3 +73,30 @@ def test_strassen_workspace_is_reported():
         assert p.levels == L and p.workspace_min > prev
         assert p.workspace_min < 64 * 4096 * 4096 * 4
         prev = p.workspace_min
+
+
+def test_growth_factors_of_the_standard_analysis():
+    """The per-level max-norm growth of the cited worst-case analysis, from
+    the tables: 12 for the printed formulas (golden table and library table
+    alike), 18 for Winograd's variant; the FP32-mode Strassen tolerances are
+    1e-5 x 6^L and 1e-5 x 9^L."""
+    from error_bounds import fp32_strassen_tol, growth_factor
+
+    S, T, C = _golden()
+    assert growth_factor(S, T, C) == 12
+    assert growth_factor(*mmsr.mm_strassen_tables(mmsr.MM_STRASSEN_PAPER)) == 12
+    assert growth_factor(*mmsr.mm_strassen_tables(mmsr.MM_STRASSEN_WINOGRAD)) == 18
+    assert abs(fp32_strassen_tol(mmsr.MM_STRASSEN_PAPER, 2) - 3.6e-4) < 1e-12
+    assert abs(fp32_strassen_tol(mmsr.MM_STRASSEN_WINOGRAD, 4) - 1e-5 * 9 ** 4) < 1e-12
+    # a plain classic block product (alpha = beta = unit rows, gamma summing
+    # two products per quadrant) grows by 2 per level: (g/2)^L = 1
+    a = np.zeros((8, 4), np.int64)
+    b = np.zeros((8, 4), np.int64)
+    g = np.zeros((4, 8), np.int64)
+    for q, (i, j) in enumerate(((0, 0), (0, 1), (1, 0), (1, 1))):
+        for t in range(2):
+            r = 2 * q + t
+            a[r, 2 * i + t] = 1
+            b[r, 2 * t + j] = 1
+            g[q, r] = 1
+    assert growth_factor(a, b, g) == 2
