@@ -362,7 +362,7 @@ def main():
 
     A_h, B_h = inputs.uniform_f64(N, N, N, seed=SEED)
     rows = sample_rows(N, SAMPLE_ROWS)
-    book.add_set("sq64", lambda: (A_h, B_h), rows)
+    book.add_set("sq64", lambda A=A_h, B=B_h: (A, B), rows)
     dA = torch.from_numpy(A_h).cuda()
     dB = torch.from_numpy(B_h).cuda()
     dC = torch.empty((N, N), dtype=torch.float64, device="cuda")
@@ -599,7 +599,7 @@ def extras_minplus(mmsr, lib, torch, sp, ctypes, book, u32_peak, u16_peak):
     SR = mmsr.MM_SR_MIN_PLUS_I32
     A_h, B_h = inputs.tropical_i32(n, n, n, seed=1)
     rows = sample_rows(n)
-    book.add_set("mp4096", lambda: (A_h, B_h), rows, kind="minplus")
+    book.add_set("mp4096", lambda A=A_h, B=B_h: (A, B), rows, kind="minplus")
     dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
     outs = [torch.empty((n, n), dtype=torch.int32, device="cuda") for _ in budgets]
     ws = torch.empty((max(budgets) * n * n * 4,), dtype=torch.uint8, device="cuda")
@@ -661,11 +661,26 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     dC = torch.empty((256, 256), dtype=torch.float64, device="cuda")
     ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC, None, 0,
                                                     sp), 50)
-    book.add_set("n256", lambda: (A, B), np.arange(256))
+    book.add_set("n256", lambda A=A, B=B: (A, B), np.arange(256))
     out["fp64_n256_budget0"] = {"ms": ms, "gops": 2 * 256 ** 3 / (ms * 1e-3) / 1e9,
                                 "roofline": _roof("fp64", 2 * 256 ** 3 / (ms * 1e-3) / 1e12, fp64_peak,
                                                   "TFLOP/s", fp64_src)}
     book.add("n256", out["fp64_n256_budget0"], "error", dC.cpu().numpy())
+    # the same product in the stream-K form (Fig. tar-mm) with the budget of
+    # its per-CTA partial tiles
+    for b in (1 << 20, 1 << 22, 1 << 24):
+        p = mmsr.mm_plan_query(mmsr.MM_SR_PLUS_TIMES_F64, -1, 256, 256, 256, b)
+        if p.kernel == 4:
+            w = int(p.workspace_used)
+            ws = torch.empty((w,), dtype=torch.uint8, device="cuda")
+            ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC,
+                                                            ws, w, sp), 50)
+            out["fp64_n256_streamk"] = {"ms": ms, "gops": 2 * 256 ** 3 / (ms * 1e-3) / 1e9, "workspace_bytes": w,
+                                        "roofline": _roof("fp64", 2 * 256 ** 3 / (ms * 1e-3) / 1e12, fp64_peak,
+                                                          "TFLOP/s", fp64_src)}
+            book.add("n256", out["fp64_n256_streamk"], "error", dC.cpu().numpy())
+            del ws
+            break
     n = 8192
     rows = sample_rows(n)
     A, B = inputs.uniform_f64(n, n, n, seed=2)
@@ -679,7 +694,7 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     del dA, dB, dC
     # FP32 mode n=8192, normal(0,1), seed 2: bf16x3 split products on tcgen05
     A, B = inputs.normal_f32(n, n, n, seed=2)
-    book.add_set("n8192_f32", lambda: (A, B), rows)
+    book.add_set("n8192_f32", lambda A=A, B=B: (A, B), rows)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
     sr = mmsr.MM_SR_PLUS_TIMES_F32
@@ -702,7 +717,7 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     torch.cuda.empty_cache()
     # FP64-accuracy mode at n = 8192 (uniform[-1,1], seed 3)
     A, B = inputs.uniform_f64(n, n, n, seed=3)
-    book.add_set("n8192_f64", lambda: (A, B), rows)
+    book.add_set("n8192_f64", lambda A=A, B=B: (A, B), rows)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
     sr = mmsr.MM_SR_PLUS_TIMES_F64ACC
@@ -779,7 +794,7 @@ def extras_strassen(mmsr, lib, torch, sp, ctypes, book, A_sq, B_sq, rows, bf16, 
                                       n, n, n, dA64, dB64, dC64, rows, bf16, bf16_src, reps=2)
     del dC64
     torch.cuda.empty_cache()
-    book.add_set("sq32", lambda: (A_sq.astype(np.float32), B_sq.astype(np.float32)), rows)
+    book.add_set("sq32", lambda A=A_sq, B=B_sq: (A.astype(np.float32), B.astype(np.float32)), rows)
     dA, dB = dA64.float(), dB64.float()
     del dA64, dB64
     dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
@@ -826,8 +841,8 @@ def extras_strassen_rect(mmsr, lib, torch, sp, ctypes, book, bf16, bf16_src):
     m, k, n = 12288, 16384, 8192
     A, B = inputs.uniform_f64(m, k, n, seed=3)
     rows = sample_rows(m)
-    book.add_set("rect64", lambda: (A, B), rows)
-    book.add_set("rect32", lambda: (A.astype(np.float32), B.astype(np.float32)), rows)
+    book.add_set("rect64", lambda A=A, B=B: (A, B), rows)
+    book.add_set("rect32", lambda A=A, B=B: (A.astype(np.float32), B.astype(np.float32)), rows)
     res = {}
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((m, n), dtype=torch.float64, device="cuda")

@@ -92,6 +92,13 @@ int plan_semiring(int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_pla
       return MM_ERR_ARG;
   }
   p->tile_k = tile_k;
+  if (sr == MM_SR_PLUS_TIMES_F64 && dfma_streamk_wanted(m, n, k) && budget >= dfma_streamk_bytes(m, n, k)) {
+    // few tiles and room for the per-CTA partial tiles: the stream-K form
+    p->tile_m = 32; p->tile_n = 32; p->tile_k = 8; p->kernel = 4;
+    p->split_k = 1;
+    p->workspace_used = (int64_t)dfma_streamk_bytes(m, n, k);
+    return MM_OK;
+  }
   int s = 1, kbs = 0;
   int64_t used = 0;
   split_for_budget(m, n, k, tile_k, acc_bytes(sr), budget, &s, &kbs, &used);
@@ -153,6 +160,11 @@ int run_semiring(int sr, int64_t m, int64_t n, int64_t k, const void* A, const v
       break;
     }
     case MM_SR_PLUS_TIMES_F64: {
+      if (p.kernel == 4) {
+        e = launch_dfma_streamk(m, n, k, static_cast<const double*>(A), static_cast<const double*>(B),
+                                static_cast<double*>(C), ws, st);
+        break;
+      }
       double* W = s > 1 ? static_cast<double*>(ws) : nullptr;
       e = launch_dfma_leaf(m, n, k, static_cast<const double*>(A), static_cast<const double*>(B),
                            static_cast<double*>(C), W, s, kbs, st);

@@ -110,5 +110,12 @@ cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, c
 cudaError_t launch_sum_reduce_f64(int64_t count, double* C, const double* W, int parts,
                                   cudaStream_t st);
 int dfma_tile_k();
+// Stream-K form of the FP64 leaf (Fig. tar-mm): workspace it needs (per-CTA
+// partial slots and per-tile counters), whether the product is small enough
+// to want it, and its launch (asynchronous on `st`, `ws` 16-byte aligned).
+size_t dfma_streamk_bytes(int64_t m, int64_t n, int64_t k);
+bool dfma_streamk_wanted(int64_t m, int64_t n, int64_t k);
+cudaError_t launch_dfma_streamk(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
+                                void* ws, cudaStream_t st);
 
 }  // namespace mmsr

@@ -223,9 +223,201 @@ __global__ void __launch_bounds__(256) sum_reduce_f64_kernel(int64_t count, doub
   }
 }
 
+// ------------------------------------------------------------ stream-K
+// The zero-temporary k-parallel form of Fig. tar-mm / Theorem tar-mm for
+// the FP64 semiring: a grid of P persistent CTAs takes equal contiguous
+// ranges of the (tile, k-block) iteration space, tile-major.  A tile covered
+// by one CTA is written straight to C; a tile shared by several CTAs has each
+// of them store its register tile in a per-CTA slot (at most two per CTA:
+// its first and its last segment, the p b^2 temporaries of the theorem) and
+// count itself on the tile's counter.  The CTA that arrives last folds the
+// slots into C in k order (contributor order), so the sum -- and the result
+// -- is the same whatever order the CTAs finish in; nothing waits.
+constexpr int SKT = 32, SKBK = 8, SK_THREADS = 256, SK_LDA = SKBK + 2;
+
+__device__ __forceinline__ int64_t sk_begin(int64_t c, int64_t total, int P) { return total * c / P; }
+
+// The CTA whose range holds iteration i.
+__device__ __forceinline__ int sk_owner(int64_t i, int64_t total, int P) {
+  int64_t c = i * P / total;
+  while (c + 1 < P && sk_begin(c + 1, total, P) <= i) ++c;
+  while (c > 0 && sk_begin(c, total, P) > i) --c;
+  return (int)c;
+}
+
+__device__ __forceinline__ void sk_load(double (*As)[SK_LDA], double (*Bs)[SKT], const double* __restrict__ A,
+                                        const double* __restrict__ B, int64_t m, int64_t n, int64_t k,
+                                        int64_t i0, int64_t j0, int64_t k0, bool vec, int tid) {
+  // A: 32 rows x 8 doubles = 128 chunks of 2; B: 8 rows x 32 doubles = 128
+  // chunks of 2 -- one chunk of each per thread of the first half / second half
+  if (tid < 128) {
+    const int row = tid >> 2, c2 = tid & 3;
+    const int64_t gi = i0 + row, gk = k0 + c2 * 2;
+    double* dst = &As[row][c2 * 2];
+    if (vec && gi < m && gk + 2 <= k) {
+      cp_async16(dst, A + gi * k + gk);
+    } else {
+      dst[0] = (gi < m && gk < k) ? A[gi * k + gk] : 0.0;
+      dst[1] = (gi < m && gk + 1 < k) ? A[gi * k + gk + 1] : 0.0;
+    }
+  } else {
+    const int u = tid - 128, row = u >> 4, c2 = u & 15;
+    const int64_t gk = k0 + row, gj = j0 + c2 * 2;
+    double* dst = &Bs[row][c2 * 2];
+    if (vec && gk < k && gj + 2 <= n) {
+      cp_async16(dst, B + gk * n + gj);
+    } else {
+      dst[0] = (gk < k && gj < n) ? B[gk * n + gj] : 0.0;
+      dst[1] = (gk < k && gj + 1 < n) ? B[gk * n + gj + 1] : 0.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SK_THREADS)
+    dfma_streamk_kernel(int64_t m, int64_t n, int64_t k, const double* __restrict__ A, const double* __restrict__ B,
+                        double* __restrict__ C, double* __restrict__ slots, int* __restrict__ counters,
+                        int64_t tiles_n, int64_t ki, int64_t total, int P, bool vec) {
+  __shared__ __align__(16) double As[2][SKT][SK_LDA];
+  __shared__ __align__(16) double Bs[2][SKBK][SKT];
+  __shared__ int s_last, s_first_c, s_last_c;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // outputs (2 ty + i, 2 tx + j)
+  const int c = blockIdx.x;
+  int64_t it = sk_begin(c, total, P);
+  const int64_t end = sk_begin(c + 1, total, P);
+  for (int seg = 0; it < end; ++seg) {
+    const int64_t t = it / ki, j0 = it - t * ki;
+    const int64_t j1 = min(ki, j0 + (end - it));
+    const int64_t ti = t / tiles_n;
+    const int64_t i0 = ti * SKT, c0 = (t - ti * tiles_n) * SKT;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    __syncthreads();  // the previous segment's readers are done with the stages
+    sk_load(As[0], Bs[0], A, B, m, n, k, i0, c0, j0 * SKBK, vec, tid);
+    cp_async_commit();
+    for (int64_t j = j0; j < j1; ++j) {
+      const int cur = (int)((j - j0) & 1);
+      if (j + 1 < j1) sk_load(As[cur ^ 1], Bs[cur ^ 1], A, B, m, n, k, i0, c0, (j + 1) * SKBK, vec, tid);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < SKBK; kk += 2) {
+        const double2 a0 = *reinterpret_cast<const double2*>(&As[cur][2 * ty][kk]);
+        const double2 a1 = *reinterpret_cast<const double2*>(&As[cur][2 * ty + 1][kk]);
+        const double2 b0 = *reinterpret_cast<const double2*>(&Bs[cur][kk][2 * tx]);
+        const double2 b1 = *reinterpret_cast<const double2*>(&Bs[cur][kk + 1][2 * tx]);
+        acc[0][0] = fma(a0.x, b0.x, acc[0][0]);
+        acc[0][1] = fma(a0.x, b0.y, acc[0][1]);
+        acc[1][0] = fma(a1.x, b0.x, acc[1][0]);
+        acc[1][1] = fma(a1.x, b0.y, acc[1][1]);
+        acc[0][0] = fma(a0.y, b1.x, acc[0][0]);
+        acc[0][1] = fma(a0.y, b1.y, acc[0][1]);
+        acc[1][0] = fma(a1.y, b1.x, acc[1][0]);
+        acc[1][1] = fma(a1.y, b1.y, acc[1][1]);
+      }
+      __syncthreads();  // stage `cur` is refilled two iterations on
+    }
+    cp_async_wait<0>();
+    const bool whole = (j0 == 0 && j1 == ki);
+    if (whole) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int64_t gi = i0 + 2 * ty + i, gj = c0 + 2 * tx + jj;
+          if (gi < m && gj < n) C[gi * n + gj] = acc[i][jj];
+        }
+    } else {
+      double* slot = slots + ((int64_t)c * 2 + (seg == 0 ? 0 : 1)) * (SKT * SKT);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        *reinterpret_cast<double2*>(slot + (2 * ty + i) * SKT + 2 * tx) = make_double2(acc[i][0], acc[i][1]);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        const int cf = sk_owner(t * ki, total, P), cl = sk_owner(t * ki + ki - 1, total, P);
+        const int prev = atomicAdd(&counters[t], 1);
+        s_last = prev == cl - cf;
+        s_first_c = cf;
+        s_last_c = cl;
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        double sum[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int q = s_first_c; q <= s_last_c; ++q) {
+          // contributor q keeps tile t in slot 0 when t is its first segment
+          const int which = (sk_begin(q, total, P) / ki == t) ? 0 : 1;
+          const double* src = slots + ((int64_t)q * 2 + which) * (SKT * SKT);
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const double2 v = __ldcg(reinterpret_cast<const double2*>(src + (2 * ty + i) * SKT + 2 * tx));
+            sum[i][0] += v.x;
+            sum[i][1] += v.y;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj) {
+            const int64_t gi = i0 + 2 * ty + i, gj = c0 + 2 * tx + jj;
+            if (gi < m && gj < n) C[gi * n + gj] = sum[i][jj];
+          }
+        if (tid == 0) counters[t] = 0;
+      }
+    }
+    it = t * ki + j1;
+  }
+}
+
+// Stream-K geometry of one product on this device.
+struct SkGeom {
+  int64_t tiles_n, tiles, ki, total;
+  int P;
+};
+
+SkGeom sk_geom(int64_t m, int64_t n, int64_t k) {
+  SkGeom g;
+  g.tiles_n = (n + SKT - 1) / SKT;
+  g.tiles = ((m + SKT - 1) / SKT) * g.tiles_n;
+  g.ki = (k + SKBK - 1) / SKBK;
+  g.total = g.tiles * g.ki;
+  // four CTAs per SM, and at least four k-blocks per CTA
+  int64_t P = (int64_t)num_sms() * 4;
+  if (P > g.total / 4) P = g.total / 4;
+  if (P < 1) P = 1;
+  g.P = (int)P;
+  return g;
+}
+
 }  // namespace
 
 int dfma_tile_k() { return BK; }
+
+size_t dfma_streamk_bytes(int64_t m, int64_t n, int64_t k) {
+  const SkGeom g = sk_geom(m, n, k);
+  return (size_t)g.P * 2 * SKT * SKT * sizeof(double) + (size_t)((g.tiles * 4 + 255) / 256 * 256);
+}
+
+bool dfma_streamk_wanted(int64_t m, int64_t n, int64_t k) {
+  // only where the 64 x 64 grid fills less than four waves of two CTAs per
+  // SM, and the k-split has room (index arithmetic in int64 without overflow)
+  const int64_t tiles64 = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  const SkGeom g = sk_geom(m, n, k);
+  return k > 0 && tiles64 < 8 * (int64_t)num_sms() && g.total < ((int64_t)1 << 40) && g.ki >= 4;
+}
+
+cudaError_t launch_dfma_streamk(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
+                                void* ws, cudaStream_t st) {
+  const SkGeom g = sk_geom(m, n, k);
+  double* slots = static_cast<double*>(ws);
+  int* counters = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + (size_t)g.P * 2 * SKT * SKT * sizeof(double));
+  TraceScope tr(kTrDfmaLeaf, st);
+  MMSR_CUDA_TRY(cudaMemsetAsync(counters, 0, (size_t)g.tiles * 4, st));
+  const bool vec = (k % 2 == 0) && (n % 2 == 0) && aligned16(A) && aligned16(B);
+  dfma_streamk_kernel<<<(unsigned)g.P, SK_THREADS, 0, st>>>(m, n, k, A, B, C, slots, counters, g.tiles_n, g.ki,
+                                                            g.total, g.P, vec);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dfma_leaf(int64_t m, int64_t n, int64_t k, const double* A, const double* B,
                              double* C, double* W, int s, int kb_per_slice, cudaStream_t st) {

@@ -77,3 +77,34 @@ def test_bench_row_sample_matches_the_tests_row_sample():
         r = bench.sample_rows(m)
         assert r[0] == 0 and r[-1] == m - 1 and np.all(np.diff(r) > 0)
         assert {m // 2 - 1, m // 2, m // 16 - 1, m // 16}.issubset(set(r.tolist()))
+
+
+def test_error_book_keeps_each_input_set():
+    """Sampled-row errors are computed after the GPU phase from the inputs
+    registered for each set, even when the caller reuses its variable names
+    for the next workload (the sets must hold their own arrays)."""
+    import numpy as np
+
+    import oracle
+
+    book = bench.ErrBook()
+    rng = np.random.default_rng(0)
+    A = rng.uniform(-1, 1, (8, 5))
+    B = rng.uniform(-1, 1, (5, 6))
+    rows = np.array([0, 3, 7])
+    book.add_set("first", lambda A=A, B=B: (A, B), rows)
+    rec1 = {}
+    book.add("first", rec1, "error", (A @ B)[rows] * (1 + 1e-9))
+    A = rng.uniform(-1, 1, (4, 9))  # the next workload reuses the names
+    B = rng.uniform(-1, 1, (9, 3))
+    book.add_set("second", lambda A=A, B=B: (A, B), np.arange(4))
+    rec2 = {}
+    book.add("second", rec2, "error", A @ B)
+    Ai = rng.integers(0, 1001, (6, 6)).astype(np.int32)
+    book.add_set("mp", lambda A=Ai: (A, A), np.arange(6), kind="minplus")
+    rec3 = {}
+    book.add("mp", rec3, "exact", oracle.mm_minplus(Ai, Ai))
+    book.resolve(oracle)
+    assert abs(rec1["error"] - 1e-9) < 1e-12
+    assert rec2["error"] < 1e-14
+    assert rec3["exact"] is True

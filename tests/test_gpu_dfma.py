@@ -60,3 +60,53 @@ def test_k_zero_writes_zero():
     mmsr.mm_semiring(SR, 3, 4, 0, empty((3, 1), torch.float64), empty((1, 4), torch.float64), dC)
     torch.cuda.synchronize()
     assert np.all(dC.cpu().numpy() == 0.0)
+
+
+def _streamk_budget(m, n, k):
+    """Smallest budget for which the planner picks the stream-K form (the
+    per-CTA partial tiles plus one counter per tile), or None when the
+    product is too large or too shallow for it."""
+    for b in (1 << 20, 1 << 22, 1 << 24, 1 << 26):
+        p = mmsr.mm_plan_query(SR, -1, m, n, k, b)
+        if p.kernel == 4:
+            return int(p.workspace_used)
+    return None
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 256, 256), (1, 1, 100), (33, 65, 77), (130, 257, 1000), (100, 40, 4096),
+                                   (512, 512, 64), (600, 700, 300)])
+def test_streamk_form_matches_oracle(m, n, k):
+    # the zero-temporary k-parallel form (Fig. tar-mm): per-CTA partial tiles
+    # folded in k order by the last CTA to arrive; ragged tiles and k tails
+    w = _streamk_budget(m, n, k)
+    assert w is not None
+    A, B = inputs.uniform_f64(m, k, n, seed=m + 3 * n + 7 * k)
+    C1 = run(A, B, w)
+    assert rel_fro(C1, oracle.mm_f64(A, B)) <= TOL
+    # fixed summation order: identical on a second run
+    np.testing.assert_array_equal(run(A, B, w), C1)
+
+
+def test_streamk_small_integers_exact():
+    m, n, k = 200, 190, 3000
+    A, B = inputs.small_int(m, k, n, seed=43)
+    w = _streamk_budget(m, n, k)
+    np.testing.assert_array_equal(run(A, B, w), oracle.mm_f64(A, B))
+
+
+def test_streamk_n256_workload():
+    # the n = 256 uniform[-1,1] workload (seed 0) in the stream-K form,
+    # beside the budget-0 path of the same product
+    A, B = inputs.uniform_f64(256, 256, 256, seed=0)
+    w = _streamk_budget(256, 256, 256)
+    assert w <= 8 << 20  # p b^2: the partial tiles of a few hundred CTAs
+    ref = oracle.mm_f64(A, B)
+    assert rel_fro(run(A, B, w), ref) <= TOL
+    assert rel_fro(run(A, B, 0), ref) <= TOL
+
+
+def test_streamk_not_taken_for_large_grids_or_small_budgets():
+    assert mmsr.mm_plan_query(SR, -1, 4096, 4096, 4096, 1 << 30).kernel != 4
+    w = _streamk_budget(256, 256, 256)
+    assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, w - 1).kernel != 4
+    assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, 0).kernel != 4
