@@ -5,6 +5,8 @@
 // k-serial CO2 order inside each k-slice (Fig. mm-n2); slices beyond the first
 // write m x n FP64 buffers and the reduction adds them into C in slice order
 // (the madd of CO3, Fig. mm-n3), so results are deterministic run to run.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace mmsr {
@@ -381,10 +383,13 @@ SkGeom sk_geom(int64_t m, int64_t n, int64_t k) {
   g.tiles = ((m + SKT - 1) / SKT) * g.tiles_n;
   g.ki = (k + SKBK - 1) / SKBK;
   g.total = g.tiles * g.ki;
-  // four CTAs per SM, and at least four k-blocks per CTA
-  int64_t P = (int64_t)num_sms() * 4;
-  if (P > g.total / 4) P = g.total / 4;
-  if (P < 1) P = 1;
+  // the same number of CTAs on every SM (up to four), each with at least
+  // four k-blocks where the product has that many: every SM then gets the
+  // same share of the iteration space, to within one k-block per CTA
+  const int64_t sms = num_sms();
+  int64_t per = g.total / (4 * sms);
+  if (per > 4) per = 4;
+  int64_t P = per >= 1 ? per * sms : std::max<int64_t>(1, std::min<int64_t>(sms, g.total / 4));
   g.P = (int)P;
   return g;
 }

@@ -151,6 +151,36 @@ __global__ void __launch_bounds__(256) fill_inf_kernel(int32_t* __restrict__ C, 
     C[e] = kInf;
 }
 
+// The same zero-workspace form for the exact 32-bit leaf, over (128 x 128
+// tile, 32-wide k-block) units; it runs when the packed leaf did not.
+__global__ void __launch_bounds__(THREADS, 2)
+    minplus32_streamk_kernel(int64_t m, int64_t n, int64_t k, const int32_t* __restrict__ A,
+                             const int32_t* __restrict__ B, int32_t* __restrict__ C, bool vec, int slot,
+                             int64_t units, int64_t nkb, int64_t tiles_n) {
+  if (slot >= 0 && pack_verdict(slot) == 1) return;
+  extern __shared__ __align__(16) int32_t smem[];
+  const int64_t G = gridDim.x;
+  int64_t u = units * blockIdx.x / G;
+  const int64_t end = units * (blockIdx.x + 1) / G;
+  while (u < end) {
+    const int64_t tile = u / nkb, b0 = u - tile * nkb;
+    const int64_t b1 = min(nkb, b0 + (end - u));
+    const bool whole = (b0 == 0 && b1 == nkb);
+    minplus32_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, (tile / tiles_n) * BM, (tile % tiles_n) * BN, b0,
+                   (int)(b1 - b0), vec, (int)threadIdx.x, smem, SyncCta(), !whole);
+    __syncthreads();  // the next segment restages shared memory
+    u += b1 - b0;
+  }
+}
+
+// C = +inf before the 32-bit stream-K merges (skipped when the packed leaf ran).
+__global__ void __launch_bounds__(256) fill_inf32_kernel(int32_t* __restrict__ C, int64_t count, int slot) {
+  if (slot >= 0 && pack_verdict(slot) == 1) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    C[e] = kInf;
+}
+
 __global__ void __launch_bounds__(THREADS, 2)
     minplus_leaf_kernel(int64_t m, int64_t n, int64_t k, const int32_t* __restrict__ A,
                         const int32_t* __restrict__ B, int32_t* __restrict__ C,
@@ -211,8 +241,9 @@ int g_streamk_mode = 1;  // 1: stream-K for unsplit packed products with few wav
 cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* A,
                                 const int32_t* B, int32_t* C, int32_t* W, int s,
                                 int kb_per_slice, cudaStream_t st) {
-  static std::atomic<uint64_t> conf32{0}, conf16{0}, conf16s{0};
+  static std::atomic<uint64_t> conf32{0}, conf32s{0}, conf16{0}, conf16s{0};
   MMSR_CUDA_TRY(smem_limit_once(minplus_leaf_kernel, SMEM_BYTES, conf32));
+  MMSR_CUDA_TRY(smem_limit_once(minplus32_streamk_kernel, SMEM_BYTES, conf32s));
   MMSR_CUDA_TRY(smem_limit_once(minplus16_leaf_kernel, PSMEM_BYTES, conf16));
   MMSR_CUDA_TRY(smem_limit_once(minplus16_streamk_kernel, PSMEM_BYTES, conf16s));
   const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C) &&
@@ -269,6 +300,26 @@ cudaError_t launch_minplus_leaf(int64_t m, int64_t n, int64_t k, const int32_t* 
   }
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)s);
   TraceScope tr(kTrMinplusLeaf, st);
+  static std::atomic<int> resident32_cache{0};
+  int resident32 = resident32_cache.load(std::memory_order_relaxed);
+  if (!resident32) {
+    int per_sm = 2;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, minplus32_streamk_kernel, THREADS, SMEM_BYTES);
+    resident32 = num_sms() * (per_sm > 0 ? per_sm : 1);
+    resident32_cache.store(resident32, std::memory_order_relaxed);
+  }
+  const int64_t tiles32 = (int64_t)grid.x * grid.y;
+  const int64_t nkb = (k + BK - 1) / BK;
+  if (s == 1 && g_streamk_mode && k > 0 && tiles32 < 4 * (int64_t)resident32) {
+    // the zero-workspace k-parallel form for the 32-bit leaf (its kernels
+    // exit at once when the packed leaf ran)
+    fill_inf32_kernel<<<(unsigned)(num_sms() * 4), 256, 0, st>>>(C, m * n, slot);
+    const int64_t units = tiles32 * nkb;
+    const int64_t G = std::min<int64_t>(resident32, units);
+    minplus32_streamk_kernel<<<(unsigned)G, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, vec, slot, units, nkb,
+                                                                       (int64_t)grid.x);
+    return cudaGetLastError();
+  }
   minplus_leaf_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(m, n, k, A, B, C, W, kb_per_slice, vec,
                                                          slot);
   return cudaGetLastError();

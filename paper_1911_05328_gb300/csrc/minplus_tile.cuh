@@ -280,12 +280,14 @@ __device__ __forceinline__ void minplus16_tile(const int32_t* __restrict__ A, co
 
 // One 128 x 128 output tile of the 32-bit leaf over k-blocks
 // [kb_begin, kb_begin + nkb), executed by 256 threads that synchronise with `bar`.
+// With `merge` the tile is folded into C by an atomic min (C must already
+// hold the sentinel or a partial result), otherwise it is stored.
 template <class Bar>
 __device__ __forceinline__ void minplus32_tile(const int32_t* __restrict__ A, const int32_t* __restrict__ B,
                                                int32_t* __restrict__ C, int32_t* __restrict__ W, int z,
                                                int64_t m, int64_t n, int64_t k,
                                                int64_t i0, int64_t j0, int64_t kb_begin, int nkb,
-                                               bool vec, int tid, int32_t* smem, Bar bar) {
+                                               bool vec, int tid, int32_t* smem, Bar bar, bool merge = false) {
   int32_t* As = smem;
   int32_t* Bs = smem + SMEM_A;
   const int tx = tid & 15, ty = tid >> 4;
@@ -353,7 +355,11 @@ __device__ __forceinline__ void minplus32_tile(const int32_t* __restrict__ A, co
     for (int h = 0; h < 2; ++h) {
       const int64_t gj = j0 + h * 64 + tx * 4;
       int32_t* dst = out + gi * n + gj;
-      if (vec && gj + 4 <= n) {
+      if (merge) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (gj + e < n) atomicMin(reinterpret_cast<unsigned int*>(dst + e), acc[i][h * 4 + e]);
+      } else if (vec && gj + 4 <= n) {
         *reinterpret_cast<uint4*>(dst) =
             make_uint4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
       } else {

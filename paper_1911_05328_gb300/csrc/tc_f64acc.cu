@@ -44,14 +44,33 @@ __device__ int g_f64acc_status;
 __device__ int g_f64acc_skip_signal;
 
 constexpr int kSlices = 7, kDigitBits = 7, kGroups = 7;
-constexpr int BM = 128, BN = 64, BK = 32, STAGES = 2, CHUNK = 8;  // CHUNK k-blocks per drain
+// GEMM k-block (16, 32 or 64 bf16: 32-, 64- or 128-byte swizzled rows), ring
+// depth, and the k-length of one exact TMEM chunk.
+#ifndef MMSR_FA_BK
+#define MMSR_FA_BK 32
+#endif
+#ifndef MMSR_FA_STAGES
+#define MMSR_FA_STAGES 2
+#endif
+#ifndef MMSR_FA_CHUNK_K
+#define MMSR_FA_CHUNK_K 256
+#endif
+constexpr int BM = 128, BN = 64, BK = MMSR_FA_BK, STAGES = MMSR_FA_STAGES;
+constexpr int CHUNK = MMSR_FA_CHUNK_K / BK;  // k-blocks per drain
+constexpr int KSTEPS = BK / 16;              // 16-deep MMA k-steps per k-block
+constexpr int KALIGN = BK > 32 ? BK : 32;    // k alignment of the slices (the split kernels' 32-k tiles)
+static_assert(BK == 16 || BK == 32 || BK == 64, "k-block / swizzle");
+static_assert(CHUNK >= 1 && CHUNK * BK == MMSR_FA_CHUNK_K, "chunks are whole k-blocks");
 static_assert((int64_t)CHUNK * BK * 36864 < (1 << 24), "chunk sums must stay exact in FP32");
 constexpr int kDrain = 8, kThreads = 64 + 32 * kDrain;
 constexpr uint32_t A_TILE = BM * BK * 2, B_TILE = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = kSlices * (A_TILE + B_TILE);
 constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+static_assert(SMEM <= 232448, "shared memory of one CTA");
 constexpr uint32_t TMEM_COLS = 512;  // 7 groups x 64 columns used
-static_assert(BK == 32, "the MMA issue loop covers two 16-deep k-steps per k-block");
+__host__ __device__ constexpr uint32_t fa_desc_hi() {
+  return BK == 16 ? tc::desc_hi_sw32() : (BK == 32 ? tc::desc_hi_sw64() : tc::desc_hi_sw128());
+}
 
 // ----------------------------------------------------------- split kernels
 // The split passes work on the bit patterns of the (finite) FP64 inputs in
@@ -343,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_f16(BM, BN, 1);
-      constexpr uint32_t dhi = tc::desc_hi_sw64();
+      constexpr uint32_t dhi = fa_desc_hi();
       // The products are small (128 x 64 x 16, ~40 tensor-core cycles), so
       // the issue loop is kept lean: descriptors are one 32-bit add of a
       // compile-time offset to a per-stage base word.
@@ -371,37 +390,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::fence_after_sync();
           const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
           const uint32_t a_lo = tc::desc_lo(base), b_lo = tc::desc_lo(base + kSlices * A_TILE);
-          if (it == first_it) {
-            // first k-block of a chunk: overwrite each group, after the
-            // drain has read the previous chunk's G_g
+          // the first k-step of a chunk overwrites each group, after the
+          // drain has read the previous chunk's G_g; the chunk's last k-step
+          // signals each group as soon as its last product is issued
+          const bool chunk_first = it == first_it, chunk_last = it == last - 1;
+#pragma unroll
+          for (int kk = 0; kk < KSTEPS; ++kk) {
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) {
-              if (c >= 1 && !aborted) {
+              if (kk == 0 && chunk_first && c >= 1 && !aborted) {
                 if (!tc::mbar_wait(&acc_empty[g], (c - 1) & 1u, abort_flag, &g_f64acc_status)) aborted = true;
                 tc::fence_after_sync();
               }
-              if (!aborted) issue_group(a_lo, b_lo, 0, g, true);
-            }
-            if (!aborted) {
-#pragma unroll
-              for (int g = 0; g < kGroups; ++g) {
-                issue_group(a_lo, b_lo, 1, g, false);
-                if (it == last - 1) tc::mma_commit(&acc_full[g]);
+              if (!aborted) {
+                issue_group(a_lo, b_lo, kk, g, kk == 0 && chunk_first);
+                if (kk == KSTEPS - 1 && chunk_last) tc::mma_commit(&acc_full[g]);
               }
-            }
-          } else {
-#pragma unroll
-            for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 0, g, false);
-            if (it == last - 1) {
-              // the chunk's last product of group g is issued: signal it
-#pragma unroll
-              for (int g = 0; g < kGroups; ++g) {
-                issue_group(a_lo, b_lo, 1, g, false);
-                tc::mma_commit(&acc_full[g]);
-              }
-            } else {
-#pragma unroll
-              for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 1, g, false);
             }
           }
           tc::mma_commit(&empty[s]);
@@ -487,7 +491,7 @@ struct F64AccLayout {
 
 F64AccLayout layout(int64_t m, int64_t n, int64_t k, int64_t batches = 1) {
   F64AccLayout L;
-  L.Kp = align_up(k > 0 ? k : 1, BK);
+  L.Kp = align_up(k > 0 ? k : 1, KALIGN);
   L.a_bytes = align_up((int64_t)kSlices * batches * m * L.Kp * 2, 1024);
   L.b_bytes = align_up((int64_t)kSlices * batches * n * L.Kp * 2, 1024);
   L.off_b = L.a_bytes;

@@ -130,6 +130,8 @@ __device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) {
 }
 constexpr uint32_t desc_hi_sw128() { return (1024u >> 4) | (1u << 14) | (2u << 29); }
 constexpr uint32_t desc_hi_sw64() { return (512u >> 4) | (1u << 14) | (4u << 29); }
+// 32-byte swizzle: rows of 32 B (one 16-deep bf16 k-step), 8-row groups 256 B apart.
+constexpr uint32_t desc_hi_sw32() { return (256u >> 4) | (1u << 14) | (6u << 29); }
 __device__ __forceinline__ uint64_t desc_join(uint32_t lo, uint32_t hi) {
   return ((uint64_t)hi << 32) | lo;
 }

@@ -130,10 +130,11 @@ def test_full_size_workload_all_budgets():
 
 
 @pytest.mark.parametrize("m,n,k", [(4096, 4096, 4096), (333, 97, 4099), (1000, 700, 300), (129, 257, 17), (64, 64, 5000)])
-def test_streamk_zero_budget_matches(m, n, k):
+def test_streamk_zero_budget_matches(m, n, k, packed):
     # budget 0, few waves: the zero-workspace k-parallel form (register tiles
     # merged into C by atomic min) must equal the oracle bit for bit, and
-    # equal the plain k-serial leaf
+    # equal the plain k-serial leaf -- for the packed 2 x 16-bit leaf and for
+    # the exact 32-bit leaf
     A, B = inputs.tropical_i32(m, k, n, seed=m + 2 * n + 3 * k)
     mmsr.mm_set_option(mmsr.MM_OPT_MINPLUS_STREAMK, 1)
     C1 = run(A, B)
