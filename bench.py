@@ -4,8 +4,9 @@
 Headline workload: FP64-accuracy (+,x) matrix multiplication by
 Strassen-Winograd, square n = 16384, entries i.i.d. uniform[-1, 1] (seed 3;
 A drawn before B), HEADLINE_LEVELS recursion levels over the tensor-core leaf
-that sums seven 7-bit digit slices per operand (28 bf16 slice products, exact
-integer accumulation, one FP64 combination per output).  One step = one
+that sums integer digit slices of each operand (six 8-bit slices and 21 bf16
+slice products up to two levels, seven 7-bit slices and 28 products beyond;
+exact integer accumulation, one FP64 combination per output).  One step = one
 product through ``mm_strassen``; ``value`` = classic-equivalent 2 n^3 / step
 time (GOp/s).  The stated accuracy is a relative Frobenius error <= 1e-12 against
 the FP64 oracle, measured on 512 sampled rows.  Beside it, on the same inputs
@@ -165,10 +166,18 @@ def ncu_traffic(kernel_files, key):
 F64ACC_SOURCES = ["tc_f64acc.cu", "tcgen05.cuh"]
 
 
+def f64acc_products(levels):
+    """bf16 slice products per leaf k-step of the FP64-accuracy scheme the
+    library picks at this Strassen depth (6 slices up to two levels, else 7)."""
+    return 21 if levels <= 2 else 28
+
+
 def bench_config(world, levels=HEADLINE_LEVELS):
     """The workload both arms report (the reference arm times a row sample of it)."""
+    sl = 6 if levels <= 2 else 7
     return {"workload": "fp64acc_strassen_winograd_L%d_n%d_uniform_seed%d" % (levels, N, SEED),
-            "semiring": "(+,x) FP64-accuracy (7 digit slices, 28 bf16 tensor-core products, exact sums)",
+            "semiring": "(+,x) FP64-accuracy (%d digit slices, %d bf16 tensor-core products, exact sums)"
+                        % (sl, f64acc_products(levels)),
             "n": N, "levels": levels, "variant": "Strassen-Winograd",
             "l2": "inputs larger than L2 (2 x 2 GiB FP64)",
             "parallelism": "replicas" if world > 1 else "single"}
@@ -407,9 +416,10 @@ def main():
     ops_per_step = 2.0 * N ** 3  # classic-equivalent
     value = world * ops_per_step * args.steps / (total_ms * 1e-3) / 1e9
     # dominant kernel: the leaf GEMM over all 7^L products (one batched launch
-    # per step); issued work = 28 bf16 slice products of every leaf
+    # per step); issued work = the 21 or 28 bf16 slice products of every leaf
     leaf = kernels.get("tc_f64acc", {"launches": 0, "ms": 0.0})
-    leaf_issued = 28 * 2.0 * (N >> L) ** 3 * 7 ** L * args.steps
+    products = 21 if plan.kernel == 7 else 28  # six- or seven-slice scheme (plan kernel id)
+    leaf_issued = products * 2.0 * (N >> L) ** 3 * 7 ** L * args.steps
     peaks, peak_src = measured_peaks()
     leaf_tflops = leaf_issued / (leaf["ms"] * 1e-3) / 1e12 if leaf["ms"] else 0.0
     sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
@@ -535,7 +545,7 @@ def main():
                      "frac_of_burst": leaf_tflops / peaks["bf16_tflops"],
                      "peak_source": "%s: bf16 dense, sustained (the leaf runs back to back inside "
                                     "seconds-long steps); burst %.1f" % (peak_src, peaks["bf16_tflops"]),
-                     "work": "28 bf16 products x 2 (n/2^L)^3 x 7^L issued FLOP per launch",
+                     "work": "%d bf16 products x 2 (n/2^L)^3 x 7^L issued FLOP per launch" % products,
                      "leaf_share_of_step": leaf["ms"] / total_ms if total_ms else None},
         "kernels": kernels,
         "gpu_launches": launches_total,
@@ -670,7 +680,7 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     # its per-CTA partial tiles
     for b in (1 << 20, 1 << 22, 1 << 24):
         p = mmsr.mm_plan_query(mmsr.MM_SR_PLUS_TIMES_F64, -1, 256, 256, 256, b)
-        if p.kernel == 4:
+        if p.kernel == 6:
             w = int(p.workspace_used)
             ws = torch.empty((w,), dtype=torch.uint8, device="cuda")
             ms = _time_call(torch, lambda: mmsr.mm_semiring(mmsr.MM_SR_PLUS_TIMES_F64, 256, 256, 256, dA, dB, dC,
@@ -721,7 +731,9 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
     sr = mmsr.MM_SR_PLUS_TIMES_F64ACC
-    wmin = int(mmsr.mm_plan_query(sr, -1, n, n, n, 0).workspace_min)
+    pl = mmsr.mm_plan_query(sr, -1, n, n, n, 0)
+    wmin = int(pl.workspace_min)
+    products = 21 if pl.kernel == 7 else 28
     ws = torch.empty((wmin,), dtype=torch.uint8, device="cuda")
     lib.mm_trace_enable(1)
     ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, wmin, sp), 4)
@@ -729,10 +741,10 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     kern = _trace(lib, ctypes)
     g = kern.get("tc_f64acc", {"launches": 1, "ms": 0.0})
     gemm_ms = g["ms"] / max(g["launches"], 1)
-    issued = 28 * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
+    issued = products * 2.0 * n ** 3 / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
     out["fp64acc_n8192"] = {
         "ms": ms, "gflops_useful": 2 * n ** 3 / (ms * 1e-3) / 1e9, "gemm_ms": gemm_ms, "kernels": kern,
-        "tensor_tflops_issued_28_slice_products": issued,
+        "tensor_tflops_issued": issued, "slice_products": products,
         "roofline": dict(_roof("tensor", issued, bf16["burst"], "TFLOP/s", bf16_src),
                          frac_of_sustained=issued / bf16["sustained"]),
         "workspace_bytes": wmin, "speedup_vs_fp64_dfma": out["fp64_dfma_n8192"]["ms"] / ms, "tolerance": 1e-12}
@@ -747,12 +759,12 @@ def _strassen_levels(mmsr, lib, torch, sp, ctypes, book, key, sr, m, n, k, dA, d
     """Time mm_strassen (Winograd) at each level on one product; record time,
     classic-equivalent GOp/s, workspace, the leaf launch's tensor roofline,
     the kernel split and the sampled-row error."""
-    products = 3 if sr == mmsr.MM_SR_PLUS_TIMES_F32 else 28
     leaf_name = "tc_bf16x3" if sr == mmsr.MM_SR_PLUS_TIMES_F32 else "tc_f64acc"
     eb = 4 if sr == mmsr.MM_SR_PLUS_TIMES_F32 else 8
     res = {}
     for L in levels:
         p = mmsr.mm_plan_query(sr, L, m, n, k, 0)
+        products = 3 if sr == mmsr.MM_SR_PLUS_TIMES_F32 else (21 if p.kernel == 7 else 28)
         ws = torch.empty((max(int(p.workspace_min), 16),), dtype=torch.uint8, device="cuda")
         fn = lambda: mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, m, n, k, dA, dB, dC, ws,
                                       int(p.workspace_min), sp)
@@ -772,7 +784,8 @@ def _strassen_levels(mmsr, lib, torch, sp, ctypes, book, key, sr, m, n, k, dA, d
         if leaf_ms > 0:
             issued = products * 2.0 * (m >> L) * (n >> L) * (k >> L) * 7 ** L / (leaf_ms * 1e-3) / 1e12
             rec["leaf_roofline"] = dict(_roof("tensor", issued, bf16["burst"], "TFLOP/s", bf16_src),
-                                        frac_of_sustained=issued / bf16["sustained"], kernel=leaf_name)
+                                        frac_of_sustained=issued / bf16["sustained"], kernel=leaf_name,
+                                        products_per_kstep=products)
             rec["leaf_share_of_time"] = leaf_ms / ms
         book.add(key, rec, "error", _rows_of(torch, dC, rows))
         res["L%d" % L] = rec

@@ -50,10 +50,12 @@ typedef enum {
    * Needs 4*(m*k + k*n) bytes of workspace for the split operands. */
   MM_SR_PLUS_TIMES_F32 = 1,
   /* (+, x) over FP64 in/out at FP64 accuracy: every row of A / column of B
-   * is scaled by a power of two and cut into seven 7-bit integer digit
-   * slices (bf16); the 28 slice products of digit order <= 6 run on tcgen05
-   * tensor cores with exact chunked integer accumulation, combined once in
-   * FP64.  Needs 14*(m+n)*Kp + 4*(m+n) + 8*n bytes of workspace
+   * is scaled by a power of two and cut into integer digit slices (bf16):
+   * six 8-bit slices (21 slice products of digit order <= 5) for a plain
+   * product, seven 7-bit slices (28 products) under three or four Strassen
+   * levels (see MM_OPT_F64ACC_SLICES).  The products run on tcgen05 tensor
+   * cores with exact chunked integer accumulation, combined once in FP64.
+   * Needs 2*S*(m+n)*Kp + 4*(m+n) + 8*n bytes of workspace for S slices
    * (Kp = k rounded up to 32); mm_plan_query reports it. */
   MM_SR_PLUS_TIMES_F64ACC = 2,
   /* (min, +) tropical semiring over int32 in [0, 2^30]; 2^30 is +infinity
@@ -83,7 +85,10 @@ typedef struct {
   int32_t split_k;          /* s: number of k slices (1 = k-serial, CO2-like) */
   int32_t levels;           /* Strassen levels (0 for mm_semiring)            */
   int32_t tile_m, tile_n, tile_k; /* CTA tile of the leaf kernel              */
-  int32_t kernel;           /* internal leaf-kernel id (diagnostic)           */
+  int32_t kernel;           /* leaf kernel: 0 FP64 DFMA, 1 (min,+), 2 FP32
+                               bf16x3, 3 FP64-accuracy (7 slices), 4 boolean,
+                               5 FP32 stream-K, 6 FP64 stream-K, 7 FP64-
+                               accuracy (6 slices)                            */
   int64_t workspace_used;   /* bytes of workspace the call touches            */
   int64_t workspace_min;    /* smallest budget for which the call is valid    */
 } mm_plan_t;
@@ -345,13 +350,20 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   wait runs out after 2 s and the call records MM_ERR_TIMEOUT (read with
  *   mm_last_device_status).  No fault is raised; the CTA quiesces and exits.
  *   0 disarms all three.  Needs a device (writes a device word).
+ *   MM_OPT_F64ACC_SLICES: digit scheme of the FP64-accuracy semiring.  0
+ *   (default) chooses by the Strassen levels above the leaves: six 8-bit
+ *   slices (21 bf16 products; scaled rounding to 2^-47) for plain products and
+ *   up to two levels, seven 7-bit slices (28 products; 2^-49) for three or
+ *   four levels, whose post-additions amplify leaf errors more.  6 or 7
+ *   forces a scheme.  Plans (and workspace sizes) follow the setting.
  * Returns MM_OK, MM_ERR_ARG, or MM_ERR_CUDA (arming the switch failed).
  */
 typedef enum {
   MM_OPT_MINPLUS_PACKED = 1,
   MM_OPT_MINPLUS_STREAMK = 2,
   MM_OPT_STRASSEN_TOP_F64 = 4,
-  MM_OPT_TEST_SKIP_SIGNAL = 5
+  MM_OPT_TEST_SKIP_SIGNAL = 5,
+  MM_OPT_F64ACC_SLICES = 6
 } mm_option_t;
 int mm_set_option(int option, int value);
 

@@ -94,7 +94,7 @@ int plan_semiring(int sr, int64_t m, int64_t n, int64_t k, size_t budget, mm_pla
   p->tile_k = tile_k;
   if (sr == MM_SR_PLUS_TIMES_F64 && dfma_streamk_wanted(m, n, k) && budget >= dfma_streamk_bytes(m, n, k)) {
     // few tiles and room for the per-CTA partial tiles: the stream-K form
-    p->tile_m = 32; p->tile_n = 32; p->tile_k = 8; p->kernel = 4;
+    p->tile_m = 32; p->tile_n = 32; p->tile_k = 8; p->kernel = 6;
     p->split_k = 1;
     p->workspace_used = (int64_t)dfma_streamk_bytes(m, n, k);
     return MM_OK;
@@ -160,7 +160,7 @@ int run_semiring(int sr, int64_t m, int64_t n, int64_t k, const void* A, const v
       break;
     }
     case MM_SR_PLUS_TIMES_F64: {
-      if (p.kernel == 4) {
+      if (p.kernel == 6) {
         e = launch_dfma_streamk(m, n, k, static_cast<const double*>(A), static_cast<const double*>(B),
                                 static_cast<double*>(C), ws, st);
         break;
@@ -314,6 +314,10 @@ int mm_set_option(int option, int value) {
     case MM_OPT_MINPLUS_STREAMK:
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_streamk_mode = value;
+      return MM_OK;
+    case MM_OPT_F64ACC_SLICES:
+      if (value != 0 && value != 6 && value != 7) return MM_ERR_ARG;
+      g_f64acc_slices = value;
       return MM_OK;
     case MM_OPT_STRASSEN_TOP_F64:
       if (value != 0 && value != 1) return MM_ERR_ARG;

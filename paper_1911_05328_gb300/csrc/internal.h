@@ -40,16 +40,20 @@ int plan_orand(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
 int run_orand(int64_t m, int64_t n, int64_t k, const uint8_t* A, const uint8_t* B, uint8_t* C,
               void* ws, size_t ws_bytes, cudaStream_t st);
 
-// FP64-accuracy mode: seven 7-bit digit slices per operand on tcgen05
+// FP64-accuracy mode: digit slices per operand on tcgen05 -- six 8-bit
+// slices (21 products) or seven 7-bit slices (28 products); the number of
+// Strassen levels above the leaves picks the scheme (f64acc_slices_for_levels)
+extern int g_f64acc_slices;  // mm_set_option(MM_OPT_F64ACC_SLICES, ...)
+int f64acc_slices_for_levels(int levels);
 int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
 int run_f64acc(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
                void* ws, size_t ws_bytes, cudaStream_t st);
 int read_f64acc_status(int* status);
 // `batches` stacked FP64-accuracy products (Strassen leaves): A is batches x
 // m x k, B batches x k x n, C batches x m x n, all contiguous.
-size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches);
+size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches, int slices);
 int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, int64_t n, int64_t k,
-                       int batches, void* ws, cudaStream_t st);
+                       int batches, int slices, void* ws, cudaStream_t st);
 int read_batched_status(int* status);
 // Test switches (one-shot): the first CTA of the next launch of the FP32
 // GEMM / FP64-accuracy GEMM / batched FP32 kernel skips its first ring

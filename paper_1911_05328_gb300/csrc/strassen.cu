@@ -701,7 +701,7 @@ StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
   off += align_up(s.leaves * s.mL * s.nL * esz, 1024);
   s.off_leafws = off;  // FP64-accuracy leaves: digit slices and exponents
   if (sr == MM_SR_PLUS_TIMES_F64ACC)
-    off += align_up((int64_t)f64acc_batched_bytes(s.mL, s.nL, s.kL, (int)s.leaves), 1024);
+    off += align_up((int64_t)f64acc_batched_bytes(s.mL, s.nL, s.kL, (int)s.leaves, f64acc_slices_for_levels(L)), 1024);
   s.total = off;
   return s;
 }
@@ -920,7 +920,8 @@ int run_view(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, c
     }
     if (e == cudaSuccess) {
       if (sr == MM_SR_PLUS_TIMES_F64ACC) {
-        const int rc = run_f64acc_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, w + S.off_leafws, st);
+        const int rc = run_f64acc_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, f64acc_slices_for_levels(levels),
+                                          w + S.off_leafws, st);
         if (rc != MM_OK) return rc;
       } else {
         e = launch_dfma_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, st);
@@ -945,7 +946,9 @@ void fill_plan(int levels, int sr, int64_t total, mm_plan_t* p) {
   p->tile_m = sr == MM_SR_PLUS_TIMES_F64 ? 64 : 128;
   p->tile_n = sr == MM_SR_PLUS_TIMES_F32 ? 256 : 64;
   p->tile_k = sr == MM_SR_PLUS_TIMES_F32 ? 64 : (sr == MM_SR_PLUS_TIMES_F64 ? 16 : 32);
-  p->kernel = sr == MM_SR_PLUS_TIMES_F32 ? 2 : (sr == MM_SR_PLUS_TIMES_F64 ? 0 : 3);
+  p->kernel = sr == MM_SR_PLUS_TIMES_F32 ? 2
+              : sr == MM_SR_PLUS_TIMES_F64 ? 0
+                                           : (f64acc_slices_for_levels(levels) == 6 ? 7 : 3);
   p->workspace_min = total;
   p->workspace_used = total;
 }

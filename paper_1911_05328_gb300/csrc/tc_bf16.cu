@@ -12,6 +12,7 @@
 // folds into C.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -428,6 +429,269 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// ------------------------------------------------------------ stream-K
+// The zero-temporary k-parallel form of Fig. tar-mm for the FP32 mode: one
+// persistent CTA per SM takes an equal contiguous range of the tile-major
+// (128 x BN tile, k-block) units.  The three roles walk the same sequence
+// of segments (the part of one tile inside the CTA's range); the ring of
+// operand stages and the two TMEM chunk buffers keep running phase
+// counters across segments.  A segment that is a whole tile goes to C; a
+// partial one is stored in one of the CTA's two slots (its first or its last
+// segment -- the p b^2 temporaries), and the CTA that completes a tile's
+// counter folds the slots in k order and writes C.  Nothing waits on
+// another CTA, and the fold order is fixed, so results repeat exactly.
+__device__ __forceinline__ int64_t skf_begin(int64_t c, int64_t total, int P) { return total * c / P; }
+__device__ __forceinline__ int skf_owner(int64_t i, int64_t total, int P) {
+  int64_t c = i * P / total;
+  while (c + 1 < P && skf_begin(c + 1, total, P) <= i) ++c;
+  while (c > 0 && skf_begin(c, total, P) > i) --c;
+  return (int)c;
+}
+// Next segment of [it, end): tile t, k-blocks [j0, j1); advances it.
+__device__ __forceinline__ bool skf_next(int64_t& it, int64_t end, int64_t kbt, int64_t& t, int64_t& j0,
+                                         int64_t& j1) {
+  if (it >= end) return false;
+  t = it / kbt;
+  j0 = it - t * kbt;
+  j1 = min(kbt, j0 + (end - it));
+  it = t * kbt + j1;
+  return true;
+}
+
+template <int BN, int STAGES, int CHUNK>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    bf16x3_streamk_kernel(const __grid_constant__ CUtensorMap tAhi, const __grid_constant__ CUtensorMap tAlo,
+                          const __grid_constant__ CUtensorMap tBhi, const __grid_constant__ CUtensorMap tBlo,
+                          float* __restrict__ C, float* __restrict__ slots, int* __restrict__ counters, int64_t m,
+                          int64_t n, int64_t tiles_n, int64_t kbt, int64_t total, int P) {
+  using Cfg = Bf16x3Cfg<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = tc::align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* quiesce = acc_empty + 2;
+  // drain-warp rendezvous of a partial tile (bounded waits, unlike a named
+  // barrier): every drain warp has stored its slot rows / the verdict is out
+  uint64_t* seg_stored = quiesce + 1;
+  uint64_t* seg_decided = seg_stored + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(seg_decided + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int* prod_state = abort_flag + 1;  // [0] k-blocks issued
+  int* fold = prod_state + 2;        // [0] last arriver, [1] first contributor, [2] last contributor
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cta = blockIdx.x;
+  const int64_t begin = skf_begin(cta, total, P), end = skf_begin(cta + 1, total, P);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kDrainWarps);
+    }
+    tc::mbar_init(quiesce, 1);
+    tc::mbar_init(seg_stored, kDrainWarps);
+    tc::mbar_init(seg_decided, 1);
+    *abort_flag = 0;
+    prod_state[0] = 0;
+    tc::mbar_init_fence();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::tma_prefetch(&tAhi);
+      tc::tma_prefetch(&tAlo);
+      tc::tma_prefetch(&tBhi);
+      tc::tma_prefetch(&tBlo);
+      int64_t it = begin, t, j0, j1;
+      uint32_t g = 0;  // k-blocks issued so far (ring position)
+      bool stop = false;
+      while (!stop && skf_next(it, end, kbt, t, j0, j1)) {
+        const int ya = (int)((t / tiles_n) * BM), yb = (int)((t % tiles_n) * BN);
+        for (int64_t j = j0; j < j1; ++j, ++g) {
+          const int s = (int)(g % STAGES);
+          const uint32_t round = g / STAGES;
+          if (g >= STAGES && !tc::mbar_wait(&empty[s], (round - 1) & 1u, abort_flag, &g_tc_status)) {
+            stop = true;
+            break;
+          }
+          tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+          uint8_t* st = smem + s * Cfg::STAGE_BYTES;
+          const int kx = (int)(j * Cfg::KB);
+          tc::tma_load_2d(st, &tAhi, &full[s], kx, ya);
+          tc::tma_load_2d(st + Cfg::A_BYTES, &tAlo, &full[s], kx, ya);
+          tc::tma_load_2d(st + 2 * Cfg::A_BYTES, &tBhi, &full[s], kx, yb);
+          tc::tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tBlo, &full[s], kx, yb);
+        }
+      }
+      prod_state[0] = (int)g;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_f16(BM, BN, 1);
+      int64_t it = begin, t, j0, j1;
+      uint32_t g = 0, gc = 0;  // k-blocks and chunks consumed so far
+      bool aborted = false;
+      while (!aborted && skf_next(it, end, kbt, t, j0, j1)) {
+        for (int64_t cs = j0; cs < j1 && !aborted; cs += CHUNK, ++gc) {
+          const int b = (int)(gc & 1);
+          if (gc >= 2 && !tc::mbar_wait(&acc_empty[b], ((gc >> 1) - 1) & 1u, abort_flag, &g_tc_status)) {
+            aborted = true;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t d = tmem + (uint32_t)(b * BN);
+          const int64_t ce = min(j1, cs + CHUNK);
+          for (int64_t j = cs; j < ce; ++j, ++g) {
+            const int s = (int)(g % STAGES);
+            if (!tc::mbar_wait(&full[s], (g / STAGES) & 1u, abort_flag, &g_tc_status)) {
+              aborted = true;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t base = smem_u32(smem + s * Cfg::STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < Cfg::KB / 16; ++kk) {
+              const uint64_t ahi = desc_kb<Cfg::KB>(base + kk * 32);
+              const uint64_t alo = desc_kb<Cfg::KB>(base + Cfg::A_BYTES + kk * 32);
+              const uint64_t bhi = desc_kb<Cfg::KB>(base + 2 * Cfg::A_BYTES + kk * 32);
+              const uint64_t blo = desc_kb<Cfg::KB>(base + 2 * Cfg::A_BYTES + Cfg::B_BYTES + kk * 32);
+              tc::mma_f16(d, ahi, bhi, idesc, (j == cs && kk == 0) ? 0u : 1u);
+              tc::mma_f16(d, ahi, blo, idesc, 1);
+              tc::mma_f16(d, alo, bhi, idesc, 1);
+            }
+            tc::mma_commit(&empty[s]);
+          }
+          if (aborted) break;  // no chunk signal: the drain must not read a partial chunk
+          tc::mma_commit(&acc_full[b]);
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const int tr = q * 32 + lane;  // tile row of this thread
+    const int tcol = half * Cfg::COLS_PER_WARP;
+    int64_t it = begin, t, j0, j1;
+    uint32_t gc = 0, ps = 0;  // chunks drained, partial segments met
+    bool ok = true;
+    for (int seg = 0; ok && skf_next(it, end, kbt, t, j0, j1); ++seg) {
+      float sum[Cfg::COLS_PER_WARP];
+#pragma unroll
+      for (int e = 0; e < Cfg::COLS_PER_WARP; ++e) sum[e] = 0.f;
+      for (int64_t cs = j0; cs < j1 && ok; cs += CHUNK, ++gc) {
+        const int b = (int)(gc & 1);
+        ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[b], (gc >> 1) & 1u, abort_flag, &g_tc_status));
+        if (!ok) break;
+        tc::fence_after_sync();
+#pragma unroll
+        for (int cc = 0; cc < Cfg::COLS_PER_WARP; cc += 32) {
+          uint32_t r[32];
+          tc::tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)(b * BN + tcol + cc), r);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 32; ++e) sum[cc + e] = __fadd_rn(sum[cc + e], __uint_as_float(r[e]));
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+      }
+      if (!ok) break;
+      const int64_t row = (t / tiles_n) * BM + tr, c0 = (t % tiles_n) * BN + tcol;
+      const int64_t cols_left = n - c0;
+      if (j0 == 0 && j1 == kbt) {
+        if (row < m) {
+          float* dst = C + row * n + c0;
+          if ((n % 4 == 0) && cols_left >= Cfg::COLS_PER_WARP) {
+#pragma unroll
+            for (int e = 0; e < Cfg::COLS_PER_WARP; e += 4)
+              *reinterpret_cast<float4*>(dst + e) = make_float4(sum[e], sum[e + 1], sum[e + 2], sum[e + 3]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < Cfg::COLS_PER_WARP; ++e)
+              if (e < cols_left) dst[e] = sum[e];
+          }
+        }
+        continue;
+      }
+      // partial tile: this CTA's slot (0: its first segment, 1: its last)
+      float* slot = slots + ((int64_t)cta * 2 + (seg == 0 ? 0 : 1)) * (BM * BN) + (int64_t)tr * BN + tcol;
+#pragma unroll
+      for (int e = 0; e < Cfg::COLS_PER_WARP; e += 4)
+        *reinterpret_cast<float4*>(slot + e) = make_float4(sum[e], sum[e + 1], sum[e + 2], sum[e + 3]);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(seg_stored);
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(seg_stored, ps & 1u, abort_flag, &g_tc_status));
+      if (!ok) break;
+      if (threadIdx.x == 64) {
+        // every drain warp's slot rows are stored and fenced: count this CTA
+        const int cf = skf_owner(t * kbt, total, P), cl = skf_owner(t * kbt + kbt - 1, total, P);
+        fold[0] = atomicAdd(&counters[t], 1) == cl - cf;
+        fold[1] = cf;
+        fold[2] = cl;
+        tc::mbar_arrive(seg_decided);  // release: the verdict is visible to the waiters
+      }
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(seg_decided, ps & 1u, abort_flag, &g_tc_status));
+      ++ps;
+      if (!ok) break;
+      if (fold[0]) {
+        __threadfence();
+#pragma unroll
+        for (int e = 0; e < Cfg::COLS_PER_WARP; ++e) sum[e] = 0.f;
+        for (int qc = fold[1]; qc <= fold[2]; ++qc) {
+          const int which = (skf_begin(qc, total, P) / kbt == t) ? 0 : 1;
+          const float* src = slots + ((int64_t)qc * 2 + which) * (BM * BN) + (int64_t)tr * BN + tcol;
+#pragma unroll
+          for (int e = 0; e < Cfg::COLS_PER_WARP; e += 4) {
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(src + e));
+            sum[e] = __fadd_rn(sum[e], v.x);
+            sum[e + 1] = __fadd_rn(sum[e + 1], v.y);
+            sum[e + 2] = __fadd_rn(sum[e + 2], v.z);
+            sum[e + 3] = __fadd_rn(sum[e + 3], v.w);
+          }
+        }
+        if (row < m) {
+          float* dst = C + row * n + c0;
+#pragma unroll
+          for (int e = 0; e < Cfg::COLS_PER_WARP; ++e)
+            if (e < cols_left) dst[e] = sum[e];
+        }
+        if (threadIdx.x == 64) counters[t] = 0;
+      }
+      // fold[] is rewritten only after the next partial segment's
+      // seg_stored completes, i.e. after every drain warp has read it here
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (*reinterpret_cast<volatile int*>(abort_flag)) {
+    if (warp == 0 && lane == 0) {
+      const int issued = prod_state[0];
+      for (int g = max(0, issued - STAGES); g < issued; ++g)
+        tc::mbar_wait_quiesce(&full[g % STAGES], (uint32_t)(g / STAGES) & 1u);
+    }
+    if (warp == 1 && lane == 0) {
+      tc::mma_commit(quiesce);
+      tc::mbar_wait_quiesce(quiesce, 0);
+    }
+    __syncwarp();
+  }
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
+}
+
 __global__ void __launch_bounds__(256) sum_reduce_f32_kernel(int64_t count, float* __restrict__ C,
                                                              const float* __restrict__ W, int parts,
                                                              bool vec) {
@@ -534,6 +798,29 @@ cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16*
                                                  kb_total, kb_total, 1, st, batches, m, n, m * n, quad);
 }
 
+// Stream-K geometry: one CTA per SM (fewer when the product has under four
+// k-blocks per CTA), two BM x BN FP32 slots per CTA and one counter per tile.
+struct F32Sk {
+  int64_t tiles_n, tiles, kbt, total, slot_bytes, bytes;
+  int P;
+};
+F32Sk f32_sk(int64_t m, int64_t n, int64_t k) {
+  F32Sk g;
+  g.tiles_n = (n + kTcBN - 1) / kTcBN;
+  g.tiles = ((m + BM - 1) / BM) * g.tiles_n;
+  g.kbt = align_up(k > 0 ? k : 1, BK) / kTcBK;
+  g.total = g.tiles * g.kbt;
+  int64_t P = std::min<int64_t>(num_sms(), g.total / 4);
+  g.P = (int)std::max<int64_t>(P, 1);
+  g.slot_bytes = (int64_t)g.P * 2 * BM * kTcBN * 4;
+  g.bytes = g.slot_bytes + align_up(g.tiles * 4, 256);
+  return g;
+}
+bool f32_sk_wanted(int64_t m, int64_t n, int64_t k) {
+  const F32Sk g = f32_sk(m, n, k);
+  return k > 0 && g.tiles < 4 * (int64_t)num_sms() && g.kbt >= 8 && g.total < ((int64_t)1 << 40);
+}
+
 int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
   memset(p, 0, sizeof(*p));
   const F32Layout L = f32_layout(m, n, k);
@@ -545,6 +832,13 @@ int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
   if (budget < (size_t)L.min_bytes) {
     p->split_k = 1;
     p->workspace_used = L.min_bytes;
+    return MM_OK;
+  }
+  if (f32_sk_wanted(m, n, k) && budget >= (size_t)(L.min_bytes + f32_sk(m, n, k).bytes)) {
+    // few tiles and room for the per-CTA partial tiles: the stream-K form
+    p->kernel = 5;
+    p->split_k = 1;
+    p->workspace_used = L.min_bytes + f32_sk(m, n, k).bytes;
     return MM_OK;
   }
   int s = 1, kbs = 0;
@@ -576,6 +870,20 @@ int run_f32(int64_t m, int64_t n, int64_t k, const float* A, const float* B, flo
       make_tmap_2d_16bit(&tb_lo, blo, n, L.Kp, L.Kp, kTcBN, true, kTcBK) != cudaSuccess)
     return MM_ERR_CUDA;
   const int kb_total = (int)(L.Kp / kTcBK);
+  if (p.kernel == 5) {
+    const F32Sk g = f32_sk(m, n, k);
+    float* slots = reinterpret_cast<float*>(w + L.off_part);
+    int* counters = reinterpret_cast<int*>(w + L.off_part + g.slot_bytes);
+    using Cfg = Bf16x3Cfg<kTcBN, kTcStages>;
+    static std::atomic<uint64_t> conf_sk{0};
+    if (smem_limit_once(bf16x3_streamk_kernel<kTcBN, kTcStages, kTcChunk>, Cfg::SMEM, conf_sk) != cudaSuccess ||
+        cudaMemsetAsync(counters, 0, (size_t)g.tiles * 4, st) != cudaSuccess)
+      return MM_ERR_CUDA;
+    TraceScope tr(kTrTcBf16x3, st);
+    bf16x3_streamk_kernel<kTcBN, kTcStages, kTcChunk><<<(unsigned)g.P, kTcThreads, Cfg::SMEM, st>>>(
+        ta_hi, ta_lo, tb_hi, tb_lo, C, slots, counters, m, n, g.tiles_n, g.kbt, g.total, g.P);
+    return cudaGetLastError() == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+  }
   const int s = p.split_k;
   const int kbs = (kb_total + s - 1) / s;
   e = launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, C, part, m, n, kb_total, kbs, s, st);

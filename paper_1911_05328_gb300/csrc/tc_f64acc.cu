@@ -43,34 +43,45 @@ __device__ int g_f64acc_status;
 // and loads of its first ring stage, so its MMA wait runs out.
 __device__ int g_f64acc_skip_signal;
 
-constexpr int kSlices = 7, kDigitBits = 7, kGroups = 7;
-// GEMM k-block (16, 32 or 64 bf16: 32-, 64- or 128-byte swizzled rows), ring
-// depth, and the k-length of one exact TMEM chunk.
-#ifndef MMSR_FA_BK
-#define MMSR_FA_BK 32
-#endif
-#ifndef MMSR_FA_STAGES
-#define MMSR_FA_STAGES 2
-#endif
-#ifndef MMSR_FA_CHUNK_K
-#define MMSR_FA_CHUNK_K 256
-#endif
-constexpr int BM = 128, BN = 64, BK = MMSR_FA_BK, STAGES = MMSR_FA_STAGES;
-constexpr int CHUNK = MMSR_FA_CHUNK_K / BK;  // k-blocks per drain
-constexpr int KSTEPS = BK / 16;              // 16-deep MMA k-steps per k-block
-constexpr int KALIGN = BK > 32 ? BK : 32;    // k alignment of the slices (the split kernels' 32-k tiles)
-static_assert(BK == 16 || BK == 32 || BK == 64, "k-block / swizzle");
-static_assert(CHUNK >= 1 && CHUNK * BK == MMSR_FA_CHUNK_K, "chunks are whole k-blocks");
-static_assert((int64_t)CHUNK * BK * 36864 < (1 << 24), "chunk sums must stay exact in FP32");
+// Two digit schemes.  Seven 7-bit slices (28 products, orders g <= 6): the
+// dropped orders and the rounding sit below 2^-49 of the scaled magnitudes,
+// room for the error growth of three or four Strassen levels above the
+// leaves.  Six 8-bit slices (21 products, orders g <= 5; digits in
+// [-128, 128], still exact in bf16): 2^-47, enough for up to two levels, with
+// a quarter fewer products and a sixth less operand traffic.  kOrderBound
+// bounds the digit products of one order at one k (7 bits: 2 x 128 x 64 +
+// 5 x 64^2; 8 bits: 6 x 128^2), which fixes how many k a chunk may sum
+// exactly in FP32.
+template <int SL>
+struct Scheme;
+template <>
+struct Scheme<7> {
+  static constexpr int kBits = 7, kIntBits = 49, kChunk = 8, kStages = 2;  // chunk: 8 k-blocks = 256 k
+  static constexpr int64_t kOrderBound = 36864;
+  static constexpr int kHiShift = 28, kLoShift = 56;  // value = hi 2^-28 + lo 2^-56
+};
+template <>
+struct Scheme<6> {
+  static constexpr int kBits = 8, kIntBits = 47, kChunk = 5, kStages = 3;  // chunk: 5 k-blocks = 160 k
+  static constexpr int64_t kOrderBound = 98304;
+  static constexpr int kHiShift = 30, kLoShift = 54;  // value = hi 2^-30 + lo 2^-54
+};
+
+constexpr int BM = 128, BN = 64, BK = 32;
 constexpr int kDrain = 8, kThreads = 64 + 32 * kDrain;
 constexpr uint32_t A_TILE = BM * BK * 2, B_TILE = BN * BK * 2;
-constexpr uint32_t STAGE_BYTES = kSlices * (A_TILE + B_TILE);
-constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
-static_assert(SMEM <= 232448, "shared memory of one CTA");
-constexpr uint32_t TMEM_COLS = 512;  // 7 groups x 64 columns used
-__host__ __device__ constexpr uint32_t fa_desc_hi() {
-  return BK == 16 ? tc::desc_hi_sw32() : (BK == 32 ? tc::desc_hi_sw64() : tc::desc_hi_sw128());
-}
+constexpr uint32_t TMEM_COLS = 512;  // SL groups x 64 columns used
+template <int SL>
+struct FaCfg {
+  using S = Scheme<SL>;
+  static constexpr int STAGES = S::kStages, CHUNK = S::kChunk;  // CHUNK k-blocks per drain
+  static constexpr uint32_t STAGE_BYTES = SL * (A_TILE + B_TILE);
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  static_assert((int64_t)CHUNK * BK * S::kOrderBound < (1 << 24), "chunk sums must stay exact in FP32");
+  static_assert(SMEM <= 232448, "shared memory of one CTA");
+  static_assert(SL * BN <= (int)TMEM_COLS, "one TMEM accumulator per digit order");
+};
+static_assert(BK == 32, "the MMA issue loop covers two 16-deep k-steps per k-block");
 
 // ----------------------------------------------------------- split kernels
 // The split passes work on the bit patterns of the (finite) FP64 inputs in
@@ -128,10 +139,12 @@ __global__ void __launch_bounds__(256) col_exponent_kernel(const unsigned long l
   if (j < count) F[j] = line_exponent(Fmax[j]);
 }
 
-// x 2^(49-E) rounded to the nearest integer, ties to even, for finite x with
-// |x| < 2^E.  x = sig 2^e2 exactly (sig the significand with its implicit
-// bit), so the scaling by a power of two is an exponent shift and the one
-// rounding is a right shift of sig with round-half-even; |result| < 2^49.
+// x 2^(INT_BITS-E) rounded to the nearest integer, ties to even, for finite
+// x with |x| < 2^E.  x = sig 2^e2 exactly (sig the significand with its
+// implicit bit), so the scaling by a power of two is an exponent shift and
+// the one rounding is a right shift of sig with round-half-even;
+// |result| <= 2^INT_BITS.
+template <int INT_BITS>
 __device__ __forceinline__ long long scaled_round(double x, int E) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
@@ -143,12 +156,12 @@ __device__ __forceinline__ long long scaled_round(double x, int E) {
   } else {
     e2 = -1074;
   }
-  const int sh = e2 + kDigitBits * kSlices - E;
+  const int sh = e2 + INT_BITS - E;
   long long M;
   if (sh >= 0) {
-    M = (long long)(sig << sh);  // sig 2^sh < 2^49 since |x| < 2^E
+    M = (long long)(sig << sh);  // sig 2^sh < 2^INT_BITS since |x| < 2^E
   } else if (sh <= -54) {
-    M = 0;  // |x 2^(49-E)| < 2^53 2^-54 = 1/2
+    M = 0;  // |x 2^(INT_BITS-E)| < 2^53 2^-54 = 1/2
   } else {
     const int r = -sh;
     const unsigned long long q = sig >> r, rem = sig & ((1ull << r) - 1), half = 1ull << (r - 1);
@@ -157,19 +170,23 @@ __device__ __forceinline__ long long scaled_round(double x, int E) {
   return (b >> 63) ? -M : M;
 }
 
-// Seven digits of x * 2^-E: one rounding of x * 2^(49-E) to an integer M
-// (|M| < 2^49, residual below 2^-50 of 2^E), then balanced base-128 digits
-// M = sum_s d_s 128^(6-s) with d_1..d_6 in [-64, 63] and |d_0| <= 128.
-// Adding K = 64 (1 + 128 + ... + 128^5) makes them plain digits: for s >= 1,
-// d_s + 64 is the 7-bit field 6-s of M + K, and d_0 = (M + K) >> 42.  The
-// fields come from the two 32-bit halves of M + K, and each digit becomes an
-// exact float by the 2^23 trick (2^23 + u has u as its low mantissa bits).
-constexpr long long kDigitOffset = 64LL * (((1LL << 42) - 1) / 127);
+// Digits of x * 2^-E: one rounding of x * 2^(INT_BITS-E) to an integer M,
+// then balanced digits.  Adding K (half the digit base in every position
+// below the top one) makes them plain fields: below the top, digit + half is
+// a field of M + K, and the top digit is (M + K) shifted down, arithmetically.
+// The fields come from the two 32-bit halves of M + K, and each digit becomes
+// an exact float by the 2^23 trick (2^23 + u has u as its low mantissa bits).
 __device__ __forceinline__ float field_digit(uint32_t u, float bias) {
   return __int_as_float(0x4B000000 | (int)u) - bias;  // (2^23 + u) - (2^23 + offset), exact
 }
-__device__ __forceinline__ void digits7(double x, int E, float (&d)[kSlices]) {
-  const long long Mk = scaled_round(x, E) + kDigitOffset;
+template <int SL>
+__device__ __forceinline__ void digits(double x, int E, float (&d)[SL]);
+// Seven 7-bit digits: |M| <= 2^49, M = sum_s d_s 128^(6-s), d_1..d_6 in
+// [-64, 63], |d_0| <= 128; K = 64 (1 + 128 + ... + 128^5).
+template <>
+__device__ __forceinline__ void digits<7>(double x, int E, float (&d)[7]) {
+  constexpr long long kOffset = 64LL * (((1LL << 42) - 1) / 127);
+  const long long Mk = scaled_round<49>(x, E) + kOffset;
   const uint32_t lo = (uint32_t)Mk, hi = (uint32_t)(Mk >> 32);
   constexpr float kB64 = 8388608.0f + 64.0f, kB128 = 8388608.0f + 128.0f;
   d[6] = field_digit(lo & 127u, kB64);
@@ -180,11 +197,27 @@ __device__ __forceinline__ void digits7(double x, int E, float (&d)[kSlices]) {
   d[1] = field_digit((hi >> 3) & 127u, kB64);
   d[0] = field_digit((uint32_t)(((int)hi >> 10) + 128), kB128);  // d_0 + 128 in [0, 256]
 }
+// Six 8-bit digits: |M| <= 2^47, M = sum_s d_s 256^(5-s), d_1..d_5 in
+// [-128, 127], |d_0| <= 128; K = 128 (1 + 256 + ... + 256^4).
+template <>
+__device__ __forceinline__ void digits<6>(double x, int E, float (&d)[6]) {
+  constexpr long long kOffset = 128LL * (((1LL << 40) - 1) / 255);
+  const long long Mk = scaled_round<47>(x, E) + kOffset;
+  const uint32_t lo = (uint32_t)Mk, hi = (uint32_t)(Mk >> 32);
+  constexpr float kB128 = 8388608.0f + 128.0f;
+  d[5] = field_digit(lo & 255u, kB128);
+  d[4] = field_digit((lo >> 8) & 255u, kB128);
+  d[3] = field_digit((lo >> 16) & 255u, kB128);
+  d[2] = field_digit(lo >> 24, kB128);
+  d[1] = field_digit(hi & 255u, kB128);
+  d[0] = field_digit((uint32_t)(((int)hi >> 8) + 128), kB128);  // d_0 + 128 in [0, 256]
+}
 
-// A (m x k) -> seven digit slices, slice s at S + s*m*Kp (row pitch Kp, zero
+// A (m x k) -> SL digit slices, slice s at S + s*m*Kp (row pitch Kp, zero
 // pad).  Each thread converts four adjacent columns and stores 8 bytes per
 // slice; blockIdx.x covers 1024 columns, blockIdx.y takes rows with the
 // grid's y stride (a few thousand blocks in all, each walking many rows).
+template <int SL>
 __global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restrict__ A, int64_t m,
                                                           int64_t k, int64_t Kp,
                                                           const int* __restrict__ E,
@@ -204,12 +237,12 @@ __global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restri
       for (int u = 0; u < 4; ++u) x[u] = t + u < k ? __ldcs(src + u) : 0.0;
     }
     const int Ei = E[i];
-    float d[4][kSlices];
+    float d[4][SL];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) digits7(x[u], Ei, d[u]);
+    for (int u = 0; u < 4; ++u) digits<SL>(x[u], Ei, d[u]);
     const int64_t e = i * Kp + t;
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
+    for (int s = 0; s < SL; ++s) {
       const __nv_bfloat162 p0 = __floats2bfloat162_rn(d[0][s], d[1][s]);
       const __nv_bfloat162 p1 = __floats2bfloat162_rn(d[2][s], d[3][s]);
       *reinterpret_cast<uint2*>(S + s * slice + e) =
@@ -218,10 +251,11 @@ __global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restri
   }
 }
 
-// B (k x n, batch blockIdx.z of a contiguous stack of `batches`) -> seven
+// B (k x n, batch blockIdx.z of a contiguous stack of `batches`) -> SL
 // digit slices of B^T: slice s holds batches*n rows of pitch Kp, batch b at
 // rows [b*n, (b+1)*n).  Via a 32 x 32 shared tile; each thread converts two
 // adjacent k of one column and stores one bf16 pair per slice.
+template <int SL>
 __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restrict__ B, int64_t k,
                                                           int64_t n, int64_t Kp,
                                                           const int* __restrict__ F,
@@ -249,12 +283,12 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
       const int nn = pn + 16 * it;
       const int64_t gn = n0 + nn, gk = k0 + 2 * pk;  // k0 + 32 <= Kp: gk + 1 < Kp
       if (gn >= n) continue;
-      float d0[kSlices], d1[kSlices];
+      float d0[SL], d1[SL];
       const int Fj = F[gn];
-      digits7(tile[2 * pk][nn], Fj, d0);
-      digits7(tile[2 * pk + 1][nn], Fj, d1);
+      digits<SL>(tile[2 * pk][nn], Fj, d0);
+      digits<SL>(tile[2 * pk + 1][nn], Fj, d1);
 #pragma unroll
-      for (int s = 0; s < kSlices; ++s)
+      for (int s = 0; s < SL; ++s)
         *reinterpret_cast<__nv_bfloat162*>(S + s * slice + (b * n + gn) * Kp + gk) =
             __floats2bfloat162_rn(d0[s], d1[s]);
     }
@@ -262,17 +296,24 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
 }
 
 // ------------------------------------------------------------ GEMM kernel
+// 2^-s as an exact double (s < 1023), folded at compile time.
+__host__ __device__ constexpr double exp2_neg(int s) { return s == 0 ? 1.0 : 0.5 * exp2_neg(s - 1); }
+
 __device__ __forceinline__ int exact_int(uint32_t fbits) {
   // fbits holds an integer-valued float of magnitude < 2^24: the conversion
   // is exact in any rounding mode.
   return __float2int_rn(__uint_as_float(fbits));
 }
 
+template <int SL>
 __global__ void __launch_bounds__(kThreads, 1)
     f64acc_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
                        const int* __restrict__ E, const int* __restrict__ F, double* __restrict__ C,
                        double* __restrict__ W, int64_t m, int64_t n, int64_t a_slice_rows,
                        int64_t b_slice_rows, int kb_total, int kb_per_slice, int kslices) {
+  using Cfg = FaCfg<SL>;
+  constexpr int kSlices = SL, kGroups = SL, STAGES = Cfg::STAGES, CHUNK = Cfg::CHUNK;
+  constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -362,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_f16(BM, BN, 1);
-      constexpr uint32_t dhi = fa_desc_hi();
+      constexpr uint32_t dhi = tc::desc_hi_sw64();
       // The products are small (128 x 64 x 16, ~40 tensor-core cycles), so
       // the issue loop is kept lean: descriptors are one 32-bit add of a
       // compile-time offset to a per-stage base word.
@@ -390,22 +431,37 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::fence_after_sync();
           const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
           const uint32_t a_lo = tc::desc_lo(base), b_lo = tc::desc_lo(base + kSlices * A_TILE);
-          // the first k-step of a chunk overwrites each group, after the
-          // drain has read the previous chunk's G_g; the chunk's last k-step
-          // signals each group as soon as its last product is issued
-          const bool chunk_first = it == first_it, chunk_last = it == last - 1;
-#pragma unroll
-          for (int kk = 0; kk < KSTEPS; ++kk) {
+          if (it == first_it) {
+            // first k-block of a chunk: overwrite each group, after the
+            // drain has read the previous chunk's G_g
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) {
-              if (kk == 0 && chunk_first && c >= 1 && !aborted) {
+              if (c >= 1 && !aborted) {
                 if (!tc::mbar_wait(&acc_empty[g], (c - 1) & 1u, abort_flag, &g_f64acc_status)) aborted = true;
                 tc::fence_after_sync();
               }
-              if (!aborted) {
-                issue_group(a_lo, b_lo, kk, g, kk == 0 && chunk_first);
-                if (kk == KSTEPS - 1 && chunk_last) tc::mma_commit(&acc_full[g]);
+              if (!aborted) issue_group(a_lo, b_lo, 0, g, true);
+            }
+            if (!aborted) {
+#pragma unroll
+              for (int g = 0; g < kGroups; ++g) {
+                issue_group(a_lo, b_lo, 1, g, false);
+                if (it == last - 1) tc::mma_commit(&acc_full[g]);
               }
+            }
+          } else {
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 0, g, false);
+            if (it == last - 1) {
+              // the chunk's last product of group g is issued: signal it
+#pragma unroll
+              for (int g = 0; g < kGroups; ++g) {
+                issue_group(a_lo, b_lo, 1, g, false);
+                tc::mma_commit(&acc_full[g]);
+              }
+            } else {
+#pragma unroll
+              for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 1, g, false);
             }
           }
           tc::mma_commit(&empty[s]);
@@ -427,7 +483,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[g], c & 1u, abort_flag, &g_f64acc_status));
         if (!ok) break;
         tc::fence_after_sync();
-        const long long wgt = g < 3 ? (1ll << (7 * (2 - g))) : (1ll << (7 * (6 - g)));
+        constexpr int kb = Scheme<SL>::kBits;
+        const long long wgt = g < 3 ? (1ll << (kb * (2 - g))) : (1ll << (kb * (SL - 1 - g)));
 #pragma unroll
         for (int half16 = 0; half16 < 2; ++half16) {
           uint32_t r[16];
@@ -455,7 +512,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int e = 0; e < 32; ++e) {
         const int64_t col = j0 + h * 32 + e;
         if (col >= n) break;
-        double v = ok ? ((double)hi[e] * 0x1p-28 + (double)lo[e] * 0x1p-56) : 0.0;
+        double v = ok ? ((double)hi[e] * exp2_neg(Scheme<SL>::kHiShift) +
+                         (double)lo[e] * exp2_neg(Scheme<SL>::kLoShift))
+                      : 0.0;
         out[row * n + col] = ldexp(v, Ei + F[rb + col]);
       }
     }
@@ -487,13 +546,15 @@ int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct F64AccLayout {
   int64_t Kp, a_bytes, b_bytes, off_b, off_e, off_f, off_fmax, off_part, min_bytes;
+  int slices;
 };
 
-F64AccLayout layout(int64_t m, int64_t n, int64_t k, int64_t batches = 1) {
+F64AccLayout layout(int64_t m, int64_t n, int64_t k, int slices, int64_t batches = 1) {
   F64AccLayout L;
-  L.Kp = align_up(k > 0 ? k : 1, KALIGN);
-  L.a_bytes = align_up((int64_t)kSlices * batches * m * L.Kp * 2, 1024);
-  L.b_bytes = align_up((int64_t)kSlices * batches * n * L.Kp * 2, 1024);
+  L.slices = slices;
+  L.Kp = align_up(k > 0 ? k : 1, BK);
+  L.a_bytes = align_up((int64_t)slices * batches * m * L.Kp * 2, 1024);
+  L.b_bytes = align_up((int64_t)slices * batches * n * L.Kp * 2, 1024);
   L.off_b = L.a_bytes;
   L.off_e = L.a_bytes + L.b_bytes;
   L.off_f = L.off_e + align_up(batches * m * 4, 256);
@@ -503,34 +564,10 @@ F64AccLayout layout(int64_t m, int64_t n, int64_t k, int64_t batches = 1) {
   return L;
 }
 
-}  // namespace
-
-int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
-  memset(p, 0, sizeof(*p));
-  const F64AccLayout L = layout(m, n, k);
-  p->tile_m = BM;
-  p->tile_n = BN;
-  p->tile_k = BK;
-  p->kernel = 3;
-  p->workspace_min = L.min_bytes;
-  if (budget < (size_t)L.min_bytes) {
-    p->split_k = 1;
-    p->workspace_used = L.min_bytes;
-    return MM_OK;
-  }
-  int s = 1, kbs = 0;
-  int64_t used = 0;
-  split_plan(m, n, L.Kp, BK, 8, budget - (size_t)L.min_bytes, &s, &kbs, &used);
-  p->split_k = s;
-  p->workspace_used = L.min_bytes + used;
-  return MM_OK;
-}
-
-// Digits, exponents and the tensor-core product for `batches` independent
-// products stacked contiguously (A: batches x m x k, B: batches x k x n,
-// C: batches x m x n), with `s` k-slices (s > 1 only when batches == 1).
-int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
-                uint8_t* w, const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
+// Digit slices and the tensor-core product for one scheme.
+template <int SL>
+int f64acc_core_t(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
+                  uint8_t* w, const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
   auto* SA = reinterpret_cast<__nv_bfloat16*>(w);
   auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
   int* E = reinterpret_cast<int*>(w + L.off_e);
@@ -547,32 +584,68 @@ int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* 
     {
       const int64_t gx = std::max<int64_t>(1, (L.Kp + 1023) / 1024);
       const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(rows_a, std::max<int64_t>(1, 4096 / gx)));
-      digits_rows_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA,
-                                                                          aligned16(A) && k % 2 == 0);
+      digits_rows_kernel<SL><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA,
+                                                                              aligned16(A) && k % 2 == 0);
     }
     // n-tiles per block: enough blocks to fill the GPU a few times over, each
     // walking several tiles
     const int64_t tiles_n = (n + 31) / 32;
     const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 8192 / (L.Kp / 32 * batches))));
     dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>(gy, kMaxGridY), (unsigned)batches);
-    digits_cols_kernel<<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
+    digits_cols_kernel<SL><<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   CUtensorMap tA, tB;
-  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tA, SA, kSlices * rows_a, L.Kp, L.Kp, BM, true, BK));
-  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tB, SB, kSlices * (int64_t)batches * n, L.Kp, L.Kp, BN, true, BK));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tA, SA, SL * rows_a, L.Kp, L.Kp, BM, true, BK));
+  MMSR_TRY_STATUS(make_tmap_2d_16bit(&tB, SB, SL * (int64_t)batches * n, L.Kp, L.Kp, BN, true, BK));
   static std::atomic<uint64_t> configured{0};
-  MMSR_TRY_STATUS(smem_limit_once(f64acc_gemm_kernel, SMEM, configured));
+  MMSR_TRY_STATUS(smem_limit_once(f64acc_gemm_kernel<SL>, FaCfg<SL>::SMEM, configured));
   const int kb_total = (int)(L.Kp / BK);
   const int kbs = (kb_total + s - 1) / s;
   {
     TraceScope tr(kTrTcF64Acc, st);
     dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)(s * batches));
-    f64acc_gemm_kernel<<<grid, kThreads, SMEM, st>>>(tA, tB, E, F, C, part, m, n, rows_a,
-                                                    (int64_t)batches * n, kb_total, kbs, s);
+    f64acc_gemm_kernel<SL><<<grid, kThreads, FaCfg<SL>::SMEM, st>>>(tA, tB, E, F, C, part, m, n, rows_a,
+                                                                   (int64_t)batches * n, kb_total, kbs, s);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   if (s > 1) MMSR_TRY_STATUS(launch_sum_reduce_f64(m * n, C, part, s - 1, st));
+  return MM_OK;
+}
+
+int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C, uint8_t* w,
+                const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
+  return L.slices == 6 ? f64acc_core_t<6>(m, n, k, A, B, C, w, L, batches, s, part, st)
+                       : f64acc_core_t<7>(m, n, k, A, B, C, w, L, batches, s, part, st);
+}
+
+}  // namespace
+
+int g_f64acc_slices = 0;  // mm_set_option(MM_OPT_F64ACC_SLICES, ...): 0 = by Strassen depth
+
+int f64acc_slices_for_levels(int levels) {
+  if (g_f64acc_slices == 6 || g_f64acc_slices == 7) return g_f64acc_slices;
+  return levels <= 2 ? 6 : 7;
+}
+
+int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
+  memset(p, 0, sizeof(*p));
+  const F64AccLayout L = layout(m, n, k, f64acc_slices_for_levels(0));
+  p->tile_m = BM;
+  p->tile_n = BN;
+  p->tile_k = BK;
+  p->kernel = f64acc_slices_for_levels(0) == 6 ? 7 : 3;
+  p->workspace_min = L.min_bytes;
+  if (budget < (size_t)L.min_bytes) {
+    p->split_k = 1;
+    p->workspace_used = L.min_bytes;
+    return MM_OK;
+  }
+  int s = 1, kbs = 0;
+  int64_t used = 0;
+  split_plan(m, n, L.Kp, BK, 8, budget - (size_t)L.min_bytes, &s, &kbs, &used);
+  p->split_k = s;
+  p->workspace_used = L.min_bytes + used;
   return MM_OK;
 }
 
@@ -581,19 +654,19 @@ int run_f64acc(int64_t m, int64_t n, int64_t k, const double* A, const double* B
   mm_plan_t p;
   plan_f64acc(m, n, k, ws_bytes, &p);
   if ((size_t)p.workspace_min > ws_bytes) return MM_ERR_WORKSPACE;
-  const F64AccLayout L = layout(m, n, k);
+  const F64AccLayout L = layout(m, n, k, f64acc_slices_for_levels(0));
   uint8_t* w = static_cast<uint8_t*>(ws);
   double* part = p.split_k > 1 ? reinterpret_cast<double*>(w + L.off_part) : nullptr;
   return f64acc_core(m, n, k, A, B, C, w, L, 1, p.split_k, part, st);
 }
 
-size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches) {
-  return (size_t)layout(m, n, k, batches).min_bytes;
+size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches, int slices) {
+  return (size_t)layout(m, n, k, slices, batches).min_bytes;
 }
 
 int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, int64_t n, int64_t k,
-                       int batches, void* ws, cudaStream_t st) {
-  const F64AccLayout L = layout(m, n, k, batches);
+                       int batches, int slices, void* ws, cudaStream_t st) {
+  const F64AccLayout L = layout(m, n, k, slices, batches);
   return f64acc_core(m, n, k, A, B, C, static_cast<uint8_t*>(ws), L, batches, 1, nullptr, st);
 }
 

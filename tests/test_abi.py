@@ -94,7 +94,7 @@ def test_split_never_exceeds_budget_or_kblocks(lib):
             for sr, accb in ((mmsr.MM_SR_MIN_PLUS_I32, 4), (mmsr.MM_SR_PLUS_TIMES_F64, 8)):
                 p = mmsr.mm_plan_query(sr, -1, m, n, k, budget)
                 assert p.workspace_used <= budget
-                if p.kernel == 4:
+                if p.kernel == 6:
                     # the FP64 stream-K form: one k-slice in the plan, its
                     # per-CTA partial tiles in the workspace
                     assert sr == mmsr.MM_SR_PLUS_TIMES_F64 and p.split_k == 1 and p.workspace_used > 0
@@ -103,7 +103,7 @@ def test_split_never_exceeds_budget_or_kblocks(lib):
                 assert 1 <= p.split_k <= max(1, -(-k // p.tile_k))
                 # monotone in the budget (while the plan stays a split-K plan)
                 q = mmsr.mm_plan_query(sr, -1, m, n, k, budget + m * n * accb)
-                assert q.kernel == 4 or q.split_k >= p.split_k
+                assert q.kernel == 6 or q.split_k >= p.split_k
 
 
 def test_closure_argument_checks(lib):
@@ -203,6 +203,8 @@ def test_option_argument_checks(lib):
     assert mmsr.mm_set_option(99, 0, check=False) == mmsr.MM_ERR_ARG
     for opt in (mmsr.MM_OPT_MINPLUS_PACKED, mmsr.MM_OPT_MINPLUS_STREAMK, mmsr.MM_OPT_STRASSEN_TOP_F64):
         assert mmsr.mm_set_option(opt, 2, check=False) == mmsr.MM_ERR_ARG
+    for v in (1, 5, 8, -1):
+        assert mmsr.mm_set_option(mmsr.MM_OPT_F64ACC_SLICES, v, check=False) == mmsr.MM_ERR_ARG
     # option 3 is retired: every value is refused
     for v in (0, 1):
         assert mmsr.mm_set_option(3, v, check=False) == mmsr.MM_ERR_ARG
@@ -222,3 +224,24 @@ def test_noalloc_host_checks(lib):
     assert f(0, 4, 4, None, None, None, 1, stream=0, check=False) == mmsr.MM_OK
     # s = 3 needs 2 partial slices of 4096 x 4096 int32 = 128 MiB > the 64 MiB scratch
     assert f(4096, 4096, 4096, FAKE, FAKE, FAKE, 3, stream=0, check=False) == mmsr.MM_ERR_WORKSPACE
+
+
+def test_f64acc_scheme_by_levels(lib):
+    """The FP64-accuracy digit scheme follows the Strassen depth: six slices
+    (12 bytes per operand element) for plain products and up to two levels,
+    seven (14 bytes) for three or four; the option forces either."""
+    sr = mmsr.MM_SR_PLUS_TIMES_F64ACC
+    m = n = k = 1024
+    try:
+        w = {}
+        for opt in (6, 7):
+            mmsr.mm_set_option(mmsr.MM_OPT_F64ACC_SLICES, opt)
+            w[opt] = [int(mmsr.mm_plan_query(sr, L, m, n, k, 0).workspace_min) for L in (-1, 1, 2, 3, 4)]
+        mmsr.mm_set_option(mmsr.MM_OPT_F64ACC_SLICES, 0)
+        auto = [int(mmsr.mm_plan_query(sr, L, m, n, k, 0).workspace_min) for L in (-1, 1, 2, 3, 4)]
+        assert auto[:3] == w[6][:3] and auto[3:] == w[7][3:]
+        # the plain product's slices: 2 S (m + n) Kp bytes plus exponents
+        assert w[7][0] - w[6][0] == 2 * (m + n) * k
+        assert all(a < b for a, b in zip(w[6], w[7]))
+    finally:
+        mmsr.mm_set_option(mmsr.MM_OPT_F64ACC_SLICES, 0)

@@ -68,7 +68,7 @@ def _streamk_budget(m, n, k):
     product is too large or too shallow for it."""
     for b in (1 << 20, 1 << 22, 1 << 24, 1 << 26):
         p = mmsr.mm_plan_query(SR, -1, m, n, k, b)
-        if p.kernel == 4:
+        if p.kernel == 6:
             return int(p.workspace_used)
     return None
 
@@ -106,7 +106,7 @@ def test_streamk_n256_workload():
 
 
 def test_streamk_not_taken_for_large_grids_or_small_budgets():
-    assert mmsr.mm_plan_query(SR, -1, 4096, 4096, 4096, 1 << 30).kernel != 4
+    assert mmsr.mm_plan_query(SR, -1, 4096, 4096, 4096, 1 << 30).kernel != 6
     w = _streamk_budget(256, 256, 256)
-    assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, w - 1).kernel != 4
-    assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, 0).kernel != 4
+    assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, w - 1).kernel != 6
+    assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, 0).kernel != 6

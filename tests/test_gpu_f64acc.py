@@ -1,7 +1,9 @@
-"""FP64-accuracy mode (+,x): seven 7-bit digit slices per operand, 28 exact
-slice products on tcgen05, vs the FP64 oracle at 1e-12 relative Frobenius
-error.  Integer inputs pin the exactness of the chunked TMEM accumulation:
-their digits are exact integers and so is the whole product."""
+"""FP64-accuracy mode (+,x) vs the FP64 oracle at 1e-12 relative Frobenius
+error, under both digit schemes: six 8-bit slices (21 exact slice products,
+the default for plain products) and seven 7-bit slices (28 products, the
+scheme under three or four Strassen levels).  Integer inputs pin the
+exactness of the chunked TMEM accumulation: their digits are exact integers
+and so is the whole product."""
 import numpy as np
 import pytest
 
@@ -13,6 +15,14 @@ from gpu_util import canary_intact, dev, empty, rel_fro, workspace
 pytestmark = pytest.mark.gpu
 SR = mmsr.MM_SR_PLUS_TIMES_F64ACC
 TOL = 1e-12
+INT_BITS = {6: 47, 7: 49}  # width of the one scaled rounding of each scheme
+
+
+@pytest.fixture(autouse=True, params=[6, 7], ids=["six-8bit-slices", "seven-7bit-slices"])
+def slices(request):
+    mmsr.mm_set_option(mmsr.MM_OPT_F64ACC_SLICES, request.param)
+    yield request.param
+    mmsr.mm_set_option(mmsr.MM_OPT_F64ACC_SLICES, 0)
 
 
 def run(A, B, extra_parts=0):
@@ -68,19 +78,20 @@ def test_split_k(parts):
     assert rel_fro(run(A, B, extra_parts=parts), oracle.mm_f64(A, B)) <= TOL
 
 
-def test_digit_rounding_edges_exact():
-    # Rows that drive the split's one rounding (x 2^(49-E) to an integer, ties
-    # to even, E = frexp exponent of the row maximum) through its edge cases;
-    # B holds small integers, so the product of what the split represents is
-    # exact in FP64 and the result must equal it bit for bit.
+def test_digit_rounding_edges_exact(slices):
+    # Rows that drive the split's one rounding (x 2^(W-E) to an integer, ties
+    # to even, E = frexp exponent of the row maximum, W = 47 or 49) through
+    # its edge cases; B holds small integers, so the product of what the split
+    # represents is exact in FP64 and the result must equal it bit for bit.
+    W = INT_BITS[slices]
     rng = np.random.default_rng(95)
     k, n = 64, 40
     B = rng.integers(-8, 9, size=(k, n)).astype(np.float64)
     A = np.zeros((4, k))
-    # ties: max 1.5 (E = 1); the others are odd multiples of 2^-49, half a unit
-    A[0] = (2 * rng.integers(0, 1000, size=k) + 1) * 2.0 ** -49 * rng.choice([-1.0, 1.0], size=k)
+    # ties: max 1.5 (E = 1); the others are odd multiples of 2^-W, half a unit
+    A[0] = (2 * rng.integers(0, 1000, size=k) + 1) * 2.0 ** -W * rng.choice([-1.0, 1.0], size=k)
     A[0, 0] = 1.5
-    # the largest value below 2^-2: its scaled value rounds up to 2^49
+    # the largest value below 2^-2: its scaled value rounds up to 2^W
     A[1] = (2 - 2.0 ** -52) * 2.0 ** -3
     # subnormal row (its exponent comes from the significand's leading bit)
     A[2] = rng.integers(-100, 101, size=k) * 2.0 ** -1074
@@ -88,7 +99,7 @@ def test_digit_rounding_edges_exact():
     A[3] = rng.integers(-100, 101, size=k) * 2.0 ** -1074
     A[3, 5] = 0.75
     E = [np.frexp(np.abs(r).max())[1] for r in A]
-    Aq = np.array([np.ldexp(np.rint(np.ldexp(r, 49 - e)), e - 49) for r, e in zip(A, E)])
+    Aq = np.array([np.ldexp(np.rint(np.ldexp(r, W - e)), e - W) for r, e in zip(A, E)])
     assert Aq[1, 0] == 0.25 and np.all(Aq[3, np.arange(k) != 5] == 0.0)
     np.testing.assert_array_equal(run(A, B), Aq @ B)
 
