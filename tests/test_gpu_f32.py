@@ -93,3 +93,51 @@ def test_full_size_n8192_sampled_rows():
     err = rel_fro(C[rows], ref)
     assert err <= TOL, err
     torch.cuda.empty_cache()
+
+
+def _sk_budget(m, n, k):
+    """Smallest budget for which the planner picks the FP32 stream-K form
+    (kernel id 5): the split operands plus two partial tiles per CTA and one
+    counter per tile."""
+    base = int(mmsr.mm_plan_query(SR, -1, m, n, k, 0).workspace_min)
+    for extra in (1 << 24, 1 << 26, 1 << 28):
+        p = mmsr.mm_plan_query(SR, -1, m, n, k, base + extra)
+        if p.kernel == 5:
+            return int(p.workspace_used)
+    return None
+
+
+def run_budget(A, B, budget):
+    import torch
+
+    m, k = A.shape
+    n = B.shape[1]
+    ws = workspace(budget)
+    dC = empty((m, n), torch.float32)
+    dC.fill_(float("nan"))  # every tile must be written, whole or folded
+    mmsr.mm_semiring(SR, m, n, k, dev(A.astype(np.float32)), dev(B.astype(np.float32)), dC, ws, budget)
+    torch.cuda.synchronize()
+    assert canary_intact(ws, budget)
+    assert mmsr.mm_last_device_status() == 0
+    return dC.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 256, 256), (256, 512, 4096), (129, 257, 1000), (1000, 700, 2048),
+                                   (300, 2000, 3000), (1, 1, 5000)])
+def test_streamk_form_matches_oracle(m, n, k):
+    # few tiles, long k: persistent CTAs split the (tile, k-block) units
+    # evenly; partial tiles meet in per-CTA slots, folded in k order
+    w = _sk_budget(m, n, k)
+    assert w is not None
+    A, B = inputs.small_int(m, k, n, seed=m + n + k, bound=4, dtype=np.float32)
+    np.testing.assert_array_equal(run_budget(A, B, w), oracle.mm_f64(A, B).astype(np.float32))
+    A, B = inputs.normal_f32(m, k, n, seed=3 * m + k)
+    C1 = run_budget(A, B, w)
+    assert rel_fro(C1, oracle.mm_f64(A, B)) <= TOL
+    np.testing.assert_array_equal(run_budget(A, B, w), C1)  # fixed fold order: repeatable
+
+
+def test_streamk_not_taken_for_large_grids():
+    assert mmsr.mm_plan_query(SR, -1, 8192, 8192, 8192, 1 << 34).kernel == 2
+    w = _sk_budget(256, 512, 4096)
+    assert mmsr.mm_plan_query(SR, -1, 256, 512, 4096, w - 1).kernel == 2
