@@ -593,7 +593,11 @@ def run_extras(mmsr, lib, torch, sp, book, A_sq, B_sq, rows_sq):
     out["orand_n4096"] = extras_orand(mmsr, lib, torch, sp, ctypes, lop_peak)
     out["probes"] = {"addmin_u32_tops": u32_peak, "addmin_u16x2_tops": u16_peak,
                      "fp64_fma_probe_tflops": _probe(lib, sp, 2, 2000) / 1e12, "fp64_peak_derived_tflops": fp64_peak,
-                     "orand_peak_derived_tops": lop_peak, "fp32_fma_probe_tflops": _probe(lib, sp, 3, 20000) / 1e12}
+                     "orand_peak_derived_tops": lop_peak, "fp32_fma_probe_tflops": _probe(lib, sp, 3, 20000) / 1e12,
+                     # tensor-core products fed from shared memory alone (no TMA):
+                     # the ceiling of the FP64-accuracy leaf's 128 x 64 x 16 shape
+                     "tc_128x64x16_smem_tflops": _probe(lib, sp, 4, 4000) / 1e12,
+                     "tc_128x128x16_smem_tflops": _probe(lib, sp, 5, 4000) / 1e12}
     torch.cuda.empty_cache()
     return out
 

@@ -245,3 +245,13 @@ def test_f64acc_scheme_by_levels(lib):
         assert all(a < b for a, b in zip(w[6], w[7]))
     finally:
         mmsr.mm_set_option(mmsr.MM_OPT_F64ACC_SLICES, 0)
+
+
+def test_probe_argument_checks(lib):
+    import ctypes
+
+    lib.mm_probe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]
+    r, t = ctypes.c_double(), ctypes.c_double()
+    for kind, iters in ((-1, 10), (6, 10), (0, 0), (4, -5)):
+        assert lib.mm_probe_peak(kind, iters, None, ctypes.byref(r), ctypes.byref(t)) == mmsr.MM_ERR_ARG
