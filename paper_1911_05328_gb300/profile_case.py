@@ -6,7 +6,8 @@ Cases: minplus4096 (the (min,+) n=4096 product, budget 0 unless --budget),
 f32_<n> (FP32 mode, bf16x3 on tensor cores), f64acc_<n> (FP64-accuracy mode),
 f64_<n> (plain FP64 path), orand_<n> (boolean), batched512 (the 512-problem
 mixed batch), strassen<L>_<n> (FP32-mode Strassen-Winograd, L levels,
-uniform[-1,1] inputs), tar_<n> (one TAR-Strassen level, FP32 mode), probes (one
+uniform[-1,1] inputs), fa_strassen<L>_<n> (the same in FP64-accuracy mode), tar_<n>
+(one TAR-Strassen level, FP32 mode), probes (one
 launch of each instruction-throughput probe, kinds 0..3).
 Inputs come from the seeded generators; nothing is checked here.
 """
@@ -74,6 +75,22 @@ def main():
         ws = torch.empty((need,), dtype=torch.uint8, device="cuda")
         for _ in range(a.reps):
             mmsr.mm_batched(table, ws, need)
+        torch.cuda.synchronize()
+        print("done", a.case, "reps", a.reps)
+        return
+    elif a.case.startswith("fa_strassen"):
+        # FP64-accuracy Strassen-Winograd: fa_strassen<L>_<n>
+        L = int(a.case[len("fa_strassen"):a.case.index("_", 3)])
+        n = int(a.case[a.case.index("_", 3) + 1:])
+        A, B = inputs.uniform_f64(n, n, n, seed=3)
+        dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        del A, B
+        dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        sr = mmsr.MM_SR_PLUS_TIMES_F64ACC
+        p = mmsr.mm_plan_query(sr, L, n, n, n, 0)
+        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min))
         torch.cuda.synchronize()
         print("done", a.case, "reps", a.reps)
         return
