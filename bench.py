@@ -525,7 +525,9 @@ def main():
     err = head.get("error")
     line = {
         "metric": METRIC, "value": value, "unit": "GOp/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "dtype_detail": "FP64 in/out; bf16 digit-slice products on tensor cores, exact FP32 chunks, "
                         "int64 group sums, FP64 combination and FP64 Strassen additions",

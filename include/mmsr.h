@@ -152,7 +152,14 @@ typedef enum {
  * levels = 0 is mm_semiring.  The temporaries (operand sums S_r, T_r and
  * products P_r of each level) are carved from `workspace`; the plan's
  * workspace_min is O(n^2) and is reported by mm_plan_query.
+ * levels = MM_LEVELS_AUTO lets the library pick the depth: the fastest
+ * measured depth of the semiring (2 for FP32 mode, 1 for FP64-accuracy
+ * mode, 4 for plain FP64), lowered until every leaf dimension stays at
+ * least 1024 (512 for plain FP64), the shape divides by 2^levels and the
+ * plan fits workspace_bytes (0 levels: mm_semiring).  mm_plan_query with
+ * the same value reports the depth it picks in plan->levels.
  */
+#define MM_LEVELS_AUTO 16
 int mm_strassen(int levels, int variant, int semiring, int64_t m, int64_t n, int64_t k,
                 const void* A, const void* B, void* C, void* workspace, size_t workspace_bytes,
                 void* stream);

@@ -197,11 +197,12 @@ int mm_strassen(int levels, int variant, int semiring, int64_t m, int64_t n, int
                 void* stream) {
   int rc = validate_common(semiring, m, n, k, A, B, C, workspace, workspace_bytes);
   if (rc != MM_OK) return rc;
-  if (levels < 0 || levels > kMaxLevels) return MM_ERR_ARG;
   if (variant != MM_STRASSEN_PAPER && variant != MM_STRASSEN_WINOGRAD) return MM_ERR_ARG;
   // Strassen-like recursions need the inverse of (+) (Section 5): only the
   // (+, x) semirings qualify.
   if (semiring == MM_SR_MIN_PLUS_I32 || semiring == MM_SR_OR_AND_U8) return MM_ERR_UNSUPPORTED;
+  if (levels == MM_LEVELS_AUTO) levels = choose_strassen_levels(semiring, m, n, k, workspace_bytes);
+  if (levels < 0 || levels > kMaxLevels) return MM_ERR_ARG;
   const int64_t mask = ((int64_t)1 << levels) - 1;
   if ((m & mask) || (n & mask) || (k & mask)) return MM_ERR_SHAPE;
   if (m == 0 || n == 0) return MM_OK;
@@ -276,8 +277,9 @@ int mm_plan_query(int semiring, int levels, int64_t m, int64_t n, int64_t k,
   if (acc_bytes(semiring) == 0 || m < 0 || n < 0 || k < 0) return MM_ERR_ARG;
   if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return MM_ERR_SHAPE;
   if (levels < 0) return plan_semiring(semiring, m, n, k, workspace_bytes, plan);
-  if (levels > kMaxLevels) return MM_ERR_ARG;
+  if (levels != MM_LEVELS_AUTO && levels > kMaxLevels) return MM_ERR_ARG;
   if (semiring == MM_SR_MIN_PLUS_I32 || semiring == MM_SR_OR_AND_U8) return MM_ERR_UNSUPPORTED;
+  if (levels == MM_LEVELS_AUTO) levels = choose_strassen_levels(semiring, m, n, k, workspace_bytes);
   const int64_t mask = ((int64_t)1 << levels) - 1;
   if ((m & mask) || (n & mask) || (k & mask)) return MM_ERR_SHAPE;
   if (levels == 0) return plan_semiring(semiring, m, n, k, workspace_bytes, plan);

@@ -83,6 +83,8 @@ cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int
                                 int64_t k, int batches, cudaStream_t st);
 
 // Strassen engine
+// Strassen depth picked for MM_LEVELS_AUTO under a workspace budget.
+int choose_strassen_levels(int sr, int64_t m, int64_t n, int64_t k, size_t budget);
 int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget,
                   mm_plan_t* p);
 int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,

@@ -656,9 +656,18 @@ struct StrassenLayout {
   int64_t mL, nL, kL, KpL, leaves;
 };
 
-// Workspace carve-up.  FP32 mode: FP32 stacks for levels 1..L-1 (ping-pong),
-// the last level's split operands (bf16 hi/lo, B transposed) and the leaf
-// products.  FP64 mode: FP64 stacks, FP64 leaf operands and products.
+// Workspace carve-up.  The level passes go two levels at a time (see
+// below), so with at most four levels only the first operand pass and the
+// first post pass can write an intermediate stack: one level down on the
+// operand side (level 1 when L = 3, level 2 when L = 4; none when L <= 2)
+// and one level up on the post side (the same levels).  The operand side is
+// finished before the post side starts, so one buffer holds either.  FP32
+// mode then holds the last level's split operands (bf16 hi/lo, B transposed)
+// and the leaf products; FP64 modes the FP64 leaf operands and products.  In
+// FP64-accuracy mode the leaf products overlay the FP64 leaf operands of A,
+// which are dead once their digit slices are written.
+int intermediate_level(int L) { return L >= 3 ? L - 2 : 0; }
+
 StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
   StrassenLayout s;
   const int esz = (sr == MM_SR_PLUS_TIMES_F32) ? 4 : 8;
@@ -667,17 +676,16 @@ StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
   s.kL = k >> L;
   s.leaves = pw7(L);
   int64_t pp = 0;
-  for (int l = 1; l <= L - 1; ++l) {
+  if (const int l = intermediate_level(L)) {
     const int64_t ml = m >> l, nl = n >> l, kl = k >> l;
     int64_t e = ml * kl;
     if (kl * nl > e) e = kl * nl;
     if (ml * nl > e) e = ml * nl;
-    const int64_t b = pw7(l) * e * esz;
-    if (b > pp) pp = b;
+    pp = pw7(l) * e * esz;
   }
   s.pp_bytes = align_up(pp, 1024);
-  s.off_pp1 = s.pp_bytes;
-  int64_t off = 2 * s.pp_bytes;
+  s.off_pp1 = 0;  // the second ping-pong buffer is never needed (see above)
+  int64_t off = s.pp_bytes;
   if (sr == MM_SR_PLUS_TIMES_F32) {
     s.KpL = align_up(s.kL > 0 ? s.kL : 1, 64);
     const int64_t a = align_up(s.leaves * s.mL * s.KpL * 2, 1024);
@@ -697,8 +705,13 @@ StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
     s.off_blo = off + a;
     off += a + b;
   }
-  s.off_p = off;
-  off += align_up(s.leaves * s.mL * s.nL * esz, 1024);
+  const int64_t pbytes = align_up(s.leaves * s.mL * s.nL * esz, 1024);
+  if (sr == MM_SR_PLUS_TIMES_F64ACC && pbytes <= s.off_bhi - s.off_ahi) {
+    s.off_p = s.off_ahi;
+  } else {
+    s.off_p = off;
+    off += pbytes;
+  }
   s.off_leafws = off;  // FP64-accuracy leaves: digit slices and exponents
   if (sr == MM_SR_PLUS_TIMES_F64ACC)
     off += align_up((int64_t)f64acc_batched_bytes(s.mL, s.nL, s.kL, (int)s.leaves, f64acc_slices_for_levels(L)), 1024);
@@ -973,6 +986,24 @@ int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t bu
   fill_plan(levels, sr, strassen_layout(levels, sr, m, n, k).total, p);
   (void)budget;
   return MM_OK;
+}
+
+// Depth for MM_LEVELS_AUTO: the preferred depth of the semiring (measured at
+// n >= 8192: FP32 mode is fastest at two levels, FP64-accuracy mode at one;
+// the FP64 DFMA leaves are bound by the FP64 pipe, so every level saves an
+// eighth of the time), lowered until every leaf dimension stays at least
+// 1024 (512 for FP64), the shape divides by 2^L and the workspace fits the
+// budget.  0 means the classic product.
+int choose_strassen_levels(int sr, int64_t m, int64_t n, int64_t k, size_t budget) {
+  int L = sr == MM_SR_PLUS_TIMES_F32 ? 2 : (sr == MM_SR_PLUS_TIMES_F64ACC ? 1 : 4);
+  const int64_t floor_dim = sr == MM_SR_PLUS_TIMES_F64 ? 512 : 1024;
+  for (; L > 0; --L) {
+    const int64_t mask = ((int64_t)1 << L) - 1;
+    if ((m & mask) || (n & mask) || (k & mask)) continue;
+    if ((m >> L) < floor_dim || (n >> L) < floor_dim || (k >> L) < floor_dim) continue;
+    if ((size_t)strassen_layout(L, sr, m, n, k).total <= budget) break;
+  }
+  return L;
 }
 
 int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A,

@@ -23,6 +23,7 @@ MM_SR_MIN_PLUS_I32 = 3
 MM_SR_OR_AND_U8 = 4
 
 MM_STRASSEN_PAPER = 0
+MM_LEVELS_AUTO = 16
 MM_STRASSEN_WINOGRAD = 1
 
 MM_OPT_MINPLUS_PACKED = 1

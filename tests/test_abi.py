@@ -255,3 +255,29 @@ def test_probe_argument_checks(lib):
     r, t = ctypes.c_double(), ctypes.c_double()
     for kind, iters in ((-1, 10), (6, 10), (0, 0), (4, -5)):
         assert lib.mm_probe_peak(kind, iters, None, ctypes.byref(r), ctypes.byref(t)) == mmsr.MM_ERR_ARG
+
+
+def test_strassen_auto_depth_under_budget(lib):
+    """MM_LEVELS_AUTO: the preferred depth per semiring, lowered for small
+    leaves, shapes that do not divide and budgets that do not hold the plan."""
+    A = mmsr.MM_LEVELS_AUTO
+    f32, acc, f64 = mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_PLUS_TIMES_F64ACC, mmsr.MM_SR_PLUS_TIMES_F64
+    n = 16384
+    big = 1 << 40
+    assert mmsr.mm_plan_query(f32, A, n, n, n, big).levels == 2
+    assert mmsr.mm_plan_query(acc, A, n, n, n, big).levels == 1
+    assert mmsr.mm_plan_query(f64, A, 8192, 8192, 8192, big).levels == 4
+    # budget between the one- and two-level plans: one level; below both: classic
+    w1 = int(mmsr.mm_plan_query(f32, 1, n, n, n, 0).workspace_min)
+    w2 = int(mmsr.mm_plan_query(f32, 2, n, n, n, 0).workspace_min)
+    p = mmsr.mm_plan_query(f32, A, n, n, n, (w1 + w2) // 2)
+    assert p.levels == 1 and p.workspace_min == w1
+    assert mmsr.mm_plan_query(f32, A, n, n, n, w1 - 1).levels == 0
+    # small leaves and shapes that do not divide
+    assert mmsr.mm_plan_query(acc, A, 1024, 1024, 1024, big).levels == 0
+    assert mmsr.mm_plan_query(f32, A, 2048, 2048, 2048, big).levels == 1
+    assert mmsr.mm_plan_query(f64, A, 4000, 4000, 4000, big).levels == 2
+    assert mmsr.mm_plan_query(f32, A, 4097, 4096, 4096, big).levels == 0
+    # the automatic depth is refused only where Strassen is undefined
+    assert mmsr.mm_plan_query(mmsr.MM_SR_MIN_PLUS_I32, A, 64, 64, 64, big, check=False).status == \
+        mmsr.MM_ERR_UNSUPPORTED
