@@ -201,3 +201,30 @@ def test_full_size_rectangular_both_modes_sampled_rows():
             torch.cuda.empty_cache()
         del dA, dB, dC
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("sr", [mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_PLUS_TIMES_F64ACC, mmsr.MM_SR_PLUS_TIMES_F64])
+def test_auto_depth_runs_the_planned_depth(sr):
+    # MM_LEVELS_AUTO under the full budget of the planned depth, and under a
+    # budget one byte short of it (one level less)
+    import torch
+
+    m = n = k = 2048
+    A, B = inputs.uniform_f64(m, k, n, seed=7)
+    f32 = sr == mmsr.MM_SR_PLUS_TIMES_F32
+    Ax, Bx = (A.astype(np.float32), B.astype(np.float32)) if f32 else (A, B)
+    ref = oracle.mm_f64(Ax, Bx)
+    big = 1 << 36
+    p = mmsr.mm_plan_query(sr, mmsr.MM_LEVELS_AUTO, m, n, k, big)
+    assert p.levels >= 1
+    for budget in (int(p.workspace_min), int(p.workspace_min) - 1):
+        q = mmsr.mm_plan_query(sr, mmsr.MM_LEVELS_AUTO, m, n, k, budget)
+        assert q.levels == (p.levels if budget == p.workspace_min else p.levels - 1)
+        ws = workspace(budget)
+        dC = empty((m, n), torch.float32 if f32 else torch.float64)
+        mmsr.mm_strassen(mmsr.MM_LEVELS_AUTO, mmsr.MM_STRASSEN_WINOGRAD, sr, m, n, k, dev(Ax), dev(Bx), dC, ws,
+                         budget)
+        torch.cuda.synchronize()
+        assert canary_intact(ws, budget)
+        tol = fp32_strassen_tol(mmsr.MM_STRASSEN_WINOGRAD, q.levels) if f32 else 1e-12
+        assert rel_fro(dC.cpu().numpy(), ref) <= tol
