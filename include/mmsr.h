@@ -249,9 +249,12 @@ typedef struct {
  * Section 6): FP32 (+, x) tiles run in a persistent tensor-core kernel that
  * pops a cost-sorted tile queue, (min,+) tiles in a CUDA-core launch over a
  * cost-sorted tile list.  Asynchronous and capturable in a CUDA graph.
- * `problems` is a HOST array read during the call.  Workspace holds the
- * tile counter, the per-problem range verdicts and the split FP32 operands;
- * mm_batched_query reports the minimum.
+ * `problems` is a HOST array read during the call; 0 <= count <= 2^20.  The
+ * call copies its cost-sorted problem table into the workspace (as kernel
+ * parameters of a few small launches, so a captured graph replays the same
+ * table).  Workspace holds the tile counter, the per-problem range verdicts,
+ * the table and the split FP32 operands; mm_batched_query reports the
+ * minimum.
  */
 int mm_batched(int count, const mm_problem_t* problems, void* workspace, size_t workspace_bytes,
                void* stream);

@@ -41,7 +41,7 @@ __device__ int g_batched_status;
 // the arrival and loads of its first ring position, so its MMA wait runs out.
 __device__ int g_batched_skip_signal;
 
-constexpr int kMaxBatch = 512;
+constexpr int kMaxBatch = 1 << 20;  // problems per call (tile counts stay in int32)
 // FP32 tiles: 128 x 128, 64-wide k-blocks (128-byte swizzled rows) in a
 // 3-deep TMA ring, TMEM chunks of 8 k-blocks (512 k).  On the 512-problem
 // workload (median k ~ 340) this measured 0.68 ms for the kernel against
@@ -67,23 +67,42 @@ constexpr size_t BSMEM = 1024 + (size_t)TSTAGES * TSTAGE + 256;
 constexpr uint32_t BTMEM_COLS = 2 * TBN;
 constexpr int MPN = 256;  // (min,+) tile: 128 x 256
 
-struct BatchTable {
+// Per-problem row of the batch table.  The table lives in the caller's
+// workspace (written at the start of every call by small upload kernels that
+// carry it as a kernel parameter, so the call stays capturable), which
+// leaves the batch size free of the kernel-parameter limit.
+struct BatchRow {
+  int kind;  // 0: FP32 (+,x) on tensor cores, 1: (min,+) 256-wide tiles, 2: 128-wide
+  int m, n, k;
+  int row0a, row0b;  // FP32: first row of this A / B^T in the stacked split buffers
+  const void* A;
+  const void* B;
+  void* C;
+};
+// What the kernels take by value: sizes and the device addresses of the
+// table (rows in cost order and three prefix sums of tile counts).
+struct BatchHeader {
   int count;
   int total_tiles;  // FP32 tiles (persistent kernel)
-  int kind[kMaxBatch];  // 0: FP32 (+,x) on tensor cores, 1: (min,+) 256-wide tiles, 2: 128-wide
-  int m[kMaxBatch], n[kMaxBatch], k[kMaxBatch];
-  int tile_start[kMaxBatch + 1];     // 128 x 128 tiles of FP32 problems
-  int mp16_tile_start[kMaxBatch + 1];  // 128 x 256 packed tiles of (min,+) problems
-  int mp_tile_start[kMaxBatch + 1];  // 128 x 128 tiles of (min,+) problems, for the fallback
-  int mp16_total;
-  int mp_total;
-  int row0a[kMaxBatch];  // FP32: first row of this A in the stacked split buffers
-  int row0b[kMaxBatch];  // FP32: first row of this B^T in the stacked split buffers
-  const void* A[kMaxBatch];
-  const void* B[kMaxBatch];
-  void* C[kMaxBatch];
+  int mp16_total;   // packed (min,+) tiles
+  int mp_total;     // 32-bit (min,+) tiles
+  const BatchRow* rows;
+  const int* tile_start;       // [count + 1] 128 x 128 tiles of FP32 problems
+  const int* mp16_tile_start;  // [count + 1] packed tiles of (min,+) problems
+  const int* mp_tile_start;    // [count + 1] 128 x 128 tiles of (min,+) problems (fallback)
 };
-static_assert(sizeof(BatchTable) + 4 * sizeof(CUtensorMap) + 64 < 32764, "kernel parameter space");
+constexpr int kUploadBytes = 30720;  // table bytes per upload launch (kernel parameter)
+struct UploadChunk {
+  uint32_t len;
+  uint32_t pad[3];
+  uint8_t bytes[kUploadBytes];
+};
+
+__global__ void __launch_bounds__(256) batched_upload_kernel(const __grid_constant__ UploadChunk c,
+                                                             uint8_t* __restrict__ dst) {
+  for (uint32_t i = threadIdx.x * 16; i < c.len; i += blockDim.x * 16)
+    *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(c.bytes + i);
+}
 
 // ----------------------------------------------------------- pre-passes
 __device__ __forceinline__ void split1(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
@@ -93,78 +112,82 @@ __device__ __forceinline__ void split1(float x, __nv_bfloat16& h, __nv_bfloat16&
 
 // FP32 problems: A -> stacked hi/lo rows (pitch KP), B -> stacked hi/lo of
 // B^T (pitch KP); columns k..roundup(k, 64) are zero.  blockIdx.y = problem.
-__global__ void __launch_bounds__(256) batched_split_kernel(const __grid_constant__ BatchTable T,
+__global__ void __launch_bounds__(256) batched_split_kernel(const BatchHeader T,
                                                             int64_t KP, __nv_bfloat16* __restrict__ ahi,
                                                             __nv_bfloat16* __restrict__ alo,
                                                             __nv_bfloat16* __restrict__ bhi,
                                                             __nv_bfloat16* __restrict__ blo) {
-  const int p = blockIdx.y;
-  if (T.kind[p] != 0) return;
-  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
-  const int64_t kp = (k + TKA - 1) / TKA * TKA;
-  const float* A = static_cast<const float*>(T.A[p]);
-  const float* B = static_cast<const float*>(T.B[p]);
-  // A rows: one thread per 8 output columns
-  const int64_t cpr = kp / 8;
-  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < m * cpr; e += (int64_t)gridDim.x * 256) {
-    const int64_t r = e / cpr, c8 = (e - r * cpr) * 8;
-    __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) split1(c8 + t < k ? A[r * k + c8 + t] : 0.f, h[t], l[t]);
-    const int64_t off = (T.row0a[p] + r) * KP + c8;
-    *reinterpret_cast<uint4*>(ahi + off) = *reinterpret_cast<const uint4*>(h);
-    *reinterpret_cast<uint4*>(alo + off) = *reinterpret_cast<const uint4*>(l);
-  }
-  // B^T: 64 (k) x 32 (n) tiles through shared memory
-  __shared__ float tile[64][33];
-  const int64_t tk = kp / 64, tn = (n + 31) / 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int64_t tt = blockIdx.x; tt < tk * tn; tt += gridDim.x) {
-    const int64_t k0 = (tt / tn) * 64, n0 = (tt % tn) * 32;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int kk = ty + 8 * i;
-      const int64_t gk = k0 + kk, gn = n0 + tx;
-      tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.f;
-    }
-    __syncthreads();
-    const int row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
-    const int64_t gn = n0 + row;
-    if (gn < n) {
+  // problems with the grid's y stride (the y extent is capped at 65535)
+  for (int p = blockIdx.y; p < T.count; p += gridDim.y) {
+    if (T.rows[p].kind != 0) continue;
+    const int64_t m = T.rows[p].m, n = T.rows[p].n, k = T.rows[p].k;
+    const int64_t kp = (k + TKA - 1) / TKA * TKA;
+    const float* A = static_cast<const float*>(T.rows[p].A);
+    const float* B = static_cast<const float*>(T.rows[p].B);
+    // A rows: one thread per 8 output columns
+    const int64_t cpr = kp / 8;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < m * cpr; e += (int64_t)gridDim.x * 256) {
+      const int64_t r = e / cpr, c8 = (e - r * cpr) * 8;
       __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], h[e], l[e]);
-      const int64_t off = (T.row0b[p] + gn) * KP + k0 + chunk * 8;
-      *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(h);
-      *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(l);
+      for (int t = 0; t < 8; ++t) split1(c8 + t < k ? A[r * k + c8 + t] : 0.f, h[t], l[t]);
+      const int64_t off = (T.rows[p].row0a + r) * KP + c8;
+      *reinterpret_cast<uint4*>(ahi + off) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(alo + off) = *reinterpret_cast<const uint4*>(l);
     }
+    // B^T: 64 (k) x 32 (n) tiles through shared memory
+    __shared__ float tile[64][33];
+    const int64_t tk = kp / 64, tn = (n + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t tt = blockIdx.x; tt < tk * tn; tt += gridDim.x) {
+      const int64_t k0 = (tt / tn) * 64, n0 = (tt % tn) * 32;
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int kk = ty + 8 * i;
+        const int64_t gk = k0 + kk, gn = n0 + tx;
+        tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.f;
+      }
+      __syncthreads();
+      const int row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
+      const int64_t gn = n0 + row;
+      if (gn < n) {
+        __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], h[e], l[e]);
+        const int64_t off = (T.rows[p].row0b + gn) * KP + k0 + chunk * 8;
+        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(l);
+      }
+    }
+    __syncthreads();  // the next problem reuses `tile`
   }
 }
 
 // (min,+) problems: flag any entry outside the packed range (violation[p]
 // starts at 0, set by a memset before the launch).  blockIdx.y = problem.
-__global__ void __launch_bounds__(256) batched_range_kernel(const __grid_constant__ BatchTable T,
+__global__ void __launch_bounds__(256) batched_range_kernel(const BatchHeader T,
                                                             int* __restrict__ violation) {
-  const int p = blockIdx.y;
-  if (T.kind[p] == 0) return;
-  int bad = 0;
-  const int64_t stride = (int64_t)gridDim.x * 256;
-  const int64_t t0 = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  for (int pass = 0; pass < 2; ++pass) {
-    const int32_t* X = static_cast<const int32_t*>(pass ? T.B[p] : T.A[p]);
-    const int64_t cnt = pass ? (int64_t)T.k[p] * T.n[p] : (int64_t)T.m[p] * T.k[p];
-    const int64_t nv = aligned16(X) ? cnt / 4 : 0;
+  for (int p = blockIdx.y; p < T.count; p += gridDim.y) {
+    if (T.rows[p].kind == 0) continue;
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * 256;
+    const int64_t t0 = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int32_t* X = static_cast<const int32_t*>(pass ? T.rows[p].B : T.rows[p].A);
+      const int64_t cnt = pass ? (int64_t)T.rows[p].k * T.rows[p].n : (int64_t)T.rows[p].m * T.rows[p].k;
+      const int64_t nv = aligned16(X) ? cnt / 4 : 0;
 #pragma unroll 4
-    for (int64_t v = t0; v < nv; v += stride) {
-      const int4 q = __ldcs(reinterpret_cast<const int4*>(X) + v);
-      bad |= mp::out_of_pack_range(q.x) | mp::out_of_pack_range(q.y) | mp::out_of_pack_range(q.z) |
-             mp::out_of_pack_range(q.w);
+      for (int64_t v = t0; v < nv; v += stride) {
+        const int4 q = __ldcs(reinterpret_cast<const int4*>(X) + v);
+        bad |= mp::out_of_pack_range(q.x) | mp::out_of_pack_range(q.y) | mp::out_of_pack_range(q.z) |
+               mp::out_of_pack_range(q.w);
+      }
+      for (int64_t e = nv * 4 + t0; e < cnt; e += stride) bad |= mp::out_of_pack_range(X[e]);
     }
-    for (int64_t e = nv * 4 + t0; e < cnt; e += stride) bad |= mp::out_of_pack_range(X[e]);
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(&violation[p], 1);
   }
-  bad = __syncthreads_or(bad);
-  if (bad && threadIdx.x == 0) atomicOr(&violation[p], 1);
 }
 
 // 32-bit fallback for (min,+) problems whose inputs fall outside the packed
@@ -172,7 +195,7 @@ __global__ void __launch_bounds__(256) batched_range_kernel(const __grid_constan
 // tiles; CTAs of in-range problems exit at once.  Kept out of the persistent
 // kernel so its register demand does not press on the kernel's main paths.
 __global__ void __launch_bounds__(256, 2)
-    batched_minplus32_kernel(const __grid_constant__ BatchTable T, const int* __restrict__ violation) {
+    batched_minplus32_kernel(const BatchHeader T, const int* __restrict__ violation) {
   const int t = blockIdx.x;
   int lo = 0, hi = T.count - 1;  // last p with mp_tile_start[p] <= t
   while (lo < hi) {
@@ -180,14 +203,14 @@ __global__ void __launch_bounds__(256, 2)
     if (T.mp_tile_start[mid] <= t) lo = mid; else hi = mid - 1;
   }
   const int p = lo;
-  if (T.kind[p] == 0 || __ldcg(&violation[p]) == 0) return;
+  if (T.rows[p].kind == 0 || __ldcg(&violation[p]) == 0) return;
   extern __shared__ __align__(16) int32_t fsmem[];
-  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+  const int64_t m = T.rows[p].m, n = T.rows[p].n, k = T.rows[p].k;
   const int local = t - T.mp_tile_start[p];
   const int tiles_n = (int)((n + mp::BN - 1) / mp::BN);
-  const int32_t* A = static_cast<const int32_t*>(T.A[p]);
-  const int32_t* B = static_cast<const int32_t*>(T.B[p]);
-  int32_t* C = static_cast<int32_t*>(T.C[p]);
+  const int32_t* A = static_cast<const int32_t*>(T.rows[p].A);
+  const int32_t* B = static_cast<const int32_t*>(T.rows[p].B);
+  int32_t* C = static_cast<int32_t*>(T.rows[p].C);
   const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
   mp::minplus32_tile(A, B, C, (int32_t*)nullptr, 0, m, n, k, (int64_t)(local / tiles_n) * mp::BM,
                      (int64_t)(local % tiles_n) * mp::BN, (int64_t)0, (int)((k + mp::BK - 1) / mp::BK), vec,
@@ -199,13 +222,13 @@ __global__ void __launch_bounds__(256, 2)
 // 128 x 128 tiles where that pads its width less.  CTAs of problems outside
 // the packed range exit at once.
 template <int NP>
-__device__ __forceinline__ void batched_packed_tile(const BatchTable& T, int p, int local, uint32_t* psmem) {
-  const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+__device__ __forceinline__ void batched_packed_tile(const BatchHeader& T, int p, int local, uint32_t* psmem) {
+  const int64_t m = T.rows[p].m, n = T.rows[p].n, k = T.rows[p].k;
   constexpr int TN = mp::PackTile<NP>::TN;
   const int tiles_n = (int)((n + TN - 1) / TN);
-  const int32_t* A = static_cast<const int32_t*>(T.A[p]);
-  const int32_t* B = static_cast<const int32_t*>(T.B[p]);
-  int32_t* C = static_cast<int32_t*>(T.C[p]);
+  const int32_t* A = static_cast<const int32_t*>(T.rows[p].A);
+  const int32_t* B = static_cast<const int32_t*>(T.rows[p].B);
+  int32_t* C = static_cast<int32_t*>(T.rows[p].C);
   const bool vec = (k % 4 == 0) && (n % 4 == 0) && aligned16(A) && aligned16(B) && aligned16(C);
   mp::minplus16_tile<mp::SyncCta, NP>(A, B, C, (int32_t*)nullptr, 0, m, n, k, (int64_t)(local / tiles_n) * mp::PBM,
                                       (int64_t)(local % tiles_n) * TN, (int64_t)0, k, vec, (int)threadIdx.x,
@@ -213,7 +236,7 @@ __device__ __forceinline__ void batched_packed_tile(const BatchTable& T, int p, 
 }
 
 __global__ void __launch_bounds__(256, 2)
-    batched_minplus16_kernel(const __grid_constant__ BatchTable T, const int* __restrict__ violation) {
+    batched_minplus16_kernel(const BatchHeader T, const int* __restrict__ violation) {
   const int t = blockIdx.x;
   int lo = 0, hi = T.count - 1;  // last p with mp16_tile_start[p] <= t
   while (lo < hi) {
@@ -221,10 +244,10 @@ __global__ void __launch_bounds__(256, 2)
     if (T.mp16_tile_start[mid] <= t) lo = mid; else hi = mid - 1;
   }
   const int p = lo;
-  if (T.kind[p] == 0 || __ldcg(&violation[p]) != 0) return;
+  if (T.rows[p].kind == 0 || __ldcg(&violation[p]) != 0) return;
   __shared__ __align__(16) uint32_t psmem[mp::PSMEM_BYTES / 4];
   const int local = t - T.mp16_tile_start[p];
-  if (T.kind[p] == 1)
+  if (T.rows[p].kind == 1)
     batched_packed_tile<8>(T, p, local, psmem);
   else
     batched_packed_tile<4>(T, p, local, psmem);
@@ -237,7 +260,7 @@ __device__ __forceinline__ uint64_t kdesc(uint32_t saddr) {
 
 // ------------------------------------------------------ persistent kernel
 __global__ void __launch_bounds__(kBThreads, 1)
-    batched_kernel(const __grid_constant__ BatchTable T, const __grid_constant__ CUtensorMap tAhi,
+    batched_kernel(const BatchHeader T, const __grid_constant__ CUtensorMap tAhi,
                    const __grid_constant__ CUtensorMap tAlo, const __grid_constant__ CUtensorMap tBhi,
                    const __grid_constant__ CUtensorMap tBlo, int* __restrict__ counter) {
   extern __shared__ uint8_t smem_raw[];
@@ -313,7 +336,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
     }
     const int p = lo;
     const int local = t - T.tile_start[p];
-    const int64_t m = T.m[p], n = T.n[p], k = T.k[p];
+    const int64_t m = T.rows[p].m, n = T.rows[p].n, k = T.rows[p].k;
 
     {
       // ------------------------------------------------ FP32 tensor-core tile
@@ -324,7 +347,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
       if (warp == 0) {
         if (lane == 0) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          const int ya = T.row0a[p] + (int)i0, yb = T.row0b[p] + (int)j0;
+          const int ya = T.rows[p].row0a + (int)i0, yb = T.rows[p].row0b + (int)j0;
           for (int it = 0; it < nkb; ++it, ++ring) {
             const int s = ring % TSTAGES;
             const uint32_t round = ring / TSTAGES;
@@ -399,7 +422,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
         }
-        float* C = static_cast<float*>(T.C[p]);
+        float* C = static_cast<float*>(T.rows[p].C);
         const int64_t row = i0 + q * 32 + lane;
         if (row < m) {
           const int64_t c0 = j0 + half * (TBN / 2);
@@ -446,15 +469,30 @@ __global__ void __launch_bounds__(kBThreads, 1)
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct BatchPlan {
-  BatchTable T;
+  int count = 0, total_tiles = 0, mp16_total = 0, mp_total = 0;
+  std::vector<uint8_t> table;  // rows, then the three prefix sums (uploaded to off_table)
+  int64_t rows_bytes = 0, starts_bytes = 0;
   int64_t KP = 0, rows_a = 0, rows_b = 0;
-  int64_t off_viol = 256, off_ahi = 0, off_alo = 0, off_bhi = 0, off_blo = 0, total = 0;
+  int64_t off_viol = 256, off_table = 0, off_ahi = 0, off_alo = 0, off_bhi = 0, off_blo = 0, total = 0;
+
+  // The kernels' view of the table once it sits at `w + off_table`.
+  BatchHeader header(uint8_t* w) const {
+    BatchHeader H;
+    H.count = count;
+    H.total_tiles = total_tiles;
+    H.mp16_total = mp16_total;
+    H.mp_total = mp_total;
+    H.rows = reinterpret_cast<const BatchRow*>(w + off_table);
+    const int* st = reinterpret_cast<const int*>(w + off_table + rows_bytes);
+    H.tile_start = st;
+    H.mp16_tile_start = st + (count + 1);
+    H.mp_tile_start = st + 2 * (count + 1);
+    return H;
+  }
 };
 
 int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
   if (count < 0 || count > kMaxBatch || (count > 0 && !probs)) return MM_ERR_ARG;
-  BatchTable& T = P->T;
-  memset(&T, 0, sizeof(T));
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
   for (int i = 0; i < count; ++i) {
@@ -473,49 +511,64 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     if (probs[a].k != probs[b].k) return probs[a].k > probs[b].k;
     return (double)probs[a].m * probs[a].n > (double)probs[b].m * probs[b].n;
   });
+  std::vector<BatchRow> rows(count);
+  std::vector<int> starts(3 * (size_t)(count + 1));
+  int* tile_start = starts.data();
+  int* mp16_start = tile_start + (count + 1);
+  int* mp_start = mp16_start + (count + 1);
   int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0, mp16_tiles = 0;
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[order[i]];
+    BatchRow& r = rows[i];
     // (min,+): 128-wide tiles where they pad the width less than 256-wide ones
     const bool narrow = ((q.n + 127) / 128) * 128 < ((q.n + 255) / 256) * 256;
-    T.kind[i] = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : (narrow ? 2 : 1);
-    T.m[i] = (int)q.m;
-    T.n[i] = (int)q.n;
-    T.k[i] = (int)q.k;
-    T.A[i] = q.A;
-    T.B[i] = q.B;
-    T.C[i] = q.C;
-    T.tile_start[i] = (int)tiles;
-    T.mp16_tile_start[i] = (int)mp16_tiles;
-    T.mp_tile_start[i] = (int)mp_tiles;
+    r.kind = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : (narrow ? 2 : 1);
+    r.m = (int)q.m;
+    r.n = (int)q.n;
+    r.k = (int)q.k;
+    r.A = q.A;
+    r.B = q.B;
+    r.C = q.C;
+    r.row0a = r.row0b = 0;
+    tile_start[i] = (int)tiles;
+    mp16_start[i] = (int)mp16_tiles;
+    mp_start[i] = (int)mp_tiles;
     if (q.semiring == MM_SR_MIN_PLUS_I32 && q.m > 0 && q.n > 0) {
       mp_tiles += ((q.m + mp::BM - 1) / mp::BM) * ((q.n + mp::BN - 1) / mp::BN);
-      const int64_t tn = T.kind[i] == 2 ? 128 : MPN;
+      const int64_t tn = r.kind == 2 ? 128 : MPN;
       mp16_tiles += ((q.m + mp::PBM - 1) / mp::PBM) * ((q.n + tn - 1) / tn);
     }
-    if (T.kind[i] == 0 && q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN);
-    if (T.kind[i] == 0) {
-      T.row0a[i] = (int)ra;
-      T.row0b[i] = (int)rb;
+    if (r.kind == 0 && q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN);
+    if (r.kind == 0) {
+      r.row0a = (int)ra;
+      r.row0b = (int)rb;
       ra += q.m;
       rb += q.n;
       kp_max = std::max<int64_t>(kp_max, align_up(q.k > 0 ? q.k : 1, TKA));
     }
+    if (tiles > (int64_t)1 << 30 || mp_tiles > (int64_t)1 << 30 || mp16_tiles > (int64_t)1 << 30 ||
+        ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30)
+      return MM_ERR_SHAPE;
   }
-  if (tiles > (int64_t)1 << 30 || mp_tiles > (int64_t)1 << 30 || ra > (int64_t)1 << 30 ||
-      rb > (int64_t)1 << 30)
-    return MM_ERR_SHAPE;
-  T.tile_start[count] = (int)tiles;
-  T.mp16_tile_start[count] = (int)mp16_tiles;
-  T.mp_tile_start[count] = (int)mp_tiles;
-  T.mp16_total = (int)mp16_tiles;
-  T.mp_total = (int)mp_tiles;
-  T.count = count;
-  T.total_tiles = (int)tiles;
+  tile_start[count] = (int)tiles;
+  mp16_start[count] = (int)mp16_tiles;
+  mp_start[count] = (int)mp_tiles;
+  P->count = count;
+  P->total_tiles = (int)tiles;
+  P->mp16_total = (int)mp16_tiles;
+  P->mp_total = (int)mp_tiles;
+  P->rows_bytes = align_up((int64_t)count * (int64_t)sizeof(BatchRow), 16);
+  P->starts_bytes = align_up((int64_t)starts.size() * 4, 16);
+  P->table.assign((size_t)(P->rows_bytes + P->starts_bytes), 0);
+  if (count > 0) memcpy(P->table.data(), rows.data(), (size_t)count * sizeof(BatchRow));
+  memcpy(P->table.data() + P->rows_bytes, starts.data(), starts.size() * 4);
   P->KP = kp_max;
   P->rows_a = ra;
   P->rows_b = rb;
-  P->off_ahi = align_up(256 + 4 * kMaxBatch, 1024);
+  // workspace: [0] tile counter, [256] per-problem (min,+) range verdicts,
+  // then the table and the stacked split operands
+  P->off_table = align_up(P->off_viol + 4 * (int64_t)count, 256);
+  P->off_ahi = align_up(P->off_table + (int64_t)P->table.size(), 1024);
   P->off_alo = P->off_ahi + align_up(ra * kp_max * 2, 1024);
   P->off_bhi = P->off_alo + align_up(ra * kp_max * 2, 1024);
   P->off_blo = P->off_bhi + align_up(rb * kp_max * 2, 1024);
@@ -553,7 +606,7 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   BatchPlan P;
   int rc = make_plan(count, problems, &P);
   if (rc != MM_OK) return rc;
-  if (count == 0 || (P.T.total_tiles == 0 && P.T.mp_total == 0)) return MM_OK;
+  if (count == 0 || (P.total_tiles == 0 && P.mp_total == 0)) return MM_OK;
   if (!workspace) return MM_ERR_ARG;
   if (!aligned16(workspace)) return MM_ERR_ALIGN;
   if ((size_t)P.total > workspace_bytes) return MM_ERR_WORKSPACE;
@@ -565,11 +618,20 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   auto* alo = reinterpret_cast<__nv_bfloat16*>(w + P.off_alo);
   auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + P.off_bhi);
   auto* blo = reinterpret_cast<__nv_bfloat16*>(w + P.off_blo);
-  MMSR_TRY_STATUS(cudaMemsetAsync(w, 0, P.off_viol + 4 * kMaxBatch, st));
+  MMSR_TRY_STATUS(cudaMemsetAsync(w, 0, P.off_viol + 4 * (size_t)count, st));
+  const BatchHeader H = P.header(w);
+  const unsigned gy = (unsigned)std::min(count, 65535);
   {
     TraceScope tr(kTrSplitBf16, st);
-    batched_split_kernel<<<dim3(32, (unsigned)count), 256, 0, st>>>(P.T, P.KP, ahi, alo, bhi, blo);
-    batched_range_kernel<<<dim3(32, (unsigned)count), 256, 0, st>>>(P.T, violation);
+    // the table: kernel parameters of a few launches (captured by value)
+    UploadChunk chunk;
+    for (size_t off = 0; off < P.table.size(); off += kUploadBytes) {
+      chunk.len = (uint32_t)std::min<size_t>(kUploadBytes, P.table.size() - off);
+      memcpy(chunk.bytes, P.table.data() + off, chunk.len);
+      batched_upload_kernel<<<1, 256, 0, st>>>(chunk, w + P.off_table + off);
+    }
+    batched_split_kernel<<<dim3(32, gy), 256, 0, st>>>(H, P.KP, ahi, alo, bhi, blo);
+    batched_range_kernel<<<dim3(32, gy), 256, 0, st>>>(H, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
@@ -582,22 +644,22 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   static std::atomic<uint64_t> configured{0};
   MMSR_TRY_STATUS(smem_limit_once(batched_kernel, BSMEM, configured));
   const int sms = num_sms();
-  if (P.T.total_tiles > 0) {
+  if (P.total_tiles > 0) {
     TraceScope tr(kTrBatched, st);
-    const int grid = std::min(sms, P.T.total_tiles);
-    batched_kernel<<<grid, kBThreads, BSMEM, st>>>(P.T, ta_hi, ta_lo, tb_hi, tb_lo, counter);
+    const int grid = std::min(sms, P.total_tiles);
+    batched_kernel<<<grid, kBThreads, BSMEM, st>>>(H, ta_hi, ta_lo, tb_hi, tb_lo, counter);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
-  if (P.T.mp16_total > 0) {
+  if (P.mp16_total > 0) {
     TraceScope tr(kTrMinplus16Leaf, st);
-    batched_minplus16_kernel<<<(unsigned)P.T.mp16_total, 256, 0, st>>>(P.T, violation);
+    batched_minplus16_kernel<<<(unsigned)P.mp16_total, 256, 0, st>>>(H, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
-  if (P.T.mp_total > 0) {
+  if (P.mp_total > 0) {
     TraceScope tr(kTrMinplusLeaf, st);
     static std::atomic<uint64_t> fb_configured{0};
     MMSR_TRY_STATUS(smem_limit_once(batched_minplus32_kernel, mp::SMEM_BYTES, fb_configured));
-    batched_minplus32_kernel<<<(unsigned)P.T.mp_total, 256, mp::SMEM_BYTES, st>>>(P.T, violation);
+    batched_minplus32_kernel<<<(unsigned)P.mp_total, 256, mp::SMEM_BYTES, st>>>(H, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   return MM_OK;

@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--case", default="minplus4096")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--budget", type=int, default=0, help="extra m x n accumulator buffers")
+    ap.add_argument("--shape", default="", help="m,n,k of a rectangular product (f32 / f64acc / f64 cases)")
+    ap.add_argument("--budget-bytes", type=int, default=-1, help="workspace budget in bytes (overrides --budget)")
     a = ap.parse_args()
     import torch
 
@@ -120,13 +122,22 @@ def main():
         acc = 8
     else:
         raise SystemExit("unknown case " + a.case)
+    m = k = n
+    if a.shape:
+        m, n, k = (int(x) for x in a.shape.split(","))
+        gen = {torch.float32: lambda: inputs.normal_f32(m, k, n, seed=2),
+               torch.float64: lambda: inputs.uniform_f64(m, k, n, seed=3)}
+        A, B = gen[dt]() if dt in gen else (A, B)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    dC = torch.empty((n, n), dtype=dt, device="cuda")
-    p0 = mmsr.mm_plan_query(sr, -1, n, n, n, 0)
-    budget = int(p0.workspace_min) + a.budget * n * n * acc
+    dC = torch.empty((m, n), dtype=dt, device="cuda")
+    p0 = mmsr.mm_plan_query(sr, -1, m, n, k, 0)
+    budget = int(p0.workspace_min) + a.budget * m * n * acc
+    if a.budget_bytes >= 0:
+        budget = a.budget_bytes
     ws = torch.empty((max(budget, 16),), dtype=torch.uint8, device="cuda")
+    print("plan", mmsr.mm_plan_query(sr, -1, m, n, k, budget).kernel, "budget", budget)
     for _ in range(a.reps):
-        mmsr.mm_semiring(sr, n, n, n, dA, dB, dC, ws, budget)
+        mmsr.mm_semiring(sr, m, n, k, dA, dB, dC, ws, budget)
     torch.cuda.synchronize()
     print("done", a.case, "reps", a.reps)
 

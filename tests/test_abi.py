@@ -281,3 +281,16 @@ def test_strassen_auto_depth_under_budget(lib):
     # the automatic depth is refused only where Strassen is undefined
     assert mmsr.mm_plan_query(mmsr.MM_SR_MIN_PLUS_I32, A, 64, 64, 64, big, check=False).status == \
         mmsr.MM_ERR_UNSUPPORTED
+
+
+def test_batched_table_size_and_cap(lib):
+    """The batched call keeps its problem table in the workspace: the query
+    grows with the count (48-byte rows plus three prefix sums) and accepts
+    counts past the old 512 limit; 2^20 + 1 problems are refused."""
+    F32 = mmsr.MM_SR_PLUS_TIMES_F32
+    one = [(F32, 8, 8, 8, FAKE, FAKE, FAKE)]
+    w1 = mmsr.mm_batched_query(one * 1000)
+    w2 = mmsr.mm_batched_query(one * 2000)
+    assert w1 > 0 and w2 > w1
+    assert mmsr.mm_batched_query(one * 600) > 0
+    assert mmsr.mm_batched_query(one * ((1 << 20) + 1)) == 0

@@ -132,3 +132,12 @@ def test_k_zero_and_tiny_problems():
     outs = _launch(probs)
     assert np.all(outs[0] == 0.0) and np.all(outs[1] == mmsr.INF)
     _check(probs, outs)
+
+
+@pytest.mark.parametrize("capture", [False, True], ids=["eager", "graph-replay"])
+def test_batch_beyond_one_table_chunk(capture):
+    # 1500 problems: past the old by-value table limit of 512 and more than
+    # one table upload launch (48 bytes per problem, 30 KB per launch); every
+    # problem checked, eagerly and as a replayed graph
+    probs = _mixed(1500, seed=206, lo=1, hi=96, integer=True)
+    _check(probs, _launch(probs, capture=capture), exact_fp32=True)
