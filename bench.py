@@ -864,6 +864,26 @@ def extras_strassen(mmsr, lib, torch, sp, ctypes, book, A_sq, B_sq, rows, bf16, 
     book.add("sq32", res["fp32_tar_L1"], "error", _rows_of(torch, dC, rows))
     del ws
     torch.cuda.empty_cache()
+    # one level with the operand sums formed in the leaf's staging against the
+    # materialised operand passes, for the paper's formulas and Winograd's
+    for vname, var in (("paper", mmsr.MM_STRASSEN_PAPER), ("winograd", mmsr.MM_STRASSEN_WINOGRAD)):
+        for fused in (0, 1):
+            mmsr.mm_set_option(mmsr.MM_OPT_STRASSEN_FUSED, fused)
+            p = mmsr.mm_plan_query(sr, 1, n, n, n, 0)
+            ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+            fn = lambda: mmsr.mm_strassen(1, var, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min), sp)
+            lib.mm_trace_enable(1)
+            ms = _time_call(torch, fn, 3)
+            lib.mm_trace_enable(0)
+            kern = {nm: v["ms"] / 4 for nm, v in _trace(lib, ctypes).items()}
+            rec = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                   "workspace_bytes": int(p.workspace_min), "workspace_n2x4B": p.workspace_min / (n * n * 4.0),
+                   "kernel_ms": kern}
+            book.add("sq32", rec, "error", _rows_of(torch, dC, rows))
+            res["fp32_L1_%s_%s" % (vname, "fused_staging" if fused else "materialised")] = rec
+            del ws
+            torch.cuda.empty_cache()
+    mmsr.mm_set_option(mmsr.MM_OPT_STRASSEN_FUSED, 0)
     # STAR-Strassen-1 mixed plans: c classic in-place levels over L Strassen
     # levels; the workspace of one block product only
     for c, L in ((1, 1), (1, 2), (2, 1), (2, 2)):

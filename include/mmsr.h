@@ -366,6 +366,13 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   up to two levels, seven 7-bit slices (28 products; 2^-49) for three or
  *   four levels, whose post-additions amplify leaf errors more.  6 or 7
  *   forces a scheme.  Plans (and workspace sizes) follow the setting.
+ *   MM_OPT_STRASSEN_FUSED: 1 runs one-level FP32-mode Strassen products
+ *   (m, n multiples of 256, k of 64) with the operand sums formed inside the
+ *   leaf kernel's staging: converter warps read the source quadrants, add and
+ *   split them into the tensor core's operand ring, so the workspace is the
+ *   product stack alone (1.75 m n x 4 B instead of 5.25).  Results are
+ *   identical; 0 (default) keeps the materialised operand passes, which are
+ *   faster on this GPU.
  * Returns MM_OK, MM_ERR_ARG, or MM_ERR_CUDA (arming the switch failed).
  */
 typedef enum {
@@ -373,7 +380,8 @@ typedef enum {
   MM_OPT_MINPLUS_STREAMK = 2,
   MM_OPT_STRASSEN_TOP_F64 = 4,
   MM_OPT_TEST_SKIP_SIGNAL = 5,
-  MM_OPT_F64ACC_SLICES = 6
+  MM_OPT_F64ACC_SLICES = 6,
+  MM_OPT_STRASSEN_FUSED = 7
 } mm_option_t;
 int mm_set_option(int option, int value);
 

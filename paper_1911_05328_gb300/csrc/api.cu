@@ -317,6 +317,10 @@ int mm_set_option(int option, int value) {
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_streamk_mode = value;
       return MM_OK;
+    case MM_OPT_STRASSEN_FUSED:
+      if (value != 0 && value != 1) return MM_ERR_ARG;
+      g_strassen_fused = value;
+      return MM_OK;
     case MM_OPT_F64ACC_SLICES:
       if (value != 0 && value != 6 && value != 7) return MM_ERR_ARG;
       g_f64acc_slices = value;

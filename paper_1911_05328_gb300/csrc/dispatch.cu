@@ -35,11 +35,14 @@ int run_extended(int sr, int64_t m, int64_t n, int64_t k, const void* A, const v
 
 int read_device_status(cudaStream_t st, int* status) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return MM_ERR_CUDA;
-  int v[3] = {MM_OK, MM_OK, MM_OK};
+  int v[4] = {MM_OK, MM_OK, MM_OK, MM_OK};
   if (read_tc_status(&v[0]) != MM_OK) return MM_ERR_CUDA;
   if (read_f64acc_status(&v[1]) != MM_OK) return MM_ERR_CUDA;
   if (read_batched_status(&v[2]) != MM_OK) return MM_ERR_CUDA;
-  *status = v[0] != MM_OK ? v[0] : (v[1] != MM_OK ? v[1] : v[2]);
+  if (read_fused_status(&v[3]) != MM_OK) return MM_ERR_CUDA;
+  *status = MM_OK;
+  for (int i = 3; i >= 0; --i)
+    if (v[i] != MM_OK) *status = v[i];
   return MM_OK;
 }
 

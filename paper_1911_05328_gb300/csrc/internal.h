@@ -83,6 +83,15 @@ cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int
                                 int64_t k, int batches, cudaStream_t st);
 
 // Strassen engine
+// One FP32-mode Strassen level with the operand sums formed in the leaf's
+// staging (MM_OPT_STRASSEN_FUSED): shapes it takes, the launch of its seven
+// leaf products into a stack of (m/2) x (n/2) FP32 matrices, and its device
+// status word.
+extern int g_strassen_fused;
+bool strassen_fused_shape_ok(int64_t m, int64_t n, int64_t k);
+cudaError_t launch_strassen_fused_leaves(int variant, const float* A, const float* B, float* P, int64_t m, int64_t n,
+                                         int64_t k, int64_t lda, int64_t ldb, cudaStream_t st);
+int read_fused_status(int* status);
 // Strassen depth picked for MM_LEVELS_AUTO under a workspace budget.
 int choose_strassen_levels(int sr, int64_t m, int64_t n, int64_t k, size_t budget);
 int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t budget,

@@ -24,58 +24,11 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "strassen_tables.cuh"
 
 namespace mmsr {
 
-// ------------------------------------------------------ coefficient tables
-// One source for host and device: alpha / beta are [variant][product r]
-// [quadrant q], gamma is [variant][quadrant q][product r].  Kernels take the
-// variant as a template argument, so every coefficient is a compile-time
-// constant and the zero terms vanish from the generated code.
-__host__ __device__ constexpr int coef_alpha(int v, int r, int q) {
-  constexpr int8_t t[2][7][4] = {
-      {{1, 0, 0, 1}, {0, 0, 1, 1}, {1, 0, 0, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}},
-      {{1, 0, 0, 0}, {0, 1, 0, 0}, {1, 1, -1, -1}, {0, 0, 0, 1}, {0, 0, 1, 1}, {-1, 0, 1, 1}, {1, 0, -1, 0}}};
-  return t[v][r][q];
-}
-__host__ __device__ constexpr int coef_beta(int v, int r, int q) {
-  constexpr int8_t t[2][7][4] = {
-      {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0}, {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}},
-      {{1, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}, {1, -1, -1, 1}, {-1, 1, 0, 0}, {1, -1, 0, 1}, {0, -1, 0, 1}}};
-  return t[v][r][q];
-}
-__host__ __device__ constexpr int coef_gamma(int v, int q, int r) {
-  constexpr int8_t t[2][4][7] = {
-      {{1, 0, 0, 1, -1, 0, 1}, {0, 0, 1, 0, 1, 0, 0}, {0, 1, 0, 1, 0, 0, 0}, {1, -1, 1, 0, 0, 1, 0}},
-      {{1, 1, 0, 0, 0, 0, 0}, {1, 0, 1, 0, 1, 1, 0}, {1, 0, 0, -1, 0, 1, 1}, {1, 0, 0, 0, 1, 1, 1}}};
-  return t[v][q][r];
-}
-
 namespace {
-
-template <typename T>
-__device__ __forceinline__ T apply(int c, T acc, T x) {
-  return c == 0 ? acc : (c > 0 ? acc + x : acc - x);
-}
-
-// Operand sum r of one side (0: alpha over A's quadrants, 1: beta over B's),
-// terms in the fixed quadrant order 00, 01, 10, 11.
-template <int VARIANT, int SIDE, typename T>
-__device__ __forceinline__ T combo4(int r, T x0, T x1, T x2, T x3) {
-  T acc = T(0);
-  if constexpr (SIDE == 0) {
-    acc = apply(coef_alpha(VARIANT, r, 0), acc, x0);
-    acc = apply(coef_alpha(VARIANT, r, 1), acc, x1);
-    acc = apply(coef_alpha(VARIANT, r, 2), acc, x2);
-    acc = apply(coef_alpha(VARIANT, r, 3), acc, x3);
-  } else {
-    acc = apply(coef_beta(VARIANT, r, 0), acc, x0);
-    acc = apply(coef_beta(VARIANT, r, 1), acc, x1);
-    acc = apply(coef_beta(VARIANT, r, 2), acc, x2);
-    acc = apply(coef_beta(VARIANT, r, 3), acc, x3);
-  }
-  return acc;
-}
 
 // ------------------------------------------------------- vector helpers
 // V consecutive elements through one 16- or 8-byte access when V * sizeof(T)
@@ -668,8 +621,22 @@ struct StrassenLayout {
 // which are dead once their digit slices are written.
 int intermediate_level(int L) { return L >= 3 ? L - 2 : 0; }
 
+bool fused_level(int L, int sr, int64_t m, int64_t n, int64_t k) {
+  return L == 1 && sr == MM_SR_PLUS_TIMES_F32 && g_strassen_fused && strassen_fused_shape_ok(m, n, k);
+}
+
 StrassenLayout strassen_layout(int L, int sr, int64_t m, int64_t n, int64_t k) {
   StrassenLayout s;
+  if (fused_level(L, sr, m, n, k)) {
+    // operand sums formed in the leaf's staging: the product stack only
+    memset(&s, 0, sizeof(s));
+    s.mL = m / 2;
+    s.nL = n / 2;
+    s.kL = k / 2;
+    s.leaves = 7;
+    s.total = align_up(7 * s.mL * s.nL * 4, 1024);
+    return s;
+  }
   const int esz = (sr == MM_SR_PLUS_TIMES_F32) ? 4 : 8;
   s.mL = m >> L;
   s.nL = n >> L;
@@ -901,6 +868,16 @@ int run_view(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, c
              int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc, int accumulate, uint8_t* w,
              const StrassenLayout& S, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
+  if (fused_level(levels, sr, m, n, k)) {
+    float* P = reinterpret_cast<float*>(w + S.off_p);
+    e = launch_strassen_fused_leaves(variant, static_cast<const float*>(A), static_cast<const float*>(B), P, m, n, k,
+                                     lda, ldb, st);
+    if (e == cudaSuccess) {
+      TraceScope tr(kTrStrassenPost, st);
+      e = fold<float>(1, variant, P, m, n, w, S, static_cast<float*>(C), ldc, accumulate, kSumPlain, st);
+    }
+    return e == cudaSuccess ? MM_OK : report_cuda(e, "fused Strassen level");
+  }
   if (sr == MM_SR_PLUS_TIMES_F32) {
     auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + S.off_ahi);
     auto* alo = reinterpret_cast<__nv_bfloat16*>(w + S.off_alo);
@@ -969,6 +946,7 @@ void fill_plan(int levels, int sr, int64_t total, mm_plan_t* p) {
 }  // namespace
 
 int g_strassen_top_f64 = 0;  // mm_set_option(MM_OPT_STRASSEN_TOP_F64, ...)
+int g_strassen_fused = 0;    // mm_set_option(MM_OPT_STRASSEN_FUSED, ...)
 
 
 void strassen_tables(int variant, int8_t* alpha, int8_t* beta, int8_t* gamma) {

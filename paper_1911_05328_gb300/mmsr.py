@@ -31,6 +31,7 @@ MM_OPT_MINPLUS_STREAMK = 2
 MM_OPT_STRASSEN_TOP_F64 = 4
 MM_OPT_TEST_SKIP_SIGNAL = 5
 MM_OPT_F64ACC_SLICES = 6
+MM_OPT_STRASSEN_FUSED = 7
 
 MM_CLOSURE_EARLY_EXIT = 1
 

@@ -294,3 +294,22 @@ def test_batched_table_size_and_cap(lib):
     assert w1 > 0 and w2 > w1
     assert mmsr.mm_batched_query(one * 600) > 0
     assert mmsr.mm_batched_query(one * ((1 << 20) + 1)) == 0
+
+
+def test_fused_staging_plan(lib):
+    """With MM_OPT_STRASSEN_FUSED a one-level FP32-mode plan whose leaves tile
+    by 128 x 128 x 32 holds only the seven products; other shapes, depths and
+    semirings keep the materialised plan."""
+    f32 = mmsr.MM_SR_PLUS_TIMES_F32
+    n = 4096
+    base = mmsr.mm_plan_query(f32, 1, n, n, n, 0).workspace_min
+    try:
+        assert mmsr.mm_set_option(mmsr.MM_OPT_STRASSEN_FUSED, 1) == mmsr.MM_OK
+        assert mmsr.mm_plan_query(f32, 1, n, n, n, 0).workspace_min == 7 * (n // 2) ** 2 * 4
+        assert mmsr.mm_plan_query(f32, 1, 400, 260, 128, 0).workspace_min == \
+            mmsr.mm_plan_query(f32, 1, 400, 260, 128, 0).workspace_min
+        assert mmsr.mm_plan_query(f32, 2, n, n, n, 0).workspace_min > 7 * (n // 2) ** 2 * 4
+        assert mmsr.mm_set_option(mmsr.MM_OPT_STRASSEN_FUSED, 2, check=False) == mmsr.MM_ERR_ARG
+    finally:
+        mmsr.mm_set_option(mmsr.MM_OPT_STRASSEN_FUSED, 0)
+    assert mmsr.mm_plan_query(f32, 1, n, n, n, 0).workspace_min == base
