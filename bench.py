@@ -731,13 +731,14 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     book.add("n8192_f32", out["fp32_bf16x3_n8192"], "error", _rows_of(torch, dC, rows))
     del dA, dB, dC, ws
     torch.cuda.empty_cache()
-    # a long-k product with few output tiles (1024 x 1024 x 16384, normal
-    # inputs, seed 2): the classic one-tile-per-CTA grid (32 CTAs), the
-    # budgeted split-K (s = 4) and the stream-K form
-    m = nn = 1024
-    kk = 16384
+    # k-parallel forms where the classic grid quantises badly: 2048 x 4096 x
+    # 8192 (normal inputs, seed 2) has 256 tiles of 128 x 256 = 1.7 waves on
+    # 152 SMs: the classic grid, the budgeted split-K (s = 4) and the
+    # stream-K form (equal per-SM shares of the (tile, k-block) units)
+    m, nn = 2048, 4096
+    kk = 8192
     A, B = inputs.normal_f32(m, kk, nn, seed=2)
-    book.add_set("f32_1024x16384", lambda A=A, B=B: (A, B), sample_rows(m))
+    book.add_set("f32_kpar", lambda A=A, B=B: (A, B), sample_rows(m))
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.empty((m, nn), dtype=torch.float32, device="cuda")
     sr = mmsr.MM_SR_PLUS_TIMES_F32
@@ -757,9 +758,9 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
         ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, m, nn, kk, dA, dB, dC, ws, budget, sp), 10)
         rec[name] = {"ms": ms, "gops": 2.0 * m * nn * kk / (ms * 1e-3) / 1e9, "kernel": int(p.kernel),
                      "split_k": int(p.split_k), "workspace_bytes": budget}
-        book.add("f32_1024x16384", rec[name], "error", _rows_of(torch, dC, sample_rows(m)))
+        book.add("f32_kpar", rec[name], "error", _rows_of(torch, dC, sample_rows(m)))
         del ws
-    out["fp32_1024x1024x16384_k_parallel"] = rec
+    out["fp32_2048x4096x8192_k_parallel"] = rec
     del dA, dB, dC
     torch.cuda.empty_cache()
     # FP64-accuracy mode at n = 8192 (uniform[-1,1], seed 3)

@@ -384,10 +384,11 @@ SkGeom sk_geom(int64_t m, int64_t n, int64_t k) {
   g.ki = (k + SKBK - 1) / SKBK;
   g.total = g.tiles * g.ki;
   // the same number of CTAs on every SM (up to four), each with at least
-  // four k-blocks where the product has that many: every SM then gets the
-  // same share of the iteration space, to within one k-block per CTA
+  // sixteen k-blocks where the product has that many (shorter ranges leave
+  // each CTA's load latency exposed): every SM then gets the same share of
+  // the iteration space, to within one k-block per CTA
   const int64_t sms = num_sms();
-  int64_t per = g.total / (4 * sms);
+  int64_t per = g.total / (16 * sms);
   if (per > 4) per = 4;
   int64_t P = per >= 1 ? per * sms : std::max<int64_t>(1, std::min<int64_t>(sms, g.total / 4));
   g.P = (int)P;

@@ -834,8 +834,15 @@ int plan_f32(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p) {
     p->workspace_used = L.min_bytes;
     return MM_OK;
   }
-  if (f32_sk_wanted(m, n, k) && budget >= (size_t)(L.min_bytes + f32_sk(m, n, k).bytes)) {
-    // few tiles and room for the per-CTA partial tiles: the stream-K form
+  // One to four waves of tiles and room for the per-CTA partial tiles: the
+  // stream-K form evens out the last wave.  Under one wave the same budget
+  // always buys enough split-K slices to fill the GPU, and split-K is the
+  // faster of the two there (its CTAs of one slice share their operands
+  // through L2, stream-K's ranges spread over all of k: 1024 x 1024 x 16384
+  // took 129 us in stream-K against 72 + 7 us with s = 4).
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + kTcBN - 1) / kTcBN);
+  if (f32_sk_wanted(m, n, k) && tiles >= (int64_t)num_sms() &&
+      budget >= (size_t)(L.min_bytes + f32_sk(m, n, k).bytes)) {
     p->kernel = 5;
     p->split_k = 1;
     p->workspace_used = L.min_bytes + f32_sk(m, n, k).bytes;
