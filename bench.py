@@ -435,7 +435,7 @@ def main():
     pC = torch.empty((N, N), dtype=torch.float64).pin_memory()
     dA2, dB2, dC2 = [dA, torch.empty_like(dA)], [dB, torch.empty_like(dB)], [dC, torch.empty_like(dC)]
     cs_up, cs_down = torch.cuda.Stream(), torch.cuda.Stream()
-    e2e_steps = max(2, min(args.steps, 10))
+    e2e_steps = max(2, min(args.steps, 20))
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     in_ready = [torch.cuda.Event() for _ in range(2)]
     in_free = [torch.cuda.Event() for _ in range(2)]
