@@ -192,8 +192,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ drain
+    // a warp reads only its own TMEM lane quarter, warp % 4; the first four
+    // drain warps take columns 0..63, the next four columns 64..127
     const int dw = warp - 1 - kConv;  // 0..7
-    const int q = dw & 3, half = dw >> 2;
+    const int q = warp & 3, half = dw >> 2;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     float sum[FBN / 2];
 #pragma unroll
