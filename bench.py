@@ -683,7 +683,9 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
                                                   "TFLOP/s", fp64_src)}
     book.add("n256", out["fp64_n256_budget0"], "error", dC.cpu().numpy())
     # the same product in the stream-K form (Fig. tar-mm) with the budget of
-    # its per-CTA partial tiles
+    # its per-CTA partial tiles (forced: the planner keeps the 8 x 8 tiles
+    # here, which balance without slots)
+    mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, 2)
     for b in (1 << 20, 1 << 22, 1 << 24):
         p = mmsr.mm_plan_query(mmsr.MM_SR_PLUS_TIMES_F64, -1, 256, 256, 256, b)
         if p.kernel == 6:
@@ -695,8 +697,12 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
                                         "roofline": _roof("fp64", 2 * 256 ** 3 / (ms * 1e-3) / 1e12, fp64_peak,
                                                           "TFLOP/s", fp64_src)}
             book.add("n256", out["fp64_n256_streamk"], "error", dC.cpu().numpy())
+            mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, 1)
+            out["fp64_n256_streamk"]["planner_kernel_at_this_budget"] = int(
+                mmsr.mm_plan_query(mmsr.MM_SR_PLUS_TIMES_F64, -1, 256, 256, 256, w).kernel)
             del ws
             break
+    mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, 1)
     n = 8192
     rows = sample_rows(n)
     A, B = inputs.uniform_f64(n, n, n, seed=2)
@@ -731,38 +737,46 @@ def extras_fp(mmsr, lib, torch, sp, ctypes, book, fp64_peak, fp64_src, bf16, bf1
     book.add("n8192_f32", out["fp32_bf16x3_n8192"], "error", _rows_of(torch, dC, rows))
     del dA, dB, dC, ws
     torch.cuda.empty_cache()
-    # k-parallel forms where the classic grid quantises badly: 2048 x 4096 x
-    # 8192 (normal inputs, seed 2) has 256 tiles of 128 x 256 = 1.7 waves on
-    # 152 SMs: the classic grid, the budgeted split-K (s = 4) and the
-    # stream-K form (equal per-SM shares of the (tile, k-block) units)
-    m, nn = 2048, 4096
-    kk = 8192
-    A, B = inputs.normal_f32(m, kk, nn, seed=2)
-    book.add_set("f32_kpar", lambda A=A, B=B: (A, B), sample_rows(m))
-    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    dC = torch.empty((m, nn), dtype=torch.float32, device="cuda")
+    # k-parallel forms where the classic grid quantises: 2048 x n x 8192
+    # (normal inputs, seed 2) in 128 x 256 tiles, n = 2560 (160 tiles, 1.05
+    # waves on 152 SMs: the planner takes stream-K) and n = 4096 (256 tiles,
+    # 1.68 waves: the classic grid).  Each shape: the classic grid (stream-K
+    # off, no budget), the budgeted split-K at the stream-K budget (stream-K
+    # off), stream-K over every tile's units (option 2), whole waves first
+    # and stream-K over the rest (option 3), and the planner's own choice.
+    m, kk = 2048, 8192
     sr = mmsr.MM_SR_PLUS_TIMES_F32
-    base = int(mmsr.mm_plan_query(sr, -1, m, nn, kk, 0).workspace_min)
-    rec = {}
-    for name, budget in (("classic", base), ("split_k4", base + 3 * m * nn * 4), ("streamk", None)):
-        if budget is None:
-            for extra in (1 << 26, 1 << 28):
-                p = mmsr.mm_plan_query(sr, -1, m, nn, kk, base + extra)
-                if p.kernel == 5:
-                    budget = int(p.workspace_used)
-                    break
-        if budget is None:
-            continue
-        p = mmsr.mm_plan_query(sr, -1, m, nn, kk, budget)
-        ws = torch.empty((budget,), dtype=torch.uint8, device="cuda")
-        ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, m, nn, kk, dA, dB, dC, ws, budget, sp), 10)
-        rec[name] = {"ms": ms, "gops": 2.0 * m * nn * kk / (ms * 1e-3) / 1e9, "kernel": int(p.kernel),
-                     "split_k": int(p.split_k), "workspace_bytes": budget}
-        book.add("f32_kpar", rec[name], "error", _rows_of(torch, dC, sample_rows(m)))
-        del ws
-    out["fp32_2048x4096x8192_k_parallel"] = rec
-    del dA, dB, dC
-    torch.cuda.empty_cache()
+    for nn in (2560, 4096):
+        A, B = inputs.normal_f32(m, kk, nn, seed=2)
+        key = "f32_kpar_%d" % nn
+        book.add_set(key, lambda A=A, B=B: (A, B), sample_rows(m))
+        dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        dC = torch.empty((m, nn), dtype=torch.float32, device="cuda")
+        base = int(mmsr.mm_plan_query(sr, -1, m, nn, kk, 0).workspace_min)
+        mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, 2)
+        skb = None
+        for extra in (1 << 26, 1 << 28):
+            p = mmsr.mm_plan_query(sr, -1, m, nn, kk, base + extra)
+            if p.kernel == 5:
+                skb = int(p.workspace_used)
+                break
+        rec = {"tiles": (m // 128) * (nn // 256)}
+        for name, opt, budget in (("classic", 0, base), ("split_k", 0, skb), ("streamk", 2, skb),
+                                  ("whole_waves_then_streamk", 3, skb), ("planner", 1, skb)):
+            if budget is None:
+                continue
+            mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, opt)
+            p = mmsr.mm_plan_query(sr, -1, m, nn, kk, budget)
+            ws = torch.empty((budget,), dtype=torch.uint8, device="cuda")
+            ms = _time_call(torch, lambda: mmsr.mm_semiring(sr, m, nn, kk, dA, dB, dC, ws, budget, sp), 10)
+            rec[name] = {"ms": ms, "gops": 2.0 * m * nn * kk / (ms * 1e-3) / 1e9, "kernel": int(p.kernel),
+                         "split_k": int(p.split_k), "workspace_bytes": budget}
+            book.add(key, rec[name], "error", _rows_of(torch, dC, sample_rows(m)))
+            del ws
+        mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, 1)
+        out["fp32_2048x%dx8192_k_parallel" % nn] = rec
+        del dA, dB, dC
+        torch.cuda.empty_cache()
     # FP64-accuracy mode at n = 8192 (uniform[-1,1], seed 3)
     A, B = inputs.uniform_f64(n, n, n, seed=3)
     book.add_set("n8192_f64", lambda A=A, B=B: (A, B), rows)

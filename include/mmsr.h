@@ -373,6 +373,19 @@ int mm_trace_summary(int kernel_id, int64_t* launches, double* total_ms);
  *   product stack alone (1.75 m n x 4 B instead of 5.25).  Results are
  *   identical; 0 (default) keeps the materialised operand passes, which are
  *   faster on this GPU.
+ *   MM_OPT_F32_STREAMK: when the FP32 mode (+,x) product may run the
+ *   stream-K form (kernel id 5, Fig. tar-mm: persistent CTAs, partial tiles
+ *   in per-CTA slots folded in k order by the last contributor).  1
+ *   (default): the planner's rule; 0: never (classic grid or split-K); 2:
+ *   whenever the budget holds its slots and the tiles fill one to four
+ *   waves, every tile split into equal ranges of (tile, k-block) units; 3:
+ *   as 2, but the whole waves of tiles run as plain tiles first and only the
+ *   tiles left over are split.  Results agree to rounding (the k order of a
+ *   split tile's sum differs).
+ *   MM_OPT_F64_STREAMK: the same for the plain FP64 product's stream-K
+ *   form (kernel id 6; 32 x 32 register tiles, two slots per CTA): 1
+ *   (default) the planner's rule, 0 never, 2 whenever the budget holds its
+ *   slots and the 64 x 64 grid fills under four waves of two CTAs per SM.
  * Returns MM_OK, MM_ERR_ARG, or MM_ERR_CUDA (arming the switch failed).
  */
 typedef enum {
@@ -381,7 +394,9 @@ typedef enum {
   MM_OPT_STRASSEN_TOP_F64 = 4,
   MM_OPT_TEST_SKIP_SIGNAL = 5,
   MM_OPT_F64ACC_SLICES = 6,
-  MM_OPT_STRASSEN_FUSED = 7
+  MM_OPT_STRASSEN_FUSED = 7,
+  MM_OPT_F32_STREAMK = 8,
+  MM_OPT_F64_STREAMK = 9
 } mm_option_t;
 int mm_set_option(int option, int value);
 

@@ -321,6 +321,14 @@ int mm_set_option(int option, int value) {
       if (value != 0 && value != 1) return MM_ERR_ARG;
       g_strassen_fused = value;
       return MM_OK;
+    case MM_OPT_F32_STREAMK:
+      if (value < 0 || value > 3) return MM_ERR_ARG;
+      g_f32_streamk = value;
+      return MM_OK;
+    case MM_OPT_F64_STREAMK:
+      if (value < 0 || value > 2) return MM_ERR_ARG;
+      g_f64_streamk = value;
+      return MM_OK;
     case MM_OPT_F64ACC_SLICES:
       if (value != 0 && value != 6 && value != 7) return MM_ERR_ARG;
       g_f64acc_slices = value;

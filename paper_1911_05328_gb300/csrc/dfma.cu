@@ -404,12 +404,27 @@ size_t dfma_streamk_bytes(int64_t m, int64_t n, int64_t k) {
   return (size_t)g.P * 2 * SKT * SKT * sizeof(double) + (size_t)((g.tiles * 4 + 255) / 256 * 256);
 }
 
+int g_f64_streamk = 1;  // mm_set_option(MM_OPT_F64_STREAMK, ...)
+
 bool dfma_streamk_wanted(int64_t m, int64_t n, int64_t k) {
-  // only where the 64 x 64 grid fills less than four waves of two CTAs per
-  // SM, and the k-split has room (index arithmetic in int64 without overflow)
+  // shapes it takes: the 64 x 64 grid fills less than four waves of two CTAs
+  // per SM, and the k-split has room (index arithmetic in int64 without
+  // overflow)
   const int64_t tiles64 = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
   const SkGeom g = sk_geom(m, n, k);
-  return k > 0 && tiles64 < 8 * (int64_t)num_sms() && g.total < ((int64_t)1 << 40) && g.ki >= 4;
+  if (g_f64_streamk == 0 || !(k > 0 && tiles64 < 8 * (int64_t)num_sms() && g.total < ((int64_t)1 << 40) && g.ki >= 4))
+    return false;
+  if (g_f64_streamk == 2) return true;
+  // The planner's rule.  The FP64 pipe bounds both forms, so the classic
+  // grid takes ceil(tiles / SMs) tile-times and stream-K tiles / SMs plus its
+  // folds (1024 x 64c x 4096: 304 tiles 8.18 against 8.25 ms, 320 tiles 12.24
+  // against 8.69).  Under two CTAs per SM of 64 x 64 tiles the classic path
+  // runs 16 x 16 or 8 x 8 tiles, many per SM, which balance without slots
+  // (n = 256: 33 against 43 us).  So: at least two tiles per SM, and a last
+  // wave empty enough to save 5%.
+  const int64_t sms = num_sms();
+  const int64_t waves = (tiles64 + sms - 1) / sms;
+  return tiles64 >= 2 * sms && waves * sms * 100 >= 105 * tiles64;
 }
 
 cudaError_t launch_dfma_streamk(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,

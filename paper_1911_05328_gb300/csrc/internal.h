@@ -44,6 +44,8 @@ int run_orand(int64_t m, int64_t n, int64_t k, const uint8_t* A, const uint8_t* 
 // slices (21 products) or seven 7-bit slices (28 products); the number of
 // Strassen levels above the leaves picks the scheme (f64acc_slices_for_levels)
 extern int g_f64acc_slices;  // mm_set_option(MM_OPT_F64ACC_SLICES, ...)
+extern int g_f32_streamk;    // mm_set_option(MM_OPT_F32_STREAMK, ...)
+extern int g_f64_streamk;    // mm_set_option(MM_OPT_F64_STREAMK, ...)
 int f64acc_slices_for_levels(int levels);
 int plan_f64acc(int64_t m, int64_t n, int64_t k, size_t budget, mm_plan_t* p);
 int run_f64acc(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,

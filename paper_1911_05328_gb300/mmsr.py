@@ -32,6 +32,8 @@ MM_OPT_STRASSEN_TOP_F64 = 4
 MM_OPT_TEST_SKIP_SIGNAL = 5
 MM_OPT_F64ACC_SLICES = 6
 MM_OPT_STRASSEN_FUSED = 7
+MM_OPT_F32_STREAMK = 8
+MM_OPT_F64_STREAMK = 9
 
 MM_CLOSURE_EARLY_EXIT = 1
 

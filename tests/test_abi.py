@@ -210,6 +210,14 @@ def test_option_argument_checks(lib):
         assert mmsr.mm_set_option(3, v, check=False) == mmsr.MM_ERR_ARG
     assert mmsr.mm_set_option(mmsr.MM_OPT_TEST_SKIP_SIGNAL, 4, check=False) == mmsr.MM_ERR_ARG
     assert mmsr.mm_set_option(mmsr.MM_OPT_TEST_SKIP_SIGNAL, -1, check=False) == mmsr.MM_ERR_ARG
+    for v in (4, -1):
+        assert mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, v, check=False) == mmsr.MM_ERR_ARG
+    for v in (0, 2, 3, 1):  # ends on the default
+        assert mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, v, check=False) == mmsr.MM_OK
+    for v in (3, -1):
+        assert mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, v, check=False) == mmsr.MM_ERR_ARG
+    for v in (0, 2, 1):
+        assert mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, v, check=False) == mmsr.MM_OK
 
 
 def test_noalloc_host_checks(lib):

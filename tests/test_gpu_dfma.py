@@ -62,6 +62,15 @@ def test_k_zero_writes_zero():
     assert np.all(dC.cpu().numpy() == 0.0)
 
 
+@pytest.fixture
+def sk_forced():
+    # the stream-K form wherever it applies (option 2), not only where the
+    # planner's rule takes it
+    mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, 2)
+    yield
+    mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, 1)
+
+
 def _streamk_budget(m, n, k):
     """Smallest budget for which the planner picks the stream-K form (the
     per-CTA partial tiles plus one counter per tile), or None when the
@@ -75,7 +84,7 @@ def _streamk_budget(m, n, k):
 
 @pytest.mark.parametrize("m,n,k", [(256, 256, 256), (1, 1, 100), (33, 65, 77), (130, 257, 1000), (100, 40, 4096),
                                    (512, 512, 64), (600, 700, 300)])
-def test_streamk_form_matches_oracle(m, n, k):
+def test_streamk_form_matches_oracle(m, n, k, sk_forced):
     # the zero-temporary k-parallel form (Fig. tar-mm): per-CTA partial tiles
     # folded in k order by the last CTA to arrive; ragged tiles and k tails
     w = _streamk_budget(m, n, k)
@@ -87,14 +96,14 @@ def test_streamk_form_matches_oracle(m, n, k):
     np.testing.assert_array_equal(run(A, B, w), C1)
 
 
-def test_streamk_small_integers_exact():
+def test_streamk_small_integers_exact(sk_forced):
     m, n, k = 200, 190, 3000
     A, B = inputs.small_int(m, k, n, seed=43)
     w = _streamk_budget(m, n, k)
     np.testing.assert_array_equal(run(A, B, w), oracle.mm_f64(A, B))
 
 
-def test_streamk_n256_workload():
+def test_streamk_n256_workload(sk_forced):
     # the n = 256 uniform[-1,1] workload (seed 0) in the stream-K form,
     # beside the budget-0 path of the same product
     A, B = inputs.uniform_f64(256, 256, 256, seed=0)
@@ -105,8 +114,25 @@ def test_streamk_n256_workload():
     assert rel_fro(run(A, B, 0), ref) <= TOL
 
 
-def test_streamk_not_taken_for_large_grids_or_small_budgets():
+def test_streamk_not_taken_for_large_grids_or_small_budgets(sk_forced):
     assert mmsr.mm_plan_query(SR, -1, 4096, 4096, 4096, 1 << 30).kernel != 6
     w = _streamk_budget(256, 256, 256)
     assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, w - 1).kernel != 6
     assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, 0).kernel != 6
+
+
+def test_streamk_planner_rule():
+    # the planner's own rule (option 1): not at n = 256, whose 8 x 8 tiles
+    # already balance; yes just past one wave of two 64 x 64 CTAs per SM
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert mmsr.mm_plan_query(SR, -1, 256, 256, 256, 1 << 26).kernel != 6
+    tiles = 2 * sms + max(1, sms // 10)
+    m, n, k = 64 * tiles, 64, 2048
+    assert mmsr.mm_plan_query(SR, -1, m, n, k, 1 << 28).kernel == 6
+    mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, 0)
+    try:
+        assert mmsr.mm_plan_query(SR, -1, m, n, k, 1 << 28).kernel != 6
+    finally:
+        mmsr.mm_set_option(mmsr.MM_OPT_F64_STREAMK, 1)

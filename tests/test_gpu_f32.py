@@ -122,11 +122,22 @@ def run_budget(A, B, budget):
     return dC.cpu().numpy()
 
 
+@pytest.fixture
+def f32_streamk_mode(request):
+    mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, request.param)
+    yield request.param
+    mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, 1)
+
+
+@pytest.mark.parametrize("f32_streamk_mode", [2, 3], indirect=True)
 @pytest.mark.parametrize("m,n,k", [(2048, 4096, 2048), (2200, 4100, 777), (2560, 4096, 4096)])
-def test_streamk_form_matches_oracle(m, n, k):
-    # one to four waves of 128 x 256 tiles: persistent CTAs split the (tile,
-    # k-block) units evenly; partial tiles meet in per-CTA slots, folded in k
-    # order by the last CTA to arrive (sampled rows, incl. tile edges)
+def test_streamk_form_matches_oracle(m, n, k, f32_streamk_mode):
+    # one to four waves of 128 x 256 tiles: persistent CTAs take the whole
+    # waves tile by tile and split the (tile, k-block) units of the tiles left
+    # over evenly; partial tiles meet in per-CTA slots, folded in k order by
+    # the last CTA to arrive (sampled rows, incl. tile edges).  2200 x 4100 x
+    # 777 leaves two tiles of thirteen k-blocks over three CTAs when the
+    # whole waves run first (mode 3); mode 2 splits every tile's units.
     w = _sk_budget(m, n, k)
     assert w is not None
     rows = oracle.sample_rows(m, 256)
@@ -142,12 +153,48 @@ def test_streamk_form_matches_oracle(m, n, k):
     assert rel_fro(C1[rows], C2[rows].astype(np.float64)) <= 2 * TOL
 
 
-def test_streamk_not_taken_for_large_or_small_grids():
-    # more than four waves: the classic grid; under one wave: split-K, which
-    # the same budget always buys enough slices of
+@pytest.mark.parametrize("f32_streamk_mode", [2, 3], indirect=True)
+def test_streamk_whole_waves_only(f32_streamk_mode):
+    # exactly two waves of 128 x 256 tiles: every CTA takes two whole tiles
+    # and no stream-K range is left, so no slot is written and the result
+    # equals the classic grid's bit for bit (same per-tile k order)
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    m, n, k = 128 * sms, 512, 1024
+    w = _sk_budget(m, n, k)
+    assert w is not None
+    A, B = inputs.normal_f32(m, k, n, seed=91)
+    C1 = run_budget(A, B, w)
+    base = int(mmsr.mm_plan_query(SR, -1, m, n, k, 0).workspace_min)
+    np.testing.assert_array_equal(C1, run_budget(A, B, base))
+    rows = oracle.sample_rows(m, 256)
+    assert rel_fro(C1[rows], oracle.mm_f64(A, B, rows=rows)) <= TOL
+
+
+def test_streamk_planner_rule():
+    # the planner's own choice (option 1): stream-K only when the classic
+    # grid's last wave would be nearly empty -- 1.05 waves of 128 x 256 tiles
+    # yes, 1.68 waves no (the budget then buys split-K); more than four waves:
+    # the classic grid; under one wave: split-K, which the same budget always
+    # buys enough slices of
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    m, k = 2048, 2048
+    n_few = 256 * -(-(sms + sms // 20) // 16)  # just over one wave of 16-row columns
+    assert _sk_budget(m, n_few, k) is not None
+    base = int(mmsr.mm_plan_query(SR, -1, m, 4096, k, 0).workspace_min)
+    if (16 * 16) % sms > 0.3 * sms:
+        assert mmsr.mm_plan_query(SR, -1, m, 4096, k, base + (1 << 28)).kernel == 2
     assert mmsr.mm_plan_query(SR, -1, 8192, 8192, 8192, 1 << 34).kernel == 2
     base = int(mmsr.mm_plan_query(SR, -1, 1024, 1024, 16384, 0).workspace_min)
     p = mmsr.mm_plan_query(SR, -1, 1024, 1024, 16384, base + (1 << 28))
     assert p.kernel == 2 and p.split_k > 1
-    w = _sk_budget(2048, 4096, 2048)
-    assert mmsr.mm_plan_query(SR, -1, 2048, 4096, 2048, w - 1).kernel == 2
+    w = _sk_budget(m, n_few, k)
+    assert mmsr.mm_plan_query(SR, -1, m, n_few, k, w - 1).kernel == 2
+    mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, 0)
+    try:
+        assert mmsr.mm_plan_query(SR, -1, m, n_few, k, w).kernel == 2
+    finally:
+        mmsr.mm_set_option(mmsr.MM_OPT_F32_STREAMK, 1)
