@@ -241,6 +241,14 @@ typedef struct {
   const void* A;
   const void* B;
   void* C;
+  /* FP32 problems: k-slices per 128 x 128 output tile (Section 3's k-split
+   * inside the batch).  0: the library's rule -- a tile whose k-blocks exceed
+   * an eighth of one SM's share of the batch's FP32 work is cut into slices
+   * of that size (at least 8 k-blocks, at most 16 slices); 1: never; s > 1:
+   * s slices (at most 64 and the tile's 64-wide k-blocks).  Must be 0 for
+   * (min,+) problems. */
+  int32_t split_k;
+  int32_t reserved; /* must be 0 */
 } mm_problem_t;
 
 /*
@@ -253,8 +261,10 @@ typedef struct {
  * call copies its cost-sorted problem table into the workspace (as kernel
  * parameters of a few small launches, so a captured graph replays the same
  * table).  Workspace holds the tile counter, the per-problem range verdicts,
- * the table and the split FP32 operands; mm_batched_query reports the
- * minimum.
+ * the table, the split FP32 operands and, for FP32 tiles cut into k-slices,
+ * one 64 KB partial tile per slice and a counter per tile: the last slice to
+ * finish folds the partials in slice order (a fixed order: results repeat
+ * exactly) and writes C.  mm_batched_query reports the minimum.
  */
 int mm_batched(int count, const mm_problem_t* problems, void* workspace, size_t workspace_bytes,
                void* stream);

@@ -78,16 +78,20 @@ struct BatchRow {
   const void* A;
   const void* B;
   void* C;
+  int s, kbs;        // FP32: k-slices per tile and k-blocks per slice
+  int64_t slot_off;  // FP32, s > 1: first float of this problem's partial tiles
+  int cnt_off;       // FP32, s > 1: first of this problem's per-tile counters
+  int pad;
 };
 // What the kernels take by value: sizes and the device addresses of the
 // table (rows in cost order and three prefix sums of tile counts).
 struct BatchHeader {
   int count;
-  int total_tiles;  // FP32 tiles (persistent kernel)
+  int total_tiles;  // FP32 tile slices (persistent kernel)
   int mp16_total;   // packed (min,+) tiles
   int mp_total;     // 32-bit (min,+) tiles
   const BatchRow* rows;
-  const int* tile_start;       // [count + 1] 128 x 128 tiles of FP32 problems
+  const int* tile_start;       // [count + 1] 128 x 128 tile slices of FP32 problems
   const int* mp16_tile_start;  // [count + 1] packed tiles of (min,+) problems
   const int* mp_tile_start;    // [count + 1] 128 x 128 tiles of (min,+) problems (fallback)
 };
@@ -119,11 +123,15 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const BatchHeader T,
                                                             __nv_bfloat16* __restrict__ blo) {
   // problems with the grid's y stride (the y extent is capped at 65535)
   for (int p = blockIdx.y; p < T.count; p += gridDim.y) {
-    if (T.rows[p].kind != 0) continue;
-    const int64_t m = T.rows[p].m, n = T.rows[p].n, k = T.rows[p].k;
+    // the row in registers: the stores below could alias the table as far as
+    // the compiler knows, which would reload its fields every iteration
+    const BatchRow R = T.rows[p];
+    if (R.kind != 0) continue;
+    const int64_t m = R.m, n = R.n, k = R.k;
     const int64_t kp = (k + TKA - 1) / TKA * TKA;
-    const float* A = static_cast<const float*>(T.rows[p].A);
-    const float* B = static_cast<const float*>(T.rows[p].B);
+    const int64_t row0a = R.row0a, row0b = R.row0b;
+    const float* __restrict__ A = static_cast<const float*>(R.A);
+    const float* __restrict__ B = static_cast<const float*>(R.B);
     // A rows: one thread per 8 output columns
     const int64_t cpr = kp / 8;
     for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < m * cpr; e += (int64_t)gridDim.x * 256) {
@@ -131,7 +139,7 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const BatchHeader T,
       __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) split1(c8 + t < k ? A[r * k + c8 + t] : 0.f, h[t], l[t]);
-      const int64_t off = (T.rows[p].row0a + r) * KP + c8;
+      const int64_t off = (row0a + r) * KP + c8;
       *reinterpret_cast<uint4*>(ahi + off) = *reinterpret_cast<const uint4*>(h);
       *reinterpret_cast<uint4*>(alo + off) = *reinterpret_cast<const uint4*>(l);
     }
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const BatchHeader T,
         __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], h[e], l[e]);
-        const int64_t off = (T.rows[p].row0b + gn) * KP + k0 + chunk * 8;
+        const int64_t off = (row0b + gn) * KP + k0 + chunk * 8;
         *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(h);
         *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(l);
       }
@@ -169,13 +177,14 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const BatchHeader T,
 __global__ void __launch_bounds__(256) batched_range_kernel(const BatchHeader T,
                                                             int* __restrict__ violation) {
   for (int p = blockIdx.y; p < T.count; p += gridDim.y) {
-    if (T.rows[p].kind == 0) continue;
+    const BatchRow R = T.rows[p];
+    if (R.kind == 0) continue;
     int bad = 0;
     const int64_t stride = (int64_t)gridDim.x * 256;
     const int64_t t0 = (int64_t)blockIdx.x * 256 + threadIdx.x;
     for (int pass = 0; pass < 2; ++pass) {
-      const int32_t* X = static_cast<const int32_t*>(pass ? T.rows[p].B : T.rows[p].A);
-      const int64_t cnt = pass ? (int64_t)T.rows[p].k * T.rows[p].n : (int64_t)T.rows[p].m * T.rows[p].k;
+      const int32_t* X = static_cast<const int32_t*>(pass ? R.B : R.A);
+      const int64_t cnt = pass ? (int64_t)R.k * R.n : (int64_t)R.m * R.k;
       const int64_t nv = aligned16(X) ? cnt / 4 : 0;
 #pragma unroll 4
       for (int64_t v = t0; v < nv; v += stride) {
@@ -262,7 +271,8 @@ __device__ __forceinline__ uint64_t kdesc(uint32_t saddr) {
 __global__ void __launch_bounds__(kBThreads, 1)
     batched_kernel(const BatchHeader T, const __grid_constant__ CUtensorMap tAhi,
                    const __grid_constant__ CUtensorMap tAlo, const __grid_constant__ CUtensorMap tBhi,
-                   const __grid_constant__ CUtensorMap tBlo, int* __restrict__ counter) {
+                   const __grid_constant__ CUtensorMap tBlo, int* __restrict__ counter,
+                   float* __restrict__ slots, int* __restrict__ split_cnt) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + TSTAGES * TSTAGE);
@@ -272,9 +282,14 @@ __global__ void __launch_bounds__(kBThreads, 1)
   uint64_t* tile_full = acc_empty + 2;         // [kTileQ]
   uint64_t* tile_empty = tile_full + kTileQ;   // [kTileQ]
   uint64_t* quiesce = tile_empty + kTileQ;     // after an abort: all issued MMAs done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(quiesce + 1);
+  // drain-warp rendezvous of a k-slice (bounded waits): every drain warp has
+  // stored its part of the partial tile / the fold verdict is out
+  uint64_t* seg_stored = quiesce + 1;
+  uint64_t* seg_decided = seg_stored + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(seg_decided + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* tile_q = abort_flag + 1;                // [kTileQ]
+  int* fold_flag = tile_q + kTileQ;            // this CTA folds the tile's slices
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -291,6 +306,8 @@ __global__ void __launch_bounds__(kBThreads, 1)
       tc::mbar_init(&tile_empty[q], 1 + kDrainW);  // the MMA thread and the drain warps
     }
     tc::mbar_init(quiesce, 1);
+    tc::mbar_init(seg_stored, kDrainW);
+    tc::mbar_init(seg_decided, 1);
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
@@ -305,7 +322,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
   // Tile indices travel through a small mbarrier queue instead of a CTA
   // barrier: the producer claims tiles ahead (and starts their TMA loads)
   // while the tensor core and the drain warps still work on earlier ones.
-  uint32_t ring = 0, chunk = 0;
+  uint32_t ring = 0, chunk = 0, ps = 0;  // ps: k-sliced tiles drained (rendezvous phase)
   const bool active = warp >= 2 || lane == 0;  // warps 0 and 1 work through one lane
   bool skipped = false;  // producer: the test switch took ring position 0 out
 
@@ -337,12 +354,16 @@ __global__ void __launch_bounds__(kBThreads, 1)
     const int p = lo;
     const int local = t - T.tile_start[p];
     const int64_t m = T.rows[p].m, n = T.rows[p].n, k = T.rows[p].k;
+    // unit = (tile, k-slice), the slices of one tile adjacent in the queue
+    const int nsl = T.rows[p].s, tile = local / nsl, z = local - tile * nsl;
 
     {
       // ------------------------------------------------ FP32 tensor-core tile
       const int tiles_n = (int)((n + TBN - 1) / TBN);
-      const int64_t i0 = (int64_t)(local / tiles_n) * TBM, j0 = (int64_t)(local % tiles_n) * TBN;
-      const int nkb = (int)((k + TBK - 1) / TBK);
+      const int64_t i0 = (int64_t)(tile / tiles_n) * TBM, j0 = (int64_t)(tile % tiles_n) * TBN;
+      const int nkb_all = (int)((k + TBK - 1) / TBK);
+      const int kb0 = z * T.rows[p].kbs;
+      const int nkb = max(0, min(nkb_all - kb0, T.rows[p].kbs));
       const int nchunks = (nkb + TCHUNK - 1) / TCHUNK;
       if (warp == 0) {
         if (lane == 0) {
@@ -355,10 +376,11 @@ __global__ void __launch_bounds__(kBThreads, 1)
             if (ring == 0 && skipped) continue;
             tc::mbar_expect_tx(&full[s], TSTAGE);
             uint8_t* st = smem + s * TSTAGE;
-            tc::tma_load_2d(st, &tAhi, &full[s], it * TBK, ya);
-            tc::tma_load_2d(st + TA_BYTES, &tAlo, &full[s], it * TBK, ya);
-            tc::tma_load_2d(st + 2 * TA_BYTES, &tBhi, &full[s], it * TBK, yb);
-            tc::tma_load_2d(st + 2 * TA_BYTES + TB_BYTES, &tBlo, &full[s], it * TBK, yb);
+            const int kx = (kb0 + it) * TBK;
+            tc::tma_load_2d(st, &tAhi, &full[s], kx, ya);
+            tc::tma_load_2d(st + TA_BYTES, &tAlo, &full[s], kx, ya);
+            tc::tma_load_2d(st + 2 * TA_BYTES, &tBhi, &full[s], kx, yb);
+            tc::tma_load_2d(st + 2 * TA_BYTES + TB_BYTES, &tBlo, &full[s], kx, yb);
           }
         }
       } else if (warp == 1) {
@@ -424,6 +446,53 @@ __global__ void __launch_bounds__(kBThreads, 1)
         }
         float* C = static_cast<float*>(T.rows[p].C);
         const int64_t row = i0 + q * 32 + lane;
+        if (nsl > 1) {
+          // One k-slice of a split tile: store the partial tile thread-major
+          // (float4 i of drain thread d at i x 256 + d, so warp-wide stores
+          // and the fold's loads are 512 contiguous bytes), count the slice on
+          // the tile's counter, and the slice that completes it folds all
+          // slices in slice order and writes C.  No CTA waits on another.
+          const int dt = threadIdx.x - 64;
+          float* tile_slots = slots + T.rows[p].slot_off + (int64_t)tile * nsl * (TBM * TBN);
+          float4* mine = reinterpret_cast<float4*>(tile_slots + (int64_t)z * (TBM * TBN)) + dt;
+#pragma unroll
+          for (int e = 0; e < TBN / 2; e += 4)
+            __stcg(mine + (e / 4) * (kDrainW * 32), ok ? make_float4(sum[e], sum[e + 1], sum[e + 2], sum[e + 3])
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f));
+          __threadfence();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(seg_stored);
+          bool go = __all_sync(0xffffffffu, tc::mbar_wait(seg_stored, ps & 1u, abort_flag, &g_batched_status));
+          if (go && warp == 2) {
+            if (lane == 0) {
+              *fold_flag = atomicAdd(&split_cnt[T.rows[p].cnt_off + tile], 1) == nsl - 1;
+              tc::mbar_arrive(seg_decided);  // release: the verdict is visible to the waiters
+            }
+            __syncwarp();
+          }
+          go = go && __all_sync(0xffffffffu, tc::mbar_wait(seg_decided, ps & 1u, abort_flag, &g_batched_status));
+          ++ps;
+          if (go && *reinterpret_cast<volatile int*>(fold_flag)) {
+            __threadfence();
+#pragma unroll
+            for (int e = 0; e < TBN / 2; ++e) sum[e] = 0.f;
+            for (int zz = 0; zz < nsl; ++zz) {
+              const float4* src = reinterpret_cast<const float4*>(tile_slots + (int64_t)zz * (TBM * TBN)) + dt;
+              float4 v[TBN / 8];  // all sixteen 16-byte loads in flight
+#pragma unroll
+              for (int u = 0; u < TBN / 8; ++u) v[u] = __ldcg(src + u * (kDrainW * 32));
+#pragma unroll
+              for (int u = 0; u < TBN / 8; ++u) {
+                sum[4 * u] = __fadd_rn(sum[4 * u], v[u].x);
+                sum[4 * u + 1] = __fadd_rn(sum[4 * u + 1], v[u].y);
+                sum[4 * u + 2] = __fadd_rn(sum[4 * u + 2], v[u].z);
+                sum[4 * u + 3] = __fadd_rn(sum[4 * u + 3], v[u].w);
+              }
+            }
+          } else {
+            continue;  // another slice folds this tile (or the call aborted)
+          }
+        }
         if (row < m) {
           const int64_t c0 = j0 + half * (TBN / 2);
           float* dst = C + row * n + c0;
@@ -473,7 +542,9 @@ struct BatchPlan {
   std::vector<uint8_t> table;  // rows, then the three prefix sums (uploaded to off_table)
   int64_t rows_bytes = 0, starts_bytes = 0;
   int64_t KP = 0, rows_a = 0, rows_b = 0;
-  int64_t off_viol = 256, off_table = 0, off_ahi = 0, off_alo = 0, off_bhi = 0, off_blo = 0, total = 0;
+  int64_t split_tiles = 0, slot_floats = 0;  // k-sliced FP32 tiles: counters and partial tiles
+  int64_t off_viol = 256, off_cnt = 0, off_table = 0, off_slots = 0, off_ahi = 0, off_alo = 0, off_bhi = 0,
+          off_blo = 0, total = 0;
 
   // The kernels' view of the table once it sits at `w + off_table`.
   BatchHeader header(uint8_t* w) const {
@@ -498,7 +569,8 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[i];
     if (q.semiring != MM_SR_PLUS_TIMES_F32 && q.semiring != MM_SR_MIN_PLUS_I32) return MM_ERR_UNSUPPORTED;
-    if (q.levels != 0) return MM_ERR_UNSUPPORTED;
+    if (q.levels != 0 || q.reserved != 0) return MM_ERR_UNSUPPORTED;
+    if (q.split_k < 0 || (q.split_k != 0 && q.semiring != MM_SR_PLUS_TIMES_F32)) return MM_ERR_ARG;
     if (q.m < 0 || q.n < 0 || q.k < 0 || q.m > (1 << 20) || q.n > (1 << 20) || q.k > (1 << 20))
       return MM_ERR_SHAPE;
     if (q.m > 0 && q.n > 0 && (!q.C || (q.k > 0 && (!q.A || !q.B)))) return MM_ERR_ARG;
@@ -511,12 +583,38 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     if (probs[a].k != probs[b].k) return probs[a].k > probs[b].k;
     return (double)probs[a].m * probs[a].n > (double)probs[b].m * probs[b].n;
   });
+  // k-slices of FP32 tiles (Section 3's k-split inside the batch).  The
+  // library's rule: a tile whose k-blocks exceed an eighth of one SM's share
+  // of the batch's FP32 work holds back the end of the batch, so it is cut
+  // into slices of about that size (at least 8 k-blocks, at most 16 slices);
+  // a hint s > 1 asks for s slices.
+  int64_t fp_work = 0;  // FP32 (tile, 64-wide k-block) units
+  for (int i = 0; i < count; ++i) {
+    const mm_problem_t& q = probs[i];
+    if (q.semiring == MM_SR_PLUS_TIMES_F32 && q.m > 0 && q.n > 0)
+      fp_work += ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN) * ((q.k + TBK - 1) / TBK);
+  }
+  const int64_t slice_target = std::max<int64_t>(8, fp_work / (8 * (int64_t)num_sms()));
+  auto slices_of = [&](const mm_problem_t& q, int* kbs) {
+    const int64_t nkb = (q.k + TBK - 1) / TBK;
+    int64_t s = 1;
+    if (q.split_k > 1)
+      s = std::min<int64_t>({(int64_t)q.split_k, 64, nkb});
+    else if (q.split_k == 0 && nkb > slice_target)
+      s = std::min<int64_t>(16, (nkb + slice_target - 1) / slice_target);
+    if (s < 1) s = 1;
+    int64_t per = (nkb + s - 1) / s;
+    if (per < 1) per = 1;
+    s = std::max<int64_t>(1, (nkb + per - 1) / per);  // no empty tail slices
+    *kbs = (int)per;
+    return (int)s;
+  };
   std::vector<BatchRow> rows(count);
   std::vector<int> starts(3 * (size_t)(count + 1));
   int* tile_start = starts.data();
   int* mp16_start = tile_start + (count + 1);
   int* mp_start = mp16_start + (count + 1);
-  int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0, mp16_tiles = 0;
+  int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0, mp16_tiles = 0, split_tiles = 0, slot_floats = 0;
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[order[i]];
     BatchRow& r = rows[i];
@@ -530,6 +628,11 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     r.B = q.B;
     r.C = q.C;
     r.row0a = r.row0b = 0;
+    r.s = 1;
+    r.kbs = (int)std::max<int64_t>(1, (q.k + TBK - 1) / TBK);
+    r.slot_off = 0;
+    r.cnt_off = 0;
+    r.pad = 0;
     tile_start[i] = (int)tiles;
     mp16_start[i] = (int)mp16_tiles;
     mp_start[i] = (int)mp_tiles;
@@ -538,7 +641,17 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
       const int64_t tn = r.kind == 2 ? 128 : MPN;
       mp16_tiles += ((q.m + mp::PBM - 1) / mp::PBM) * ((q.n + tn - 1) / tn);
     }
-    if (r.kind == 0 && q.m > 0 && q.n > 0) tiles += ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN);
+    if (r.kind == 0 && q.m > 0 && q.n > 0) {
+      const int64_t pt = ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN);
+      r.s = slices_of(q, &r.kbs);
+      if (r.s > 1) {
+        r.slot_off = slot_floats;
+        r.cnt_off = (int)split_tiles;
+        slot_floats += pt * r.s * TBM * TBN;
+        split_tiles += pt;
+      }
+      tiles += pt * r.s;
+    }
     if (r.kind == 0) {
       r.row0a = (int)ra;
       r.row0b = (int)rb;
@@ -547,7 +660,7 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
       kp_max = std::max<int64_t>(kp_max, align_up(q.k > 0 ? q.k : 1, TKA));
     }
     if (tiles > (int64_t)1 << 30 || mp_tiles > (int64_t)1 << 30 || mp16_tiles > (int64_t)1 << 30 ||
-        ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30)
+        ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30 || split_tiles > (int64_t)1 << 30)
       return MM_ERR_SHAPE;
   }
   tile_start[count] = (int)tiles;
@@ -565,10 +678,15 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
   P->KP = kp_max;
   P->rows_a = ra;
   P->rows_b = rb;
+  P->split_tiles = split_tiles;
+  P->slot_floats = slot_floats;
   // workspace: [0] tile counter, [256] per-problem (min,+) range verdicts,
-  // then the table and the stacked split operands
-  P->off_table = align_up(P->off_viol + 4 * (int64_t)count, 256);
-  P->off_ahi = align_up(P->off_table + (int64_t)P->table.size(), 1024);
+  // the per-tile counters of k-sliced tiles (all zeroed by one memset per
+  // call), then the table, the partial tiles and the stacked split operands
+  P->off_cnt = align_up(P->off_viol + 4 * (int64_t)count, 16);
+  P->off_table = align_up(P->off_cnt + 4 * split_tiles, 256);
+  P->off_slots = align_up(P->off_table + (int64_t)P->table.size(), 1024);
+  P->off_ahi = align_up(P->off_slots + 4 * slot_floats, 1024);
   P->off_alo = P->off_ahi + align_up(ra * kp_max * 2, 1024);
   P->off_bhi = P->off_alo + align_up(ra * kp_max * 2, 1024);
   P->off_blo = P->off_bhi + align_up(rb * kp_max * 2, 1024);
@@ -618,7 +736,7 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   auto* alo = reinterpret_cast<__nv_bfloat16*>(w + P.off_alo);
   auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + P.off_bhi);
   auto* blo = reinterpret_cast<__nv_bfloat16*>(w + P.off_blo);
-  MMSR_TRY_STATUS(cudaMemsetAsync(w, 0, P.off_viol + 4 * (size_t)count, st));
+  MMSR_TRY_STATUS(cudaMemsetAsync(w, 0, (size_t)(P.off_cnt + 4 * P.split_tiles), st));
   const BatchHeader H = P.header(w);
   const unsigned gy = (unsigned)std::min(count, 65535);
   {
@@ -647,7 +765,9 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   if (P.total_tiles > 0) {
     TraceScope tr(kTrBatched, st);
     const int grid = std::min(sms, P.total_tiles);
-    batched_kernel<<<grid, kBThreads, BSMEM, st>>>(H, ta_hi, ta_lo, tb_hi, tb_lo, counter);
+    batched_kernel<<<grid, kBThreads, BSMEM, st>>>(H, ta_hi, ta_lo, tb_hi, tb_lo, counter,
+                                                   reinterpret_cast<float*>(w + P.off_slots),
+                                                   reinterpret_cast<int*>(w + P.off_cnt));
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   if (P.mp16_total > 0) {

@@ -65,7 +65,8 @@ class mm_plan_t(ctypes.Structure):
 class mm_problem_t(ctypes.Structure):
     _fields_ = [("semiring", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
-                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("split_k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -230,13 +231,14 @@ def mm_star_strassen_query(classic_levels, levels, semiring, m, n, k, workspace_
 def _problems(problems):
     arr = (mm_problem_t * len(problems))()
     for i, p in enumerate(problems):
-        sr, m, n, k, A, B, C = p
-        arr[i] = mm_problem_t(int(sr), 0, int(m), int(n), int(k), _addr(A), _addr(B), _addr(C))
+        sr, m, n, k, A, B, C = p[:7]
+        split = int(p[7]) if len(p) > 7 else 0
+        arr[i] = mm_problem_t(int(sr), 0, int(m), int(n), int(k), _addr(A), _addr(B), _addr(C), split, 0)
     return arr
 
 
 def mm_batched(problems, workspace=None, workspace_bytes=0, stream=None, check=True) -> int:
-    """problems: sequence of (semiring, m, n, k, A, B, C)."""
+    """problems: sequence of (semiring, m, n, k, A, B, C[, split_k])."""
     arr = _problems(problems)
     rc = load().mm_batched(len(problems), arr, _addr(workspace), int(workspace_bytes),
                            _stream(stream))

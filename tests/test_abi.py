@@ -293,7 +293,7 @@ def test_strassen_auto_depth_under_budget(lib):
 
 def test_batched_table_size_and_cap(lib):
     """The batched call keeps its problem table in the workspace: the query
-    grows with the count (48-byte rows plus three prefix sums) and accepts
+    grows with the count (72-byte rows plus three prefix sums) and accepts
     counts past the old 512 limit; 2^20 + 1 problems are refused."""
     F32 = mmsr.MM_SR_PLUS_TIMES_F32
     one = [(F32, 8, 8, 8, FAKE, FAKE, FAKE)]
@@ -302,6 +302,22 @@ def test_batched_table_size_and_cap(lib):
     assert w1 > 0 and w2 > w1
     assert mmsr.mm_batched_query(one * 600) > 0
     assert mmsr.mm_batched_query(one * ((1 << 20) + 1)) == 0
+
+
+def test_batched_k_slices(lib):
+    """FP32 tiles cut into k-slices hold one 64 KB partial tile per slice in
+    the workspace (plus a counter per tile); hints are checked on the host."""
+    F32, MP = mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_MIN_PLUS_I32
+    prob = (F32, 256, 256, 4096, FAKE, FAKE, FAKE)
+    w1 = mmsr.mm_batched_query([prob + (1,)])
+    w4 = mmsr.mm_batched_query([prob + (4,)])
+    # 4 tiles x 4 slices x 128 x 128 x 4 B, counters and alignment aside
+    assert 4 * 4 * 65536 <= w4 - w1 < 4 * 4 * 65536 + 4096
+    # hints beyond the tile's 64 k-blocks are clamped to them
+    assert mmsr.mm_batched_query([prob + (64,)]) == mmsr.mm_batched_query([prob + (1000,)])
+    assert mmsr.mm_batched_query([prob + (-1,)]) == 0
+    assert mmsr.mm_batched_query([(MP, 64, 64, 64, FAKE, FAKE, FAKE, 2)]) == 0
+    assert mmsr.mm_batched_query([(MP, 64, 64, 64, FAKE, FAKE, FAKE, 0)]) > 0
 
 
 def test_fused_staging_plan(lib):

@@ -13,14 +13,17 @@ pytestmark = pytest.mark.gpu
 F32, MP = mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_MIN_PLUS_I32
 
 
-def _launch(probs, capture=False):
-    """probs: list of inputs.Problem; returns the list of output arrays."""
+def _launch(probs, capture=False, splits=None, reps=1):
+    """probs: list of inputs.Problem; splits: optional per-problem k-slice
+    hints (mm_problem_t.split_k); returns the list of output arrays (of the
+    last of `reps` eager calls)."""
     import torch
 
     dA = [dev(p.A) for p in probs]
     dB = [dev(p.B) for p in probs]
     dC = [empty((p.m, p.n), torch.float32 if p.semiring == F32 else torch.int32) for p in probs]
-    table = [(p.semiring, p.m, p.n, p.k, a, b, c) for p, a, b, c in zip(probs, dA, dB, dC)]
+    splits = splits or [0] * len(probs)
+    table = [(p.semiring, p.m, p.n, p.k, a, b, c, h) for p, a, b, c, h in zip(probs, dA, dB, dC, splits)]
     need = mmsr.mm_batched_query(table)
     assert need > 0
     ws = empty((need,), torch.uint8)
@@ -40,7 +43,10 @@ def _launch(probs, capture=False):
             c.fill_(-1)
         g.replay()
     else:
-        mmsr.mm_batched(table, ws, need)
+        for _ in range(reps):
+            for c in dC:
+                c.fill_(-7)
+            mmsr.mm_batched(table, ws, need)
     torch.cuda.synchronize()
     assert mmsr.mm_last_device_status() == 0
     return [c.cpu().numpy() for c in dC]
@@ -137,7 +143,63 @@ def test_k_zero_and_tiny_problems():
 @pytest.mark.parametrize("capture", [False, True], ids=["eager", "graph-replay"])
 def test_batch_beyond_one_table_chunk(capture):
     # 1500 problems: past the old by-value table limit of 512 and more than
-    # one table upload launch (48 bytes per problem, 30 KB per launch); every
+    # one table upload launch (72 bytes per problem, 30 KB per launch); every
     # problem checked, eagerly and as a replayed graph
     probs = _mixed(1500, seed=206, lo=1, hi=96, integer=True)
     _check(probs, _launch(probs, capture=capture), exact_fp32=True)
+
+
+def _fp32(rng, m, n, k, integer=False):
+    if integer:
+        A = rng.integers(-4, 5, size=(m, k)).astype(np.float32)
+        B = rng.integers(-4, 5, size=(k, n)).astype(np.float32)
+    else:
+        A = rng.standard_normal((m, k)).astype(np.float32)
+        B = rng.standard_normal((k, n)).astype(np.float32)
+    return inputs.Problem(F32, m, n, k, A, B)
+
+
+@pytest.mark.parametrize("integer", [True, False], ids=["integer-exact", "normal"])
+def test_k_sliced_tiles_by_hint(integer):
+    # FP32 tiles cut into 2, 3 and 7 k-slices (ragged last slices, ragged
+    # tiles), beside unsplit FP32 and (min,+) problems: the last slice to
+    # finish folds the partial tiles in slice order, so repeated calls agree
+    # bit for bit
+    rng = np.random.default_rng(207)
+    probs = [_fp32(rng, 200, 300, 1000, integer), _fp32(rng, 129, 257, 3000, integer),
+             _fp32(rng, 64, 64, 4500, integer), _fp32(rng, 300, 100, 200, integer)]
+    probs += [p for p in _mixed(8, seed=208, lo=40, hi=300) if p.semiring == MP][:3]
+    splits = [2, 3, 7, 1] + [0] * (len(probs) - 4)
+    outs = _launch(probs, splits=splits)
+    _check(probs, outs, exact_fp32=integer)
+    again = _launch(probs, splits=splits, reps=2)
+    for a, b in zip(outs, again):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_k_sliced_tiles_library_rule():
+    # a few long-k FP32 problems among many short ones: their tiles exceed an
+    # eighth of an SM's share of the batch's work, so the library slices them
+    # (the workspace grows by their partial tiles); results as unsliced
+    rng = np.random.default_rng(209)
+    probs = [_fp32(rng, 256, 256, 16384), _fp32(rng, 130, 200, 12000)]
+    probs += [_fp32(rng, 128, 128, 64) for _ in range(6)]
+    import torch
+
+    d = empty((8,), torch.float32)
+    auto = [(F32, p.m, p.n, p.k, d, d, d, 0) for p in probs]
+    plain = [(F32, p.m, p.n, p.k, d, d, d, 1) for p in probs]
+    assert mmsr.mm_batched_query(auto) > mmsr.mm_batched_query(plain)
+    sliced = _launch(probs)
+    _check(probs, sliced)
+    unsliced = _launch(probs, splits=[1] * len(probs))
+    for a, b in zip(sliced, unsliced):
+        assert rel_fro(a, b.astype(np.float64)) <= 2e-6
+
+
+def test_k_sliced_tiles_graph_replay():
+    # the per-tile counters are zeroed by the call's own memset, so a captured
+    # call replays correctly
+    rng = np.random.default_rng(210)
+    probs = [_fp32(rng, 190, 260, 2500, integer=True), _fp32(rng, 70, 90, 700, integer=True)]
+    _check(probs, _launch(probs, capture=True, splits=[5, 2]), exact_fp32=True)
