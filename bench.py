@@ -591,6 +591,7 @@ def run_extras(mmsr, lib, torch, sp, book, A_sq, B_sq, rows_sq):
     out["strassen_rect_12288x16384x8192"] = extras_strassen_rect(mmsr, lib, torch, sp, ctypes, book, bf16,
                                                                   bf16_src)
     out["batched_512"] = extras_batched(mmsr, lib, torch, sp, ctypes, bf16["burst"], u16_peak, bf16_src)
+    out["batched_long_k_fp32"] = extras_batched_long_k(mmsr, torch, sp, book, bf16["burst"], bf16_src)
     out["closure_minplus_n4096"] = extras_closure(mmsr, torch, sp, u16_peak)
     out["orand_n4096"] = extras_orand(mmsr, lib, torch, sp, ctypes, lop_peak)
     out["probes"] = {"addmin_u32_tops": u32_peak, "addmin_u16x2_tops": u16_peak,
@@ -985,6 +986,48 @@ def extras_batched(mmsr, lib, torch, sp, ctypes, bf16_peak, u16_peak, bf16_src):
     del dA, dB, dC, ws, g
     torch.cuda.empty_cache()
     return res
+
+
+def extras_batched_long_k(mmsr, torch, sp, book, bf16_peak, bf16_src):
+    """A batch whose few long-k FP32 products would end it alone: 8 products
+    of 256 x 384 x 32768 among 56 with m, n, k log-uniform in [64, 1024]
+    (normal(0,1), seed 11), FP32 mode.  Tiles unsliced (split_k = 1), the
+    library's slicing rule (split_k = 0) and the autotuner's per-k-bucket
+    choice, each captured in a graph and replayed."""
+    from paper_1911_05328_gb300 import autotune, inputs
+
+    probs = inputs.batched_long_k_problems(seed=11)
+    dA = [torch.from_numpy(p.A).cuda() for p in probs]
+    dB = [torch.from_numpy(p.B).cuda() for p in probs]
+    dC = [torch.empty((p.m, p.n), dtype=torch.float32, device="cuda") for p in probs]
+    base = [(p.semiring, p.m, p.n, p.k, a, b, c) for p, a, b, c in zip(probs, dA, dB, dC)]
+    ops = sum(2.0 * p.m * p.n * p.k for p in probs)
+    rows0 = sample_rows(probs[0].m, 32)
+    book.add_set("batched_long_k_0", lambda p=probs[0]: (p.A, p.B), rows0)
+    need = max(mmsr.mm_batched_query(autotune.apply_splits(base, [h] * len(base))) for h in (0, 1, 16))
+    ws = torch.empty((need,), dtype=torch.uint8, device="cuda")
+    tuned = autotune.tune_batched(base, ws, need, cache={}, persist=False)
+    out = {"problems": len(probs), "ops": ops}
+    for name, splits in (("unsliced", [1] * len(base)), ("library_rule", [0] * len(base)),
+                         ("autotuned", tuned["splits"])):
+        table = autotune.apply_splits(base, splits)
+        mmsr.mm_batched(table, ws, need, stream=sp)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            mmsr.mm_batched(table, ws, need, stream=torch.cuda.current_stream())
+        ms = _time_call(torch, g.replay, 10)
+        out[name] = {"ms": ms, "gops": ops / (ms * 1e-3) / 1e9,
+                     "roofline": _roof("tensor", 3 * ops / (ms * 1e-3) / 1e12, bf16_peak, "TFLOP/s", bf16_src),
+                     "workspace_bytes": int(mmsr.mm_batched_query(table))}
+        # sampled rows of the first long-k product against the oracle
+        book.add("batched_long_k_0", out[name], "error_long_k_product", _rows_of(torch, dC[0], rows0))
+        del g
+    out["autotuned"]["buckets"] = tuned["buckets"]
+    del dA, dB, dC, ws
+    torch.cuda.empty_cache()
+    return out
 
 
 def extras_orand(mmsr, lib, torch, sp, ctypes, lop_peak):

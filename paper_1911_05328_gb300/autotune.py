@@ -12,7 +12,10 @@ fastest per shape bucket:
   and whose shape divides by 2^L;
 * ``mm_star_strassen``: mixed plans (Theorem star-strassen-1) of c classic
   in-place levels over L Strassen levels, c + L <= 4 -- at a small budget a
-  deep Strassen plan fits only below a few classic levels.
+  deep Strassen plan fits only below a few classic levels;
+* ``mm_batched``: the k-slices of FP32 tiles (``split_k`` of each problem),
+  one choice per power-of-two k bucket, found by coordinate descent over the
+  buckets (longest k first) with the whole batch timed for each candidate.
 
 Choices are cached in JSON (``MMSR_TUNE_CACHE``, default
 ``~/.cache/mmsr_tune.json``) keyed by semiring, power-of-two shape bucket and
@@ -204,3 +207,86 @@ def mm_semiring_tuned(semiring, m, n, k, A, B, C, workspace, budget, stream=None
     rec = c.get(key("semiring", semiring, m, n, k, budget))
     b = rec["budget"] if rec and rec["budget"] <= budget else budget
     return mmsr.mm_semiring(semiring, m, n, k, A, B, C, workspace, b, stream)
+
+
+BATCH_SPLITS = (0, 1, 2, 4, 8, 16)  # 0: the library's own rule
+
+
+def batch_signature(problems) -> str:
+    """Cache key of a batch: the multiset of (semiring, shape buckets)."""
+    items = sorted("%d:%dx%dx%d" % (int(p[0]), _bucket(int(p[1])), _bucket(int(p[2])), _bucket(int(p[3])))
+                   for p in problems)
+    import hashlib
+
+    return "batched/%d/%s" % (len(items), hashlib.sha1(",".join(items).encode()).hexdigest()[:16])
+
+
+def batch_buckets(problems, min_k: int = 1024):
+    """k buckets of the FP32 problems worth slicing (k >= min_k), longest
+    first, each with the indices of its problems."""
+    groups = {}
+    for i, p in enumerate(problems):
+        if int(p[0]) == mmsr.MM_SR_PLUS_TIMES_F32 and int(p[3]) >= min_k:
+            groups.setdefault(_bucket(int(p[3])), []).append(i)
+    return [(b, groups[b]) for b in sorted(groups, reverse=True)]
+
+
+def apply_splits(problems, splits):
+    """The problem tuples with their split_k hints set."""
+    return [tuple(p[:7]) + (int(h),) for p, h in zip(problems, splits)]
+
+
+def tune_batched(problems, workspace, workspace_bytes, timer=None, cache=None, persist=True,
+                 candidates=BATCH_SPLITS):
+    """Choose the k-slices of the batch's long-k FP32 problems.  problems:
+    (semiring, m, n, k, A, B, C[, split_k]) tuples as ``mmsr.mm_batched``
+    takes them.  Candidates whose workspace exceeds ``workspace_bytes`` are
+    skipped.  Returns {"splits": [hint per problem], "buckets": {k bucket:
+    hint}, "ms": time of the chosen batch}."""
+    timer = timer or cuda_timer
+    kk = batch_signature(problems)
+    buckets = batch_buckets(problems)
+    with _lock:
+        c = load_cache() if cache is None else cache
+        if kk in c and len(c[kk].get("splits", [])) == len(problems):
+            return c[kk]
+    splits = [0] * len(problems)
+
+    def run(sp):
+        table = apply_splits(problems, sp)
+        if mmsr.mm_batched_query(table) > workspace_bytes:
+            return None
+        return timer(lambda: mmsr.mm_batched(table, workspace, workspace_bytes))
+
+    best_ms = run(splits)
+    chosen = {}
+    for b, idx in buckets:
+        best_h = 0
+        for h in candidates:
+            if h == 0:
+                continue
+            trial = list(splits)
+            for i in idx:
+                trial[i] = h
+            ms = run(trial)
+            if ms is not None and (best_ms is None or ms < best_ms):
+                best_ms, best_h = ms, h
+        for i in idx:
+            splits[i] = best_h
+        chosen[str(b)] = best_h
+    rec = {"splits": splits, "buckets": chosen, "ms": best_ms}
+    with _lock:
+        c[kk] = rec
+        if persist and cache is None:
+            save_cache(c)
+    return rec
+
+
+def mm_batched_tuned(problems, workspace, workspace_bytes, stream=None):
+    """mm_batched with the cached k-slice choices for this batch's signature
+    (the library's own rule when the batch was never tuned)."""
+    rec = load_cache().get(batch_signature(problems))
+    table = problems
+    if rec and len(rec.get("splits", [])) == len(problems):
+        table = apply_splits(problems, rec["splits"])
+    return mmsr.mm_batched(table, workspace, workspace_bytes, stream)

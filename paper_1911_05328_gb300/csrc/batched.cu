@@ -3,11 +3,12 @@
 // schedule relies on, Section 6: idle workers take the next available task).
 //
 // Host side: problems are sorted by tile cost (k, longest first) and cut
-// into output tiles; the sorted problem table travels by value as a kernel
-// parameter.  FP32 problems are split into bf16 hi/lo operands by one
-// pre-pass into stacked buffers with a common row pitch (so four tensor maps
-// describe every FP32 problem of the batch); a second pre-pass decides, per
-// (min,+) problem, whether the exact packed 2 x 16-bit leaf applies.
+// into output tiles; the sorted problem table is copied into the workspace
+// by small launches that carry it as kernel parameters.  One pre-pass, its
+// work cut into equal blocks over the whole batch, splits the FP32 problems
+// into bf16 hi/lo operands in stacked buffers with a common row pitch (so
+// four tensor maps describe every FP32 problem of the batch) and decides,
+// per (min,+) problem, whether the exact packed 2 x 16-bit leaf applies.
 //
 // Device side: FP32 tiles run in one persistent tcgen05 kernel -- one CTA
 // per SM pops tile indices from an atomic counter and runs the pipeline
@@ -81,7 +82,7 @@ struct BatchRow {
   int s, kbs;        // FP32: k-slices per tile and k-blocks per slice
   int64_t slot_off;  // FP32, s > 1: first float of this problem's partial tiles
   int cnt_off;       // FP32, s > 1: first of this problem's per-tile counters
-  int pad;
+  int prep_a;        // pre-pass blocks of A (the rest of the problem's blocks are B's)
 };
 // What the kernels take by value: sizes and the device addresses of the
 // table (rows in cost order and three prefix sums of tile counts).
@@ -94,6 +95,8 @@ struct BatchHeader {
   const int* tile_start;       // [count + 1] 128 x 128 tile slices of FP32 problems
   const int* mp16_tile_start;  // [count + 1] packed tiles of (min,+) problems
   const int* mp_tile_start;    // [count + 1] 128 x 128 tiles of (min,+) problems (fallback)
+  const int* prep_start;       // [count + 1] pre-pass blocks
+  int prep_total;
 };
 constexpr int kUploadBytes = 30720;  // table bytes per upload launch (kernel parameter)
 struct UploadChunk {
@@ -114,88 +117,138 @@ __device__ __forceinline__ void split1(float x, __nv_bfloat16& h, __nv_bfloat16&
   l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// FP32 problems: A -> stacked hi/lo rows (pitch KP), B -> stacked hi/lo of
-// B^T (pitch KP); columns k..roundup(k, 64) are zero.  blockIdx.y = problem.
-__global__ void __launch_bounds__(256) batched_split_kernel(const BatchHeader T,
-                                                            int64_t KP, __nv_bfloat16* __restrict__ ahi,
-                                                            __nv_bfloat16* __restrict__ alo,
-                                                            __nv_bfloat16* __restrict__ bhi,
-                                                            __nv_bfloat16* __restrict__ blo) {
-  // problems with the grid's y stride (the y extent is capped at 65535)
-  for (int p = blockIdx.y; p < T.count; p += gridDim.y) {
-    // the row in registers: the stores below could alias the table as far as
-    // the compiler knows, which would reload its fields every iteration
-    const BatchRow R = T.rows[p];
-    if (R.kind != 0) continue;
-    const int64_t m = R.m, n = R.n, k = R.k;
-    const int64_t kp = (k + TKA - 1) / TKA * TKA;
-    const int64_t row0a = R.row0a, row0b = R.row0b;
-    const float* __restrict__ A = static_cast<const float*>(R.A);
-    const float* __restrict__ B = static_cast<const float*>(R.B);
-    // A rows: one thread per 8 output columns
-    const int64_t cpr = kp / 8;
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < m * cpr; e += (int64_t)gridDim.x * 256) {
-      const int64_t r = e / cpr, c8 = (e - r * cpr) * 8;
-      __align__(16) __nv_bfloat16 h[8], l[8];
+// One pre-pass over the whole batch, its work cut into equal blocks so that
+// a few large problems do not leave most SMs idle (with a fixed number of
+// blocks per problem, 8 products of 256 x 384 x 32768 among 56 small ones
+// took 1.07 ms at 16% of the HBM bandwidth).  Block b works for the problem
+// p with prep_start[p] <= b < prep_start[p + 1]:
+//  - FP32: A -> stacked hi/lo rows (pitch KP), kPrepA items of 8 columns per
+//    block; then B -> stacked hi/lo of B^T, kPrepB tiles of 64 (k) x 64 (n)
+//    per block through shared memory; columns k..roundup(k, 64) are zero;
+//  - (min,+): kPrepR entries of A, then of B, per block, any entry outside
+//    the packed range flags violation[p] (zeroed by the call's memset).
+constexpr int kPrepA = 4096, kPrepB = 4, kPrepR = 4096;
+
+// Eight consecutive entries of row r of A starting at column c8 (zero past
+// column k), by 16-byte loads where the row allows them.
+__device__ __forceinline__ void load8(const float* __restrict__ A, int64_t r, int64_t c8, int64_t k, bool vec,
+                                      float* x) {
+  const float* src = A + r * k + c8;
+  if (vec && c8 + 8 <= k) {
+    const float4 u = __ldcs(reinterpret_cast<const float4*>(src));
+    const float4 w = __ldcs(reinterpret_cast<const float4*>(src + 4));
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w; x[4] = w.x; x[5] = w.y; x[6] = w.z; x[7] = w.w;
+  } else {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) split1(c8 + t < k ? A[r * k + c8 + t] : 0.f, h[t], l[t]);
-      const int64_t off = (row0a + r) * KP + c8;
-      *reinterpret_cast<uint4*>(ahi + off) = *reinterpret_cast<const uint4*>(h);
-      *reinterpret_cast<uint4*>(alo + off) = *reinterpret_cast<const uint4*>(l);
-    }
-    // B^T: 64 (k) x 32 (n) tiles through shared memory
-    __shared__ float tile[64][33];
-    const int64_t tk = kp / 64, tn = (n + 31) / 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int64_t tt = blockIdx.x; tt < tk * tn; tt += gridDim.x) {
-      const int64_t k0 = (tt / tn) * 64, n0 = (tt % tn) * 32;
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int kk = ty + 8 * i;
-        const int64_t gk = k0 + kk, gn = n0 + tx;
-        tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.f;
-      }
-      __syncthreads();
-      const int row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
-      const int64_t gn = n0 + row;
-      if (gn < n) {
-        __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) split1(tile[chunk * 8 + e][row], h[e], l[e]);
-        const int64_t off = (row0b + gn) * KP + k0 + chunk * 8;
-        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(h);
-        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(l);
-      }
-    }
-    __syncthreads();  // the next problem reuses `tile`
+    for (int t = 0; t < 8; ++t) x[t] = c8 + t < k ? src[t] : 0.f;
   }
 }
 
-// (min,+) problems: flag any entry outside the packed range (violation[p]
-// starts at 0, set by a memset before the launch).  blockIdx.y = problem.
-__global__ void __launch_bounds__(256) batched_range_kernel(const BatchHeader T,
-                                                            int* __restrict__ violation) {
-  for (int p = blockIdx.y; p < T.count; p += gridDim.y) {
+__global__ void __launch_bounds__(256, 4) batched_prepass_kernel(const BatchHeader T, int64_t KP,
+                                                              __nv_bfloat16* __restrict__ ahi,
+                                                              __nv_bfloat16* __restrict__ alo,
+                                                              __nv_bfloat16* __restrict__ bhi,
+                                                              __nv_bfloat16* __restrict__ blo,
+                                                              int* __restrict__ violation) {
+  __shared__ float tile[64][65];
+  for (int blk = blockIdx.x; blk < T.prep_total; blk += gridDim.x) {
+    int lo = 0, hi = T.count - 1;  // last p with prep_start[p] <= blk
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&T.prep_start[mid]) <= blk) lo = mid; else hi = mid - 1;
+    }
+    const int p = lo;
+    // the row in registers: the stores below could alias the table as far as
+    // the compiler knows, which would reload its fields every iteration
     const BatchRow R = T.rows[p];
-    if (R.kind == 0) continue;
-    int bad = 0;
-    const int64_t stride = (int64_t)gridDim.x * 256;
-    const int64_t t0 = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    for (int pass = 0; pass < 2; ++pass) {
-      const int32_t* X = static_cast<const int32_t*>(pass ? R.B : R.A);
-      const int64_t cnt = pass ? (int64_t)R.k * R.n : (int64_t)R.m * R.k;
-      const int64_t nv = aligned16(X) ? cnt / 4 : 0;
+    const int lb = blk - __ldg(&T.prep_start[p]);
+    const int64_t m = R.m, n = R.n, k = R.k;
+    if (R.kind == 0) {
+      const int64_t kp = (k + TKA - 1) / TKA * TKA;
+      if (lb < R.prep_a) {
+        // A rows: items of 8 columns, four per thread in flight (a streaming
+        // pass needs many bytes in flight per SM to approach the HBM rate)
+        const float* __restrict__ A = static_cast<const float*>(R.A);
+        const int64_t cpr = kp / 8, items = m * cpr;
+        const int64_t e0 = (int64_t)lb * kPrepA, e_end = min(items, e0 + kPrepA);
+        const bool vec = (k & 3) == 0;
+        for (int64_t e = e0 + threadIdx.x; e < e_end; e += 4 * 256) {
+          float x[4][8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int64_t ej = e + j * 256;
+            if (ej < e_end) {
+              const int64_t r = ej / cpr;
+              load8(A, r, (ej - r * cpr) * 8, k, vec, x[j]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int64_t ej = e + j * 256;
+            if (ej < e_end) {
+              const int64_t r = ej / cpr, c8 = (ej - r * cpr) * 8;
+              __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+              for (int t = 0; t < 8; ++t) split1(x[j][t], h[t], l[t]);
+              const int64_t off = (R.row0a + r) * KP + c8;
+              *reinterpret_cast<uint4*>(ahi + off) = *reinterpret_cast<const uint4*>(h);
+              *reinterpret_cast<uint4*>(alo + off) = *reinterpret_cast<const uint4*>(l);
+            }
+          }
+        }
+      } else {
+        // B^T: 64 (k) x 64 (n) tiles through shared memory, sixteen loads
+        // per thread in flight
+        const float* __restrict__ B = static_cast<const float*>(R.B);
+        const int64_t tk = kp / 64, tn = (n + 63) / 64;
+        const int64_t t_begin = (int64_t)(lb - R.prep_a) * kPrepB, t_end = min(tk * tn, t_begin + kPrepB);
+        const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+        for (int64_t tt = t_begin; tt < t_end; ++tt) {
+          const int64_t k0 = (tt / tn) * 64, n0 = (tt % tn) * 64;
+          const int64_t gn = n0 + tx;
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int64_t gk = k0 + ty + 4 * i;
+            v[i] = (gk < k && gn < n) ? __ldcs(B + gk * n + gn) : 0.f;
+          }
+          __syncthreads();  // the previous tile's readers are done
+#pragma unroll
+          for (int i = 0; i < 16; ++i) tile[ty + 4 * i][tx] = v[i];
+          __syncthreads();
+          // B^T row n0 + row, k0 + 16 q .. +15: four threads per row
+          const int row = threadIdx.x >> 2, q = threadIdx.x & 3;
+          const int64_t gr = n0 + row;
+          if (gr < n) {
+            __align__(16) __nv_bfloat16 h[16], l[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) split1(tile[q * 16 + e][row], h[e], l[e]);
+            const int64_t off = (R.row0b + gr) * KP + k0 + q * 16;
+            *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(h);
+            *reinterpret_cast<uint4*>(bhi + off + 8) = *reinterpret_cast<const uint4*>(h + 8);
+            *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(l);
+            *reinterpret_cast<uint4*>(blo + off + 8) = *reinterpret_cast<const uint4*>(l + 8);
+          }
+        }
+      }
+    } else {
+      const bool second = lb >= R.prep_a;
+      const int32_t* X = static_cast<const int32_t*>(second ? R.B : R.A);
+      const int64_t cnt = second ? k * n : m * k;
+      const int64_t i0 = (int64_t)(second ? lb - R.prep_a : lb) * kPrepR, i1 = min(cnt, i0 + kPrepR);
+      int bad = 0;
+      // i0 is a multiple of 4 and X is 16-byte aligned (checked on the host)
 #pragma unroll 4
-      for (int64_t v = t0; v < nv; v += stride) {
+      for (int64_t v = i0 / 4 + threadIdx.x; v < i1 / 4; v += 256) {
         const int4 q = __ldcs(reinterpret_cast<const int4*>(X) + v);
         bad |= mp::out_of_pack_range(q.x) | mp::out_of_pack_range(q.y) | mp::out_of_pack_range(q.z) |
                mp::out_of_pack_range(q.w);
       }
-      for (int64_t e = nv * 4 + t0; e < cnt; e += stride) bad |= mp::out_of_pack_range(X[e]);
+      for (int64_t e = max(i0, i1 / 4 * 4) + threadIdx.x; e < i1; e += 256) bad |= mp::out_of_pack_range(X[e]);
+      bad = __syncthreads_or(bad);
+      if (bad && threadIdx.x == 0) atomicOr(&violation[p], 1);
     }
-    bad = __syncthreads_or(bad);
-    if (bad && threadIdx.x == 0) atomicOr(&violation[p], 1);
+    __syncthreads();  // the next block of work may reuse `tile`
   }
 }
 
@@ -538,7 +591,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct BatchPlan {
-  int count = 0, total_tiles = 0, mp16_total = 0, mp_total = 0;
+  int count = 0, total_tiles = 0, mp16_total = 0, mp_total = 0, prep_total = 0;
   std::vector<uint8_t> table;  // rows, then the three prefix sums (uploaded to off_table)
   int64_t rows_bytes = 0, starts_bytes = 0;
   int64_t KP = 0, rows_a = 0, rows_b = 0;
@@ -558,6 +611,8 @@ struct BatchPlan {
     H.tile_start = st;
     H.mp16_tile_start = st + (count + 1);
     H.mp_tile_start = st + 2 * (count + 1);
+    H.prep_start = st + 3 * (count + 1);
+    H.prep_total = prep_total;
     return H;
   }
 };
@@ -610,10 +665,12 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     return (int)s;
   };
   std::vector<BatchRow> rows(count);
-  std::vector<int> starts(3 * (size_t)(count + 1));
+  std::vector<int> starts(4 * (size_t)(count + 1));
   int* tile_start = starts.data();
   int* mp16_start = tile_start + (count + 1);
   int* mp_start = mp16_start + (count + 1);
+  int* prep_start = mp_start + (count + 1);
+  int64_t prep = 0;
   int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0, mp16_tiles = 0, split_tiles = 0, slot_floats = 0;
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[order[i]];
@@ -632,7 +689,18 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     r.kbs = (int)std::max<int64_t>(1, (q.k + TBK - 1) / TBK);
     r.slot_off = 0;
     r.cnt_off = 0;
-    r.pad = 0;
+    r.prep_a = 0;
+    prep_start[i] = (int)prep;
+    if (q.m > 0 && q.n > 0 && q.k > 0) {
+      if (r.kind == 0) {
+        const int64_t kp = align_up(q.k, TKA);
+        r.prep_a = (int)((q.m * (kp / 8) + kPrepA - 1) / kPrepA);
+        prep += r.prep_a + ((kp / 64) * ((q.n + 63) / 64) + kPrepB - 1) / kPrepB;
+      } else {
+        r.prep_a = (int)((q.m * q.k + kPrepR - 1) / kPrepR);
+        prep += r.prep_a + (q.k * q.n + kPrepR - 1) / kPrepR;
+      }
+    }
     tile_start[i] = (int)tiles;
     mp16_start[i] = (int)mp16_tiles;
     mp_start[i] = (int)mp_tiles;
@@ -660,12 +728,15 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
       kp_max = std::max<int64_t>(kp_max, align_up(q.k > 0 ? q.k : 1, TKA));
     }
     if (tiles > (int64_t)1 << 30 || mp_tiles > (int64_t)1 << 30 || mp16_tiles > (int64_t)1 << 30 ||
-        ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30 || split_tiles > (int64_t)1 << 30)
+        ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30 || split_tiles > (int64_t)1 << 30 ||
+        prep > (int64_t)1 << 30)
       return MM_ERR_SHAPE;
   }
   tile_start[count] = (int)tiles;
   mp16_start[count] = (int)mp16_tiles;
   mp_start[count] = (int)mp_tiles;
+  prep_start[count] = (int)prep;
+  P->prep_total = (int)prep;
   P->count = count;
   P->total_tiles = (int)tiles;
   P->mp16_total = (int)mp16_tiles;
@@ -738,7 +809,6 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
   auto* blo = reinterpret_cast<__nv_bfloat16*>(w + P.off_blo);
   MMSR_TRY_STATUS(cudaMemsetAsync(w, 0, (size_t)(P.off_cnt + 4 * P.split_tiles), st));
   const BatchHeader H = P.header(w);
-  const unsigned gy = (unsigned)std::min(count, 65535);
   {
     TraceScope tr(kTrSplitBf16, st);
     // the table: kernel parameters of a few launches (captured by value)
@@ -748,8 +818,9 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
       memcpy(chunk.bytes, P.table.data() + off, chunk.len);
       batched_upload_kernel<<<1, 256, 0, st>>>(chunk, w + P.off_table + off);
     }
-    batched_split_kernel<<<dim3(32, gy), 256, 0, st>>>(H, P.KP, ahi, alo, bhi, blo);
-    batched_range_kernel<<<dim3(32, gy), 256, 0, st>>>(H, violation);
+    if (P.prep_total > 0)
+      batched_prepass_kernel<<<(unsigned)std::min(P.prep_total, 64 * num_sms()), 256, 0, st>>>(
+          H, P.KP, ahi, alo, bhi, blo, violation);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;

@@ -118,3 +118,20 @@ def batched_problems(count=512, seed=4, lo=64, hi=2048, frac_fp32=0.7, dims=None
             B = rng.integers(0, 1001, size=(k, n), dtype=np.int32)
         probs.append(Problem(int(kinds[p]), m, n, k, A, B))
     return probs
+
+
+def batched_long_k_problems(seed=11, long_count=8, long_shape=(256, 384, 32768), short_count=56, lo=64,
+                            hi=1024):
+    """FP32 batch whose few long-k products would end it alone:
+    ``long_count`` products of ``long_shape`` and ``short_count`` with m, n,
+    k log-uniform in [lo, hi], normal(0,1) entries."""
+    rng = np.random.default_rng(seed)
+    dims = [tuple(long_shape)] * long_count
+    dims += [tuple(int(round(math.exp(x))) for x in rng.uniform(math.log(lo), math.log(hi), size=3))
+             for _ in range(short_count)]
+    probs = []
+    for m, n, k in dims:
+        A = rng.standard_normal((m, k), dtype=np.float32)
+        B = rng.standard_normal((k, n), dtype=np.float32)
+        probs.append(Problem(SR_PLUS_TIMES_F32, m, n, k, A, B))
+    return probs

@@ -5,7 +5,8 @@
 Cases: minplus4096 (the (min,+) n=4096 product, budget 0 unless --budget),
 f32_<n> (FP32 mode, bf16x3 on tensor cores), f64acc_<n> (FP64-accuracy mode),
 f64_<n> (plain FP64 path), orand_<n> (boolean), batched512 (the 512-problem
-mixed batch), strassen<L>_<n> (FP32-mode Strassen-Winograd, L levels,
+mixed batch), batched_longk (8 long-k FP32 products among 56 short ones),
+strassen<L>_<n> (FP32-mode Strassen-Winograd, L levels,
 uniform[-1,1] inputs), fa_strassen<L>_<n> (the same in FP64-accuracy mode), tar_<n>
 (one TAR-Strassen level, FP32 mode), probes (one
 launch of each instruction-throughput probe, kinds 0..3).
@@ -66,8 +67,11 @@ def main():
         A, B = inputs.boolean_u8(n, n, n, seed=6, density=0.01)
         sr, dt = mmsr.MM_SR_OR_AND_U8, torch.uint8
         acc = 1
-    elif a.case == "batched512":
-        probs = inputs.batched_problems(count=512, seed=4)
+    elif a.case in ("batched512", "batched_longk"):
+        if a.case == "batched512":
+            probs = inputs.batched_problems(count=512, seed=4)
+        else:
+            probs = inputs.batched_long_k_problems(seed=11)
         dA = [torch.from_numpy(p.A).cuda() for p in probs]
         dB = [torch.from_numpy(p.B).cuda() for p in probs]
         dC = [torch.empty((p.m, p.n), dtype=torch.float32 if p.semiring == mmsr.MM_SR_PLUS_TIMES_F32

@@ -99,3 +99,53 @@ def test_star_choice(tmp_path, monkeypatch):
     times = iter([10.0 - i for i in range(len(cands))])
     best = autotune.tune_star_strassen(sr, n, n, n, 0, 0, 0, 0, w, timer=lambda fn: next(times))
     assert (best["classic"], best["levels"], best["workspace"]) == cands[-1]
+
+
+def test_batched_split_tuning(tmp_path, monkeypatch):
+    """Coordinate descent over k buckets: the fastest hint per bucket wins,
+    short-k and (min,+) problems keep the library's rule, candidates that need
+    more workspace than given are skipped, and the choice is cached."""
+    monkeypatch.setenv("MMSR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    F32, MP = mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_MIN_PLUS_I32
+    FAKE = 1 << 20
+    probs = [(F32, 256, 256, 16384, FAKE, FAKE, FAKE), (F32, 128, 128, 3000, FAKE, FAKE, FAKE),
+             (F32, 64, 64, 100, FAKE, FAKE, FAKE), (MP, 64, 64, 5000, FAKE, FAKE, FAKE)]
+    assert [b for b, _ in autotune.batch_buckets(probs)] == [16384, 4096]
+    budget = mmsr.mm_batched_query(autotune.apply_splits(probs, [8, 16, 0, 0]))
+    seen = []
+    # pretend the 16384 bucket likes 8 slices and the 4096 bucket 2
+    cost = {16384: {0: 9.0, 1: 12.0, 2: 8.0, 4: 7.0, 8: 5.0, 16: 6.0}, 4096: {0: 3.0, 1: 2.5, 2: 1.0, 4: 2.0,
+                                                                            8: 2.2, 16: 2.4}}
+
+    def fake_timer(fn):
+        sp = fake_timer.current
+        seen.append(tuple(sp))
+        return cost[16384][sp[0]] + cost[4096][sp[1]]
+
+    real_run = mmsr.mm_batched
+
+    def spy(table, *a, **k):
+        fake_timer.current = [t[7] for t in table]
+        return 0
+
+    monkeypatch.setattr(mmsr, "mm_batched", spy)
+
+    def timer(fn):
+        fn()
+        return fake_timer(fn)
+
+    rec = autotune.tune_batched(probs, FAKE, budget, timer=timer)
+    assert rec["buckets"] == {"16384": 8, "4096": 2}
+    assert rec["splits"] == [8, 2, 0, 0]
+    assert all(t[2] == 0 and t[3] == 0 for t in seen)  # untuned problems keep the rule
+    # a smaller workspace rules out the widest candidates
+    small = mmsr.mm_batched_query(autotune.apply_splits(probs, [4, 16, 0, 0])) - 1
+    monkeypatch.setenv("MMSR_TUNE_CACHE", str(tmp_path / "tune2.json"))
+    seen.clear()
+    rec2 = autotune.tune_batched(probs, FAKE, small, timer=timer)
+    assert seen and all(mmsr.mm_batched_query(autotune.apply_splits(probs, t)) <= small for t in seen)
+    assert mmsr.mm_batched_query(autotune.apply_splits(probs, rec2["splits"])) <= small
+    # cached: no timing on the second call
+    seen.clear()
+    assert autotune.tune_batched(probs, FAKE, small, timer=timer) == rec2 and not seen
+    monkeypatch.setattr(mmsr, "mm_batched", real_run)

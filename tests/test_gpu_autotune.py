@@ -46,3 +46,32 @@ def test_tuned_strassen_depth(tmp_path, monkeypatch):
                      best["workspace"])
     torch.cuda.synchronize()
     np.testing.assert_array_equal(dC.cpu().numpy(), oracle.mm_f64(A, B).astype(np.float32))
+
+
+def test_tuned_batched_k_slices(tmp_path, monkeypatch):
+    # the batch tuner times k-slice hints per k bucket on the device and the
+    # tuned call still reproduces the oracle (integer inputs: exact)
+    import torch
+
+    monkeypatch.setenv("MMSR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    rng = np.random.default_rng(302)
+    shapes = [(256, 256, 8192), (128, 192, 8192), (100, 100, 2000), (64, 64, 64)]
+    probs, dCs = [], []
+    for m, n, k in shapes:
+        A = rng.integers(-3, 4, size=(m, k)).astype(np.float32)
+        B = rng.integers(-3, 4, size=(k, n)).astype(np.float32)
+        dC = empty((m, n), torch.float32)
+        probs.append((mmsr.MM_SR_PLUS_TIMES_F32, m, n, k, dev(A), dev(B), dC, A, B))
+        dCs.append(dC)
+    table = [p[:7] for p in probs]
+    need = max(mmsr.mm_batched_query(autotune.apply_splits(table, [h] * len(table))) for h in (0, 16))
+    ws = empty((need,), torch.uint8)
+    rec = autotune.tune_batched(table, ws, need)
+    assert set(rec["buckets"]) == {"8192", "2048"} and len(rec["splits"]) == 4 and rec["splits"][3] == 0
+    for c in dCs:
+        c.fill_(-1)
+    autotune.mm_batched_tuned(table, ws, need)
+    torch.cuda.synchronize()
+    assert mmsr.mm_last_device_status() == 0
+    for p, c in zip(probs, dCs):
+        np.testing.assert_array_equal(c.cpu().numpy(), oracle.mm_f64(p[7], p[8]).astype(np.float32))
