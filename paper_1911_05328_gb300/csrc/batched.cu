@@ -60,7 +60,11 @@ constexpr int kMaxBatch = 1 << 20;  // problems per call (tile counts stay in in
 #endif
 constexpr int TBM = 128, TBN = 128, TBK = MMSR_B_BK, TSTAGES = MMSR_B_STAGES, TCHUNK = MMSR_B_CHUNK, TKA = 64;
 static_assert(TKA % TBK == 0 && (TBK == 32 || TBK == 64), "k-block / swizzle");
-constexpr int kDrainW = 8, kBThreads = 64 + 32 * kDrainW;
+// warp 0: TMA producer, warp 1: MMA issuer, warps 2..9: drain, warp 10:
+// tile scheduler (claims tile indices and finds their problems ahead of the
+// other roles, so the claim's atomic and the table search stay off the
+// producer's path between two tiles)
+constexpr int kDrainW = 8, kSchedWarp = 2 + kDrainW, kBThreads = 64 + 32 * kDrainW + 32;
 constexpr uint32_t TA_BYTES = TBM * TBK * 2, TB_BYTES = TBN * TBK * 2;
 constexpr uint32_t TSTAGE = 2 * TA_BYTES + 2 * TB_BYTES;
 constexpr int kTileQ = 4;  // tile indices the producer may claim ahead of the consumers
@@ -343,6 +347,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   int* tile_q = abort_flag + 1;                // [kTileQ]
   int* fold_flag = tile_q + kTileQ;            // this CTA folds the tile's slices
+  int* tile_qp = fold_flag + 1;                // [kTileQ] problem of each queued tile
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
     }
     for (int q = 0; q < kTileQ; ++q) {
       tc::mbar_init(&tile_full[q], 1);
-      tc::mbar_init(&tile_empty[q], 1 + kDrainW);  // the MMA thread and the drain warps
+      tc::mbar_init(&tile_empty[q], 2 + kDrainW);  // producer, MMA thread and drain warps
     }
     tc::mbar_init(quiesce, 1);
     tc::mbar_init(seg_stored, kDrainW);
@@ -376,35 +381,46 @@ __global__ void __launch_bounds__(kBThreads, 1)
   // barrier: the producer claims tiles ahead (and starts their TMA loads)
   // while the tensor core and the drain warps still work on earlier ones.
   uint32_t ring = 0, chunk = 0, ps = 0;  // ps: k-sliced tiles drained (rendezvous phase)
-  const bool active = warp >= 2 || lane == 0;  // warps 0 and 1 work through one lane
+  // warps 0, 1 and the scheduler work through one lane
+  const bool active = (warp >= 2 && warp < kSchedWarp) || lane == 0;
   bool skipped = false;  // producer: the test switch took ring position 0 out
 
   for (uint32_t j = 0; active; ++j) {
     const int slot = (int)(j % kTileQ);
     const uint32_t ph = (j / kTileQ) & 1u;
-    int t = INT_MAX;
-    if (warp == 0) {
+    int t = INT_MAX, p = 0;
+    if (warp == kSchedWarp) {
       if (j < kTileQ || tc::mbar_wait(&tile_empty[slot], ph ^ 1u, abort_flag, &g_batched_status)) {
         t = atomicAdd(counter, 1);
-        // tile 0 is always its CTA's first claim, so the ring is at position 0
-        if (t == 0) skipped = atomicExch(&g_batched_skip_signal, 0) != 0;
+        if (t < T.total_tiles) {
+          int lo = 0, hi = T.count - 1;  // last p with tile_start[p] <= t
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (T.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+          }
+          p = lo;
+        }
         tile_q[slot] = t;
-        tc::mbar_arrive(&tile_full[slot]);  // release: the index is visible to the waiters
+        tile_qp[slot] = p;
+        tc::mbar_arrive(&tile_full[slot]);  // release: the entry is visible to the waiters
       }
-    } else {
+      if (t >= T.total_tiles) break;
+      continue;
+    }
+    {
+      const bool drain = warp >= 2;
       bool ok = tc::mbar_wait(&tile_full[slot], ph, abort_flag, &g_batched_status);
-      if (warp >= 2) ok = __all_sync(0xffffffffu, ok);
-      if (ok) t = *reinterpret_cast<volatile int*>(&tile_q[slot]);
-      if (warp >= 2) __syncwarp();
+      if (drain) ok = __all_sync(0xffffffffu, ok);
+      if (ok) {
+        t = *reinterpret_cast<volatile int*>(&tile_q[slot]);
+        p = *reinterpret_cast<volatile int*>(&tile_qp[slot]);
+      }
+      if (drain) __syncwarp();
       if (ok && lane == 0) tc::mbar_arrive(&tile_empty[slot]);
+      // tile 0 is always its CTA's first tile, so the ring is at position 0
+      if (warp == 0 && t == 0) skipped = atomicExch(&g_batched_skip_signal, 0) != 0;
     }
     if (t >= T.total_tiles) break;
-    int lo = 0, hi = T.count - 1;  // last p with tile_start[p] <= t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (T.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const int p = lo;
     const int local = t - T.tile_start[p];
     const int64_t m = T.rows[p].m, n = T.rows[p].n, k = T.rows[p].k;
     // unit = (tile, k-slice), the slices of one tile adjacent in the queue
