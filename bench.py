@@ -858,7 +858,19 @@ def extras_strassen(mmsr, lib, torch, sp, ctypes, book, A_sq, B_sq, rows, bf16, 
     dC64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
     res["fp64acc"] = _strassen_levels(mmsr, lib, torch, sp, ctypes, book, "sq64", mmsr.MM_SR_PLUS_TIMES_F64ACC,
                                       n, n, n, dA64, dB64, dC64, rows, bf16, bf16_src, reps=2)
-    del dC64
+    # TAR-Strassen in FP64-accuracy mode: one Winograd level whose seven
+    # digit-slice products add straight into C's quadrants (no post pass)
+    fa = mmsr.MM_SR_PLUS_TIMES_F64ACC
+    p = mmsr.mm_strassen_tar_query(1, fa, n, n, n)
+    ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+    fn = lambda: mmsr.mm_strassen_tar(1, mmsr.MM_STRASSEN_WINOGRAD, fa, n, n, n, dA64, dB64, dC64, ws,
+                                      int(p.workspace_min), sp)
+    ms = _time_call(torch, fn, 2)
+    res["fp64acc_tar_L1"] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                             "workspace_bytes": int(p.workspace_min),
+                             "workspace_over_mn_x_elem": p.workspace_min / (n * n * 8.0)}
+    book.add("sq64", res["fp64acc_tar_L1"], "error", _rows_of(torch, dC64, rows))
+    del ws, dC64
     torch.cuda.empty_cache()
     book.add_set("sq32", lambda A=A_sq, B=B_sq: (A.astype(np.float32), B.astype(np.float32)), rows)
     dA, dB = dA64.float(), dB64.float()
@@ -867,19 +879,20 @@ def extras_strassen(mmsr, lib, torch, sp, ctypes, book, A_sq, B_sq, rows, bf16, 
     sr = mmsr.MM_SR_PLUS_TIMES_F32
     res["fp32"] = _strassen_levels(mmsr, lib, torch, sp, ctypes, book, "sq32", sr, n, n, n, dA, dB, dC, rows,
                                    bf16, bf16_src)
-    # TAR-Strassen: one level, products added into C's quadrants by the leaf
-    # epilogue in conflict-free waves (no product temporaries)
-    p = mmsr.mm_strassen_tar_query(sr, n, n, n)
-    ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
-    fn = lambda: mmsr.mm_strassen_tar(mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws,
-                                      int(p.workspace_min), sp)
-    ms = _time_call(torch, fn, 3)
-    res["fp32_tar_L1"] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
-                          "workspace_bytes": int(p.workspace_min),
-                          "workspace_n2x4B": p.workspace_min / (n * n * 4.0)}
-    book.add("sq32", res["fp32_tar_L1"], "error", _rows_of(torch, dC, rows))
-    del ws
-    torch.cuda.empty_cache()
+    # TAR-Strassen: leaf products added into C's blocks by the leaf epilogue
+    # in conflict-free waves (no product temporaries): one Winograd level,
+    # two levels of the paper's formulas
+    for key, L, var in (("fp32_tar_L1", 1, mmsr.MM_STRASSEN_WINOGRAD), ("fp32_tar_L2_paper", 2, mmsr.MM_STRASSEN_PAPER)):
+        p = mmsr.mm_strassen_tar_query(L, sr, n, n, n)
+        ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
+        fn = lambda: mmsr.mm_strassen_tar(L, var, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min), sp)
+        ms = _time_call(torch, fn, 3)
+        res[key] = {"ms": ms, "gops_classic_equiv": 2.0 * n ** 3 / (ms * 1e-3) / 1e9,
+                    "workspace_bytes": int(p.workspace_min), "workspace_n2x4B": p.workspace_min / (n * n * 4.0),
+                    "waves": mmsr.mm_strassen_tar_waves(L, var)[0]}
+        book.add("sq32", res[key], "error", _rows_of(torch, dC, rows))
+        del ws
+        torch.cuda.empty_cache()
     # one level with the operand sums formed in the leaf's staging against the
     # materialised operand passes, for the paper's formulas and Winograd's
     for vname, var in (("paper", mmsr.MM_STRASSEN_PAPER), ("winograd", mmsr.MM_STRASSEN_WINOGRAD)):

@@ -194,34 +194,45 @@ int mm_star_strassen_query(int classic_levels, int levels, int semiring, int64_t
                            int64_t k, size_t workspace_bytes, mm_plan_t* plan);
 
 /*
- * mm_strassen_tar -- C := A (x) B with one Strassen level in the paper's
- * zero-temporary schedule (TAR-Strassen, Section 5): the seven products are
- * not stored; the leaf epilogue adds each one (times its +-1 coefficients)
- * straight into the quadrants of C.  Products run in waves in which no two
- * touch the same quadrant -- a greedy colouring of the coefficient table in
- * product order, for the paper's formulas P1; P2 || P5; P3 || P4; P6 || P7 --
- * so the read-modify-writes of a wave never collide; a quadrant's first
- * writer overwrites it.
- *   variant           MM_STRASSEN_PAPER or MM_STRASSEN_WINOGRAD
- *   semiring          MM_SR_PLUS_TIMES_F32 only (MM_ERR_UNSUPPORTED otherwise:
- *                     the quadrant epilogue lives in the FP32-mode leaf)
- *   m, n, k           even (MM_ERR_SHAPE otherwise)
+ * mm_strassen_tar -- C := A (x) B with one or two Strassen levels in the
+ * paper's zero-temporary schedule (TAR-Strassen, Section 5): the leaf
+ * products are not stored; the leaf epilogue adds each one (times its +-1
+ * coefficient) straight into the blocks of C it contributes to -- leaf
+ * product 7 r1 + r2 into block (q1, q2) with coefficient gamma[q1][r1]
+ * gamma[q2][r2].  Products run in waves in which no two touch the same block
+ * -- a greedy colouring of the coefficients in product order, for one level
+ * of the paper's formulas P1; P2 || P5; P3 || P4; P6 || P7 -- so the
+ * read-modify-writes of a wave never collide; a block's first writer
+ * overwrites it.
+ *   levels            1 or 2 (MM_ERR_ARG otherwise)
+ *   variant           MM_STRASSEN_PAPER or MM_STRASSEN_WINOGRAD; a product
+ *                     may reach at most four blocks, so two Winograd levels
+ *                     (its P1 reaches all four quadrants) are
+ *                     MM_ERR_UNSUPPORTED
+ *   semiring          MM_SR_PLUS_TIMES_F32 or MM_SR_PLUS_TIMES_F64ACC
+ *                     (MM_ERR_UNSUPPORTED otherwise: the block epilogue lives
+ *                     in the bf16x3 and digit-slice leaves)
+ *   m, n, k           divisible by 2^levels (MM_ERR_SHAPE otherwise)
  *   A, B, C, workspace, workspace_bytes, stream   as in mm_strassen
- * Workspace: the operand sums of the seven products only (bf16 hi/lo),
- * mm_strassen_tar_query reports it -- the product stack of mm_strassen with
- * one level (7 (m/2)(n/2) FP32 values) is not needed.
+ * Workspace (mm_strassen_tar_query): the leaf operand sums (FP32 mode: bf16
+ * hi/lo; FP64-accuracy mode: FP64 sums and their digit slices) -- in FP32
+ * mode the product stack of mm_strassen (7^L (m/2^L)(n/2^L) values) is not
+ * needed; in FP64-accuracy mode mm_strassen already overlays it on the FP64
+ * operand stack, so both need the same.
  * Returns MM_OK or a negative mm_status_t.
  */
-int mm_strassen_tar(int variant, int semiring, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
-                    void* C, void* workspace, size_t workspace_bytes, void* stream);
+int mm_strassen_tar(int levels, int variant, int semiring, int64_t m, int64_t n, int64_t k, const void* A,
+                    const void* B, void* C, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Plan (workspace_min / workspace_used) of mm_strassen_tar.  Host-only. */
-int mm_strassen_tar_query(int semiring, int64_t m, int64_t n, int64_t k, mm_plan_t* plan);
+int mm_strassen_tar_query(int levels, int semiring, int64_t m, int64_t n, int64_t k, mm_plan_t* plan);
 
-/* The wave schedule of mm_strassen_tar: writes, for products r = 0..6 (the
- * order of mm_strassen_tables), the wave each one runs in, and returns the
- * number of waves (or MM_ERR_ARG).  Host-only. */
-int mm_strassen_tar_waves(int variant, int* wave_of_product);
+/* The wave schedule of mm_strassen_tar: writes, for leaf products p = 0 ..
+ * 7^levels - 1 (p = 7 r1 + r2 at two levels, r in the order of
+ * mm_strassen_tables), the wave each one runs in, and returns the number of
+ * waves, MM_ERR_UNSUPPORTED when a product would reach more than four blocks
+ * (the waves are still written), or MM_ERR_ARG.  Host-only. */
+int mm_strassen_tar_waves(int levels, int variant, int* wave_of_product);
 
 /*
  * mm_strassen_tables -- the bilinear coefficients one level of `variant`

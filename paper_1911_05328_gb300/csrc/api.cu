@@ -244,31 +244,35 @@ int mm_star_strassen_query(int classic_levels, int levels, int semiring, int64_t
   return plan_star_strassen(classic_levels, levels, semiring, m, n, k, workspace_bytes, plan);
 }
 
-int mm_strassen_tar(int variant, int semiring, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
-                    void* C, void* workspace, size_t workspace_bytes, void* stream) {
+int mm_strassen_tar(int levels, int variant, int semiring, int64_t m, int64_t n, int64_t k, const void* A,
+                    const void* B, void* C, void* workspace, size_t workspace_bytes, void* stream) {
   int rc = validate_common(semiring, m, n, k, A, B, C, workspace, workspace_bytes);
   if (rc != MM_OK) return rc;
   if (variant != MM_STRASSEN_PAPER && variant != MM_STRASSEN_WINOGRAD) return MM_ERR_ARG;
-  if (semiring != MM_SR_PLUS_TIMES_F32) return MM_ERR_UNSUPPORTED;
-  if ((m & 1) || (n & 1) || (k & 1)) return MM_ERR_SHAPE;
+  if (levels < 1 || levels > 2) return MM_ERR_ARG;
+  if (semiring != MM_SR_PLUS_TIMES_F32 && semiring != MM_SR_PLUS_TIMES_F64ACC) return MM_ERR_UNSUPPORTED;
+  const int64_t mask = (1 << levels) - 1;
+  if ((m & mask) || (n & mask) || (k & mask)) return MM_ERR_SHAPE;
   if (m == 0 || n == 0) return MM_OK;
-  return run_strassen_tar(variant, semiring, m, n, k, A, B, C, workspace, workspace_bytes,
+  return run_strassen_tar(levels, variant, semiring, m, n, k, A, B, C, workspace, workspace_bytes,
                           static_cast<cudaStream_t>(stream));
 }
 
-int mm_strassen_tar_query(int semiring, int64_t m, int64_t n, int64_t k, mm_plan_t* plan) {
+int mm_strassen_tar_query(int levels, int semiring, int64_t m, int64_t n, int64_t k, mm_plan_t* plan) {
   if (!plan) return MM_ERR_ARG;
-  if (acc_bytes(semiring) == 0 || m < 0 || n < 0 || k < 0) return MM_ERR_ARG;
+  if (acc_bytes(semiring) == 0 || m < 0 || n < 0 || k < 0 || levels < 1 || levels > 2) return MM_ERR_ARG;
   if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return MM_ERR_SHAPE;
-  if (semiring != MM_SR_PLUS_TIMES_F32) return MM_ERR_UNSUPPORTED;
-  if ((m & 1) || (n & 1) || (k & 1)) return MM_ERR_SHAPE;
-  return plan_strassen_tar(semiring, m, n, k, plan);
+  if (semiring != MM_SR_PLUS_TIMES_F32 && semiring != MM_SR_PLUS_TIMES_F64ACC) return MM_ERR_UNSUPPORTED;
+  const int64_t mask = (1 << levels) - 1;
+  if ((m & mask) || (n & mask) || (k & mask)) return MM_ERR_SHAPE;
+  return plan_strassen_tar(levels, semiring, m, n, k, plan);
 }
 
-int mm_strassen_tar_waves(int variant, int* wave_of_product) {
+int mm_strassen_tar_waves(int levels, int variant, int* wave_of_product) {
   if (!wave_of_product) return MM_ERR_ARG;
   if (variant != MM_STRASSEN_PAPER && variant != MM_STRASSEN_WINOGRAD) return MM_ERR_ARG;
-  return strassen_tar_waves(variant, wave_of_product);
+  if (levels < 1 || levels > 2) return MM_ERR_ARG;
+  return strassen_tar_waves(levels, variant, wave_of_product);
 }
 
 int mm_plan_query(int semiring, int levels, int64_t m, int64_t n, int64_t k,

@@ -64,23 +64,38 @@ int arm_tc_skip_signal(int on);
 int arm_f64acc_skip_signal(int on);
 int arm_batched_skip_signal(int on);
 
-// Leaf epilogue that adds each product into quadrants of C instead of
-// writing it out: batch entry b adds sign[b][d] x product into dst[b][d]
-// (d < 4, nullptr = unused; row pitch ld), overwriting where add[b][d] == 0.
+// Leaf epilogue that adds each product into blocks of C instead of writing
+// it out (TAR-Strassen): batch entry b computes the product of stacked leaf
+// operands leaf[b] and adds sign[b][d] x product into dst[b][d] (d < 4,
+// nullptr = unused; row pitch ld), overwriting where add[b][d] == 0.
 // entries == 0 selects the ordinary output.
-struct QuadOut {
-  float* dst[7][4];
-  int8_t sign[7][4];
-  int8_t add[7][4];
+constexpr int kQuadEntries = 16;
+template <typename T>
+struct QuadOutT {
+  T* dst[kQuadEntries][4];
+  int8_t sign[kQuadEntries][4];
+  int8_t add[kQuadEntries][4];
+  int16_t leaf[kQuadEntries];
   int64_t ld;
   int entries;
 };
+using QuadOut = QuadOutT<float>;
+using QuadOut64 = QuadOutT<double>;
 
-// batched leaves (independent products on stacked operands)
+// TAR-Strassen leaves in FP64-accuracy mode: exponents and digit slices of
+// `batches` stacked products once, then launches whose entries add their
+// products into blocks of C (QuadOut64); `ws` as for run_f64acc_batched
+int f64acc_prepare_batched(const double* A, const double* B, int64_t m, int64_t n, int64_t k, int batches,
+                           int slices, void* ws, cudaStream_t st);
+int f64acc_gemm_quad(int64_t m, int64_t n, int64_t k, int batches, int slices, void* ws, const QuadOut64& quad,
+                     cudaStream_t st);
+
+// batched leaves (independent products on stacked operands); with `quad`,
+// the entries' leaves index a stack of `map_batches` operands
 cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
                                   const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,
                                   int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st,
-                                  const QuadOut* quad = nullptr);
+                                  const QuadOut* quad = nullptr, int map_batches = 0);
 cudaError_t launch_dfma_batched(const double* A, const double* B, double* C, int64_t m, int64_t n,
                                 int64_t k, int batches, cudaStream_t st);
 
@@ -109,12 +124,12 @@ int run_star_strassen(int classic, int levels, int variant, int sr, int64_t m, i
                       const void* A, const void* B, void* C, void* ws, size_t ws_bytes,
                       cudaStream_t st);
 
-// TAR-Strassen level: products added straight into the quadrants of C in
-// conflict-free waves (FP32 mode)
-int plan_strassen_tar(int sr, int64_t m, int64_t n, int64_t k, mm_plan_t* p);
-int run_strassen_tar(int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
-                     void* ws, size_t ws_bytes, cudaStream_t st);
-int strassen_tar_waves(int variant, int* wave_of_product);
+// TAR-Strassen, one or two levels: leaf products added straight into the
+// blocks of C in conflict-free waves (FP32 and FP64-accuracy modes)
+int plan_strassen_tar(int L, int sr, int64_t m, int64_t n, int64_t k, mm_plan_t* p);
+int run_strassen_tar(int L, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                     void* C, void* ws, size_t ws_bytes, cudaStream_t st);
+int strassen_tar_waves(int L, int variant, int* wave_of_product);
 
 // closure by repeated squaring
 int closure_squarings(int64_t n);

@@ -102,20 +102,14 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Output slot of each of the seven products (identity, or the wave order of
-// a TAR-Strassen level, whose waves must sit in consecutive slots).
-struct Slots7 {
-  int8_t s[7];
-};
-
 // Last level, A side, FP32 mode: seven (h x w) sums written as bf16 hi/lo
-// rows of pitch Kp (columns w..Kp-1 zero), product p into slot slot.s[p].
+// rows of pitch Kp (columns w..Kp-1 zero), product p into stack slot 7 r + p.
 // Blocks walk rows, threads walk 8-column groups; `vec` = the source rows
 // allow 16-byte loads.
 template <int VARIANT>
 __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
     const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int h, int w, int Kp,
-    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int vec, Slots7 slot) {
+    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int vec) {
   const int r = blockIdx.y;
   const float* s = src + (int64_t)r * src_stride;
   for (int i = blockIdx.x; i < h; i += gridDim.x) {
@@ -140,7 +134,7 @@ __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
 #pragma unroll
         for (int t = 0; t < 8; ++t)
           split_bf16(combo4<VARIANT, 0>(p, x[0][t], x[1][t], x[2][t], x[3][t]), hh[t], ll[t]);
-        const int64_t off = ((int64_t)(r * 7 + slot.s[p]) * h + i) * Kp + c8;
+        const int64_t off = ((int64_t)(r * 7 + p) * h + i) * Kp + c8;
         *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(hh);
         *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(ll);
       }
@@ -150,12 +144,12 @@ __global__ void __launch_bounds__(256) pre_combine_split_rows_kernel(
 
 // Last level, B side, FP32 mode: source stack matrix r is (2h x 2w) = (k x n);
 // the seven sums T_p (h x w) are written transposed as bf16 hi/lo (w x Kp),
-// product p into slot slot.s[p].  Tile: 64 k x 32 n of each quadrant
+// product p into stack slot 7 r + p.  Tile: 64 k x 32 n of each quadrant
 // through shared memory.
 template <int VARIANT>
 __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
     const float* __restrict__ src, int64_t src_ld, int64_t src_stride, int64_t h, int64_t w,
-    int64_t Kp, __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT, Slots7 slot) {
+    int64_t Kp, __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT) {
   __shared__ float tile[4][64][33];
   const int r = blockIdx.z;
   const float* s = src + (int64_t)r * src_stride;
@@ -186,7 +180,7 @@ __global__ void __launch_bounds__(256) pre_combine_split_transpose_kernel(
       split_bf16(combo4<VARIANT, 1>(p, tile[0][kk][row], tile[1][kk][row], tile[2][kk][row], tile[3][kk][row]),
                  hh[t], ll[t]);
     }
-    const int64_t off = ((int64_t)(r * 7 + slot.s[p]) * w + gn) * Kp + k0 + chunk * 8;
+    const int64_t off = ((int64_t)(r * 7 + p) * w + gn) * Kp + k0 + chunk * 8;
     *reinterpret_cast<uint4*>(hiT + off) = *reinterpret_cast<const uint4*>(hh);
     *reinterpret_cast<uint4*>(loT + off) = *reinterpret_cast<const uint4*>(ll);
   }
@@ -726,7 +720,7 @@ inline int pass_first_level(int L, int l) { return (L & 1) && l == 1 ? 1 : 2; }
 // cols with row pitch ld.
 cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t rows, int64_t cols,
                        int64_t ld, uint8_t* ws, const StrassenLayout& S, __nv_bfloat16* hi,
-                       __nv_bfloat16* lo, cudaStream_t st, Slots7 slot = {{0, 1, 2, 3, 4, 5, 6}}) {
+                       __nv_bfloat16* lo, cudaStream_t st) {
   const float* src = X;
   int64_t src_ld = ld, src_stride = 0;
   int pass = 0;
@@ -760,10 +754,10 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
         const dim3 g(rows_grid(h, R, threads), (unsigned)R);
         if (variant == 0)
           pre_combine_split_rows_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
-                                                                 (int)S.KpL, hi, lo, vec, slot);
+                                                                 (int)S.KpL, hi, lo, vec);
         else
           pre_combine_split_rows_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, (int)h, (int)w,
-                                                                 (int)S.KpL, hi, lo, vec, slot);
+                                                                 (int)S.KpL, hi, lo, vec);
       }
       MMSR_CUDA_TRY(cudaGetLastError());
     } else {
@@ -778,11 +772,9 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
       } else {
         const dim3 g((unsigned)(S.KpL / 64), (unsigned)std::min<int64_t>((w + 31) / 32, kMaxGridY), (unsigned)R);
         if (variant == 0)
-          pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo,
-                                                                  slot);
+          pre_combine_split_transpose_kernel<0><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
         else
-          pre_combine_split_transpose_kernel<1><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo,
-                                                                  slot);
+          pre_combine_split_transpose_kernel<1><<<g, 256, 0, st>>>(src, src_ld, src_stride, h, w, S.KpL, hi, lo);
       }
       MMSR_CUDA_TRY(cudaGetLastError());
     }
@@ -993,110 +985,171 @@ int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t 
 }
 
 // TAR-Strassen (the zero-temporary Strassen schedule the paper sketches in
-// Section 5): one level whose seven products are added straight into the
-// quadrants of C by the leaf epilogue -- no product temporaries.  Products
-// run in waves in which no two touch the same quadrant, so the read-modify-
-// writes of one launch never collide; a quadrant's first writer overwrites
-// it.  The waves are a greedy colouring of the gamma table in product order
-// (for the paper's formulas exactly the order P1; P2 || P5; P3 || P4;
-// P6 || P7).  FP32 mode only (the quadrant epilogue lives in the bf16x3
-// leaf).  Workspace: the operand sums only.
-struct TarWaves {
-  int count;
-  int size[7];
-  int member[7][7];
+// Section 5), one or two levels: the leaf products are not stored; the leaf
+// epilogue adds each one, times its +-1 coefficient, straight into the
+// blocks of C it contributes to.  Leaf product p = 7 r1 + r2 (r1 the top
+// level's product, the order of the operand passes) goes to block (q1, q2)
+// with coefficient gamma(q1, r1) gamma(q2, r2).  Products run in waves in
+// which no two touch the same block, so the read-modify-writes of one launch
+// never collide; a block's first writer overwrites it.  The waves are a
+// greedy colouring in product order (one level of the paper's formulas:
+// exactly P1; P2 || P5; P3 || P4; P6 || P7).  A product may reach at most four
+// blocks (the epilogue's limit): every product of the paper's formulas at
+// one or two levels and of Winograd's at one level; two Winograd levels
+// (P1 x P1 reaches all sixteen blocks) are refused.  FP32 mode (bf16x3 leaf)
+// and FP64-accuracy mode (digit-slice leaf).  Workspace: the operand sums.
+struct TarPlan {
+  int levels = 0, products = 0, waves = 0;
+  bool fits = true;  // every product reaches at most four blocks
+  int wave_of[49];
+  int ndst[49];
+  int block[49][4];  // block index br * 2^L + bc
+  int sign[49][4];
 };
 
-TarWaves tar_waves(int variant) {
-  TarWaves W;
-  memset(&W, 0, sizeof(W));
-  int used[7] = {0};  // quadrant mask per wave
-  for (int r = 0; r < 7; ++r) {
-    int mask = 0;
-    for (int q = 0; q < 4; ++q)
-      if (coef_gamma(variant, q, r) != 0) mask |= 1 << q;
-    int w = 0;
-    while (w < W.count && (used[w] & mask)) ++w;
-    if (w == W.count) ++W.count;
-    used[w] |= mask;
-    W.member[w][W.size[w]++] = r;
-  }
-  return W;
-}
-
-size_t tar_workspace(int64_t m, int64_t n, int64_t k) {
-  return (size_t)strassen_layout(1, MM_SR_PLUS_TIMES_F32, m, n, k).off_p;
-}
-
-int run_tar_view(int variant, int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B,
-                 int64_t ldb, float* C, int64_t ldc, uint8_t* w, cudaStream_t st) {
-  const StrassenLayout S = strassen_layout(1, MM_SR_PLUS_TIMES_F32, m, n, k);
-  const TarWaves W = tar_waves(variant);
-  Slots7 slot;
-  int next = 0;
-  for (int v = 0; v < W.count; ++v)
-    for (int i = 0; i < W.size[v]; ++i) slot.s[W.member[v][i]] = (int8_t)next++;
-  auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + S.off_ahi);
-  auto* alo = reinterpret_cast<__nv_bfloat16*>(w + S.off_alo);
-  auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + S.off_bhi);
-  auto* blo = reinterpret_cast<__nv_bfloat16*>(w + S.off_blo);
-  cudaError_t e;
-  {
-    TraceScope tr(kTrStrassenCombine, st);
-    e = expand_f32(1, variant, 0, A, m, k, lda, w, S, ahi, alo, st, slot);
-    if (e == cudaSuccess) e = expand_f32(1, variant, 1, B, k, n, ldb, w, S, bhi, blo, st, slot);
-  }
-  if (e != cudaSuccess) return report_cuda(e, "TAR-Strassen operand pass");
-  bool written[4] = {false, false, false, false};
-  int first_slot = 0;
-  for (int v = 0; v < W.count; ++v) {
-    QuadOut qo;
-    memset(&qo, 0, sizeof(qo));
-    qo.entries = W.size[v];
-    qo.ld = ldc;
-    bool wrote[4] = {false, false, false, false};
-    for (int i = 0; i < W.size[v]; ++i) {
-      const int r = W.member[v][i];
-      int d = 0;
-      for (int q = 0; q < 4; ++q) {
-        const int g = coef_gamma(variant, q, r);
-        if (g == 0) continue;
-        qo.dst[i][d] = C + (q >> 1) * S.mL * ldc + (q & 1) * S.nL;
-        qo.sign[i][d] = (int8_t)g;
-        qo.add[i][d] = written[q] ? 1 : 0;
-        wrote[q] = true;
-        ++d;
+TarPlan tar_plan(int L, int variant) {
+  TarPlan T;
+  T.levels = L;
+  T.products = pw7(L);
+  const int side = 1 << L;
+  uint32_t used[49];
+  memset(used, 0, sizeof(used));
+  for (int p = 0; p < T.products; ++p) {
+    const int r1 = L == 2 ? p / 7 : p, r2 = L == 2 ? p % 7 : 0;
+    T.ndst[p] = 0;
+    uint32_t mask = 0;
+    for (int q1 = 0; q1 < 4; ++q1) {
+      const int g1 = coef_gamma(variant, q1, r1);
+      if (g1 == 0) continue;
+      for (int q2 = 0; q2 < (L == 2 ? 4 : 1); ++q2) {
+        const int g2 = L == 2 ? coef_gamma(variant, q2, r2) : 1;
+        if (g2 == 0) continue;
+        const int br = (q1 >> 1) * (side / 2) + (L == 2 ? (q2 >> 1) : 0);
+        const int bc = (q1 & 1) * (side / 2) + (L == 2 ? (q2 & 1) : 0);
+        const int b = br * side + bc;
+        mask |= 1u << b;
+        if (T.ndst[p] < 4) {
+          T.block[p][T.ndst[p]] = b;
+          T.sign[p][T.ndst[p]] = g1 * g2;
+        }
+        ++T.ndst[p];
       }
     }
-    for (int q = 0; q < 4; ++q) written[q] = written[q] || wrote[q];
-    e = launch_bf16x3_batched(ahi + (int64_t)first_slot * S.mL * S.KpL, alo + (int64_t)first_slot * S.mL * S.KpL,
-                              bhi + (int64_t)first_slot * S.nL * S.KpL, blo + (int64_t)first_slot * S.nL * S.KpL,
-                              nullptr, S.mL, S.nL, S.KpL, W.size[v], st, &qo);
-    if (e != cudaSuccess) return report_cuda(e, "TAR-Strassen leaf wave");
-    first_slot += W.size[v];
+    if (T.ndst[p] > 4) T.fits = false;
+    int w = 0;
+    while (w < T.waves && (used[w] & mask)) ++w;
+    if (w == T.waves) ++T.waves;
+    used[w] |= mask;
+    T.wave_of[p] = w;
   }
+  return T;
+}
+
+size_t tar_workspace(int L, int sr, int64_t m, int64_t n, int64_t k) {
+  const StrassenLayout S = strassen_layout(L, sr, m, n, k);
+  // FP32 mode: everything before the product stack; FP64-accuracy mode: the
+  // FP64 leaf operands and their digit slices (its products overlay the A
+  // leaf stack in mm_strassen too, so the two need the same)
+  return (size_t)(sr == MM_SR_PLUS_TIMES_F32 ? S.off_p : S.total);
+}
+
+template <typename T, typename Launch>
+cudaError_t tar_waves_run(const TarPlan& TP, const StrassenLayout& S, T* C, int64_t ldc, Launch&& launch) {
+  const int side = 1 << TP.levels;
+  bool written[16] = {false};
+  for (int v = 0; v < TP.waves; ++v) {
+    QuadOutT<T> qo;
+    memset(&qo, 0, sizeof(qo));
+    qo.ld = ldc;
+    bool wrote[16] = {false};
+    auto flush = [&]() -> cudaError_t {
+      if (qo.entries == 0) return cudaSuccess;
+      cudaError_t e = launch(qo);
+      memset(&qo, 0, sizeof(qo));
+      qo.ld = ldc;
+      return e;
+    };
+    for (int p = 0; p < TP.products; ++p) {
+      if (TP.wave_of[p] != v) continue;
+      const int i = qo.entries++;
+      qo.leaf[i] = (int16_t)p;
+      for (int d = 0; d < TP.ndst[p]; ++d) {
+        const int b = TP.block[p][d];
+        qo.dst[i][d] = C + (int64_t)(b / side) * S.mL * ldc + (int64_t)(b % side) * S.nL;
+        qo.sign[i][d] = (int8_t)TP.sign[p][d];
+        qo.add[i][d] = written[b] ? 1 : 0;
+        wrote[b] = true;
+      }
+      if (qo.entries == kQuadEntries) MMSR_CUDA_TRY(flush());
+    }
+    MMSR_CUDA_TRY(flush());
+    for (int b = 0; b < 16; ++b) written[b] = written[b] || wrote[b];
+  }
+  return cudaSuccess;
+}
+
+int run_tar_view(int L, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                 const void* B, int64_t ldb, void* C, int64_t ldc, uint8_t* w, cudaStream_t st) {
+  const StrassenLayout S = strassen_layout(L, sr, m, n, k);
+  const TarPlan TP = tar_plan(L, variant);
+  if (!TP.fits) return MM_ERR_UNSUPPORTED;
+  cudaError_t e;
+  if (sr == MM_SR_PLUS_TIMES_F32) {
+    auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + S.off_ahi);
+    auto* alo = reinterpret_cast<__nv_bfloat16*>(w + S.off_alo);
+    auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + S.off_bhi);
+    auto* blo = reinterpret_cast<__nv_bfloat16*>(w + S.off_blo);
+    {
+      TraceScope tr(kTrStrassenCombine, st);
+      e = expand_f32(L, variant, 0, static_cast<const float*>(A), m, k, lda, w, S, ahi, alo, st);
+      if (e == cudaSuccess) e = expand_f32(L, variant, 1, static_cast<const float*>(B), k, n, ldb, w, S, bhi, blo, st);
+    }
+    if (e != cudaSuccess) return report_cuda(e, "TAR-Strassen operand pass");
+    e = tar_waves_run<float>(TP, S, static_cast<float*>(C), ldc, [&](const QuadOut& qo) {
+      return launch_bf16x3_batched(ahi, alo, bhi, blo, nullptr, S.mL, S.nL, S.KpL, qo.entries, st, &qo,
+                                   (int)S.leaves);
+    });
+    return e == cudaSuccess ? MM_OK : report_cuda(e, "TAR-Strassen leaf wave");
+  }
+  double* la = reinterpret_cast<double*>(w + S.off_ahi);
+  double* lb = reinterpret_cast<double*>(w + S.off_bhi);
+  {
+    TraceScope tr(kTrStrassenCombine, st);
+    e = expand_f64(L, variant, 0, static_cast<const double*>(A), m, k, lda, w, S, la, st);
+    if (e == cudaSuccess) e = expand_f64(L, variant, 1, static_cast<const double*>(B), k, n, ldb, w, S, lb, st);
+  }
+  if (e != cudaSuccess) return report_cuda(e, "TAR-Strassen operand pass");
+  const int slices = f64acc_slices_for_levels(L);
+  int rc = f64acc_prepare_batched(la, lb, S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, st);
+  if (rc != MM_OK) return rc;
+  e = tar_waves_run<double>(TP, S, static_cast<double*>(C), ldc, [&](const QuadOut64& qo) {
+    return f64acc_gemm_quad(S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, qo, st) == MM_OK
+               ? cudaSuccess
+               : cudaErrorLaunchFailure;
+  });
+  return e == cudaSuccess ? MM_OK : report_cuda(e, "TAR-Strassen leaf wave");
+}
+
+bool tar_semiring(int sr) { return sr == MM_SR_PLUS_TIMES_F32 || sr == MM_SR_PLUS_TIMES_F64ACC; }
+
+int plan_strassen_tar(int L, int sr, int64_t m, int64_t n, int64_t k, mm_plan_t* p) {
+  if (!tar_semiring(sr)) return MM_ERR_UNSUPPORTED;
+  fill_plan(L, sr, (int64_t)tar_workspace(L, sr, m, n, k), p);
   return MM_OK;
 }
 
-int plan_strassen_tar(int sr, int64_t m, int64_t n, int64_t k, mm_plan_t* p) {
-  if (sr != MM_SR_PLUS_TIMES_F32) return MM_ERR_UNSUPPORTED;
-  fill_plan(1, sr, (int64_t)tar_workspace(m, n, k), p);
-  return MM_OK;
+int run_strassen_tar(int L, int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                     void* C, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!tar_semiring(sr)) return MM_ERR_UNSUPPORTED;
+  if (!tar_plan(L, variant).fits) return MM_ERR_UNSUPPORTED;
+  if (tar_workspace(L, sr, m, n, k) > ws_bytes) return MM_ERR_WORKSPACE;
+  return run_tar_view(L, variant, sr, m, n, k, A, k, B, n, C, n, static_cast<uint8_t*>(ws), st);
 }
 
-int run_strassen_tar(int variant, int sr, int64_t m, int64_t n, int64_t k, const void* A, const void* B, void* C,
-                     void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (sr != MM_SR_PLUS_TIMES_F32) return MM_ERR_UNSUPPORTED;
-  if (tar_workspace(m, n, k) > ws_bytes) return MM_ERR_WORKSPACE;
-  return run_tar_view(variant, m, n, k, static_cast<const float*>(A), k, static_cast<const float*>(B), n,
-                      static_cast<float*>(C), n, static_cast<uint8_t*>(ws), st);
-}
-
-int strassen_tar_waves(int variant, int* wave_of_product) {
-  const TarWaves W = tar_waves(variant);
-  for (int v = 0; v < W.count; ++v)
-    for (int i = 0; i < W.size[v]; ++i) wave_of_product[W.member[v][i]] = v;
-  return W.count;
+int strassen_tar_waves(int L, int variant, int* wave_of_product) {
+  const TarPlan T = tar_plan(L, variant);
+  for (int p = 0; p < T.products; ++p) wave_of_product[p] = T.wave_of[p];
+  return T.fits ? T.waves : MM_ERR_UNSUPPORTED;
 }
 
 // STAR-Strassen-1 (Theorem star-strassen-1): the top `classic` levels are

@@ -187,11 +187,12 @@ struct Bf16x3Cfg {
   static constexpr int COLS_PER_WARP = BN / 2;   // two drain warps share each lane quarter
 };
 
-// QUAD epilogue: instead of writing its tile to C, batch entry b adds
-// sign[b][d] x tile into up to four destinations dst[b][d] (row pitch ld),
-// overwriting where add[b][d] is 0 -- the leaf epilogue of a Strassen level
-// whose products go straight into the quadrants of C (no product
-// temporaries).  Entries of one launch must write disjoint destinations.
+// QUAD epilogue: instead of writing its tile to C, batch entry b multiplies
+// the stacked operands of leaf[b] and adds sign[b][d] x tile into up to four
+// destinations dst[b][d] (row pitch ld), overwriting where add[b][d] is 0 --
+// the leaf epilogue of Strassen levels whose products go straight into the
+// blocks of C (no product temporaries).  Entries of one launch must write
+// disjoint destinations.
 template <int BN, int STAGES, int CHUNK, bool QUAD>
 __global__ void __launch_bounds__(kTcThreads, 1)
     bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAhi, const __grid_constant__ CUtensorMap tAlo,
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // whose operands sit at row offset batch * {a,b}_batch_rows of the stacks
   const int z = blockIdx.z % slices;
   const int batch = blockIdx.z / slices;
-  const int ya = (int)(batch * a_batch_rows + i0), yb = (int)(batch * b_batch_rows + j0);
+  const int64_t leaf = QUAD ? (int64_t)quad.leaf[batch] : (int64_t)batch;  // stacked operands of this entry
+  const int ya = (int)(leaf * a_batch_rows + i0), yb = (int)(leaf * b_batch_rows + j0);
   const int kb_begin = z * kb_per_slice;
   const int kb_end = min(kb_total, kb_begin + kb_per_slice);
   const int nkb = kb_end > kb_begin ? kb_end - kb_begin : 0;
@@ -837,12 +839,13 @@ cudaError_t launch_split_bf16(const float* A, const float* B, int64_t m, int64_t
 cudaError_t launch_bf16x3_batched(const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
                                   const __nv_bfloat16* bhi, const __nv_bfloat16* blo, float* P,
                                   int64_t m, int64_t n, int64_t Kp, int batches, cudaStream_t st,
-                                  const QuadOut* quad) {
+                                  const QuadOut* quad, int map_batches) {
+  const int64_t mb = map_batches > 0 ? map_batches : batches;
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_hi, ahi, batches * m, Kp, Kp, BM, true, kTcBK));
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_lo, alo, batches * m, Kp, Kp, BM, true, kTcBK));
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_hi, bhi, batches * n, Kp, Kp, kTcBN, true, kTcBK));
-  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, batches * n, Kp, Kp, kTcBN, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_hi, ahi, mb * m, Kp, Kp, BM, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&ta_lo, alo, mb * m, Kp, Kp, BM, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_hi, bhi, mb * n, Kp, Kp, kTcBN, true, kTcBK));
+  MMSR_CUDA_TRY(make_tmap_2d_16bit(&tb_lo, blo, mb * n, Kp, Kp, kTcBN, true, kTcBK));
   const int kb_total = (int)(Kp / kTcBK);
   return launch_gemm<kTcBN, kTcStages, kTcChunk>(ta_hi, ta_lo, tb_hi, tb_lo, P, nullptr, m, n,
                                                  kb_total, kb_total, 1, st, batches, m, n, m * n, quad);

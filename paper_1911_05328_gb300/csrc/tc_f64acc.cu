@@ -299,18 +299,32 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
 // 2^-s as an exact double (s < 1023), folded at compile time.
 __host__ __device__ constexpr double exp2_neg(int s) { return s == 0 ? 1.0 : 0.5 * exp2_neg(s - 1); }
 
+// x 2^s with the result ldexp(x, s) gives, by one multiplication with the
+// power of two built from its exponent field wherever 2^s is a normal double
+// (this GPU's FP64 pipe retires about two operations per clock per SM, so
+// the epilogue counts them).
+__device__ __forceinline__ double scale_pow2(double x, int s) {
+  if (s >= -1022 && s <= 1023) return x * __longlong_as_double((long long)(s + 1023) << 52);
+  return ldexp(x, s);
+}
+
 __device__ __forceinline__ int exact_int(uint32_t fbits) {
   // fbits holds an integer-valued float of magnitude < 2^24: the conversion
   // is exact in any rounding mode.
   return __float2int_rn(__uint_as_float(fbits));
 }
 
-template <int SL>
+// QUAD: the TAR-Strassen epilogue -- batch entry b multiplies the stacked
+// operands of leaf quad.leaf[b] and adds quad.sign[b][d] x its tile into up
+// to four blocks quad.dst[b][d] of C (row pitch quad.ld), overwriting where
+// quad.add[b][d] is 0.  Entries of one launch write disjoint blocks.
+template <int SL, bool QUAD>
 __global__ void __launch_bounds__(kThreads, 1)
     f64acc_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
                        const int* __restrict__ E, const int* __restrict__ F, double* __restrict__ C,
                        double* __restrict__ W, int64_t m, int64_t n, int64_t a_slice_rows,
-                       int64_t b_slice_rows, int kb_total, int kb_per_slice, int kslices) {
+                       int64_t b_slice_rows, int kb_total, int kb_per_slice, int kslices,
+                       const __grid_constant__ QuadOut64 quad) {
   using Cfg = FaCfg<SL>;
   constexpr int kSlices = SL, kGroups = SL, STAGES = Cfg::STAGES, CHUNK = Cfg::CHUNK;
   constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES;
@@ -348,7 +362,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   // of every A slice (and of E), rows [b*n, (b+1)*n) of every B^T slice
   const int z = blockIdx.z % kslices;
   const int batch = blockIdx.z / kslices;
-  const int64_t ra = (int64_t)batch * m, rb = (int64_t)batch * n;
+  const int64_t leaf = QUAD ? (int64_t)quad.leaf[batch] : (int64_t)batch;
+  const int64_t ra = leaf * m, rb = leaf * n;
   const int kb_begin = z * kb_per_slice;
   const int kb_end = min(kb_total, kb_begin + kb_per_slice);
   const int nkb = kb_end > kb_begin ? kb_end - kb_begin : 0;
@@ -504,18 +519,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) tc::mbar_arrive(&acc_empty[g]);
       }
     }
-    double* out = (z == 0) ? C + ra * n : W + (int64_t)(z - 1) * m * n;
     const int64_t row = i0 + q * 32 + lane;
     if (row < m) {
+      // C_ij = 2^(E_i + F_j) (hi 2^-kHiShift + lo 2^-kLoShift), rounded once
+      // (the fma; hi and lo convert exactly, the power-of-two scalings are
+      // exact away from the subnormal range)
+      constexpr int kHi = Scheme<SL>::kHiShift;
+      constexpr double kLoW = exp2_neg(Scheme<SL>::kLoShift - kHi);
       const int Ei = E[ra + row];
+      double v[32];
 #pragma unroll
       for (int e = 0; e < 32; ++e) {
         const int64_t col = j0 + h * 32 + e;
-        if (col >= n) break;
-        double v = ok ? ((double)hi[e] * exp2_neg(Scheme<SL>::kHiShift) +
-                         (double)lo[e] * exp2_neg(Scheme<SL>::kLoShift))
-                      : 0.0;
-        out[row * n + col] = ldexp(v, Ei + F[rb + col]);
+        v[e] = (ok && col < n) ? scale_pow2(fma((double)lo[e], kLoW, (double)hi[e]), Ei + F[rb + col] - kHi) : 0.0;
+      }
+      if constexpr (QUAD) {
+#pragma unroll 1
+        for (int d = 0; d < 4; ++d) {
+          double* base = quad.dst[batch][d];
+          if (base == nullptr) continue;
+          const bool neg = quad.sign[batch][d] < 0;
+          const bool add = quad.add[batch][d] != 0;
+          double* dst = base + row * quad.ld;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int64_t col = j0 + h * 32 + e;
+            if (col >= n) break;
+            const double x = neg ? -v[e] : v[e];
+            dst[col] = add ? dst[col] + x : x;
+          }
+        }
+      } else {
+        double* out = (z == 0) ? C + ra * n : W + (int64_t)(z - 1) * m * n;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int64_t col = j0 + h * 32 + e;
+          if (col >= n) break;
+          out[row * n + col] = v[e];
+        }
       }
     }
   }
@@ -565,50 +606,74 @@ F64AccLayout layout(int64_t m, int64_t n, int64_t k, int slices, int64_t batches
 }
 
 // Digit slices and the tensor-core product for one scheme.
+// Exponents and digit slices of `batches` stacked products (A: batches x m
+// rows, B: batches matrices of k x n).
 template <int SL>
-int f64acc_core_t(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
-                  uint8_t* w, const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
+int f64acc_prepare_t(int64_t m, int64_t n, int64_t k, const double* A, const double* B, uint8_t* w,
+                     const F64AccLayout& L, int batches, cudaStream_t st) {
   auto* SA = reinterpret_cast<__nv_bfloat16*>(w);
   auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
   int* E = reinterpret_cast<int*>(w + L.off_e);
   int* F = reinterpret_cast<int*>(w + L.off_f);
   const int64_t rows_a = (int64_t)batches * m;
+  TraceScope tr(kTrSplitF64Slices, st);
+  row_exponent_kernel<<<(unsigned)((rows_a + 7) / 8), 256, 0, st>>>(A, rows_a, k, E);
+  auto* Fmax = reinterpret_cast<unsigned long long*>(w + L.off_fmax);
+  MMSR_TRY_STATUS(cudaMemsetAsync(Fmax, 0, (size_t)batches * n * 8, st));
+  col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256, 0,
+                   st>>>(B, k, n, Fmax);
+  col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
   {
-    TraceScope tr(kTrSplitF64Slices, st);
-    row_exponent_kernel<<<(unsigned)((rows_a + 7) / 8), 256, 0, st>>>(A, rows_a, k, E);
-    auto* Fmax = reinterpret_cast<unsigned long long*>(w + L.off_fmax);
-    MMSR_TRY_STATUS(cudaMemsetAsync(Fmax, 0, (size_t)batches * n * 8, st));
-    col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256, 0,
-                     st>>>(B, k, n, Fmax);
-    col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
-    {
-      const int64_t gx = std::max<int64_t>(1, (L.Kp + 1023) / 1024);
-      const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(rows_a, std::max<int64_t>(1, 4096 / gx)));
-      digits_rows_kernel<SL><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA,
-                                                                              aligned16(A) && k % 2 == 0);
-    }
-    // n-tiles per block: enough blocks to fill the GPU a few times over, each
-    // walking several tiles
-    const int64_t tiles_n = (n + 31) / 32;
-    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 8192 / (L.Kp / 32 * batches))));
-    dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>(gy, kMaxGridY), (unsigned)batches);
-    digits_cols_kernel<SL><<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
-    MMSR_TRY_STATUS(cudaGetLastError());
+    const int64_t gx = std::max<int64_t>(1, (L.Kp + 1023) / 1024);
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(rows_a, std::max<int64_t>(1, 4096 / gx)));
+    digits_rows_kernel<SL><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(A, rows_a, k, L.Kp, E, SA,
+                                                                            aligned16(A) && k % 2 == 0);
   }
+  // n-tiles per block: enough blocks to fill the GPU a few times over, each
+  // walking several tiles
+  const int64_t tiles_n = (n + 31) / 32;
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 8192 / (L.Kp / 32 * batches))));
+  dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>(gy, kMaxGridY), (unsigned)batches);
+  digits_cols_kernel<SL><<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
+  MMSR_TRY_STATUS(cudaGetLastError());
+  return MM_OK;
+}
+
+// The tensor-core products over prepared slices: `entries` products (k-split
+// s), each writing C (ordinary) or adding into the blocks `quad` names.
+template <int SL, bool QUAD>
+int f64acc_gemm_t(int64_t m, int64_t n, uint8_t* w, const F64AccLayout& L, int batches, int entries, int s,
+                  double* C, double* part, const QuadOut64& quad, cudaStream_t st) {
+  auto* SA = reinterpret_cast<__nv_bfloat16*>(w);
+  auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
+  const int* E = reinterpret_cast<const int*>(w + L.off_e);
+  const int* F = reinterpret_cast<const int*>(w + L.off_f);
+  const int64_t rows_a = (int64_t)batches * m;
   CUtensorMap tA, tB;
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&tA, SA, SL * rows_a, L.Kp, L.Kp, BM, true, BK));
   MMSR_TRY_STATUS(make_tmap_2d_16bit(&tB, SB, SL * (int64_t)batches * n, L.Kp, L.Kp, BN, true, BK));
   static std::atomic<uint64_t> configured{0};
-  MMSR_TRY_STATUS(smem_limit_once(f64acc_gemm_kernel<SL>, FaCfg<SL>::SMEM, configured));
+  MMSR_TRY_STATUS(smem_limit_once(f64acc_gemm_kernel<SL, QUAD>, FaCfg<SL>::SMEM, configured));
   const int kb_total = (int)(L.Kp / BK);
   const int kbs = (kb_total + s - 1) / s;
-  {
-    TraceScope tr(kTrTcF64Acc, st);
-    dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)(s * batches));
-    f64acc_gemm_kernel<SL><<<grid, kThreads, FaCfg<SL>::SMEM, st>>>(tA, tB, E, F, C, part, m, n, rows_a,
-                                                                   (int64_t)batches * n, kb_total, kbs, s);
-    MMSR_TRY_STATUS(cudaGetLastError());
-  }
+  TraceScope tr(kTrTcF64Acc, st);
+  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)(s * entries));
+  f64acc_gemm_kernel<SL, QUAD><<<grid, kThreads, FaCfg<SL>::SMEM, st>>>(tA, tB, E, F, C, part, m, n, rows_a,
+                                                                       (int64_t)batches * n, kb_total, kbs, s,
+                                                                       quad);
+  MMSR_TRY_STATUS(cudaGetLastError());
+  return MM_OK;
+}
+
+template <int SL>
+int f64acc_core_t(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
+                  uint8_t* w, const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
+  int rc = f64acc_prepare_t<SL>(m, n, k, A, B, w, L, batches, st);
+  if (rc != MM_OK) return rc;
+  QuadOut64 none;
+  memset(&none, 0, sizeof(none));
+  rc = f64acc_gemm_t<SL, false>(m, n, w, L, batches, batches, s, C, part, none, st);
+  if (rc != MM_OK) return rc;
   if (s > 1) MMSR_TRY_STATUS(launch_sum_reduce_f64(m * n, C, part, s - 1, st));
   return MM_OK;
 }
@@ -668,6 +733,21 @@ int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, i
                        int batches, int slices, void* ws, cudaStream_t st) {
   const F64AccLayout L = layout(m, n, k, slices, batches);
   return f64acc_core(m, n, k, A, B, C, static_cast<uint8_t*>(ws), L, batches, 1, nullptr, st);
+}
+
+int f64acc_prepare_batched(const double* A, const double* B, int64_t m, int64_t n, int64_t k, int batches,
+                           int slices, void* ws, cudaStream_t st) {
+  const F64AccLayout L = layout(m, n, k, slices, batches);
+  return slices == 6 ? f64acc_prepare_t<6>(m, n, k, A, B, static_cast<uint8_t*>(ws), L, batches, st)
+                     : f64acc_prepare_t<7>(m, n, k, A, B, static_cast<uint8_t*>(ws), L, batches, st);
+}
+
+int f64acc_gemm_quad(int64_t m, int64_t n, int64_t k, int batches, int slices, void* ws, const QuadOut64& quad,
+                     cudaStream_t st) {
+  const F64AccLayout L = layout(m, n, k, slices, batches);
+  auto* w = static_cast<uint8_t*>(ws);
+  return slices == 6 ? f64acc_gemm_t<6, true>(m, n, w, L, batches, quad.entries, 1, nullptr, nullptr, quad, st)
+                     : f64acc_gemm_t<7, true>(m, n, w, L, batches, quad.entries, 1, nullptr, nullptr, quad, st);
 }
 
 int arm_f64acc_skip_signal(int on) {

@@ -101,11 +101,11 @@ def load(path: str = LIB_PATH):
             lib.mm_star_strassen.restype = ctypes.c_int
             lib.mm_star_strassen_query.argtypes = [i32, i32, i32, i64, i64, i64, sz, ctypes.POINTER(mm_plan_t)]
             lib.mm_star_strassen_query.restype = ctypes.c_int
-            lib.mm_strassen_tar.argtypes = [i32, i32, i64, i64, i64, vp, vp, vp, vp, sz, vp]
+            lib.mm_strassen_tar.argtypes = [i32, i32, i32, i64, i64, i64, vp, vp, vp, vp, sz, vp]
             lib.mm_strassen_tar.restype = ctypes.c_int
-            lib.mm_strassen_tar_query.argtypes = [i32, i64, i64, i64, ctypes.POINTER(mm_plan_t)]
+            lib.mm_strassen_tar_query.argtypes = [i32, i32, i64, i64, i64, ctypes.POINTER(mm_plan_t)]
             lib.mm_strassen_tar_query.restype = ctypes.c_int
-            lib.mm_strassen_tar_waves.argtypes = [i32, ctypes.POINTER(ctypes.c_int)]
+            lib.mm_strassen_tar_waves.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_int)]
             lib.mm_strassen_tar_waves.restype = ctypes.c_int
             lib.mm_closure.argtypes = [i32, i64, vp, vp, vp, sz, i32, ctypes.POINTER(ctypes.c_int), vp]
             lib.mm_closure.restype = ctypes.c_int
@@ -186,26 +186,27 @@ def mm_closure_query(semiring, n, workspace_bytes=0, check=True) -> mm_plan_t:
     return plan
 
 
-def mm_strassen_tar(variant, semiring, m, n, k, A, B, C, workspace=None, workspace_bytes=0, stream=None,
+def mm_strassen_tar(levels, variant, semiring, m, n, k, A, B, C, workspace=None, workspace_bytes=0, stream=None,
                     check=True) -> int:
-    rc = load().mm_strassen_tar(int(variant), int(semiring), int(m), int(n), int(k), _addr(A), _addr(B),
-                                _addr(C), _addr(workspace), int(workspace_bytes), _stream(stream))
+    rc = load().mm_strassen_tar(int(levels), int(variant), int(semiring), int(m), int(n), int(k), _addr(A),
+                                _addr(B), _addr(C), _addr(workspace), int(workspace_bytes), _stream(stream))
     return _check(rc, "mm_strassen_tar", check)
 
 
-def mm_strassen_tar_query(semiring, m, n, k, check=True) -> mm_plan_t:
+def mm_strassen_tar_query(levels, semiring, m, n, k, check=True) -> mm_plan_t:
     plan = mm_plan_t()
-    rc = load().mm_strassen_tar_query(int(semiring), int(m), int(n), int(k), ctypes.byref(plan))
+    rc = load().mm_strassen_tar_query(int(levels), int(semiring), int(m), int(n), int(k), ctypes.byref(plan))
     _check(rc, "mm_strassen_tar_query", check)
     plan.status = rc
     return plan
 
 
-def mm_strassen_tar_waves(variant):
-    """(number of waves, [wave of product r for r = 0..6])."""
-    w = (ctypes.c_int * 7)()
-    rc = load().mm_strassen_tar_waves(int(variant), w)
-    if rc < 0:
+def mm_strassen_tar_waves(levels, variant):
+    """(number of waves or MM_ERR_UNSUPPORTED, [wave of leaf product p for
+    p = 0 .. 7^levels - 1])."""
+    w = (ctypes.c_int * (7 ** int(levels)))()
+    rc = load().mm_strassen_tar_waves(int(levels), int(variant), w)
+    if rc < 0 and rc != MM_ERR_UNSUPPORTED:
         raise MMError(rc, "mm_strassen_tar_waves")
     return rc, list(w)
 

@@ -109,11 +109,11 @@ def main():
         dB = torch.from_numpy(B.astype("float32")).cuda()
         dC = torch.empty((n, n), dtype=torch.float32, device="cuda")
         sr = mmsr.MM_SR_PLUS_TIMES_F32
-        p = mmsr.mm_strassen_tar_query(sr, n, n, n) if tar else mmsr.mm_plan_query(sr, L, n, n, n, 0)
+        p = mmsr.mm_strassen_tar_query(1, sr, n, n, n) if tar else mmsr.mm_plan_query(sr, L, n, n, n, 0)
         ws = torch.empty((int(p.workspace_min),), dtype=torch.uint8, device="cuda")
         for _ in range(a.reps):
             if tar:
-                mmsr.mm_strassen_tar(mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min))
+                mmsr.mm_strassen_tar(1, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min))
             else:
                 mmsr.mm_strassen(L, mmsr.MM_STRASSEN_WINOGRAD, sr, n, n, n, dA, dB, dC, ws, int(p.workspace_min))
         torch.cuda.synchronize()

@@ -167,11 +167,11 @@ def test_star_strassen_argument_checks_and_workspace(lib):
 def test_tar_strassen_waves_follow_the_papers_order(lib):
     # Section 5's zero-temporary Strassen writes P1; then P2 and P5 together;
     # then P3 and P4; then P6 and P7 (products numbered P1..P7 as printed).
-    count, wave = mmsr.mm_strassen_tar_waves(mmsr.MM_STRASSEN_PAPER)
+    count, wave = mmsr.mm_strassen_tar_waves(1, mmsr.MM_STRASSEN_PAPER)
     assert count == 4
     assert wave == [0, 1, 2, 2, 1, 3, 3]
     for variant in (mmsr.MM_STRASSEN_PAPER, mmsr.MM_STRASSEN_WINOGRAD):
-        count, wave = mmsr.mm_strassen_tar_waves(variant)
+        count, wave = mmsr.mm_strassen_tar_waves(1, variant)
         _, _, gamma = mmsr.mm_strassen_tables(variant)
         for w in range(count):
             members = [r for r in range(7) if wave[r] == w]
@@ -180,22 +180,56 @@ def test_tar_strassen_waves_follow_the_papers_order(lib):
             assert len(touched) == len(set(touched)), (variant, w, members)
 
 
+def test_tar_strassen_two_level_waves(lib):
+    """Two levels: leaf product p = 7 r1 + r2 adds gamma[q1, r1] gamma[q2, r2]
+    times itself into block (q1, q2); products of one wave touch disjoint
+    blocks and every block is reached.  Two Winograd levels put P1 x P1 into
+    all sixteen blocks, past the epilogue's four: refused."""
+    _, _, gamma = mmsr.mm_strassen_tables(mmsr.MM_STRASSEN_PAPER)
+    count, wave = mmsr.mm_strassen_tar_waves(2, mmsr.MM_STRASSEN_PAPER)
+    assert count > 0 and len(wave) == 49
+
+    def blocks(p):
+        r1, r2 = divmod(p, 7)
+        return [(q1, q2) for q1 in range(4) for q2 in range(4) if gamma[q1, r1] * gamma[q2, r2] != 0]
+
+    assert max(len(blocks(p)) for p in range(49)) <= 4
+    for w in range(count):
+        touched = [b for p in range(49) if wave[p] == w for b in blocks(p)]
+        assert touched and len(touched) == len(set(touched)), w
+    assert len({b for p in range(49) for b in blocks(p)}) == 16
+    rc, _ = mmsr.mm_strassen_tar_waves(2, mmsr.MM_STRASSEN_WINOGRAD)
+    assert rc == mmsr.MM_ERR_UNSUPPORTED
+
+
 def test_tar_strassen_argument_checks_and_workspace(lib):
-    W = mmsr.MM_STRASSEN_WINOGRAD
-    for sr in (mmsr.MM_SR_PLUS_TIMES_F64, mmsr.MM_SR_PLUS_TIMES_F64ACC, mmsr.MM_SR_MIN_PLUS_I32):
-        assert mmsr.mm_strassen_tar(W, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_UNSUPPORTED
+    W, P = mmsr.MM_STRASSEN_WINOGRAD, mmsr.MM_STRASSEN_PAPER
+    for sr in (mmsr.MM_SR_PLUS_TIMES_F64, mmsr.MM_SR_MIN_PLUS_I32):
+        assert mmsr.mm_strassen_tar(1, W, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == \
+            mmsr.MM_ERR_UNSUPPORTED
     sr = mmsr.MM_SR_PLUS_TIMES_F32
-    assert mmsr.mm_strassen_tar(W, sr, 9, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_SHAPE
-    assert mmsr.mm_strassen_tar(5, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    assert mmsr.mm_strassen_tar(1, W, sr, 9, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_SHAPE
+    assert mmsr.mm_strassen_tar(2, P, sr, 6, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_SHAPE
+    assert mmsr.mm_strassen_tar(1, 5, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
+    for L in (0, 3):
+        assert mmsr.mm_strassen_tar(L, P, sr, 8, 8, 8, FAKE, FAKE, FAKE, stream=0, check=False) == mmsr.MM_ERR_ARG
     n = 4096
-    tar = mmsr.mm_strassen_tar_query(sr, n, n, n)
-    full = mmsr.mm_plan_query(sr, 1, n, n, n)
-    # exactly the product stack of one level is saved: 7 (n/2)^2 FP32 values
-    assert full.workspace_min - tar.workspace_min == 7 * (n // 2) ** 2 * 4
-    rc = mmsr.mm_strassen_tar(W, sr, 64, 64, 64, FAKE, FAKE, FAKE, FAKE,
-                              int(mmsr.mm_strassen_tar_query(sr, 64, 64, 64).workspace_min) - 1024, stream=0,
+    for L in (1, 2):
+        tar = mmsr.mm_strassen_tar_query(L, sr, n, n, n)
+        full = mmsr.mm_plan_query(sr, L, n, n, n)
+        # exactly the product stack is saved: 7^L (n/2^L)^2 FP32 values
+        assert full.workspace_min - tar.workspace_min == 7 ** L * (n >> L) ** 2 * 4
+    # FP64-accuracy mode: mm_strassen overlays its products on the FP64
+    # operand stack already, so TAR needs the same workspace
+    fa = mmsr.MM_SR_PLUS_TIMES_F64ACC
+    assert mmsr.mm_strassen_tar_query(1, fa, n, n, n).workspace_min == mmsr.mm_plan_query(fa, 1, n, n, n).workspace_min
+    rc = mmsr.mm_strassen_tar(1, W, sr, 64, 64, 64, FAKE, FAKE, FAKE, FAKE,
+                              int(mmsr.mm_strassen_tar_query(1, sr, 64, 64, 64).workspace_min) - 1024, stream=0,
                               check=False)
     assert rc == mmsr.MM_ERR_WORKSPACE
+    big = 1 << 34
+    assert mmsr.mm_strassen_tar(2, W, sr, 64, 64, 64, FAKE, FAKE, FAKE, FAKE, big, stream=0, check=False) == \
+        mmsr.MM_ERR_UNSUPPORTED
 
 
 def test_option_argument_checks(lib):
