@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "GOp/s & % of dtype peak at stated error vs plain FP64 path; peak workspace bytes"
 N = 16384
 SEED = 3
-HEADLINE_LEVELS = 1
+HEADLINE_LEVELS = 2
 TOL_F64 = 1e-12
 SAMPLE_ROWS = 512
 

@@ -153,7 +153,7 @@ typedef enum {
  * products P_r of each level) are carved from `workspace`; the plan's
  * workspace_min is O(n^2) and is reported by mm_plan_query.
  * levels = MM_LEVELS_AUTO lets the library pick the depth: the fastest
- * measured depth of the semiring (2 for FP32 mode, 1 for FP64-accuracy
+ * measured depth of the semiring (2 for FP32 mode, 2 for FP64-accuracy
  * mode, 4 for plain FP64), lowered until every leaf dimension stays at
  * least 1024 (512 for plain FP64), the shape divides by 2^levels and the
  * plan fits workspace_bytes (0 levels: mm_semiring).  mm_plan_query with

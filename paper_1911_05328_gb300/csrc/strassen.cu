@@ -959,13 +959,13 @@ int plan_strassen(int levels, int sr, int64_t m, int64_t n, int64_t k, size_t bu
 }
 
 // Depth for MM_LEVELS_AUTO: the preferred depth of the semiring (measured at
-// n >= 8192: FP32 mode is fastest at two levels, FP64-accuracy mode at one;
+// n >= 8192: FP32 mode and FP64-accuracy mode are fastest at two levels;
 // the FP64 DFMA leaves are bound by the FP64 pipe, so every level saves an
 // eighth of the time), lowered until every leaf dimension stays at least
 // 1024 (512 for FP64), the shape divides by 2^L and the workspace fits the
 // budget.  0 means the classic product.
 int choose_strassen_levels(int sr, int64_t m, int64_t n, int64_t k, size_t budget) {
-  int L = sr == MM_SR_PLUS_TIMES_F32 ? 2 : (sr == MM_SR_PLUS_TIMES_F64ACC ? 1 : 4);
+  int L = sr == MM_SR_PLUS_TIMES_F32 ? 2 : (sr == MM_SR_PLUS_TIMES_F64ACC ? 2 : 4);
   const int64_t floor_dim = sr == MM_SR_PLUS_TIMES_F64 ? 512 : 1024;
   for (; L > 0; --L) {
     const int64_t mask = ((int64_t)1 << L) - 1;

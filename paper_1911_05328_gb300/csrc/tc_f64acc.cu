@@ -533,6 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t col = j0 + h * 32 + e;
         v[e] = (ok && col < n) ? scale_pow2(fma((double)lo[e], kLoW, (double)hi[e]), Ei + F[rb + col] - kHi) : 0.0;
       }
+      const int64_t c0 = j0 + h * 32;
       if constexpr (QUAD) {
 #pragma unroll 1
         for (int d = 0; d < 4; ++d) {
@@ -540,22 +541,43 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (base == nullptr) continue;
           const bool neg = quad.sign[batch][d] < 0;
           const bool add = quad.add[batch][d] != 0;
-          double* dst = base + row * quad.ld;
+          double* dst = base + row * quad.ld + c0;
+          if (c0 + 32 <= n && aligned16(dst)) {
+            // eight 16-byte reads of the old values in flight, then the sums
+            // and their stores
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int64_t col = j0 + h * 32 + e;
-            if (col >= n) break;
-            const double x = neg ? -v[e] : v[e];
-            dst[col] = add ? dst[col] + x : x;
+            for (int u0 = 0; u0 < 16; u0 += 8) {
+              double2 o[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                o[u] = add ? reinterpret_cast<const double2*>(dst)[u0 + u] : make_double2(0.0, 0.0);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int e = 2 * (u0 + u);
+                const double x0 = neg ? -v[e] : v[e], x1 = neg ? -v[e + 1] : v[e + 1];
+                reinterpret_cast<double2*>(dst)[u0 + u] =
+                    add ? make_double2(o[u].x + x0, o[u].y + x1) : make_double2(x0, x1);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              if (c0 + e < n) {
+                const double x = neg ? -v[e] : v[e];
+                dst[e] = add ? dst[e] + x : x;
+              }
+            }
           }
         }
       } else {
-        double* out = (z == 0) ? C + ra * n : W + (int64_t)(z - 1) * m * n;
+        double* out = ((z == 0) ? C + ra * n : W + (int64_t)(z - 1) * m * n) + row * n + c0;
+        if (c0 + 32 <= n && aligned16(out)) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          const int64_t col = j0 + h * 32 + e;
-          if (col >= n) break;
-          out[row * n + col] = v[e];
+          for (int u = 0; u < 16; ++u) reinterpret_cast<double2*>(out)[u] = make_double2(v[2 * u], v[2 * u + 1]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (c0 + e < n) out[e] = v[e];
         }
       }
     }

@@ -307,7 +307,8 @@ def test_strassen_auto_depth_under_budget(lib):
     n = 16384
     big = 1 << 40
     assert mmsr.mm_plan_query(f32, A, n, n, n, big).levels == 2
-    assert mmsr.mm_plan_query(acc, A, n, n, n, big).levels == 1
+    assert mmsr.mm_plan_query(acc, A, n, n, n, big).levels == 2
+    assert mmsr.mm_plan_query(acc, A, 2048, 2048, 2048, big).levels == 1
     assert mmsr.mm_plan_query(f64, A, 8192, 8192, 8192, big).levels == 4
     # budget between the one- and two-level plans: one level; below both: classic
     w1 = int(mmsr.mm_plan_query(f32, 1, n, n, n, 0).workspace_min)
