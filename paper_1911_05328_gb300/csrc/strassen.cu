@@ -22,6 +22,8 @@
 #include <cuda_bf16.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 #include "strassen_tables.cuh"
@@ -992,8 +994,8 @@ int run_strassen(int levels, int variant, int sr, int64_t m, int64_t n, int64_t 
 // with coefficient gamma(q1, r1) gamma(q2, r2).  Products run in waves in
 // which no two touch the same block, so the read-modify-writes of one launch
 // never collide; a block's first writer overwrites it.  The waves are a
-// greedy colouring in product order (one level of the paper's formulas:
-// exactly P1; P2 || P5; P3 || P4; P6 || P7).  A product may reach at most four
+// greedy colouring (one level of the paper's formulas: exactly P1;
+// P2 || P5; P3 || P4; P6 || P7).  A product may reach at most four
 // blocks (the epilogue's limit): every product of the paper's formulas at
 // one or two levels and of Winograd's at one level; two Winograd levels
 // (P1 x P1 reaches all sixteen blocks) are refused.  FP32 mode (bf16x3 leaf)
@@ -1012,7 +1014,7 @@ TarPlan tar_plan(int L, int variant) {
   T.levels = L;
   T.products = pw7(L);
   const int side = 1 << L;
-  uint32_t used[49];
+  uint32_t used[49], mask_of[49];
   memset(used, 0, sizeof(used));
   for (int p = 0; p < T.products; ++p) {
     const int r1 = L == 2 ? p / 7 : p, r2 = L == 2 ? p % 7 : 0;
@@ -1036,10 +1038,21 @@ TarPlan tar_plan(int L, int variant) {
       }
     }
     if (T.ndst[p] > 4) T.fits = false;
+    mask_of[p] = mask;
+  }
+  // greedy colouring, products with more blocks first (ties in product
+  // order): one Winograd level then takes four waves, {P1}, {P6, P2},
+  // {P5, P4}, {P7, P3}, instead of five in plain product order; the paper's
+  // formulas keep their printed order
+  int order[49];
+  for (int p = 0; p < T.products; ++p) order[p] = p;
+  std::stable_sort(order, order + T.products, [&](int a, int b) { return T.ndst[a] > T.ndst[b]; });
+  for (int i = 0; i < T.products; ++i) {
+    const int p = order[i];
     int w = 0;
-    while (w < T.waves && (used[w] & mask)) ++w;
+    while (w < T.waves && (used[w] & mask_of[p])) ++w;
     if (w == T.waves) ++T.waves;
-    used[w] |= mask;
+    used[w] |= mask_of[p];
     T.wave_of[p] = w;
   }
   return T;
