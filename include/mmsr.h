@@ -247,7 +247,10 @@ int mm_strassen_tables(int variant, int8_t* alpha, int8_t* beta, int8_t* gamma);
 /* One problem of a batch (host-side descriptor; pointers are device). */
 typedef struct {
   int32_t semiring; /* MM_SR_PLUS_TIMES_F32 or MM_SR_MIN_PLUS_I32 */
-  int32_t levels;   /* reserved, must be 0 */
+  int32_t levels;   /* Strassen-Winograd levels: 0, or 1 for an FP32 problem with
+                     * even m, n, k (its seven leaf products join the batch's tile
+                     * queue, their operand sums are formed by the pre-pass and a
+                     * post pass folds them into C); (min,+): 0 */
   int64_t m, n, k;
   const void* A;
   const void* B;
@@ -275,7 +278,12 @@ typedef struct {
  * the table, the split FP32 operands and, for FP32 tiles cut into k-slices,
  * one 64 KB partial tile per slice and a counter per tile: the last slice to
  * finish folds the partials in slice order (a fixed order: results repeat
- * exactly) and writes C.  mm_batched_query reports the minimum.
+ * exactly) and writes C; for problems with a Strassen level, the seven leaf
+ * products ((m/2)(n/2) FP32 values each).  mm_batched_query reports the
+ * minimum.  Errors: MM_ERR_ARG (levels outside 0..1, split_k < 0, a
+ * nonzero split_k on a (min,+) problem), MM_ERR_UNSUPPORTED (another
+ * semiring, levels on (min,+), reserved != 0), MM_ERR_SHAPE (odd m, n or k
+ * with levels = 1).
  */
 int mm_batched(int count, const mm_problem_t* problems, void* workspace, size_t workspace_bytes,
                void* stream);

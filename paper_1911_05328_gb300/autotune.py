@@ -15,7 +15,9 @@ fastest per shape bucket:
   deep Strassen plan fits only below a few classic levels;
 * ``mm_batched``: the k-slices of FP32 tiles (``split_k`` of each problem),
   one choice per power-of-two k bucket, found by coordinate descent over the
-  buckets (longest k first) with the whole batch timed for each candidate.
+  buckets (longest k first) with the whole batch timed for each candidate;
+  then one Strassen-Winograd level (``levels``) for the large FP32 problems
+  (every dimension >= 1024 and even), kept if the batch gets faster.
 
 Choices are cached in JSON (``MMSR_TUNE_CACHE``, default
 ``~/.cache/mmsr_tune.json``) keyed by semiring, power-of-two shape bucket and
@@ -231,9 +233,18 @@ def batch_buckets(problems, min_k: int = 1024):
     return [(b, groups[b]) for b in sorted(groups, reverse=True)]
 
 
-def apply_splits(problems, splits):
-    """The problem tuples with their split_k hints set."""
-    return [tuple(p[:7]) + (int(h),) for p, h in zip(problems, splits)]
+def apply_splits(problems, splits, levels=None):
+    """The problem tuples with their split_k hints (and Strassen levels) set."""
+    levels = levels or [int(p[8]) if len(p) > 8 else 0 for p in problems]
+    return [tuple(p[:7]) + (int(h), int(lv)) for p, h, lv in zip(problems, splits, levels)]
+
+
+def strassen_candidates_in_batch(problems, min_dim: int = 1024):
+    """Indices of the FP32 problems one Strassen level may serve: every
+    dimension at least min_dim and even."""
+    return [i for i, p in enumerate(problems)
+            if int(p[0]) == mmsr.MM_SR_PLUS_TIMES_F32 and min(int(p[1]), int(p[2]), int(p[3])) >= min_dim
+            and not (int(p[1]) | int(p[2]) | int(p[3])) & 1]
 
 
 def tune_batched(problems, workspace, workspace_bytes, timer=None, cache=None, persist=True,
@@ -241,8 +252,9 @@ def tune_batched(problems, workspace, workspace_bytes, timer=None, cache=None, p
     """Choose the k-slices of the batch's long-k FP32 problems.  problems:
     (semiring, m, n, k, A, B, C[, split_k]) tuples as ``mmsr.mm_batched``
     takes them.  Candidates whose workspace exceeds ``workspace_bytes`` are
-    skipped.  Returns {"splits": [hint per problem], "buckets": {k bucket:
-    hint}, "ms": time of the chosen batch}."""
+    skipped.  Returns {"splits": [hint per problem], "levels": [Strassen
+    levels per problem], "buckets": {k bucket: hint}, "ms": time of the chosen
+    batch}."""
     timer = timer or cuda_timer
     kk = batch_signature(problems)
     buckets = batch_buckets(problems)
@@ -251,9 +263,10 @@ def tune_batched(problems, workspace, workspace_bytes, timer=None, cache=None, p
         if kk in c and len(c[kk].get("splits", [])) == len(problems):
             return c[kk]
     splits = [0] * len(problems)
+    levels = [0] * len(problems)
 
-    def run(sp):
-        table = apply_splits(problems, sp)
+    def run(sp, lv=None):
+        table = apply_splits(problems, sp, lv or levels)
         if mmsr.mm_batched_query(table) > workspace_bytes:
             return None
         return timer(lambda: mmsr.mm_batched(table, workspace, workspace_bytes))
@@ -274,7 +287,15 @@ def tune_batched(problems, workspace, workspace_bytes, timer=None, cache=None, p
         for i in idx:
             splits[i] = best_h
         chosen[str(b)] = best_h
-    rec = {"splits": splits, "buckets": chosen, "ms": best_ms}
+    big = strassen_candidates_in_batch(problems)
+    if big:
+        trial = list(levels)
+        for i in big:
+            trial[i] = 1
+        ms = run(splits, trial)
+        if ms is not None and (best_ms is None or ms < best_ms):
+            best_ms, levels = ms, trial
+    rec = {"splits": splits, "levels": levels, "buckets": chosen, "ms": best_ms}
     with _lock:
         c[kk] = rec
         if persist and cache is None:
@@ -288,5 +309,5 @@ def mm_batched_tuned(problems, workspace, workspace_bytes, stream=None):
     rec = load_cache().get(batch_signature(problems))
     table = problems
     if rec and len(rec.get("splits", [])) == len(problems):
-        table = apply_splits(problems, rec["splits"])
+        table = apply_splits(problems, rec["splits"], rec.get("levels"))
     return mmsr.mm_batched(table, workspace, workspace_bytes, stream)

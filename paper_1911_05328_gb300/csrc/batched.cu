@@ -32,6 +32,7 @@
 
 #include "internal.h"
 #include "minplus_tile.cuh"
+#include "strassen_tables.cuh"
 #include "tcgen05.cuh"
 
 namespace mmsr {
@@ -77,7 +78,8 @@ constexpr int MPN = 256;  // (min,+) tile: 128 x 256
 // carry it as a kernel parameter, so the call stays capturable), which
 // leaves the batch size free of the kernel-parameter limit.
 struct BatchRow {
-  int kind;  // 0: FP32 (+,x) on tensor cores, 1: (min,+) 256-wide tiles, 2: 128-wide
+  int kind;  // 0: FP32 (+,x) on tensor cores, 1: (min,+) 256-wide tiles, 2: 128-wide,
+             // 3: a Strassen-Winograd parent (its post pass only)
   int m, n, k;
   int row0a, row0b;  // FP32: first row of this A / B^T in the stacked split buffers
   const void* A;
@@ -87,6 +89,11 @@ struct BatchRow {
   int64_t slot_off;  // FP32, s > 1: first float of this problem's partial tiles
   int cnt_off;       // FP32, s > 1: first of this problem's per-tile counters
   int prep_a;        // pre-pass blocks of A (the rest of the problem's blocks are B's)
+  int lda, ldb;      // row pitches of A and B (a Strassen leaf reads its parent's)
+  int sr;            // Strassen leaf: its product r (operands sum the parent's
+                     // quadrants by alpha_r / beta_r, output is P_r); -1 otherwise
+  int8_t ca[4], cb[4];  // Strassen leaf: alpha_r and beta_r over quadrants 00, 01, 10, 11
+  int64_t p_off;     // Strassen leaf: first float of P_r; parent: of P_0
 };
 // What the kernels take by value: sizes and the device addresses of the
 // table (rows in cost order and three prefix sums of tile counts).
@@ -100,7 +107,9 @@ struct BatchHeader {
   const int* mp16_tile_start;  // [count + 1] packed tiles of (min,+) problems
   const int* mp_tile_start;    // [count + 1] 128 x 128 tiles of (min,+) problems (fallback)
   const int* prep_start;       // [count + 1] pre-pass blocks
-  int prep_total;
+  const int* post_start;       // [count + 1] post-pass blocks (Strassen parents)
+  int prep_total, post_total;
+  float* pstack;               // the leaf products of the Strassen problems
 };
 constexpr int kUploadBytes = 30720;  // table bytes per upload launch (kernel parameter)
 struct UploadChunk {
@@ -133,11 +142,10 @@ __device__ __forceinline__ void split1(float x, __nv_bfloat16& h, __nv_bfloat16&
 //    the packed range flags violation[p] (zeroed by the call's memset).
 constexpr int kPrepA = 4096, kPrepB = 4, kPrepR = 4096;
 
-// Eight consecutive entries of row r of A starting at column c8 (zero past
-// column k), by 16-byte loads where the row allows them.
-__device__ __forceinline__ void load8(const float* __restrict__ A, int64_t r, int64_t c8, int64_t k, bool vec,
-                                      float* x) {
-  const float* src = A + r * k + c8;
+// Eight consecutive entries of a row starting at column c8 (zero past column
+// k), by 16-byte loads where the row allows them.
+__device__ __forceinline__ void load8(const float* __restrict__ row, int64_t c8, int64_t k, bool vec, float* x) {
+  const float* src = row + c8;
   if (vec && c8 + 8 <= k) {
     const float4 u = __ldcs(reinterpret_cast<const float4*>(src));
     const float4 w = __ldcs(reinterpret_cast<const float4*>(src + 4));
@@ -173,17 +181,32 @@ __global__ void __launch_bounds__(256, 4) batched_prepass_kernel(const BatchHead
         // A rows: items of 8 columns, four per thread in flight (a streaming
         // pass needs many bytes in flight per SM to approach the HBM rate)
         const float* __restrict__ A = static_cast<const float*>(R.A);
-        const int64_t cpr = kp / 8, items = m * cpr;
+        const int64_t cpr = kp / 8, items = m * cpr, lda = R.lda;
         const int64_t e0 = (int64_t)lb * kPrepA, e_end = min(items, e0 + kPrepA);
-        const bool vec = (k & 3) == 0;
+        const bool vec = (k & 3) == 0 && (lda & 3) == 0;
         for (int64_t e = e0 + threadIdx.x; e < e_end; e += 4 * 256) {
           float x[4][8];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int64_t ej = e + j * 256;
             if (ej < e_end) {
-              const int64_t r = ej / cpr;
-              load8(A, r, (ej - r * cpr) * 8, k, vec, x[j]);
+              const int64_t r = ej / cpr, c8 = (ej - r * cpr) * 8;
+              if (R.sr < 0) {
+                load8(A + r * lda, c8, k, vec, x[j]);
+              } else {
+                // S_r = sum_q alpha_rq A_q over the parent's quadrants (Section 5)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) x[j][t] = 0.f;
+#pragma unroll
+                for (int qd = 0; qd < 4; ++qd) {
+                  const int c = R.ca[qd];
+                  if (c == 0) continue;
+                  float y[8];
+                  load8(A + ((qd >> 1) * m + r) * lda + (qd & 1) * k, c8, k, vec, y);
+#pragma unroll
+                  for (int t = 0; t < 8; ++t) x[j][t] = c > 0 ? x[j][t] + y[t] : x[j][t] - y[t];
+                }
+              }
             }
           }
 #pragma unroll
@@ -211,10 +234,29 @@ __global__ void __launch_bounds__(256, 4) batched_prepass_kernel(const BatchHead
           const int64_t k0 = (tt / tn) * 64, n0 = (tt % tn) * 64;
           const int64_t gn = n0 + tx;
           float v[16];
+          const int64_t ldb = R.ldb;
+          if (R.sr < 0) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int64_t gk = k0 + ty + 4 * i;
-            v[i] = (gk < k && gn < n) ? __ldcs(B + gk * n + gn) : 0.f;
+            for (int i = 0; i < 16; ++i) {
+              const int64_t gk = k0 + ty + 4 * i;
+              v[i] = (gk < k && gn < n) ? __ldcs(B + gk * ldb + gn) : 0.f;
+            }
+          } else {
+            // T_r = sum_q beta_rq B_q over the parent's quadrants
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+            for (int qd = 0; qd < 4; ++qd) {
+              const int c = R.cb[qd];
+              if (c == 0) continue;
+              const float* Bq = B + (qd >> 1) * k * ldb + (qd & 1) * n;
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int64_t gk = k0 + ty + 4 * i;
+                const float y = (gk < k && gn < n) ? __ldcs(Bq + gk * ldb + gn) : 0.f;
+                v[i] = c > 0 ? v[i] + y : v[i] - y;
+              }
+            }
           }
           __syncthreads();  // the previous tile's readers are done
 #pragma unroll
@@ -253,6 +295,40 @@ __global__ void __launch_bounds__(256, 4) batched_prepass_kernel(const BatchHead
       if (bad && threadIdx.x == 0) atomicOr(&violation[p], 1);
     }
     __syncthreads();  // the next block of work may reuse `tile`
+  }
+}
+
+// Post pass of the Strassen-Winograd problems (one level, Section 5's
+// bilinear form): C_q = sum_r gamma_qr P_r for the four quadrants, products
+// in order r = 0..6, kPostE entries of the half-size blocks per block.
+constexpr int kPostE = 4096;
+constexpr int kBatchVariant = 1;  // Strassen-Winograd
+
+__global__ void __launch_bounds__(256) batched_post_kernel(const BatchHeader T) {
+  for (int blk = blockIdx.x; blk < T.post_total; blk += gridDim.x) {
+    int lo = 0, hi = T.count - 1;  // last p with post_start[p] <= blk
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&T.post_start[mid]) <= blk) lo = mid; else hi = mid - 1;
+    }
+    const BatchRow R = T.rows[lo];
+    const int64_t m2 = R.m / 2, n2 = R.n / 2, n = R.n, ps = m2 * n2;
+    const float* __restrict__ P0 = T.pstack + R.p_off;
+    float* __restrict__ C = static_cast<float*>(R.C);
+    const int64_t e0 = (int64_t)(blk - __ldg(&T.post_start[lo])) * kPostE, e1 = min(ps, e0 + kPostE);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += 256) {
+      const int64_t i = e / n2, j = e - i * n2;
+      float pr[7];
+#pragma unroll
+      for (int r = 0; r < 7; ++r) pr[r] = __ldcs(P0 + r * ps + e);
+#pragma unroll
+      for (int qd = 0; qd < 4; ++qd) {
+        float acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < 7; ++r) acc = apply(coef_gamma(kBatchVariant, qd, r), acc, pr[r]);
+        C[((qd >> 1) * m2 + i) * n + (qd & 1) * n2 + j] = acc;
+      }
+    }
   }
 }
 
@@ -513,7 +589,8 @@ __global__ void __launch_bounds__(kBThreads, 1)
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
         }
-        float* C = static_cast<float*>(T.rows[p].C);
+        // a Strassen leaf writes its product P_r into the stack, else C
+        float* C = T.rows[p].sr >= 0 ? T.pstack + T.rows[p].p_off : static_cast<float*>(T.rows[p].C);
         const int64_t row = i0 + q * 32 + lane;
         if (nsl > 1) {
           // One k-slice of a split tile: store the partial tile thread-major
@@ -607,13 +684,14 @@ __global__ void __launch_bounds__(kBThreads, 1)
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct BatchPlan {
-  int count = 0, total_tiles = 0, mp16_total = 0, mp_total = 0, prep_total = 0;
+  int count = 0, total_tiles = 0, mp16_total = 0, mp_total = 0, prep_total = 0, post_total = 0;
   std::vector<uint8_t> table;  // rows, then the three prefix sums (uploaded to off_table)
   int64_t rows_bytes = 0, starts_bytes = 0;
   int64_t KP = 0, rows_a = 0, rows_b = 0;
   int64_t split_tiles = 0, slot_floats = 0;  // k-sliced FP32 tiles: counters and partial tiles
-  int64_t off_viol = 256, off_cnt = 0, off_table = 0, off_slots = 0, off_ahi = 0, off_alo = 0, off_bhi = 0,
-          off_blo = 0, total = 0;
+  int64_t pstack_floats = 0;                 // Strassen leaf products
+  int64_t off_viol = 256, off_cnt = 0, off_table = 0, off_slots = 0, off_pstack = 0, off_ahi = 0, off_alo = 0,
+          off_bhi = 0, off_blo = 0, total = 0;
 
   // The kernels' view of the table once it sits at `w + off_table`.
   BatchHeader header(uint8_t* w) const {
@@ -628,31 +706,68 @@ struct BatchPlan {
     H.mp16_tile_start = st + (count + 1);
     H.mp_tile_start = st + 2 * (count + 1);
     H.prep_start = st + 3 * (count + 1);
+    H.post_start = st + 4 * (count + 1);
     H.prep_total = prep_total;
+    H.post_total = post_total;
+    H.pstack = reinterpret_cast<float*>(w + off_pstack);
     return H;
   }
 };
 
+// One row of the table before sorting: a problem, or for a problem with one
+// Strassen-Winograd level its seven leaf products and the parent row whose
+// post pass folds them into C.
+struct Item {
+  int kind;  // as BatchRow::kind
+  int64_t m, n, k, lda, ldb;
+  const void* A;
+  const void* B;
+  void* C;
+  int sr;         // Strassen leaf r, or -1
+  int64_t p_off;  // leaf: its product's first float; parent: P_0's
+  int split;      // split_k hint
+};
+
 int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
   if (count < 0 || count > kMaxBatch || (count > 0 && !probs)) return MM_ERR_ARG;
-  std::vector<int> order(count);
-  std::iota(order.begin(), order.end(), 0);
+  std::vector<Item> items;
+  items.reserve(count);
+  int64_t pfl = 0;  // floats of the leaf-product stack
   for (int i = 0; i < count; ++i) {
     const mm_problem_t& q = probs[i];
     if (q.semiring != MM_SR_PLUS_TIMES_F32 && q.semiring != MM_SR_MIN_PLUS_I32) return MM_ERR_UNSUPPORTED;
-    if (q.levels != 0 || q.reserved != 0) return MM_ERR_UNSUPPORTED;
+    if (q.reserved != 0) return MM_ERR_UNSUPPORTED;
+    if (q.levels < 0 || q.levels > 1) return MM_ERR_ARG;
+    if (q.levels == 1 && q.semiring != MM_SR_PLUS_TIMES_F32) return MM_ERR_UNSUPPORTED;  // no (min,+) Strassen
     if (q.split_k < 0 || (q.split_k != 0 && q.semiring != MM_SR_PLUS_TIMES_F32)) return MM_ERR_ARG;
     if (q.m < 0 || q.n < 0 || q.k < 0 || q.m > (1 << 20) || q.n > (1 << 20) || q.k > (1 << 20))
       return MM_ERR_SHAPE;
+    if (q.levels == 1 && ((q.m | q.n | q.k) & 1)) return MM_ERR_SHAPE;
     if (q.m > 0 && q.n > 0 && (!q.C || (q.k > 0 && (!q.A || !q.B)))) return MM_ERR_ARG;
     if (!aligned16(q.C) || !aligned16(q.A) || !aligned16(q.B)) return MM_ERR_ALIGN;
+    const bool f32 = q.semiring == MM_SR_PLUS_TIMES_F32;
+    if (q.levels == 1 && q.m > 0 && q.n > 0 && q.k > 0) {
+      const int64_t m2 = q.m / 2, n2 = q.n / 2, k2 = q.k / 2;
+      items.push_back({3, q.m, q.n, q.k, q.k, q.n, nullptr, nullptr, q.C, -1, pfl, 0});
+      for (int r = 0; r < 7; ++r)
+        items.push_back({0, m2, n2, k2, q.k, q.n, q.A, q.B, nullptr, r, pfl + r * m2 * n2, q.split_k});
+      pfl += 7 * m2 * n2;
+    } else {
+      // (min,+): 128-wide tiles where they pad the width less than 256-wide ones
+      const bool narrow = ((q.n + 127) / 128) * 128 < ((q.n + 255) / 256) * 256;
+      items.push_back({f32 ? 0 : (narrow ? 2 : 1), q.m, q.n, q.k, q.k, q.n, q.A, q.B, q.C, -1, 0, q.split_k});
+    }
   }
+  if ((int64_t)items.size() > kMaxBatch * 4) return MM_ERR_SHAPE;
+  const int rows_n = (int)items.size();
+  std::vector<int> order(rows_n);
+  std::iota(order.begin(), order.end(), 0);
   // Longest tiles first: every tile of a problem costs ~k (tiles have a fixed
   // size), so descending k is longest-processing-time order for the tile
   // queues; ties by m n (more tiles first), then by index for determinism.
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    if (probs[a].k != probs[b].k) return probs[a].k > probs[b].k;
-    return (double)probs[a].m * probs[a].n > (double)probs[b].m * probs[b].n;
+    if (items[a].k != items[b].k) return items[a].k > items[b].k;
+    return (double)items[a].m * items[a].n > (double)items[b].m * items[b].n;
   });
   // k-slices of FP32 tiles (Section 3's k-split inside the batch).  The
   // library's rule: a tile whose k-blocks exceed an eighth of one SM's share
@@ -660,18 +775,16 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
   // into slices of about that size (at least 8 k-blocks, at most 16 slices);
   // a hint s > 1 asks for s slices.
   int64_t fp_work = 0;  // FP32 (tile, 64-wide k-block) units
-  for (int i = 0; i < count; ++i) {
-    const mm_problem_t& q = probs[i];
-    if (q.semiring == MM_SR_PLUS_TIMES_F32 && q.m > 0 && q.n > 0)
-      fp_work += ((q.m + TBM - 1) / TBM) * ((q.n + TBN - 1) / TBN) * ((q.k + TBK - 1) / TBK);
-  }
+  for (const Item& it : items)
+    if (it.kind == 0 && it.m > 0 && it.n > 0)
+      fp_work += ((it.m + TBM - 1) / TBM) * ((it.n + TBN - 1) / TBN) * ((it.k + TBK - 1) / TBK);
   const int64_t slice_target = std::max<int64_t>(8, fp_work / (8 * (int64_t)num_sms()));
-  auto slices_of = [&](const mm_problem_t& q, int* kbs) {
+  auto slices_of = [&](const Item& q, int* kbs) {
     const int64_t nkb = (q.k + TBK - 1) / TBK;
     int64_t s = 1;
-    if (q.split_k > 1)
-      s = std::min<int64_t>({(int64_t)q.split_k, 64, nkb});
-    else if (q.split_k == 0 && nkb > slice_target)
+    if (q.split > 1)
+      s = std::min<int64_t>({(int64_t)q.split, 64, nkb});
+    else if (q.split == 0 && nkb > slice_target)
       s = std::min<int64_t>(16, (nkb + slice_target - 1) / slice_target);
     if (s < 1) s = 1;
     int64_t per = (nkb + s - 1) / s;
@@ -680,34 +793,41 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     *kbs = (int)per;
     return (int)s;
   };
-  std::vector<BatchRow> rows(count);
-  std::vector<int> starts(4 * (size_t)(count + 1));
+  std::vector<BatchRow> rows(rows_n);
+  std::vector<int> starts(5 * (size_t)(rows_n + 1));
   int* tile_start = starts.data();
-  int* mp16_start = tile_start + (count + 1);
-  int* mp_start = mp16_start + (count + 1);
-  int* prep_start = mp_start + (count + 1);
-  int64_t prep = 0;
+  int* mp16_start = tile_start + (rows_n + 1);
+  int* mp_start = mp16_start + (rows_n + 1);
+  int* prep_start = mp_start + (rows_n + 1);
+  int* post_start = prep_start + (rows_n + 1);
+  int64_t prep = 0, post = 0;
   int64_t kp_max = 0, ra = 0, rb = 0, tiles = 0, mp_tiles = 0, mp16_tiles = 0, split_tiles = 0, slot_floats = 0;
-  for (int i = 0; i < count; ++i) {
-    const mm_problem_t& q = probs[order[i]];
+  for (int i = 0; i < rows_n; ++i) {
+    const Item& q = items[order[i]];
     BatchRow& r = rows[i];
-    // (min,+): 128-wide tiles where they pad the width less than 256-wide ones
-    const bool narrow = ((q.n + 127) / 128) * 128 < ((q.n + 255) / 256) * 256;
-    r.kind = q.semiring == MM_SR_PLUS_TIMES_F32 ? 0 : (narrow ? 2 : 1);
+    memset(&r, 0, sizeof(r));
+    r.kind = q.kind;
     r.m = (int)q.m;
     r.n = (int)q.n;
     r.k = (int)q.k;
     r.A = q.A;
     r.B = q.B;
     r.C = q.C;
-    r.row0a = r.row0b = 0;
+    r.lda = (int)q.lda;
+    r.ldb = (int)q.ldb;
+    r.sr = q.sr;
+    r.p_off = q.p_off;
+    for (int qd = 0; qd < 4; ++qd) {
+      r.ca[qd] = (int8_t)(q.sr >= 0 ? coef_alpha(kBatchVariant, q.sr, qd) : 0);
+      r.cb[qd] = (int8_t)(q.sr >= 0 ? coef_beta(kBatchVariant, q.sr, qd) : 0);
+    }
     r.s = 1;
     r.kbs = (int)std::max<int64_t>(1, (q.k + TBK - 1) / TBK);
-    r.slot_off = 0;
-    r.cnt_off = 0;
-    r.prep_a = 0;
     prep_start[i] = (int)prep;
-    if (q.m > 0 && q.n > 0 && q.k > 0) {
+    post_start[i] = (int)post;
+    if (r.kind == 3) {
+      post += (q.m / 2 * (q.n / 2) + kPostE - 1) / kPostE;
+    } else if (q.m > 0 && q.n > 0 && q.k > 0) {
       if (r.kind == 0) {
         const int64_t kp = align_up(q.k, TKA);
         r.prep_a = (int)((q.m * (kp / 8) + kPrepA - 1) / kPrepA);
@@ -720,7 +840,7 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     tile_start[i] = (int)tiles;
     mp16_start[i] = (int)mp16_tiles;
     mp_start[i] = (int)mp_tiles;
-    if (q.semiring == MM_SR_MIN_PLUS_I32 && q.m > 0 && q.n > 0) {
+    if ((r.kind == 1 || r.kind == 2) && q.m > 0 && q.n > 0) {
       mp_tiles += ((q.m + mp::BM - 1) / mp::BM) * ((q.n + mp::BN - 1) / mp::BN);
       const int64_t tn = r.kind == 2 ? 128 : MPN;
       mp16_tiles += ((q.m + mp::PBM - 1) / mp::PBM) * ((q.n + tn - 1) / tn);
@@ -745,35 +865,40 @@ int make_plan(int count, const mm_problem_t* probs, BatchPlan* P) {
     }
     if (tiles > (int64_t)1 << 30 || mp_tiles > (int64_t)1 << 30 || mp16_tiles > (int64_t)1 << 30 ||
         ra > (int64_t)1 << 30 || rb > (int64_t)1 << 30 || split_tiles > (int64_t)1 << 30 ||
-        prep > (int64_t)1 << 30)
+        prep > (int64_t)1 << 30 || post > (int64_t)1 << 30)
       return MM_ERR_SHAPE;
   }
-  tile_start[count] = (int)tiles;
-  mp16_start[count] = (int)mp16_tiles;
-  mp_start[count] = (int)mp_tiles;
-  prep_start[count] = (int)prep;
+  tile_start[rows_n] = (int)tiles;
+  mp16_start[rows_n] = (int)mp16_tiles;
+  mp_start[rows_n] = (int)mp_tiles;
+  prep_start[rows_n] = (int)prep;
+  post_start[rows_n] = (int)post;
   P->prep_total = (int)prep;
-  P->count = count;
+  P->post_total = (int)post;
+  P->count = rows_n;
   P->total_tiles = (int)tiles;
   P->mp16_total = (int)mp16_tiles;
   P->mp_total = (int)mp_tiles;
-  P->rows_bytes = align_up((int64_t)count * (int64_t)sizeof(BatchRow), 16);
+  P->rows_bytes = align_up((int64_t)rows_n * (int64_t)sizeof(BatchRow), 16);
   P->starts_bytes = align_up((int64_t)starts.size() * 4, 16);
   P->table.assign((size_t)(P->rows_bytes + P->starts_bytes), 0);
-  if (count > 0) memcpy(P->table.data(), rows.data(), (size_t)count * sizeof(BatchRow));
+  if (rows_n > 0) memcpy(P->table.data(), rows.data(), (size_t)rows_n * sizeof(BatchRow));
   memcpy(P->table.data() + P->rows_bytes, starts.data(), starts.size() * 4);
   P->KP = kp_max;
   P->rows_a = ra;
   P->rows_b = rb;
   P->split_tiles = split_tiles;
   P->slot_floats = slot_floats;
-  // workspace: [0] tile counter, [256] per-problem (min,+) range verdicts,
-  // the per-tile counters of k-sliced tiles (all zeroed by one memset per
-  // call), then the table, the partial tiles and the stacked split operands
-  P->off_cnt = align_up(P->off_viol + 4 * (int64_t)count, 16);
+  P->pstack_floats = pfl;
+  // workspace: [0] tile counter, [256] per-row (min,+) range verdicts, the
+  // per-tile counters of k-sliced tiles (all zeroed by one memset per call),
+  // then the table, the partial tiles, the Strassen leaf products and the
+  // stacked split operands
+  P->off_cnt = align_up(P->off_viol + 4 * (int64_t)rows_n, 16);
   P->off_table = align_up(P->off_cnt + 4 * split_tiles, 256);
   P->off_slots = align_up(P->off_table + (int64_t)P->table.size(), 1024);
-  P->off_ahi = align_up(P->off_slots + 4 * slot_floats, 1024);
+  P->off_pstack = align_up(P->off_slots + 4 * slot_floats, 1024);
+  P->off_ahi = align_up(P->off_pstack + 4 * pfl, 1024);
   P->off_alo = P->off_ahi + align_up(ra * kp_max * 2, 1024);
   P->off_bhi = P->off_alo + align_up(ra * kp_max * 2, 1024);
   P->off_blo = P->off_bhi + align_up(rb * kp_max * 2, 1024);
@@ -855,6 +980,11 @@ extern "C" int mm_batched(int count, const mm_problem_t* problems, void* workspa
     batched_kernel<<<grid, kBThreads, BSMEM, st>>>(H, ta_hi, ta_lo, tb_hi, tb_lo, counter,
                                                    reinterpret_cast<float*>(w + P.off_slots),
                                                    reinterpret_cast<int*>(w + P.off_cnt));
+    MMSR_TRY_STATUS(cudaGetLastError());
+  }
+  if (P.post_total > 0) {
+    TraceScope tr(kTrStrassenPost, st);
+    batched_post_kernel<<<(unsigned)std::min(P.post_total, 16 * sms), 256, 0, st>>>(H);
     MMSR_TRY_STATUS(cudaGetLastError());
   }
   if (P.mp16_total > 0) {

@@ -234,12 +234,13 @@ def _problems(problems):
     for i, p in enumerate(problems):
         sr, m, n, k, A, B, C = p[:7]
         split = int(p[7]) if len(p) > 7 else 0
-        arr[i] = mm_problem_t(int(sr), 0, int(m), int(n), int(k), _addr(A), _addr(B), _addr(C), split, 0)
+        levels = int(p[8]) if len(p) > 8 else 0
+        arr[i] = mm_problem_t(int(sr), levels, int(m), int(n), int(k), _addr(A), _addr(B), _addr(C), split, 0)
     return arr
 
 
 def mm_batched(problems, workspace=None, workspace_bytes=0, stream=None, check=True) -> int:
-    """problems: sequence of (semiring, m, n, k, A, B, C[, split_k])."""
+    """problems: sequence of (semiring, m, n, k, A, B, C[, split_k[, levels]])."""
     arr = _problems(problems)
     rc = load().mm_batched(len(problems), arr, _addr(workspace), int(workspace_bytes),
                            _stream(stream))

@@ -339,6 +339,24 @@ def test_batched_table_size_and_cap(lib):
     assert mmsr.mm_batched_query(one * ((1 << 20) + 1)) == 0
 
 
+def test_batched_strassen_level_checks(lib):
+    """levels = 1 runs an FP32 problem as one Strassen-Winograd level inside the
+    batch: the workspace adds its seven leaf products and their operand
+    stacks; odd shapes, (min,+) and deeper levels are refused on the host."""
+    F32, MP = mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_MIN_PLUS_I32
+    n = 256
+    plain = mmsr.mm_batched_query([(F32, n, n, n, FAKE, FAKE, FAKE, 0, 0)])
+    lev = mmsr.mm_batched_query([(F32, n, n, n, FAKE, FAKE, FAKE, 0, 1)])
+    assert lev - plain >= 7 * (n // 2) ** 2 * 4  # the leaf products at least
+    assert mmsr.mm_batched_query([(F32, n + 1, n, n, FAKE, FAKE, FAKE, 0, 1)]) == 0
+    assert mmsr.mm_batched_query([(F32, n, n, n, FAKE, FAKE, FAKE, 0, 2)]) == 0
+    assert mmsr.mm_batched_query([(F32, n, n, n, FAKE, FAKE, FAKE, 0, -1)]) == 0
+    assert mmsr.mm_batched_query([(MP, n, n, n, FAKE, FAKE, FAKE, 0, 1)]) == 0
+    # k = 0 with a level: the plain zero-fill product
+    assert mmsr.mm_batched_query([(F32, n, n, 0, FAKE, FAKE, FAKE, 0, 1)]) == \
+        mmsr.mm_batched_query([(F32, n, n, 0, FAKE, FAKE, FAKE, 0, 0)])
+
+
 def test_batched_k_slices(lib):
     """FP32 tiles cut into k-slices hold one 64 KB partial tile per slice in
     the workspace (plus a counter per tile); hints are checked on the host."""

@@ -149,3 +149,35 @@ def test_batched_split_tuning(tmp_path, monkeypatch):
     seen.clear()
     assert autotune.tune_batched(probs, FAKE, small, timer=timer) == rec2 and not seen
     monkeypatch.setattr(mmsr, "mm_batched", real_run)
+
+
+def test_batched_strassen_level_tuning(tmp_path, monkeypatch):
+    """After the k-slices, the tuner tries one Strassen-Winograd level for the
+    large FP32 problems (every dimension >= 1024 and even) and keeps it only if
+    the batch gets faster."""
+    monkeypatch.setenv("MMSR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    F32 = mmsr.MM_SR_PLUS_TIMES_F32
+    FAKE = 1 << 20
+    probs = [(F32, 2048, 2048, 2048, FAKE, FAKE, FAKE), (F32, 1024, 1025, 2048, FAKE, FAKE, FAKE),
+             (F32, 512, 512, 512, FAKE, FAKE, FAKE)]
+    assert autotune.strassen_candidates_in_batch(probs) == [0]
+    budget = mmsr.mm_batched_query(autotune.apply_splits(probs, [16, 16, 0], [1, 0, 0]))
+    real_run = mmsr.mm_batched
+    for faster in (True, False):
+        seen = []
+
+        def spy(table, *a, **k):
+            seen.append([t[8] for t in table])
+            return 0
+
+        monkeypatch.setattr(mmsr, "mm_batched", spy)
+
+        def timer(fn):
+            fn()
+            lv = seen[-1]
+            return 1.0 if (lv[0] == 1) == faster else 2.0
+
+        rec = autotune.tune_batched(probs, FAKE, budget, timer=timer, cache={}, persist=False)
+        assert rec["levels"] == ([1, 0, 0] if faster else [0, 0, 0])
+        assert any(lv == [1, 0, 0] for lv in seen)
+    monkeypatch.setattr(mmsr, "mm_batched", real_run)

@@ -13,17 +13,19 @@ pytestmark = pytest.mark.gpu
 F32, MP = mmsr.MM_SR_PLUS_TIMES_F32, mmsr.MM_SR_MIN_PLUS_I32
 
 
-def _launch(probs, capture=False, splits=None, reps=1):
-    """probs: list of inputs.Problem; splits: optional per-problem k-slice
-    hints (mm_problem_t.split_k); returns the list of output arrays (of the
-    last of `reps` eager calls)."""
+def _launch(probs, capture=False, splits=None, reps=1, levels=None):
+    """probs: list of inputs.Problem; splits / levels: optional per-problem
+    k-slice hints and Strassen levels (mm_problem_t.split_k / .levels);
+    returns the list of output arrays (of the last of `reps` eager calls)."""
     import torch
 
     dA = [dev(p.A) for p in probs]
     dB = [dev(p.B) for p in probs]
     dC = [empty((p.m, p.n), torch.float32 if p.semiring == F32 else torch.int32) for p in probs]
     splits = splits or [0] * len(probs)
-    table = [(p.semiring, p.m, p.n, p.k, a, b, c, h) for p, a, b, c, h in zip(probs, dA, dB, dC, splits)]
+    levels = levels or [0] * len(probs)
+    table = [(p.semiring, p.m, p.n, p.k, a, b, c, h, lv)
+             for p, a, b, c, h, lv in zip(probs, dA, dB, dC, splits, levels)]
     need = mmsr.mm_batched_query(table)
     assert need > 0
     ws = empty((need,), torch.uint8)
@@ -203,3 +205,29 @@ def test_k_sliced_tiles_graph_replay():
     rng = np.random.default_rng(210)
     probs = [_fp32(rng, 190, 260, 2500, integer=True), _fp32(rng, 70, 90, 700, integer=True)]
     _check(probs, _launch(probs, capture=True, splits=[5, 2]), exact_fp32=True)
+
+
+def test_strassen_level_in_batch_integer_exact():
+    # FP32 problems with one Strassen-Winograd level beside plain FP32 and
+    # (min,+) problems: leaf operand sums in the pre-pass, leaf products in the
+    # tile queue, the post pass folds them into C -- exact on small integers
+    rng = np.random.default_rng(211)
+    probs = [_fp32(rng, 256, 384, 512, True), _fp32(rng, 130, 66, 258, True), _fp32(rng, 2, 2, 2, True),
+             _fp32(rng, 300, 200, 100, True)]
+    probs += [p for p in _mixed(10, seed=212, lo=40, hi=300) if p.semiring == MP][:3]
+    levels = [1, 1, 1, 0] + [0] * (len(probs) - 4)
+    _check(probs, _launch(probs, levels=levels), exact_fp32=True)
+
+
+def test_strassen_level_in_batch_normal_and_sliced():
+    # normal inputs within the derived one-level Winograd tolerance, also with
+    # the leaves' tiles cut into k-slices, and as a replayed graph
+    from error_bounds import fp32_strassen_tol
+
+    rng = np.random.default_rng(213)
+    probs = [_fp32(rng, 512, 512, 4096), _fp32(rng, 200, 300, 1000), _fp32(rng, 128, 128, 64)]
+    tol = fp32_strassen_tol(mmsr.MM_STRASSEN_WINOGRAD, 1)
+    for kw in ({}, {"splits": [4, 0, 0]}, {"capture": True}):
+        outs = _launch(probs, levels=[1, 1, 0], **kw)
+        for p, C in zip(probs, outs):
+            assert rel_fro(C, oracle.mm_f64(p.A, p.B)) <= tol, (p.m, p.n, p.k, kw)
