@@ -592,6 +592,7 @@ def run_extras(mmsr, lib, torch, sp, book, A_sq, B_sq, rows_sq):
                                                                   bf16_src)
     out["batched_512"] = extras_batched(mmsr, lib, torch, sp, ctypes, bf16["burst"], u16_peak, bf16_src)
     out["batched_long_k_fp32"] = extras_batched_long_k(mmsr, torch, sp, book, bf16["burst"], bf16_src)
+    out["batched_strassen_fp32"] = extras_batched_strassen(mmsr, torch, sp, book, bf16["burst"], bf16_src)
     out["closure_minplus_n4096"] = extras_closure(mmsr, torch, sp, u16_peak)
     out["orand_n4096"] = extras_orand(mmsr, lib, torch, sp, ctypes, lop_peak)
     out["probes"] = {"addmin_u32_tops": u32_peak, "addmin_u16x2_tops": u16_peak,
@@ -1038,6 +1039,49 @@ def extras_batched_long_k(mmsr, torch, sp, book, bf16_peak, bf16_src):
         book.add("batched_long_k_0", out[name], "error_long_k_product", _rows_of(torch, dC[0], rows0))
         del g
     out["autotuned"]["buckets"] = tuned["buckets"]
+    del dA, dB, dC, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def extras_batched_strassen(mmsr, torch, sp, book, bf16_peak, bf16_src):
+    """FP32 batch with large products: 16 of 2048^3 among 48 with m, n, k
+    log-uniform in [64, 512] (normal(0,1), seed 12).  The large products
+    classic (levels = 0), with one Strassen-Winograd level inside the batch
+    (levels = 1), and the autotuner's choice; each captured in a graph."""
+    from paper_1911_05328_gb300 import autotune, inputs
+
+    probs = inputs.batched_long_k_problems(seed=12, long_count=16, long_shape=(2048, 2048, 2048), short_count=48,
+                                           lo=64, hi=512)
+    dA = [torch.from_numpy(p.A).cuda() for p in probs]
+    dB = [torch.from_numpy(p.B).cuda() for p in probs]
+    dC = [torch.empty((p.m, p.n), dtype=torch.float32, device="cuda") for p in probs]
+    base = [(p.semiring, p.m, p.n, p.k, a, b, c) for p, a, b, c in zip(probs, dA, dB, dC)]
+    ops = sum(2.0 * p.m * p.n * p.k for p in probs)
+    rows0 = sample_rows(probs[0].m, 32)
+    book.add_set("batched_strassen_0", lambda p=probs[0]: (p.A, p.B), rows0)
+    big = autotune.strassen_candidates_in_batch(base)
+    lv1 = [1 if i in big else 0 for i in range(len(base))]
+    need = max(mmsr.mm_batched_query(autotune.apply_splits(base, [h] * len(base), lv))
+               for h in (0, 16) for lv in ([0] * len(base), lv1))
+    ws = torch.empty((need,), dtype=torch.uint8, device="cuda")
+    tuned = autotune.tune_batched(base, ws, need, cache={}, persist=False)
+    out = {"problems": len(probs), "ops": ops, "large_products": len(big)}
+    for name, splits, levels in (("classic", [0] * len(base), [0] * len(base)), ("strassen_L1", [0] * len(base), lv1),
+                                 ("autotuned", tuned["splits"], tuned["levels"])):
+        table = autotune.apply_splits(base, splits, levels)
+        mmsr.mm_batched(table, ws, need, stream=sp)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            mmsr.mm_batched(table, ws, need, stream=torch.cuda.current_stream())
+        ms = _time_call(torch, g.replay, 10)
+        out[name] = {"ms": ms, "gops_classic_equiv": ops / (ms * 1e-3) / 1e9,
+                     "workspace_bytes": int(mmsr.mm_batched_query(table))}
+        book.add("batched_strassen_0", out[name], "error_first_large_product", _rows_of(torch, dC[0], rows0))
+        del g
+    out["autotuned"]["levels_of_large"] = sorted({tuned["levels"][i] for i in big})
     del dA, dB, dC, ws
     torch.cuda.empty_cache()
     return out
