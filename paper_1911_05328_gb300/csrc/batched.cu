@@ -323,10 +323,7 @@ __global__ void __launch_bounds__(256) batched_post_kernel(const BatchHeader T) 
       for (int r = 0; r < 7; ++r) pr[r] = __ldcs(P0 + r * ps + e);
 #pragma unroll
       for (int qd = 0; qd < 4; ++qd) {
-        float acc = 0.f;
-#pragma unroll
-        for (int r = 0; r < 7; ++r) acc = apply(coef_gamma(kBatchVariant, qd, r), acc, pr[r]);
-        C[((qd >> 1) * m2 + i) * n + (qd & 1) * n2 + j] = acc;
+        C[((qd >> 1) * m2 + i) * n + (qd & 1) * n2 + j] = combo7<kBatchVariant>(qd, pr);
       }
     }
   }

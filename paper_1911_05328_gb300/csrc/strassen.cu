@@ -499,9 +499,10 @@ __global__ void __launch_bounds__(256) post_combine2_kernel(const TP* __restrict
         for (int q2 = 0; q2 < 4; ++q2)
 #pragma unroll
           for (int t = 0; t < V; ++t) {
-            TP tq = TP(0);
+            TP pr[7];
 #pragma unroll
-            for (int r2 = 0; r2 < 7; ++r2) tq = apply(coef_gamma(VARIANT, q2, r2), tq, p7[r2][t]);
+            for (int r2 = 0; r2 < 7; ++r2) pr[r2] = p7[r2][t];
+            const TP tq = combo7<VARIANT>(q2, pr);
 #pragma unroll
             for (int q1 = 0; q1 < 4; ++q1) acc[q1][q2][t].add(coef_gamma(VARIANT, q1, r1), tq);
           }
