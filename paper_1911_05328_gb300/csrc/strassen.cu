@@ -88,11 +88,14 @@ __global__ void __launch_bounds__(256) pre_combine_kernel(const T* __restrict__ 
       vload<T, V>(top + w + j, x1);
       vload<T, V>(bot + j, x2);
       vload<T, V>(bot + w + j, x3);
+      T sv[V][7];
+#pragma unroll
+      for (int t = 0; t < V; ++t) sums7<VARIANT, SIDE>(x0[t], x1[t], x2[t], x3[t], sv[t]);
 #pragma unroll
       for (int p = 0; p < 7; ++p) {
         T y[V];
 #pragma unroll
-        for (int t = 0; t < V; ++t) y[t] = combo4<VARIANT, SIDE>(p, x0[t], x1[t], x2[t], x3[t]);
+        for (int t = 0; t < V; ++t) y[t] = sv[t][p];
         vstore<T, V>(d + (int64_t)p * total + (int64_t)i * w + j, y);
       }
     }
@@ -211,6 +214,7 @@ struct PostAcc {
   TP v;
   __device__ __forceinline__ void init(TP x0) { v = x0; }
   __device__ __forceinline__ void add(int g, TP x) { v = apply(g, v, x); }
+  __device__ __forceinline__ void set(int g, TP x) { v = g > 0 ? x : -x; }  // first term, no old value
   __device__ __forceinline__ TP get() const { return v; }
 };
 template <typename TP>
@@ -218,6 +222,7 @@ struct PostAcc<TP, kSumF64> {
   double v;
   __device__ __forceinline__ void init(TP x0) { v = (double)x0; }
   __device__ __forceinline__ void add(int g, TP x) { v = apply(g, v, (double)x); }
+  __device__ __forceinline__ void set(int g, TP x) { v = g > 0 ? (double)x : -(double)x; }
   __device__ __forceinline__ TP get() const { return (TP)v; }
 };
 template <typename TP>
@@ -225,6 +230,10 @@ struct PostAcc<TP, kSumDoubleFloat> {
   float s, e;
   __device__ __forceinline__ void init(TP x0) {
     s = (float)x0;
+    e = 0.f;
+  }
+  __device__ __forceinline__ void set(int g, TP x) {
+    s = g > 0 ? (float)x : -(float)x;
     e = 0.f;
   }
   __device__ __forceinline__ void add(int g, TP x) {
@@ -256,6 +265,28 @@ __global__ void __launch_bounds__(256) post_combine_kernel(const TP* __restrict_
       TP x[7][V];
 #pragma unroll
       for (int p = 0; p < 7; ++p) vload<TP, V>(pp + (int64_t)p * total + e, x[p]);
+      if constexpr (MODE == kSumPlain) {
+        // plain sums: the variant's shared form of the four quadrant sums,
+        // then the old value where it is accumulated into
+        TP c[V][4];
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          TP xt[7];
+#pragma unroll
+          for (int p = 0; p < 7; ++p) xt[p] = x[p][t];
+          post4<VARIANT>(xt, c[t]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          TP* out = d + (int64_t)((q >> 1) * h + i) * dst_ld + (q & 1) * w + jv * V;
+          TP y[V];
+          if (accumulate) vload<TP, V>(out, y);
+#pragma unroll
+          for (int t = 0; t < V; ++t) y[t] = accumulate ? y[t] + c[t][q] : c[t][q];
+          vstore<TP, V>(out, y);
+        }
+        continue;
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         TP* out = d + (int64_t)((q >> 1) * h + i) * dst_ld + (q & 1) * w + jv * V;
@@ -266,7 +297,13 @@ __global__ void __launch_bounds__(256) post_combine_kernel(const TP* __restrict_
           PostAcc<TP, MODE> acc;
           acc.init(accumulate ? y[t] : TP(0));
 #pragma unroll
-          for (int p = 0; p < 7; ++p) acc.add(coef_gamma(VARIANT, q, p), x[p][t]);
+          for (int p = 0; p < 7; ++p) {
+            const int g = coef_gamma(VARIANT, q, p);
+            if (!accumulate && p == first_gamma_term(VARIANT, q))
+              acc.set(g, x[p][t]);
+            else
+              acc.add(g, x[p][t]);
+          }
           y[t] = acc.get();
         }
         vstore<TP, V>(out, y);
@@ -284,16 +321,19 @@ __global__ void __launch_bounds__(256) post_combine_kernel(const TP* __restrict_
 // identical.  emit(7 r1 + r2, value) receives each level-2 sum.
 template <int VARIANT, int SIDE, typename T, typename Emit>
 __device__ __forceinline__ void combine2(const T (&x)[4][4], Emit&& emit) {
+  // level-1 sums of the four sub-positions, then level-2 sums of each
+  T s1[4][7];
+#pragma unroll
+  for (int q2 = 0; q2 < 4; ++q2) {
+    const int u = q2 >> 1, v = q2 & 1;
+    sums7<VARIANT, SIDE>(x[u][v], x[u][2 + v], x[2 + u][v], x[2 + u][2 + v], s1[q2]);
+  }
 #pragma unroll
   for (int r1 = 0; r1 < 7; ++r1) {
-    T s1[4];
+    T s2[7];
+    sums7<VARIANT, SIDE>(s1[0][r1], s1[1][r1], s1[2][r1], s1[3][r1], s2);
 #pragma unroll
-    for (int q2 = 0; q2 < 4; ++q2) {
-      const int u = q2 >> 1, v = q2 & 1;
-      s1[q2] = combo4<VARIANT, SIDE>(r1, x[u][v], x[u][2 + v], x[2 + u][v], x[2 + u][2 + v]);
-    }
-#pragma unroll
-    for (int r2 = 0; r2 < 7; ++r2) emit(7 * r1 + r2, combo4<VARIANT, SIDE>(r2, s1[0], s1[1], s1[2], s1[3]));
+    for (int r2 = 0; r2 < 7; ++r2) emit(7 * r1 + r2, s2[r2]);
   }
 }
 
@@ -475,6 +515,47 @@ __global__ void __launch_bounds__(256) post_combine2_kernel(const TP* __restrict
   for (int i = blockIdx.x; i < h; i += gridDim.x) {
     for (int jv = threadIdx.x; jv < wv; jv += blockDim.x) {
       const int j = jv * V;
+      if constexpr (MODE == kSumPlain) {
+        // plain sums: the variant's shared form at both levels -- the level-2
+        // quadrant sums of each r1's seven products, then the level-1 sums of
+        // those over r1 -- and the old value where it is accumulated into
+        TP* drow = d + (int64_t)i * dst_ld + j;
+        const TP* src = pp + (int64_t)i * w + j;
+        TP t2[V][4][7];  // [column][level-2 quadrant][r1]
+#pragma unroll
+        for (int r1 = 0; r1 < 7; ++r1) {
+          TP p7[7][V];
+#pragma unroll
+          for (int r2 = 0; r2 < 7; ++r2, src += total) vload<TP, V>(src, p7[r2]);
+#pragma unroll
+          for (int t = 0; t < V; ++t) {
+            TP pr[7], c[4];
+#pragma unroll
+            for (int r2 = 0; r2 < 7; ++r2) pr[r2] = p7[r2][t];
+            post4<VARIANT>(pr, c);
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) t2[t][q2][r1] = c[q2];
+          }
+        }
+        TP c1[V][4][4];  // [column][level-2 quadrant][level-1 quadrant]
+#pragma unroll
+        for (int t = 0; t < V; ++t)
+#pragma unroll
+          for (int q2 = 0; q2 < 4; ++q2) post4<VARIANT>(t2[t][q2], c1[t][q2]);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            TP* out = drow + (int64_t)a * h * dst_ld + b * w;
+            const int q1 = (a >> 1) * 2 + (b >> 1), q2 = (a & 1) * 2 + (b & 1);
+            TP y[V];
+            if (accumulate) vload<TP, V>(out, y);
+#pragma unroll
+            for (int t = 0; t < V; ++t) y[t] = accumulate ? y[t] + c1[t][q2][q1] : c1[t][q2][q1];
+            vstore<TP, V>(out, y);
+          }
+        continue;
+      }
       PostAcc<TP, MODE> acc[4][4][V];  // [level-1 quadrant][level-2 quadrant][column]
       // sub-block (a, b) of the destination = level-1 quadrant
       // (a >> 1, b >> 1), level-2 quadrant (a & 1, b & 1)
@@ -504,7 +585,15 @@ __global__ void __launch_bounds__(256) post_combine2_kernel(const TP* __restrict
             for (int r2 = 0; r2 < 7; ++r2) pr[r2] = p7[r2][t];
             const TP tq = combo7<VARIANT>(q2, pr);
 #pragma unroll
-            for (int q1 = 0; q1 < 4; ++q1) acc[q1][q2][t].add(coef_gamma(VARIANT, q1, r1), tq);
+            for (int q1 = 0; q1 < 4; ++q1) {
+              // the first product of quadrant q1 sets the sum where there is
+              // no old value to add to (one FP64 addition fewer per output)
+              const int g = coef_gamma(VARIANT, q1, r1);
+              if (!accumulate && r1 == first_gamma_term(VARIANT, q1))
+                acc[q1][q2][t].set(g, tq);
+              else
+                acc[q1][q2][t].add(g, tq);
+            }
           }
       }
 #pragma unroll

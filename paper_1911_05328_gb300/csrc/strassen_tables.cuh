@@ -72,6 +72,13 @@ __device__ __forceinline__ T combo4(int r, T x0, T x1, T x2, T x3) {
   return acc;
 }
 
+// The first product r with gamma_qr != 0.
+__host__ __device__ constexpr int first_gamma_term(int v, int q) {
+  int r = 0;
+  while (r < 7 && coef_gamma(v, q, r) == 0) ++r;
+  return r;
+}
+
 // Post-addition of quadrant q: sum_r gamma_qr P_r in product order.
 template <int VARIANT, typename T>
 __device__ __forceinline__ T combo7(int q, const T (&p)[7]) {
@@ -80,6 +87,55 @@ __device__ __forceinline__ T combo7(int q, const T (&p)[7]) {
 #pragma unroll
   for (int r = 0; r < 7; ++r) acc = accumulate_term(coef_gamma(VARIANT, q, r), started, acc, p[r]);
   return acc;
+}
+
+// All seven operand sums of one side at one position (s[r] for product r).
+// Strassen-Winograd's sums share terms -- A side: s4 = A10 + A11, s5 = s4 -
+// A00, s6 = A00 - A10, s2 = A01 - s5; B side: s4 = B01 - B00, s5 = B11 - s4,
+// s6 = B11 - B01, s3 = s5 - B10 -- four additions instead of seven; other
+// variants sum each product's terms in quadrant order (combo4).
+template <int VARIANT, int SIDE, typename T>
+__device__ __forceinline__ void sums7(T x0, T x1, T x2, T x3, T (&s)[7]) {
+  if constexpr (VARIANT == 1 && SIDE == 0) {
+    s[0] = x0;
+    s[1] = x1;
+    s[3] = x3;
+    s[4] = x2 + x3;
+    s[5] = s[4] - x0;
+    s[6] = x0 - x2;
+    s[2] = x1 - s[5];
+  } else if constexpr (VARIANT == 1 && SIDE == 1) {
+    s[0] = x0;
+    s[1] = x2;
+    s[2] = x3;
+    s[4] = x1 - x0;
+    s[5] = x3 - s[4];
+    s[6] = x3 - x1;
+    s[3] = s[5] - x2;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 7; ++r) s[r] = combo4<VARIANT, SIDE>(r, x0, x1, x2, x3);
+  }
+}
+
+// The four quadrant sums of seven products (c[q] = sum_r gamma_qr p[r]).
+// Strassen-Winograd shares terms: u2 = p0 + p5, u3 = u2 + p6, u4 = u2 + p4;
+// c0 = p0 + p1, c1 = u4 + p2, c2 = u3 - p3, c3 = u3 + p4 -- seven additions
+// instead of ten.
+template <int VARIANT, typename T>
+__device__ __forceinline__ void post4(const T (&p)[7], T (&c)[4]) {
+  if constexpr (VARIANT == 1) {
+    const T u2 = p[0] + p[5];
+    const T u3 = u2 + p[6];
+    const T u4 = u2 + p[4];
+    c[0] = p[0] + p[1];
+    c[1] = u4 + p[2];
+    c[2] = u3 - p[3];
+    c[3] = u3 + p[4];
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = combo7<VARIANT>(q, p);
+  }
 }
 
 }  // namespace mmsr
