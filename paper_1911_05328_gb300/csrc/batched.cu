@@ -59,7 +59,10 @@ constexpr int kMaxBatch = 1 << 20;  // problems per call (tile counts stay in in
 #ifndef MMSR_B_CHUNK
 #define MMSR_B_CHUNK 8
 #endif
-constexpr int TBM = 128, TBN = 128, TBK = MMSR_B_BK, TSTAGES = MMSR_B_STAGES, TCHUNK = MMSR_B_CHUNK, TKA = 64;
+#ifndef MMSR_B_BN
+#define MMSR_B_BN 128
+#endif
+constexpr int TBM = 128, TBN = MMSR_B_BN, TBK = MMSR_B_BK, TSTAGES = MMSR_B_STAGES, TCHUNK = MMSR_B_CHUNK, TKA = 64;
 static_assert(TKA % TBK == 0 && (TBK == 32 || TBK == 64), "k-block / swizzle");
 // warp 0: TMA producer, warp 1: MMA issuer, warps 2..9: drain, warp 10:
 // tile scheduler (claims tile indices and finds their problems ahead of the
