@@ -22,8 +22,11 @@
 // lo 2^-56) in FP64.  FP64 arithmetic is used only for that final sum and
 // for split-K partials.
 //
-// Tile 128 x 64, k-blocks of 32 (64-byte swizzled rows), 2-stage TMA ring of
-// the 14 slice tiles, 7 x 64 TMEM columns, warp roles as in the FP32 mode.
+// Tile 128 x 64, k-blocks of 32 (64-byte swizzled rows), a TMA ring of the
+// slice tiles, one 64-column TMEM accumulator per order (adjacent), warp
+// roles as in the FP32 mode.  Within a k-step one MMA takes an A slice
+// against several stacked B slices (N up to 256), so each A slice is read
+// from shared memory once per four orders instead of once per product.
 // Each group accumulator has its own full / empty mbarrier pair: the drain
 // warps read group g as soon as its last product of a chunk has completed
 // (while the tensor core still works on groups g+1..6), and the MMA issuer
@@ -419,8 +422,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_f16(BM, BN, 1);
       constexpr uint32_t dhi = tc::desc_hi_sw64();
-      // The products are small (128 x 64 x 16, ~40 tensor-core cycles), so
-      // the issue loop is kept lean: descriptors are one 32-bit add of a
+      // The first k-step of a chunk overwrites the accumulators order by
+      // order, each as soon as the drain has read it: the 128 x 64 products
+      // of order g one by one.  Descriptors are one 32-bit add of a
       // compile-time offset to a per-stage base word.
       auto issue_group = [&](uint32_t a_lo, uint32_t b_lo, int kk, int g, bool overwrite) {
 #pragma unroll
@@ -429,6 +433,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t boff = (uint32_t)((g - sa) * B_TILE + kk * 32) >> 4;
           tc::mma_f16(tmem + (uint32_t)(g * BN), tc::desc_join(a_lo + aoff, dhi),
                       tc::desc_join(b_lo + boff, dhi), idesc, (overwrite && sa == 0) ? 0u : 1u);
+        }
+      };
+      // One 16-deep k-step of all the slice products with few, wide MMAs: A
+      // slice sa meets B slices 0..SL-1-sa, which lie one after another in
+      // the stage (one K-major operand of 64 (SL - sa) rows), and their
+      // products belong to orders sa..SL-1, whose accumulators are adjacent
+      // in TMEM.  So one MMA of N = 64 x (orders it covers) does up to four
+      // of the 128 x 64 products and reads its A slice from shared memory
+      // once for all of them (pieces of at most four orders: N <= 256).
+      // With six slices a k-step is 8 MMAs instead of 21 and reads 74 KB of
+      // operands instead of 126 KB.  Order sa is complete once the first
+      // piece of slice sa is issued (later slices do not reach it), which is
+      // where the chunk's last k-step signals its drain.
+      auto issue_stacked = [&](uint32_t a_lo, uint32_t b_lo, int kk, bool last_step) {
+#pragma unroll
+        for (int sa = 0; sa < kSlices; ++sa) {
+#pragma unroll
+          for (int g0 = sa; g0 < kGroups; g0 += 4) {
+            const int cnt = min(4, kGroups - g0);
+            const uint32_t aoff = (uint32_t)(sa * A_TILE + kk * 32) >> 4;
+            const uint32_t boff = (uint32_t)((g0 - sa) * B_TILE + kk * 32) >> 4;
+            tc::mma_f16(tmem + (uint32_t)(g0 * BN), tc::desc_join(a_lo + aoff, dhi),
+                        tc::desc_join(b_lo + boff, dhi), tc::idesc_f16(BM, BN * cnt, 1), 1u);
+            if (last_step && g0 == sa) tc::mma_commit(&acc_full[sa]);
+          }
         }
       };
       int it = 0;
@@ -458,26 +487,17 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (!aborted) issue_group(a_lo, b_lo, 0, g, true);
             }
             if (!aborted) {
-#pragma unroll
-              for (int g = 0; g < kGroups; ++g) {
-                issue_group(a_lo, b_lo, 1, g, false);
-                if (it == last - 1) tc::mma_commit(&acc_full[g]);
-              }
+              if (it == last - 1)
+                issue_stacked(a_lo, b_lo, 1, true);
+              else
+                issue_stacked(a_lo, b_lo, 1, false);
             }
           } else {
-#pragma unroll
-            for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 0, g, false);
-            if (it == last - 1) {
-              // the chunk's last product of group g is issued: signal it
-#pragma unroll
-              for (int g = 0; g < kGroups; ++g) {
-                issue_group(a_lo, b_lo, 1, g, false);
-                tc::mma_commit(&acc_full[g]);
-              }
-            } else {
-#pragma unroll
-              for (int g = 0; g < kGroups; ++g) issue_group(a_lo, b_lo, 1, g, false);
-            }
+            issue_stacked(a_lo, b_lo, 0, false);
+            if (it == last - 1)
+              issue_stacked(a_lo, b_lo, 1, true);
+            else
+              issue_stacked(a_lo, b_lo, 1, false);
           }
           tc::mma_commit(&empty[s]);
         }
