@@ -311,6 +311,12 @@ __device__ __forceinline__ double scale_pow2(double x, int s) {
   return ldexp(x, s);
 }
 
+// c + a b with a 64-bit sum, one instruction.
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
 __device__ __forceinline__ int exact_int(uint32_t fbits) {
   // fbits holds an integer-valued float of magnitude < 2^24: the conversion
   // is exact in any rounding mode.
@@ -519,19 +525,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         tc::fence_after_sync();
         constexpr int kb = Scheme<SL>::kBits;
-        const long long wgt = g < 3 ? (1ll << (kb * (2 - g))) : (1ll << (kb * (SL - 1 - g)));
-#pragma unroll
-        for (int half16 = 0; half16 < 2; ++half16) {
-          uint32_t r[16];
-          tc::tmem_ld_32x32b_x16(tmem + lane_base + (uint32_t)(g * BN + h * 32 + half16 * 16), r);
+        const int wgt = g < 3 ? (1 << (kb * (2 - g))) : (1 << (kb * (SL - 1 - g)));
+        {
+          // The tensor core waits for this at every chunk boundary, so it is
+          // kept to one 32-column TMEM load and one wait per order, and per
+          // value one conversion and one 32 x 32 + 64-bit multiply-add.
+          uint32_t r[32];
+          tc::tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)(g * BN + h * 32), r);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const long long v = (long long)exact_int(r[e]) * wgt;
+          for (int e = 0; e < 32; ++e) {
             if (g < 3)
-              hi[half16 * 16 + e] += v;
+              hi[e] = mad_wide(exact_int(r[e]), wgt, hi[e]);
             else
-              lo[half16 * 16 + e] += v;
+              lo[e] = mad_wide(exact_int(r[e]), wgt, lo[e]);
           }
         }
         tc::fence_before_sync();
