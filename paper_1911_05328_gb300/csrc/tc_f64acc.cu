@@ -83,6 +83,12 @@ struct FaCfg {
   static_assert((int64_t)CHUNK * BK * S::kOrderBound < (1 << 24), "chunk sums must stay exact in FP32");
   static_assert(SMEM <= 232448, "shared memory of one CTA");
   static_assert(SL * BN <= (int)TMEM_COLS, "one TMEM accumulator per digit order");
+  // orders with a second accumulator in the TMEM columns the others leave
+  // free (six slices: orders 0 and 1, all 512 columns in use; seven: none)
+  static constexpr int PP = SL == 6 ? 2 : 0;
+  static_assert(SL * BN + PP * BN <= (int)TMEM_COLS, "alternate buffers fit in TMEM");
+  static_assert(PP == 0 || SL * BN == 384, "alternate buffer at column 384");
+  static_assert((2 * STAGES + 2 * SL + 4 * PP + 1) * 8 + 16 <= 256, "barriers fit the reserved bytes");
 };
 static_assert(BK == 32, "the MMA issue loop covers two 16-deep k-steps per k-block");
 
@@ -336,14 +342,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                        const __grid_constant__ QuadOut64 quad) {
   using Cfg = FaCfg<SL>;
   constexpr int kSlices = SL, kGroups = SL, STAGES = Cfg::STAGES, CHUNK = Cfg::CHUNK;
+  // Orders below kPP alternate between two TMEM buffers from chunk to chunk
+  // (columns g*64 in even chunks, 384 + g*64 in odd ones: the columns the
+  // six orders leave free), so at a chunk boundary they restart at once in
+  // the other buffer and only orders kPP.. wait for the drain.  Orders 0 and
+  // 1 appear only in slice 0's and slice 1's products, so splitting the
+  // stacked MMAs at order kPP costs no extra MMA.
+  constexpr int kPP = Cfg::PP;
   constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;       // [kGroups]
+  uint64_t* acc_full = empty + STAGES;       // [kGroups] (orders kPP.. only)
   uint64_t* acc_empty = acc_full + kGroups;   // [kGroups]
-  uint64_t* quiesce = acc_empty + kGroups;    // after an abort: all issued MMAs done
+  uint64_t* pp_full = acc_empty + kGroups;    // [2][kPP]: alternating orders, per buffer
+  uint64_t* pp_empty = pp_full + 2 * kPP;     // [2][kPP]
+  uint64_t* quiesce = pp_empty + 2 * kPP;     // after an abort: all issued MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(quiesce + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   // producer state read after an abort (shared, so that no register stays
@@ -386,6 +401,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int g = 0; g < kGroups; ++g) {
       tc::mbar_init(&acc_full[g], 1);
       tc::mbar_init(&acc_empty[g], kDrain);
+    }
+    for (int i = 0; i < 2 * kPP; ++i) {
+      tc::mbar_init(&pp_full[i], 1);
+      tc::mbar_init(&pp_empty[i], kDrain);
     }
     tc::mbar_init(quiesce, 1);
     *abort_flag = 0;
@@ -445,20 +464,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       // slice sa meets B slices 0..SL-1-sa, which lie one after another in
       // the stage (one K-major operand of 64 (SL - sa) rows), and their
       // products belong to orders sa..SL-1, whose accumulators are adjacent
-      // in TMEM.  So one MMA of N = 64 x (orders it covers) does up to four
-      // of the 128 x 64 products and reads its A slice from shared memory
-      // once for all of them (pieces of at most four orders: N <= 256).
-      // With six slices a k-step is 8 MMAs instead of 21 and reads 74 KB of
-      // operands instead of 126 KB.  Order sa is complete once the first
-      // piece of slice sa is issued (later slices do not reach it), which is
-      // where the chunk's last k-step signals its drain.
-      auto issue_stacked = [&](uint32_t a_lo, uint32_t b_lo, int kk, bool last_step) {
+      // in TMEM (orders below kPP adjacent among themselves, in this chunk's
+      // buffer `pp_col`).  So one MMA of N = 64 x (orders it covers) does up
+      // to four of the 128 x 64 products and reads its A slice from shared
+      // memory once for all of them (pieces of at most four orders:
+      // N <= 256).  With six slices a k-step is 8 MMAs instead of 21 and
+      // reads 74 KB of operands instead of 126 KB.  Order sa is complete once
+      // the first piece of slice sa is issued (later slices do not reach
+      // it), which is where the chunk's last k-step signals its drain.
+      auto issue_stacked = [&](uint32_t a_lo, uint32_t b_lo, int kk, bool last_step, uint32_t pp_col,
+                               uint64_t* ppf) {
 #pragma unroll
         for (int sa = 0; sa < kSlices; ++sa) {
+          const uint32_t aoff = (uint32_t)(sa * A_TILE + kk * 32) >> 4;
+          if (sa < kPP) {
+            const uint32_t boff = (uint32_t)(kk * 32) >> 4;
+            tc::mma_f16(tmem + pp_col + (uint32_t)(sa * BN), tc::desc_join(a_lo + aoff, dhi),
+                        tc::desc_join(b_lo + boff, dhi), tc::idesc_f16(BM, BN * (kPP - sa), 1), 1u);
+            if (last_step) tc::mma_commit(&ppf[sa]);
+          }
 #pragma unroll
-          for (int g0 = sa; g0 < kGroups; g0 += 4) {
+          for (int g0 = sa < kPP ? kPP : sa; g0 < kGroups; g0 += 4) {
             const int cnt = min(4, kGroups - g0);
-            const uint32_t aoff = (uint32_t)(sa * A_TILE + kk * 32) >> 4;
             const uint32_t boff = (uint32_t)((g0 - sa) * B_TILE + kk * 32) >> 4;
             tc::mma_f16(tmem + (uint32_t)(g0 * BN), tc::desc_join(a_lo + aoff, dhi),
                         tc::desc_join(b_lo + boff, dhi), tc::idesc_f16(BM, BN * cnt, 1), 1u);
@@ -471,6 +498,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = 0; c < nchunks && !aborted; ++c) {
         const int first_it = it;
         const int last = min(nkb, (c + 1) * CHUNK);
+        const int buf = c & 1;
+        const uint32_t pp_col = buf ? (uint32_t)(kGroups * BN) : 0u;
+        uint64_t* ppf = pp_full + buf * kPP;
         for (; it < last && !aborted; ++it) {
           const int s = it % STAGES;
           const uint32_t round = (uint32_t)(it / STAGES);
@@ -482,28 +512,37 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
           const uint32_t a_lo = tc::desc_lo(base), b_lo = tc::desc_lo(base + kSlices * A_TILE);
           if (it == first_it) {
-            // first k-block of a chunk: overwrite each group, after the
-            // drain has read the previous chunk's G_g
+            // first k-block of a chunk: the alternating orders restart in this
+            // chunk's buffer (read by the drain two chunks ago), then every
+            // other order once the drain has read its previous chunk
+            if constexpr (kPP > 0) {
+              if (c >= 2) {
 #pragma unroll
-            for (int g = 0; g < kGroups; ++g) {
+                for (int g = 0; g < kPP; ++g)
+                  if (!aborted && !tc::mbar_wait(&pp_empty[buf * kPP + g], (uint32_t)((c >> 1) - 1) & 1u, abort_flag,
+                                                 &g_f64acc_status))
+                    aborted = true;
+                tc::fence_after_sync();
+              }
+              if (!aborted) {
+#pragma unroll
+                for (int sa = 0; sa < kPP; ++sa)
+                  tc::mma_f16(tmem + pp_col + (uint32_t)(sa * BN), tc::desc_join(a_lo + ((uint32_t)(sa * A_TILE) >> 4), dhi),
+                              tc::desc_join(b_lo, dhi), tc::idesc_f16(BM, BN * (kPP - sa), 1), sa == 0 ? 0u : 1u);
+              }
+            }
+#pragma unroll
+            for (int g = kPP; g < kGroups; ++g) {
               if (c >= 1 && !aborted) {
                 if (!tc::mbar_wait(&acc_empty[g], (c - 1) & 1u, abort_flag, &g_f64acc_status)) aborted = true;
                 tc::fence_after_sync();
               }
               if (!aborted) issue_group(a_lo, b_lo, 0, g, true);
             }
-            if (!aborted) {
-              if (it == last - 1)
-                issue_stacked(a_lo, b_lo, 1, true);
-              else
-                issue_stacked(a_lo, b_lo, 1, false);
-            }
+            if (!aborted) issue_stacked(a_lo, b_lo, 1, it == last - 1, pp_col, ppf);
           } else {
-            issue_stacked(a_lo, b_lo, 0, false);
-            if (it == last - 1)
-              issue_stacked(a_lo, b_lo, 1, true);
-            else
-              issue_stacked(a_lo, b_lo, 1, false);
+            issue_stacked(a_lo, b_lo, 0, false, pp_col, ppf);
+            issue_stacked(a_lo, b_lo, 1, it == last - 1, pp_col, ppf);
           }
           tc::mma_commit(&empty[s]);
         }
@@ -518,10 +557,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int e = 0; e < 32; ++e) hi[e] = lo[e] = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
+      // orders kPP.. first (the issuer waits for them), then the alternating
+      // ones, whose buffer is not needed again until two chunks later
 #pragma unroll
-      for (int g = 0; g < kGroups; ++g) {
+      for (int i = 0; i < kGroups; ++i) {
+        const int g = i + kPP < kGroups ? i + kPP : i + kPP - kGroups;
+        const bool alt = g < kPP;
+        uint64_t* fbar = alt ? &pp_full[(c & 1) * kPP + g] : &acc_full[g];
+        uint64_t* ebar = alt ? &pp_empty[(c & 1) * kPP + g] : &acc_empty[g];
+        const uint32_t par = alt ? (uint32_t)(c >> 1) & 1u : (uint32_t)c & 1u;
+        const uint32_t col = (alt && (c & 1)) ? (uint32_t)((kGroups + g) * BN) : (uint32_t)(g * BN);
         // warp-uniform verdict: the __syncwarp below needs every lane
-        ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[g], c & 1u, abort_flag, &g_f64acc_status));
+        ok = __all_sync(0xffffffffu, tc::mbar_wait(fbar, par, abort_flag, &g_f64acc_status));
         if (!ok) break;
         tc::fence_after_sync();
         constexpr int kb = Scheme<SL>::kBits;
@@ -531,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // kept to one 32-column TMEM load and one wait per order, and per
           // value one conversion and one 32 x 32 + 64-bit multiply-add.
           uint32_t r[32];
-          tc::tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)(g * BN + h * 32), r);
+          tc::tmem_ld_32x32b_x32(tmem + lane_base + col + (uint32_t)(h * 32), r);
           tc::tmem_wait_ld();
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
@@ -543,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&acc_empty[g]);
+        if (lane == 0) tc::mbar_arrive(ebar);
       }
     }
     const int64_t row = i0 + q * 32 + lane;
