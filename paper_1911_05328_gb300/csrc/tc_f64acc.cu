@@ -323,6 +323,34 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
   asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
   return d;
 }
+// RN((hi + lo 2^-W) 2^sc) -- the value scale_pow2(fma((double)lo, 2^-W,
+// (double)hi), sc) gives, bit for bit -- with one FP64 operation instead of
+// four (this GPU's FP64 pipe retires about two per clock per SM, and the
+// tile's tensor core idles while its epilogue runs).  With s = hi + (lo >> W)
+// and r = lo mod 2^W the value is s + r 2^-W; c = s - 2^(52-W) is an integer
+// below 2^53, so c 2^sc and (2^52 + r) 2^(sc-W) are doubles built exactly
+// from their bits, and one fma of them forms (s + r 2^-W) 2^sc exactly and
+// rounds it once.  Scales far from 1, or |c| >= 2^53, take the plain path.
+template <int W>
+__device__ __forceinline__ double combine_scaled(long long hi, long long lo, int sc) {
+  const long long s = hi + (lo >> W);
+  const long long r = lo & ((1ll << W) - 1);
+  const long long c = s - (1ll << (52 - W));
+  const unsigned long long a = c < 0 ? 0ull - (unsigned long long)c : (unsigned long long)c;
+  if (sc < -900 || sc > 900 || a >= (1ull << 53))
+    return scale_pow2(fma((double)lo, exp2_neg(W), (double)hi), sc);
+  double cs = 0.0;
+  if (a != 0) {
+    const int lz = __clzll((long long)a);  // >= 11
+    const unsigned long long mant = (a << (lz - 11)) & ((1ull << 52) - 1);
+    const unsigned long long be = (unsigned long long)((63 - lz) + 1023 + sc);
+    cs = __longlong_as_double((long long)((c < 0 ? (1ull << 63) : 0ull) | (be << 52) | mant));
+  }
+  const double drb = __longlong_as_double(0x4330000000000000ll | r);
+  const double f = __longlong_as_double((long long)(sc - W + 1023) << 52);
+  return fma(drb, f, cs);
+}
+
 __device__ __forceinline__ int exact_int(uint32_t fbits) {
   // fbits holds an integer-valued float of magnitude < 2^24: the conversion
   // is exact in any rounding mode.
@@ -596,16 +624,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t row = i0 + q * 32 + lane;
     if (row < m) {
       // C_ij = 2^(E_i + F_j) (hi 2^-kHiShift + lo 2^-kLoShift), rounded once
-      // (the fma; hi and lo convert exactly, the power-of-two scalings are
-      // exact away from the subnormal range)
+      // (combine_scaled: one fma of exact operands)
       constexpr int kHi = Scheme<SL>::kHiShift;
-      constexpr double kLoW = exp2_neg(Scheme<SL>::kLoShift - kHi);
       const int Ei = E[ra + row];
       double v[32];
 #pragma unroll
       for (int e = 0; e < 32; ++e) {
         const int64_t col = j0 + h * 32 + e;
-        v[e] = (ok && col < n) ? scale_pow2(fma((double)lo[e], kLoW, (double)hi[e]), Ei + F[rb + col] - kHi) : 0.0;
+        v[e] = (ok && col < n) ? combine_scaled<Scheme<SL>::kLoShift - kHi>(hi[e], lo[e], Ei + F[rb + col] - kHi) : 0.0;
       }
       const int64_t c0 = j0 + h * 32;
       if constexpr (QUAD) {
