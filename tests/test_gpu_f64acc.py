@@ -71,6 +71,23 @@ def test_row_and_column_scaling():
     assert rel_fro(C / rs / cs, ref / rs / cs) <= TOL
 
 
+def test_extreme_scales_both_epilogue_paths():
+    # row and column scales of 2^-500, 1 and 2^500: their sums reach 2^+-1000,
+    # beyond the range where the epilogue builds its fma operands from bits
+    # (it then takes the plain FP64 path); every output stays a normal double
+    rng = np.random.default_rng(93)
+    m, n, k = 192, 160, 384
+    A, B = inputs.uniform_f64(m, k, n, seed=94)
+    A *= np.exp2(rng.choice([-500.0, 0.0, 500.0], size=(m, 1)))
+    B *= np.exp2(rng.choice([-500.0, 0.0, 500.0], size=(1, n)))
+    C = run(A, B)
+    ref = oracle.mm_f64(A, B)
+    rs = np.abs(ref).max(axis=1, keepdims=True)
+    cs = np.abs(ref / rs).max(axis=0, keepdims=True)
+    assert np.all(np.isfinite(C))
+    assert rel_fro(C / rs / cs, ref / rs / cs) <= TOL
+
+
 @pytest.mark.parametrize("parts", [2, 5])
 def test_split_k(parts):
     m, n, k = 256, 192, 4096
