@@ -54,8 +54,17 @@ int read_f64acc_status(int* status);
 // `batches` stacked FP64-accuracy products (Strassen leaves): A is batches x
 // m x k, B batches x k x n, C batches x m x n, all contiguous.
 size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches, int slices);
+// maxima_ready: the row exponents E and column maxima Fmax of A and B
+// (f64acc_maxima_buffers) were already written by the pass that produced
+// them, so the split skips its own passes over A's rows and B's columns.
 int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, int64_t n, int64_t k,
-                       int batches, int slices, void* ws, cudaStream_t st);
+                       int batches, int slices, void* ws, cudaStream_t st, bool maxima_ready = false);
+// Where the split of those stacked products keeps, inside ws, the row
+// exponents E (int, batches x m: frexp's exponent of each row's max |a|)
+// and the column maxima Fmax (|b| bit patterns, batches x n, to be folded
+// in with atomicMax from zero).
+void f64acc_maxima_buffers(int64_t m, int64_t n, int64_t k, int batches, int slices, void* ws, int** E,
+                           unsigned long long** Fmax);
 int read_batched_status(int* status);
 // Test switches (one-shot): the first CTA of the next launch of the FP32
 // GEMM / FP64-accuracy GEMM / batched FP32 kernel skips its first ring
@@ -86,7 +95,7 @@ using QuadOut64 = QuadOutT<double>;
 // `batches` stacked products once, then launches whose entries add their
 // products into blocks of C (QuadOut64); `ws` as for run_f64acc_batched
 int f64acc_prepare_batched(const double* A, const double* B, int64_t m, int64_t n, int64_t k, int batches,
-                           int slices, void* ws, cudaStream_t st);
+                           int slices, void* ws, cudaStream_t st, bool maxima_ready = false);
 int f64acc_gemm_quad(int64_t m, int64_t n, int64_t k, int batches, int slices, void* ws, const QuadOut64& quad,
                      cudaStream_t st);
 

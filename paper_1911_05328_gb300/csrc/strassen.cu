@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "f64bits.cuh"
 #include "internal.h"
 #include "strassen_tables.cuh"
 
@@ -363,6 +364,122 @@ __global__ void __launch_bounds__(256) pre_combine2_kernel(const T* __restrict__
         o += total;
       });
     }
+  }
+}
+
+// The last two operand levels of the FP64-accuracy mode, also producing
+// what the digit split needs first: frexp's exponent of each leaf row's
+// max |a| (A side) or each leaf column's max |b| (B side), bit-identical to
+// the split's own passes over the leaf operands, which are then skipped.
+// Each thread keeps, per leaf, the maximum of the high words of |x|
+// (abs_hi_word); a line whose maximum high word is zero is re-scanned in
+// full from the values just written.
+
+// A side: each block owns whole rows of the 49 leaf operands, so it reduces
+// each row's maximum itself and stores the row exponent E[leaf][row].
+template <int VARIANT>
+__global__ void __launch_bounds__(256) pre_combine2_rowexp_kernel(const double* __restrict__ src, int64_t src_ld,
+                                                                  int64_t src_stride, int h, int w,
+                                                                  double* __restrict__ dst, int* __restrict__ E) {
+  __shared__ uint32_t red[8][49];
+  __shared__ uint32_t hi_max[49];
+  __shared__ unsigned long long rescan_max[49];
+  const int r = blockIdx.y;
+  const double* s = src + (int64_t)r * src_stride;
+  const int64_t total = (int64_t)h * w;
+  double* d = dst + (int64_t)r * 49 * total;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int i = blockIdx.x; i < h; i += gridDim.x) {
+    uint32_t mx[49];
+#pragma unroll
+    for (int q = 0; q < 49; ++q) mx[q] = 0;
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+      double x[4][4];
+      const double* row = s + (int64_t)i * src_ld + j;
+#pragma unroll
+      for (int a = 0; a < 4; ++a, row += (int64_t)h * src_ld)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) x[a][b] = row[b * w];
+      double* o = d + (int64_t)i * w + j;
+      combine2<VARIANT, 0>(x, [&](int q, double v) {
+        *o = v;
+        o += total;
+        mx[q] = max(mx[q], abs_hi_word(v));
+      });
+    }
+#pragma unroll
+    for (int q = 0; q < 49; ++q) {
+      uint32_t v = mx[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();  // also orders this block's stores of row i before the re-scan below
+    for (int q = threadIdx.x; q < 49; q += blockDim.x) {
+      uint32_t v = 0;
+      for (int u = 0; u < nwarps; ++u) v = max(v, red[u][q]);
+      hi_max[q] = v;
+      rescan_max[q] = 0;
+    }
+    __syncthreads();
+    // rows whose high words are all zero: the exact maximum of the patterns
+    // (hi_max is not written below, so every warp takes the same branches)
+    for (int q = 0; q < 49; ++q) {
+      if (hi_max[q] != 0) continue;
+      const double* line = d + (int64_t)q * total + (int64_t)i * w;
+      unsigned long long b = 0;
+      for (int j = threadIdx.x; j < w; j += blockDim.x) b = max(b, abs_bits(line[j]));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, off));
+      if (lane == 0 && b != 0) atomicMax(&rescan_max[q], b);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 49; q += blockDim.x)
+      E[(int64_t)(49 * r + q) * h + i] =
+          line_exponent(hi_max[q] != 0 ? (unsigned long long)hi_max[q] << 32 : rescan_max[q]);
+    __syncthreads();
+  }
+}
+
+// B side: a thread owns one column of a band of rows and folds each leaf
+// column's maximum pattern into Fmax[leaf][column] (zeroed beforehand) with
+// an atomic max.
+template <int VARIANT>
+__global__ void __launch_bounds__(256) pre_combine2_colmax_kernel(const double* __restrict__ src, int64_t src_ld,
+                                                                  int64_t src_stride, int h, int w, int band,
+                                                                  double* __restrict__ dst,
+                                                                  unsigned long long* __restrict__ Fmax) {
+  const int r = blockIdx.z;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= w) return;
+  const double* s = src + (int64_t)r * src_stride;
+  const int64_t total = (int64_t)h * w;
+  double* d = dst + (int64_t)r * 49 * total;
+  const int i0 = blockIdx.y * band, i1 = min(h, i0 + band);
+  uint32_t mx[49];
+#pragma unroll
+  for (int q = 0; q < 49; ++q) mx[q] = 0;
+  for (int i = i0; i < i1; ++i) {
+    double x[4][4];
+    const double* row = s + (int64_t)i * src_ld + j;
+#pragma unroll
+    for (int a = 0; a < 4; ++a, row += (int64_t)h * src_ld)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) x[a][b] = row[b * w];
+    double* o = d + (int64_t)i * w + j;
+    combine2<VARIANT, 1>(x, [&](int q, double v) {
+      *o = v;
+      o += total;
+      mx[q] = max(mx[q], abs_hi_word(v));
+    });
+  }
+  unsigned long long* fm = Fmax + (int64_t)49 * r * w + j;
+#pragma unroll
+  for (int q = 0; q < 49; ++q) {
+    unsigned long long b = (unsigned long long)mx[q] << 32;
+    if (b == 0)  // the thread's own stores, re-read in full
+      for (int i = i0; i < i1; ++i) b = max(b, abs_bits(d[(int64_t)q * total + (int64_t)i * w + j]));
+    if (b != 0) atomicMax(fm + (int64_t)q * w, b);
   }
 }
 
@@ -790,6 +907,36 @@ cudaError_t launch_pre_combine2(const T* src, int64_t src_ld, int64_t src_stride
   return cudaGetLastError();
 }
 
+// The last two FP64 operand levels with the split's line maxima (above):
+// side 0 stores row exponents E, side 1 folds column maxima into Fmax.
+cudaError_t launch_pre_combine2_maxima(const double* src, int64_t src_ld, int64_t src_stride, int64_t h,
+                                       int64_t w, int64_t R, double* dst, int variant, int side, int* E,
+                                       unsigned long long* Fmax, cudaStream_t st) {
+  const int hh = (int)h, ww = (int)w;
+  if (side == 0) {
+    const int threads = row_threads(w);
+    const dim3 g(rows_grid(h, R, threads), (unsigned)R);
+    if (variant == 0)
+      pre_combine2_rowexp_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, dst, E);
+    else
+      pre_combine2_rowexp_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, dst, E);
+  } else {
+    // column blocks x bands of rows: about four blocks per SM in all
+    const int threads = row_threads(w);
+    const int64_t gx = (w + threads - 1) / threads;
+    int64_t gy = ((int64_t)num_sms() * 4 + gx * R - 1) / (gx * R);
+    gy = gy < 1 ? 1 : (gy > h ? h : gy);
+    const int band = (int)((h + gy - 1) / gy);
+    gy = (h + band - 1) / band;
+    const dim3 g((unsigned)gx, (unsigned)gy, (unsigned)R);
+    if (variant == 0)
+      pre_combine2_colmax_kernel<0><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, band, dst, Fmax);
+    else
+      pre_combine2_colmax_kernel<1><<<g, threads, 0, st>>>(src, src_ld, src_stride, hh, ww, band, dst, Fmax);
+  }
+  return cudaGetLastError();
+}
+
 template <typename TP, int MODE>
 cudaError_t launch_post_combine2(const TP* P, int64_t h, int64_t w, int64_t R, TP* dst, int64_t dst_ld,
                                  int64_t dst_stride, int variant, int accumulate, cudaStream_t st) {
@@ -876,10 +1023,14 @@ cudaError_t expand_f32(int L, int variant, int side, const float* X, int64_t row
   return cudaSuccess;
 }
 
-// Operand side, FP64 mode: FP64 stacks all the way to the leaves.
+// Operand side, FP64 mode: FP64 stacks all the way to the leaves.  With E
+// (side 0) or Fmax (side 1) given, a last pass of two levels also leaves the
+// FP64-accuracy split's row exponents or column maxima and sets *maxima.
 cudaError_t expand_f64(int L, int variant, int side, const double* X, int64_t rows, int64_t cols,
                        int64_t ld, uint8_t* ws, const StrassenLayout& S, double* leaf,
-                       cudaStream_t st) {
+                       cudaStream_t st, int* E = nullptr, unsigned long long* Fmax = nullptr,
+                       bool* maxima = nullptr) {
+  if (maxima) *maxima = false;
   const double* src = X;
   int64_t src_ld = ld, src_stride = 0;
   int pass = 0;
@@ -888,7 +1039,11 @@ cudaError_t expand_f64(int L, int variant, int side, const double* X, int64_t ro
     const int lend = l + span - 1;
     const int64_t h = rows >> lend, w = cols >> lend, R = pw7(l - 1);
     double* dst = (lend < L) ? reinterpret_cast<double*>(ws + ((pass & 1) ? S.off_pp1 : 0)) : leaf;
-    if (span == 2)
+    if (span == 2 && lend == L && maxima && (side == 0 ? E != nullptr : Fmax != nullptr)) {
+      if (side == 1) MMSR_CUDA_TRY(cudaMemsetAsync(Fmax, 0, (size_t)(R * 49) * (size_t)w * 8, st));
+      MMSR_CUDA_TRY(launch_pre_combine2_maxima(src, src_ld, src_stride, h, w, R, dst, variant, side, E, Fmax, st));
+      *maxima = true;
+    } else if (span == 2)
       MMSR_CUDA_TRY(launch_pre_combine2<double>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
     else
       MMSR_CUDA_TRY(launch_pre_combine<double>(src, src_ld, src_stride, h, w, R, dst, variant, side, st));
@@ -986,16 +1141,26 @@ int run_view(int levels, int variant, int sr, int64_t m, int64_t n, int64_t k, c
     double* la = reinterpret_cast<double*>(w + S.off_ahi);
     double* lb = reinterpret_cast<double*>(w + S.off_bhi);
     double* P = reinterpret_cast<double*>(w + S.off_p);
+    // FP64-accuracy leaves: the last operand pass leaves the digit split's
+    // line maxima where the split reads them
+    const bool fa = sr == MM_SR_PLUS_TIMES_F64ACC;
+    const int slices = f64acc_slices_for_levels(levels);
+    int* E = nullptr;
+    unsigned long long* Fmax = nullptr;
+    if (fa) f64acc_maxima_buffers(S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, &E, &Fmax);
+    bool max_a = false, max_b = false;
     {
       TraceScope tr(kTrStrassenCombine, st);
-      e = expand_f64(levels, variant, 0, static_cast<const double*>(A), m, k, lda, w, S, la, st);
+      e = expand_f64(levels, variant, 0, static_cast<const double*>(A), m, k, lda, w, S, la, st, E, nullptr,
+                     fa ? &max_a : nullptr);
       if (e == cudaSuccess)
-        e = expand_f64(levels, variant, 1, static_cast<const double*>(B), k, n, ldb, w, S, lb, st);
+        e = expand_f64(levels, variant, 1, static_cast<const double*>(B), k, n, ldb, w, S, lb, st, nullptr, Fmax,
+                       fa ? &max_b : nullptr);
     }
     if (e == cudaSuccess) {
-      if (sr == MM_SR_PLUS_TIMES_F64ACC) {
-        const int rc = run_f64acc_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, f64acc_slices_for_levels(levels),
-                                          w + S.off_leafws, st);
+      if (fa) {
+        const int rc = run_f64acc_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, st,
+                                          max_a && max_b);
         if (rc != MM_OK) return rc;
       } else {
         e = launch_dfma_batched(la, lb, P, S.mL, S.nL, S.kL, (int)S.leaves, st);
@@ -1216,14 +1381,20 @@ int run_tar_view(int L, int variant, int sr, int64_t m, int64_t n, int64_t k, co
   }
   double* la = reinterpret_cast<double*>(w + S.off_ahi);
   double* lb = reinterpret_cast<double*>(w + S.off_bhi);
+  const int slices = f64acc_slices_for_levels(L);
+  int* E = nullptr;
+  unsigned long long* Fmax = nullptr;
+  f64acc_maxima_buffers(S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, &E, &Fmax);
+  bool max_a = false, max_b = false;
   {
     TraceScope tr(kTrStrassenCombine, st);
-    e = expand_f64(L, variant, 0, static_cast<const double*>(A), m, k, lda, w, S, la, st);
-    if (e == cudaSuccess) e = expand_f64(L, variant, 1, static_cast<const double*>(B), k, n, ldb, w, S, lb, st);
+    e = expand_f64(L, variant, 0, static_cast<const double*>(A), m, k, lda, w, S, la, st, E, nullptr, &max_a);
+    if (e == cudaSuccess)
+      e = expand_f64(L, variant, 1, static_cast<const double*>(B), k, n, ldb, w, S, lb, st, nullptr, Fmax, &max_b);
   }
   if (e != cudaSuccess) return report_cuda(e, "TAR-Strassen operand pass");
-  const int slices = f64acc_slices_for_levels(L);
-  int rc = f64acc_prepare_batched(la, lb, S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, st);
+  int rc = f64acc_prepare_batched(la, lb, S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, st,
+                                  max_a && max_b);
   if (rc != MM_OK) return rc;
   e = tar_waves_run<double>(TP, S, static_cast<double*>(C), ldc, [&](const QuadOut64& qo) {
     return f64acc_gemm_quad(S.mL, S.nL, S.kL, (int)S.leaves, slices, w + S.off_leafws, qo, st) == MM_OK

@@ -35,6 +35,7 @@
 #include <cuda_bf16.h>
 #include <string.h>
 
+#include "f64bits.cuh"
 #include "internal.h"
 #include "tcgen05.cuh"
 
@@ -98,22 +99,7 @@ static_assert(BK == 32, "the MMA issue loop covers two 16-deep k-steps per k-blo
 // clock per SM, so maxima, exponents and the scaled rounding are read from
 // the exponent and significand fields instead.
 
-// |x| as a bit pattern: for finite doubles the unsigned order of these
-// patterns is the numeric order of |x|.
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-}
-
-// Exponent E with max|x| < 2^E, from the bit pattern of max|x| (0 for an
-// all-zero line): frexp's exponent, max|x| = f 2^E with f in [0.5, 1) --
-// the exponent field minus 1022 for a normal number, the position of the
-// leading significand bit for a subnormal one (value = b 2^-1074).
-__device__ __forceinline__ int line_exponent(unsigned long long b) {
-  if (b == 0) return 0;
-  const int ex = (int)(b >> 52);
-  if (ex != 0) return ex - 1022;
-  return (63 - __clzll((long long)b)) - 1073;
-}
+// abs_bits and line_exponent: f64bits.cuh.
 
 // Row maxima of A (one warp per row), stored as the exponent E of the row.
 __global__ void __launch_bounds__(256) row_exponent_kernel(const double* __restrict__ A, int64_t m,
@@ -732,18 +718,21 @@ F64AccLayout layout(int64_t m, int64_t n, int64_t k, int slices, int64_t batches
 // rows, B: batches matrices of k x n).
 template <int SL>
 int f64acc_prepare_t(int64_t m, int64_t n, int64_t k, const double* A, const double* B, uint8_t* w,
-                     const F64AccLayout& L, int batches, cudaStream_t st) {
+                     const F64AccLayout& L, int batches, cudaStream_t st, bool maxima_ready = false) {
   auto* SA = reinterpret_cast<__nv_bfloat16*>(w);
   auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
   int* E = reinterpret_cast<int*>(w + L.off_e);
   int* F = reinterpret_cast<int*>(w + L.off_f);
   const int64_t rows_a = (int64_t)batches * m;
   TraceScope tr(kTrSplitF64Slices, st);
-  row_exponent_kernel<<<(unsigned)((rows_a + 7) / 8), 256, 0, st>>>(A, rows_a, k, E);
   auto* Fmax = reinterpret_cast<unsigned long long*>(w + L.off_fmax);
-  MMSR_TRY_STATUS(cudaMemsetAsync(Fmax, 0, (size_t)batches * n * 8, st));
-  col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256, 0,
-                   st>>>(B, k, n, Fmax);
+  if (!maxima_ready) {
+    // (otherwise the operand pass that wrote A and B left E and Fmax)
+    row_exponent_kernel<<<(unsigned)((rows_a + 7) / 8), 256, 0, st>>>(A, rows_a, k, E);
+    MMSR_TRY_STATUS(cudaMemsetAsync(Fmax, 0, (size_t)batches * n * 8, st));
+    col_max_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)(k > 0 ? (k + 255) / 256 : 1), (unsigned)batches), 256,
+                     0, st>>>(B, k, n, Fmax);
+  }
   col_exponent_kernel<<<(unsigned)(((int64_t)batches * n + 255) / 256), 256, 0, st>>>(Fmax, (int64_t)batches * n, F);
   {
     const int64_t gx = std::max<int64_t>(1, (L.Kp + 1023) / 1024);
@@ -789,8 +778,9 @@ int f64acc_gemm_t(int64_t m, int64_t n, uint8_t* w, const F64AccLayout& L, int b
 
 template <int SL>
 int f64acc_core_t(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C,
-                  uint8_t* w, const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
-  int rc = f64acc_prepare_t<SL>(m, n, k, A, B, w, L, batches, st);
+                  uint8_t* w, const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st,
+                  bool maxima_ready) {
+  int rc = f64acc_prepare_t<SL>(m, n, k, A, B, w, L, batches, st, maxima_ready);
   if (rc != MM_OK) return rc;
   QuadOut64 none;
   memset(&none, 0, sizeof(none));
@@ -801,9 +791,10 @@ int f64acc_core_t(int64_t m, int64_t n, int64_t k, const double* A, const double
 }
 
 int f64acc_core(int64_t m, int64_t n, int64_t k, const double* A, const double* B, double* C, uint8_t* w,
-                const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st) {
-  return L.slices == 6 ? f64acc_core_t<6>(m, n, k, A, B, C, w, L, batches, s, part, st)
-                       : f64acc_core_t<7>(m, n, k, A, B, C, w, L, batches, s, part, st);
+                const F64AccLayout& L, int batches, int s, double* part, cudaStream_t st,
+                bool maxima_ready = false) {
+  return L.slices == 6 ? f64acc_core_t<6>(m, n, k, A, B, C, w, L, batches, s, part, st, maxima_ready)
+                       : f64acc_core_t<7>(m, n, k, A, B, C, w, L, batches, s, part, st, maxima_ready);
 }
 
 }  // namespace
@@ -852,16 +843,23 @@ size_t f64acc_batched_bytes(int64_t m, int64_t n, int64_t k, int batches, int sl
 }
 
 int run_f64acc_batched(const double* A, const double* B, double* C, int64_t m, int64_t n, int64_t k,
-                       int batches, int slices, void* ws, cudaStream_t st) {
+                       int batches, int slices, void* ws, cudaStream_t st, bool maxima_ready) {
   const F64AccLayout L = layout(m, n, k, slices, batches);
-  return f64acc_core(m, n, k, A, B, C, static_cast<uint8_t*>(ws), L, batches, 1, nullptr, st);
+  return f64acc_core(m, n, k, A, B, C, static_cast<uint8_t*>(ws), L, batches, 1, nullptr, st, maxima_ready);
 }
 
 int f64acc_prepare_batched(const double* A, const double* B, int64_t m, int64_t n, int64_t k, int batches,
-                           int slices, void* ws, cudaStream_t st) {
+                           int slices, void* ws, cudaStream_t st, bool maxima_ready) {
   const F64AccLayout L = layout(m, n, k, slices, batches);
-  return slices == 6 ? f64acc_prepare_t<6>(m, n, k, A, B, static_cast<uint8_t*>(ws), L, batches, st)
-                     : f64acc_prepare_t<7>(m, n, k, A, B, static_cast<uint8_t*>(ws), L, batches, st);
+  return slices == 6 ? f64acc_prepare_t<6>(m, n, k, A, B, static_cast<uint8_t*>(ws), L, batches, st, maxima_ready)
+                     : f64acc_prepare_t<7>(m, n, k, A, B, static_cast<uint8_t*>(ws), L, batches, st, maxima_ready);
+}
+
+void f64acc_maxima_buffers(int64_t m, int64_t n, int64_t k, int batches, int slices, void* ws, int** E,
+                           unsigned long long** Fmax) {
+  const F64AccLayout L = layout(m, n, k, slices, batches);
+  *E = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + L.off_e);
+  *Fmax = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(ws) + L.off_fmax);
 }
 
 int f64acc_gemm_quad(int64_t m, int64_t n, int64_t k, int batches, int slices, void* ws, const QuadOut64& quad,

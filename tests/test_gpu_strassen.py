@@ -147,6 +147,35 @@ def test_f64acc_uniform_tolerance_every_level(variant, L):
     assert err <= 1e-12, err
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_f64acc_zero_and_scaled_leaf_lines(variant, L):
+    # The last operand pass also produces the digit split's row exponents and
+    # column maxima.  Zero rows of A at one position in every row block of
+    # the leaves' size (and zero columns of B likewise) make zero leaf lines
+    # -- the pass's full re-scan -- and zero lines of C; rows and columns
+    # scaled by 2^-900 and 2^600 move the exponents far from 0.
+    m, k, n = 512, 1024, 384
+    h, w = m >> L, n >> L
+    A, B = inputs.uniform_f64(m, k, n, seed=7)
+    zr, sr_ = [5 % h + a * h for a in range(1 << L)], [(17 % h) + a * h for a in range(1 << L)]
+    zc, sc_ = [3 % w + b * w for b in range(1 << L)], [(11 % w) + b * w for b in range(1 << L)]
+    A[zr] = 0.0
+    A[sr_] *= 2.0 ** -900
+    B[:, zc] = 0.0
+    B[:, sc_] *= 2.0 ** 600
+    C = run(L, variant, mmsr.MM_SR_PLUS_TIMES_F64ACC, A, B)
+    ref = oracle.mm_f64(A, B)
+    assert not np.any(C[zr]) and not np.any(C[:, zc])
+    keep_r = np.setdiff1d(np.arange(m), zr)
+    keep_c = np.setdiff1d(np.arange(n), zc)
+    Ck, Rk = C[np.ix_(keep_r, keep_c)], ref[np.ix_(keep_r, keep_c)]
+    rs = np.abs(Rk).max(axis=1, keepdims=True)
+    cs = np.abs(Rk / rs).max(axis=0, keepdims=True)
+    err = rel_fro(Ck / rs / cs, Rk / rs / cs)
+    assert err <= 1e-12, err
+
+
 def test_full_size_n16384_f64acc_sampled_rows():
     import torch
 
