@@ -248,26 +248,28 @@ __global__ void __launch_bounds__(256) digits_rows_kernel(const double* __restri
 
 // B (k x n, batch blockIdx.z of a contiguous stack of `batches`) -> SL
 // digit slices of B^T: slice s holds batches*n rows of pitch Kp, batch b at
-// rows [b*n, (b+1)*n).  Via a 32 x 32 shared tile; each thread converts two
-// adjacent k of one column and stores one bf16 pair per slice.
+// rows [b*n, (b+1)*n).  Via a 64 (k) x 32 (n) shared tile; each thread
+// converts four adjacent k of one column and stores 8 bytes per slice, so a
+// warp writes two full 128-byte rows of each slice.
 template <int SL>
 __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restrict__ B, int64_t k,
                                                           int64_t n, int64_t Kp,
                                                           const int* __restrict__ F,
                                                           __nv_bfloat16* __restrict__ S, int batches) {
-  __shared__ double tile[32][33];
+  __shared__ double tile[64][33];
   const int64_t b = blockIdx.z;
   B += b * k * n;
   F += b * n;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int pk = threadIdx.x & 15, pn = threadIdx.x >> 4;  // k pair, n row (of 16) when storing
-  const int64_t k0 = (int64_t)blockIdx.x * 32;
+  const int pk = threadIdx.x & 15, pn = threadIdx.x >> 4;  // k quad, n row (of 16) when storing
+  const int64_t k0 = (int64_t)blockIdx.x * 64;
   const int64_t slice = (int64_t)batches * n * Kp;
+  const bool full_k = k0 + 64 <= Kp;  // Kp % 32 == 0: the last block may hold 32 k
   // n-tiles with stride gridDim.y (the grid's y extent is capped at 65535)
   for (int64_t n0 = (int64_t)blockIdx.y * 32; n0 < n; n0 += (int64_t)gridDim.y * 32) {
     __syncthreads();  // the previous n-tile's readers are done with `tile`
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < 8; ++it) {
       const int kk = ty + 8 * it;
       const int64_t gk = k0 + kk, gn = n0 + tx;
       tile[kk][tx] = (gk < k && gn < n) ? B[gk * n + gn] : 0.0;
@@ -276,16 +278,21 @@ __global__ void __launch_bounds__(256) digits_cols_kernel(const double* __restri
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
       const int nn = pn + 16 * it;
-      const int64_t gn = n0 + nn, gk = k0 + 2 * pk;  // k0 + 32 <= Kp: gk + 1 < Kp
-      if (gn >= n) continue;
-      float d0[SL], d1[SL];
+      const int64_t gn = n0 + nn, gk = k0 + 4 * pk;
+      if (gn >= n || (!full_k && 4 * pk >= 32)) continue;
+      float d[4][SL];
       const int Fj = F[gn];
-      digits<SL>(tile[2 * pk][nn], Fj, d0);
-      digits<SL>(tile[2 * pk + 1][nn], Fj, d1);
 #pragma unroll
-      for (int s = 0; s < SL; ++s)
-        *reinterpret_cast<__nv_bfloat162*>(S + s * slice + (b * n + gn) * Kp + gk) =
-            __floats2bfloat162_rn(d0[s], d1[s]);
+      for (int u = 0; u < 4; ++u) digits<SL>(tile[4 * pk + u][nn], Fj, d[u]);
+#pragma unroll
+      for (int s = 0; s < SL; ++s) {
+        uint2 v;
+        const __nv_bfloat162 p0 = __floats2bfloat162_rn(d[0][s], d[1][s]);
+        const __nv_bfloat162 p1 = __floats2bfloat162_rn(d[2][s], d[3][s]);
+        memcpy(&v.x, &p0, 4);
+        memcpy(&v.y, &p1, 4);
+        *reinterpret_cast<uint2*>(S + s * slice + (b * n + gn) * Kp + gk) = v;
+      }
     }
   }
 }
@@ -743,8 +750,8 @@ int f64acc_prepare_t(int64_t m, int64_t n, int64_t k, const double* A, const dou
   // n-tiles per block: enough blocks to fill the GPU a few times over, each
   // walking several tiles
   const int64_t tiles_n = (n + 31) / 32;
-  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 8192 / (L.Kp / 32 * batches))));
-  dim3 g((unsigned)(L.Kp / 32), (unsigned)std::min<int64_t>(gy, kMaxGridY), (unsigned)batches);
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(tiles_n, std::max<int64_t>(1, 8192 / ((L.Kp + 63) / 64 * batches))));
+  dim3 g((unsigned)((L.Kp + 63) / 64), (unsigned)std::min<int64_t>(gy, kMaxGridY), (unsigned)batches);
   digits_cols_kernel<SL><<<g, 256, 0, st>>>(B, k, n, L.Kp, F, SB, batches);
   MMSR_TRY_STATUS(cudaGetLastError());
   return MM_OK;
