@@ -333,6 +333,41 @@ class ErrBook:
         self.cache.clear()
 
 
+def kernels_per_call(torch, call):
+    """Kernel launches of one call, counted from a CUDA graph that captures
+    it on a side stream (nothing is launched).  call(stream_handle) issues
+    the work; None when this runtime or the call cannot be captured."""
+    import ctypes
+    try:
+        rt = ctypes.CDLL("libcudart.so.13")
+    except OSError:
+        return None
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    h = ctypes.c_void_p(side.cuda_stream)
+    if rt.cudaStreamBeginCapture(h, ctypes.c_int(2)) != 0:  # relaxed capture mode
+        return None
+    graph = ctypes.c_void_p()
+    try:
+        call(int(side.cuda_stream))
+    finally:
+        rc = rt.cudaStreamEndCapture(h, ctypes.byref(graph))
+    if rc != 0 or not graph.value:
+        rt.cudaGetLastError()
+        return None
+    count = ctypes.c_size_t(0)
+    rt.cudaGraphGetNodes(graph, None, ctypes.byref(count))
+    nodes = (ctypes.c_void_p * max(1, count.value))()
+    rt.cudaGraphGetNodes(graph, nodes, ctypes.byref(count))
+    kernels = 0
+    for i in range(count.value):
+        t = ctypes.c_int(-1)
+        rt.cudaGraphNodeGetType(ctypes.c_void_p(nodes[i]), ctypes.byref(t))
+        kernels += 1 if t.value == 0 else 0  # cudaGraphNodeTypeKernel
+    rt.cudaGraphDestroy(graph)
+    return kernels
+
+
 def _rows_of(torch, dC, rows):
     idx = torch.from_numpy(np.asarray(rows, np.int64)).to(dC.device)
     return dC.index_select(0, idx).cpu().numpy()
@@ -409,7 +444,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     kernels = _trace(lib, ctypes)
-    launches_total = sum(v["launches"] for v in kernels.values())
+    per_call = kernels_per_call(torch, lambda h: call(dA, dB, dC, s=h))
+    if per_call is not None:
+        launches_total = per_call * args.steps
+        launches_how = "%d kernels per step (counted from a CUDA graph capturing one step) x %d steps" % (
+            per_call, args.steps)
+    else:
+        launches_total = sum(v["launches"] for v in kernels.values())
+        launches_how = "trace scopes in the timed region (each covers one or more kernels)"
     head = {}
     book.add("sq64", head, "error", _rows_of(torch, dC, rows))
 
@@ -441,6 +483,9 @@ def main():
     in_free = [torch.cuda.Event() for _ in range(2)]
     out_ready = [torch.cuda.Event() for _ in range(2)]
     out_free = [torch.cuda.Event() for _ in range(2)]
+    # per step: the product on the compute stream, the uploads on theirs
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    uev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -452,13 +497,17 @@ def main():
         with torch.cuda.stream(cs_up):
             if t >= 2:
                 cs_up.wait_event(in_free[j])
+            uev[t][0].record(cs_up)
             dA2[j].copy_(pA, non_blocking=True)
             dB2[j].copy_(pB, non_blocking=True)
+            uev[t][1].record(cs_up)
             in_ready[j].record(cs_up)
         stream.wait_event(in_ready[j])
         if t >= 2:
             stream.wait_event(out_free[j])
+        cev[t][0].record(stream)
         call(dA2[j], dB2[j], dC2[j])
+        cev[t][1].record(stream)
         out_ready[j].record(stream)
         in_free[j].record(stream)
         with torch.cuda.stream(cs_down):
@@ -477,6 +526,8 @@ def main():
     e2e = {"value": world * ops_per_step * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GOp/s",
            "h2d_bytes_per_step": int(A_h.nbytes + B_h.nbytes), "d2h_bytes_per_step": int(pC.numel() * 8),
            "steps": e2e_steps,
+           "product_ms_median": float(np.median([a.elapsed_time(b) for a, b in cev])),
+           "upload_ms_median": float(np.median([a.elapsed_time(b) for a, b in uev])),
            "overlap": "uploads and downloads on two copy streams, double-buffered device buffers"}
     e2e_same = bool(torch.equal(pC, dC2[(e2e_steps - 1) & 1].cpu()))
     del pA, pB, pC, dA2, dB2, dC2, ws
@@ -551,6 +602,7 @@ def main():
                      "leaf_share_of_step": leaf["ms"] / total_ms if total_ms else None},
         "kernels": kernels,
         "gpu_launches": launches_total,
+        "gpu_launches_how": launches_how,
         "clocks": clocks,
         "e2e": dict(e2e, result_matches_device_run=e2e_same),
         "cpu_baseline": cpu,
