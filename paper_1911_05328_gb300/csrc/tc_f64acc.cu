@@ -493,17 +493,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       // reads 74 KB of operands instead of 126 KB.  Order sa is complete once
       // the first piece of slice sa is issued (later slices do not reach
       // it), which is where the chunk's last k-step signals its drain.
+      // parts: 1 = the pieces of the alternating orders, 2 = the others.  A
+      // chunk's last k-step issues the others first, so the orders the next
+      // chunk waits for are complete (and drained) a few products earlier.
       auto issue_stacked = [&](uint32_t a_lo, uint32_t b_lo, int kk, bool last_step, uint32_t pp_col,
-                               uint64_t* ppf) {
-#pragma unroll
-        for (int sa = 0; sa < kSlices; ++sa) {
+                               uint64_t* ppf, int parts) {
+        auto pp_piece = [&](int sa) {
           const uint32_t aoff = (uint32_t)(sa * A_TILE + kk * 32) >> 4;
-          if (sa < kPP) {
-            const uint32_t boff = (uint32_t)(kk * 32) >> 4;
-            tc::mma_f16(tmem + pp_col + (uint32_t)(sa * BN), tc::desc_join(a_lo + aoff, dhi),
-                        tc::desc_join(b_lo + boff, dhi), tc::idesc_f16(BM, BN * (kPP - sa), 1), 1u);
-            if (last_step) tc::mma_commit(&ppf[sa]);
-          }
+          const uint32_t boff = (uint32_t)(kk * 32) >> 4;
+          tc::mma_f16(tmem + pp_col + (uint32_t)(sa * BN), tc::desc_join(a_lo + aoff, dhi),
+                      tc::desc_join(b_lo + boff, dhi), tc::idesc_f16(BM, BN * (kPP - sa), 1), 1u);
+          if (last_step) tc::mma_commit(&ppf[sa]);
+        };
+        auto main_pieces = [&](int sa) {
+          const uint32_t aoff = (uint32_t)(sa * A_TILE + kk * 32) >> 4;
 #pragma unroll
           for (int g0 = sa < kPP ? kPP : sa; g0 < kGroups; g0 += 4) {
             const int cnt = min(4, kGroups - g0);
@@ -511,6 +514,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mma_f16(tmem + (uint32_t)(g0 * BN), tc::desc_join(a_lo + aoff, dhi),
                         tc::desc_join(b_lo + boff, dhi), tc::idesc_f16(BM, BN * cnt, 1), 1u);
             if (last_step && g0 == sa) tc::mma_commit(&acc_full[sa]);
+          }
+        };
+        if (last_step || parts != 3) {
+          if (parts & 2) {
+#pragma unroll
+            for (int sa = 0; sa < kSlices; ++sa) main_pieces(sa);
+          }
+          if (parts & 1) {
+#pragma unroll
+            for (int sa = 0; sa < kPP; ++sa) pp_piece(sa);
+          }
+        } else {
+#pragma unroll
+          for (int sa = 0; sa < kSlices; ++sa) {
+            if (sa < kPP) pp_piece(sa);
+            main_pieces(sa);
           }
         }
       };
@@ -550,6 +569,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int sa = 0; sa < kPP; ++sa)
                   tc::mma_f16(tmem + pp_col + (uint32_t)(sa * BN), tc::desc_join(a_lo + ((uint32_t)(sa * A_TILE) >> 4), dhi),
                               tc::desc_join(b_lo, dhi), tc::idesc_f16(BM, BN * (kPP - sa), 1), sa == 0 ? 0u : 1u);
+                // their second half-step too: more work for the tensor core
+                // while the other orders drain
+                issue_stacked(a_lo, b_lo, 1, it == last - 1, pp_col, ppf, 1);
               }
             }
 #pragma unroll
@@ -560,10 +582,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if (!aborted) issue_group(a_lo, b_lo, 0, g, true);
             }
-            if (!aborted) issue_stacked(a_lo, b_lo, 1, it == last - 1, pp_col, ppf);
+            if (!aborted) issue_stacked(a_lo, b_lo, 1, it == last - 1, pp_col, ppf, kPP > 0 ? 2 : 3);
           } else {
-            issue_stacked(a_lo, b_lo, 0, false, pp_col, ppf);
-            issue_stacked(a_lo, b_lo, 1, it == last - 1, pp_col, ppf);
+            issue_stacked(a_lo, b_lo, 0, false, pp_col, ppf, 3);
+            issue_stacked(a_lo, b_lo, 1, it == last - 1, pp_col, ppf, 3);
           }
           tc::mma_commit(&empty[s]);
         }
